@@ -1,0 +1,273 @@
+"""Python access to the FP64 CPU oracle (``svm_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
+CPU-baseline leg use this module to state what the GPU path must compute.
+The CUDA library never imports it, and it never imports the CUDA library.
+
+Every function takes and returns numpy arrays in float64 (points as (n, 3)).
+``build()`` compiles the C source with gcc and OpenMP; it runs on first use.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "svm_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lib = None
+
+DOF = 6
+NCAPS = 7
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (plain C, -O2, no fast-math, no FMA contraction)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-std=gnu11", "-O2", "-fPIC", "-shared", "-fopenmp",
+               "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_D = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_F = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
+_I32 = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_I64 = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        L = _lib
+        L.orc_num_threads.restype = C.c_int
+        L.orc_set_num_threads.argtypes = [C.c_int]
+        L.orc_fk.argtypes = [_D, _D, _D]
+        L.orc_capsules.argtypes = [_D, C.c_double, _D, _D, _D]
+        L.orc_point_capsule.argtypes = [_D, _D, _D, C.c_double]
+        L.orc_point_capsule.restype = C.c_double
+        L.orc_robot_sdf.argtypes = [_D, C.c_double, _D, _D, _D]
+        L.orc_robot_sdf.restype = C.c_double
+        L.orc_swept_sdf.argtypes = [_D, C.c_double, _D, _D, _D, C.c_int, _D]
+        L.orc_swept_sdf.restype = C.c_double
+        L.orc_swept_sdf_batch.argtypes = [_D, C.c_double, _D, _D, _D, C.c_int, C.c_int, _D, C.c_long, _D]
+        L.orc_gcc_motion.argtypes = [_D, C.c_double, _D, _D, _D, C.c_int, C.c_int, _D, C.c_long,
+                                     C.c_double, _D, _I32]
+        L.orc_param_count.argtypes = [C.c_int, C.c_int]
+        L.orc_param_count.restype = C.c_long
+        L.orc_mlp_forward.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, C.c_long, _D]
+        L.orc_mlp_pairs.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, _D, C.c_int, _D, C.c_long, _D]
+        L.orc_mlp_loss_grad.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, _D, C.c_long, _D]
+        L.orc_mlp_loss_grad.restype = C.c_double
+        L.orc_adam_step.argtypes = [_D, _D, _D, _D, C.c_long, C.c_long, C.c_double, C.c_double,
+                                    C.c_double, C.c_double]
+        L.orc_check_motions.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, C.c_double, _D,
+                                        _D, _D, C.c_int, C.c_int, _D, C.c_long, C.c_double,
+                                        C.c_double, C.c_int, C.c_void_p, _I32, _D, _D, _I64]
+        L.orc_round_bf16.argtypes = [C.c_float]
+        L.orc_round_bf16.restype = C.c_float
+        L.orc_round_bf16_array.argtypes = [_F, C.c_long]
+        L.orc_round_e4m3.argtypes = [C.c_double]
+        L.orc_round_e4m3.restype = C.c_double
+        L.orc_quantize_e4m3.argtypes = [_F, C.c_long, _F]
+        L.orc_quantize_e4m3.restype = C.c_float
+        L.orc_splitmix64_u01.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
+        L.orc_splitmix64_u01.restype = C.c_double
+    return _lib
+
+
+def _d(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    lib().orc_set_num_threads(int(n))
+
+
+# ----------------------------------------------------------------- robot
+
+class RobotArrays:
+    """The oracle's view of a robot: DH table, radii, tool length."""
+
+    def __init__(self, robot):
+        self.dh = _d(robot.dh).reshape(6, 4)
+        self.radius = _d(robot.radius).reshape(7)
+        self.tool_len = float(robot.tool_len)
+
+
+def fk(robot, q) -> np.ndarray:
+    """Frames T_0..T_6 as (7, 4, 4)."""
+    R = RobotArrays(robot)
+    T = np.zeros(7 * 16)
+    lib().orc_fk(R.dh, _d(q), T)
+    return T.reshape(7, 4, 4)
+
+
+def capsules(robot, q):
+    """Capsule axes (a, b), each (7, 3)."""
+    R = RobotArrays(robot)
+    a = np.zeros(21)
+    b = np.zeros(21)
+    lib().orc_capsules(R.dh, R.tool_len, _d(q), a, b)
+    return a.reshape(7, 3), b.reshape(7, 3)
+
+
+def point_capsule(x, a, b, r) -> float:
+    return lib().orc_point_capsule(_d(x), _d(a), _d(b), float(r))
+
+
+def robot_sdf(robot, q, x) -> float:
+    R = RobotArrays(robot)
+    return lib().orc_robot_sdf(R.dh, R.tool_len, R.radius, _d(q), _d(x))
+
+
+def swept_sdf(robot, q0, q1, N, x) -> float:
+    R = RobotArrays(robot)
+    return lib().orc_swept_sdf(R.dh, R.tool_len, R.radius, _d(q0), _d(q1), int(N), _d(x))
+
+
+def _xyz(points) -> np.ndarray:
+    p = np.asarray(points)
+    return _d(p[:, :3])
+
+
+def swept_sdf_batch(robot, q0, q1, N, points) -> np.ndarray:
+    """delta[m, i] for every motion m and point i (points (n, 3) or (n, 4))."""
+    R = RobotArrays(robot)
+    q0 = _d(q0).reshape(-1, 6)
+    q1 = _d(q1).reshape(-1, 6)
+    pts = _xyz(points)
+    M, n = q0.shape[0], pts.shape[0]
+    out = np.zeros(M * n)
+    lib().orc_swept_sdf_batch(R.dh, R.tool_len, R.radius, q0, q1, M, int(N), pts, n, out)
+    return out.reshape(M, n)
+
+
+def gcc_motion(robot, q0, q1, N, points, eps):
+    """Eq. 5 per motion: (dmin (M,), collision (M,) int32)."""
+    R = RobotArrays(robot)
+    q0 = _d(q0).reshape(-1, 6)
+    q1 = _d(q1).reshape(-1, 6)
+    pts = _xyz(points)
+    M = q0.shape[0]
+    dmin = np.zeros(M)
+    coll = np.zeros(M, dtype=np.int32)
+    lib().orc_gcc_motion(R.dh, R.tool_len, R.radius, q0, q1, M, int(N), pts, pts.shape[0],
+                         float(eps), dmin, coll)
+    return dmin, coll
+
+
+# ------------------------------------------------------------------- MLP
+
+def flatten_params(layers) -> np.ndarray:
+    """[(W, b), ...] -> one float64 vector, W row-major then b per layer."""
+    return np.concatenate([np.concatenate([_d(W).ravel(), _d(b).ravel()]) for W, b in layers])
+
+
+def unflatten_params(P, width, n_hidden):
+    """Inverse of flatten_params for the 15 -> W, L x (W -> W), W -> 1 net."""
+    shapes = [(width, 15)] + [(width, width)] * n_hidden + [(1, width)]
+    out, off = [], 0
+    for (o, i) in shapes:
+        W = P[off:off + o * i].reshape(o, i)
+        off += o * i
+        b = P[off:off + o]
+        off += o
+        out.append((W.copy(), b.copy()))
+    return out
+
+
+def param_count(width, n_hidden) -> int:
+    return int(lib().orc_param_count(width, n_hidden))
+
+
+def mlp_forward(P, width, n_hidden, act, inputs) -> np.ndarray:
+    inputs = _d(inputs).reshape(-1, 15)
+    out = np.zeros(inputs.shape[0])
+    lib().orc_mlp_forward(_d(P), width, n_hidden, act, inputs, inputs.shape[0], out)
+    return out
+
+
+def mlp_pairs(P, width, n_hidden, act, q0, q1, points) -> np.ndarray:
+    """f_theta(x_i, q0_m, q1_m) for all pairs: (M, n)."""
+    q0 = _d(q0).reshape(-1, 6)
+    q1 = _d(q1).reshape(-1, 6)
+    pts = _xyz(points)
+    M, n = q0.shape[0], pts.shape[0]
+    out = np.zeros(M * n)
+    lib().orc_mlp_pairs(_d(P), width, n_hidden, act, q0, q1, M, pts, n, out)
+    return out.reshape(M, n)
+
+
+def mlp_loss_grad(P, width, n_hidden, act, inputs, target):
+    inputs = _d(inputs).reshape(-1, 15)
+    G = np.zeros(param_count(width, n_hidden))
+    loss = lib().orc_mlp_loss_grad(_d(P), width, n_hidden, act, inputs, _d(target),
+                                   inputs.shape[0], G)
+    return loss, G
+
+
+def adam_step(P, G, M1, V1, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """In-place Adam step on float64 arrays P, M1, V1."""
+    lib().orc_adam_step(P, _d(G), M1, V1, P.shape[0], int(t), lr, b1, b2, eps)
+
+
+def check_motions(P, width, n_hidden, act, robot, q0, q1, N, points, eps, gate,
+                  strict=False, f=None):
+    """Margin-gated combined check; returns dict of per-motion arrays."""
+    R = RobotArrays(robot)
+    q0 = _d(q0).reshape(-1, 6)
+    q1 = _d(q1).reshape(-1, 6)
+    pts = _xyz(points)
+    M, n = q0.shape[0], pts.shape[0]
+    coll = np.zeros(M, dtype=np.int32)
+    dmin = np.zeros(M)
+    dhat = np.zeros(M)
+    nf = np.zeros(M, dtype=np.int64)
+    fptr = None
+    if f is not None:
+        f = _d(f).reshape(M, n)
+        fptr = f.ctypes.data_as(C.c_void_p)
+    Pd = _d(P) if P is not None else np.zeros(1)
+    lib().orc_check_motions(Pd, width, n_hidden, act, R.dh, R.tool_len, R.radius, q0, q1,
+                            M, int(N), pts, n, float(eps), float(gate), int(bool(strict)),
+                            fptr, coll, dmin, dhat, nf)
+    return {"collision": coll, "d_min": dmin, "dhat_min": dhat, "n_flagged": nf}
+
+
+# ------------------------------------------------------------ quantisers
+
+def round_bf16(a) -> np.ndarray:
+    """Nearest-even bfloat16 of every element, returned as float32."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    flat = a.ravel().copy()
+    lib().orc_round_bf16_array(flat, flat.shape[0])
+    return flat.reshape(a.shape)
+
+
+def round_e4m3(v: float) -> float:
+    return lib().orc_round_e4m3(float(v))
+
+
+def quantize_e4m3(w):
+    """(scale, dequantised float32 copy) of a weight tensor."""
+    w = np.ascontiguousarray(w, dtype=np.float32).ravel()
+    q = np.zeros_like(w)
+    s = lib().orc_quantize_e4m3(w, w.shape[0], q)
+    return s, q
+
+
+def splitmix64_u01(seed, stream, i) -> float:
+    return lib().orc_splitmix64_u01(int(seed), int(stream), int(i))

@@ -1,0 +1,461 @@
+"""Pins of the FP64 CPU oracle against closed forms, invariants, brute force
+and library routines -- never against the oracle's own formulas retyped.
+
+Each test names the part of the oracle it pins and the fact that pins it.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2402_15281_gb300 import synth as S
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def robot():
+    return S.make_robot(1)
+
+
+# --------------------------------------------------------------- capsules
+
+def test_point_capsule_closed_forms():
+    a = np.array([0.1, -0.2, 0.3])
+    b = np.array([0.1, -0.2, 0.9])
+    r = 0.05
+    # beyond the b end, on the axis: distance to the end point minus r
+    assert oracle.point_capsule([0.1, -0.2, 1.4], a, b, r) == pytest.approx(0.5 - r, abs=1e-15)
+    # before the a end, on the axis
+    assert oracle.point_capsule([0.1, -0.2, 0.0], a, b, r) == pytest.approx(0.3 - r, abs=1e-15)
+    # perpendicular foot inside the segment: radial distance minus r
+    assert oracle.point_capsule([0.1 + 0.3, -0.2 + 0.4, 0.5], a, b, r) == pytest.approx(0.5 - r, abs=1e-15)
+    # on the axis inside: -r (deepest point)
+    assert oracle.point_capsule([0.1, -0.2, 0.6], a, b, r) == pytest.approx(-r, abs=1e-15)
+    # zero-length axis is a sphere
+    c = np.array([1.0, 2.0, 3.0])
+    assert oracle.point_capsule([1.0, 2.0, 5.0], c, c, 0.5) == pytest.approx(1.5, abs=1e-15)
+
+
+def test_point_capsule_brute_force():
+    """Distance to the segment = min over densely sampled segment points; the
+    sampled minimum converges to the closed-form projection from above."""
+    rng = np.random.default_rng(7)
+    ts = np.linspace(0.0, 1.0, 200001)
+    for _ in range(50):
+        a, b, x = rng.normal(size=3), rng.normal(size=3), rng.normal(size=3) * 2
+        r = rng.uniform(0.01, 0.2)
+        seg = a[None, :] + ts[:, None] * (b - a)[None, :]
+        brute = np.min(np.linalg.norm(seg - x[None, :], axis=1)) - r
+        exact = oracle.point_capsule(x, a, b, r)
+        h = np.linalg.norm(b - a) / (len(ts) - 1)
+        assert exact <= brute + 1e-15
+        assert brute - exact <= h / 2 + 1e-12
+
+
+# --------------------------------------------------------------------- FK
+
+def test_fk_home_pose_closed_form(robot):
+    """At q = 0 the chain with alpha = (-pi/2, 0, -pi/2, pi/2, -pi/2, 0) puts
+    the origins at sums of the DH lengths (derived by hand):
+    o1 = (a1, 0, d1), o2 = (a1+a2, 0, d1), o3 = (a1+a2+a3, 0, d1),
+    o4 = o5 = (a1+a2+a3, 0, d1-d4), o6 = (a1+a2+a3, 0, d1-d4-d6), z6 = -z."""
+    d1, a1 = robot.dh[0, 0], robot.dh[0, 1]
+    a2, a3 = robot.dh[1, 1], robot.dh[2, 1]
+    d4, d6 = robot.dh[3, 0], robot.dh[5, 0]
+    T = oracle.fk(robot, np.zeros(6))
+    s = a1 + a2 + a3
+    want = [(0, 0, 0), (a1, 0, d1), (a1 + a2, 0, d1), (s, 0, d1), (s, 0, d1 - d4),
+            (s, 0, d1 - d4), (s, 0, d1 - d4 - d6)]
+    for j, o in enumerate(want):
+        np.testing.assert_allclose(T[j, :3, 3], o, atol=1e-15)
+    np.testing.assert_allclose(T[6, :3, 2], (0, 0, -1), atol=1e-15)
+    a, b = oracle.capsules(robot, np.zeros(6))
+    np.testing.assert_allclose(b[6], (s, 0, d1 - d4 - d6 - robot.tool_len), atol=1e-15)
+
+
+def test_fk_rotations_orthonormal(robot):
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        T = oracle.fk(robot, rng.uniform(-3, 3, 6))
+        for j in range(7):
+            R = T[j, :3, :3]
+            assert np.abs(R.T @ R - np.eye(3)).max() < 1e-14
+            assert np.linalg.det(R) == pytest.approx(1.0, abs=1e-14)
+            np.testing.assert_array_equal(T[j, 3], [0, 0, 0, 1])
+
+
+def test_fk_planar_two_link():
+    """alpha = 0 and d = 0: a planar arm with o2 = (a1 c1 + a2 c12, a1 s1 + a2 s12, 0)."""
+    R = S.Robot(dh=np.array([[0, 0.7, 0, 0], [0, 0.4, 0, 0]] + [[0, 0, 0, 0]] * 4, float),
+                radius=np.full(7, 0.05), tool_len=0.0, qmin=-np.ones(6), qmax=np.ones(6))
+    for q1, q2 in [(0.3, -1.1), (2.0, 0.5), (-2.5, 3.0)]:
+        T = oracle.fk(R, np.array([q1, q2, 0, 0, 0, 0]))
+        want = (0.7 * math.cos(q1) + 0.4 * math.cos(q1 + q2),
+                0.7 * math.sin(q1) + 0.4 * math.sin(q1 + q2), 0.0)
+        np.testing.assert_allclose(T[2, :3, 3], want, atol=1e-15)
+
+
+def _rodrigues(w, th):
+    K = np.array([[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]])
+    return np.eye(3) + math.sin(th) * K + (1 - math.cos(th)) * K @ K
+
+
+def test_fk_product_of_exponentials(robot):
+    """Independent formulation: each joint j turns everything after it about
+    the fixed line (axis z_{j-1}, through o_{j-1}) of the home pose, applied
+    from the tool end inwards.  The origins must agree with the DH chain."""
+    T0 = oracle.fk(robot, np.zeros(6))
+    axes = [T0[j, :3, 2] for j in range(6)]
+    pivots = [T0[j, :3, 3] for j in range(6)]
+    rng = np.random.default_rng(3)
+    for _ in range(10):
+        q = rng.uniform(-2.9, 2.9, 6)
+        T = oracle.fk(robot, q)
+        for k in range(1, 7):
+            p = T0[k, :3, 3].copy()
+            for j in reversed(range(k)):
+                p = pivots[j] + _rodrigues(axes[j], q[j]) @ (p - pivots[j])
+            np.testing.assert_allclose(T[k, :3, 3], p, atol=1e-13)
+
+
+# ------------------------------------------------------------- swept SDF
+
+def test_swept_static_motion_equals_robot_sdf(robot):
+    """q0 = q1: every sample is q0 bitwise when q0 is dyadic, so the swept SDF
+    is the static robot SDF bitwise; otherwise within rounding."""
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        q = np.round(rng.uniform(-2.9, 2.9, 6) * 2 ** 20) / 2 ** 20
+        x = rng.uniform(-0.8, 0.8, 3)
+        assert oracle.swept_sdf(robot, q, q, 64, x) == oracle.robot_sdf(robot, q, x)
+        q = rng.uniform(-2.9, 2.9, 6)
+        assert oracle.swept_sdf(robot, q, q, 64, x) == pytest.approx(oracle.robot_sdf(robot, q, x), abs=1e-12)
+
+
+def test_swept_symmetry_bitwise(robot):
+    """f_d(x, q0, q1) = f_d(x, q1, q0): the swept volume does not depend on
+    the direction of travel; the sampled form keeps this bitwise."""
+    q0, q1 = S.uniform_motions(robot, 6, seed=11)
+    pts = S.cube_cloud(300, seed=4)
+    d01 = oracle.swept_sdf_batch(robot, q0, q1, 37, pts)
+    d10 = oracle.swept_sdf_batch(robot, q1, q0, 37, pts)
+    np.testing.assert_array_equal(d01, d10)
+
+
+def test_swept_refinement_monotone_and_converges(robot):
+    """Nested grids N, 2N, 4N, ...: the sampled union only grows, so the
+    sampled SDF never increases, and it converges."""
+    q0, q1 = S.uniform_motions(robot, 3, seed=12)
+    pts = S.cube_cloud(200, seed=5)
+    prev = None
+    gaps = []
+    ref = oracle.swept_sdf_batch(robot, q0, q1, 2048, pts)
+    for N in (4, 8, 16, 32, 64, 128, 256):
+        d = oracle.swept_sdf_batch(robot, q0, q1, N, pts)
+        if prev is not None:
+            assert np.all(d <= prev)
+        assert np.all(d >= ref)
+        gaps.append(np.max(d - ref))
+        prev = d
+    assert gaps[-1] < gaps[0] / 20
+
+
+def test_swept_sphere_along_arc_closed_form():
+    """A sphere of radius r carried on a single revolute joint sweeps a tube
+    around a circular arc; its SDF is (distance to the arc) - r.  The sampled
+    SDF is above it by at most half the arc spacing."""
+    R, r = 0.6, 0.05
+    far = -1e6    # capsules with this radius are never the minimum
+    rob = S.Robot(dh=np.array([[0, R, 0, 0]] + [[0, 0, 0, 0]] * 5, float),
+                  radius=np.array([far, r, far, far, far, far, far]), tool_len=0.0,
+                  qmin=-np.ones(6) * 3, qmax=np.ones(6) * 3)
+    th0, th1 = -0.4, 1.3
+    q0 = np.array([th0, 0, 0, 0, 0, 0])
+    q1 = np.array([th1, 0, 0, 0, 0, 0])
+    rng = np.random.default_rng(9)
+    X = rng.uniform(-1, 1, (300, 3))
+
+    def arc_sdf(x):
+        rho, phi = math.hypot(x[0], x[1]), math.atan2(x[1], x[0])
+        cands = [np.array([R * math.cos(t), R * math.sin(t), 0.0]) for t in (th0, th1)]
+        if th0 <= phi <= th1:
+            cands.append(np.array([R * math.cos(phi), R * math.sin(phi), 0.0]))
+        return min(np.linalg.norm(x - c) for c in cands) - r
+
+    for N in (8, 64, 512):
+        h = R * (th1 - th0) / N
+        d = oracle.swept_sdf_batch(rob, q0, q1, N, X)[0]
+        exact = np.array([arc_sdf(x) for x in X])
+        assert np.all(d >= exact - 1e-12)
+        assert np.all(d - exact <= h / 2 + 1e-12)
+
+
+def test_swept_brute_force_tiny(robot):
+    """Tiny cases by explicit enumeration of samples, capsules and a dense
+    point-on-segment search (no projection formula)."""
+    q0, q1 = S.uniform_motions(robot, 2, seed=13)
+    pts = S.cube_cloud(4, seed=6)[:, :3].astype(np.float64)
+    N = 4
+    ts = np.linspace(0, 1, 20001)
+    d = oracle.swept_sdf_batch(robot, q0, q1, N, pts)
+    for m in range(2):
+        for i in range(4):
+            best = np.inf
+            for k in range(N + 1):
+                qk = ((N - k) * q0[m] + k * q1[m]) / N
+                a, b = oracle.capsules(robot, qk)
+                for j in range(7):
+                    seg = a[j][None, :] + ts[:, None] * (b[j] - a[j])[None, :]
+                    best = min(best, np.min(np.linalg.norm(seg - pts[i], axis=1)) - robot.radius[j])
+            assert d[m, i] <= best + 1e-15
+            assert best - d[m, i] < 2e-5
+
+
+def test_gcc_motion_is_min_over_cloud(robot):
+    q0, q1 = S.uniform_motions(robot, 4, seed=14, max_step_deg=15)
+    pts = S.cube_cloud(500, seed=7)
+    dmin, coll = oracle.gcc_motion(robot, q0, q1, 16, pts, 0.05)
+    d = oracle.swept_sdf_batch(robot, q0, q1, 16, pts)
+    np.testing.assert_array_equal(dmin, d.min(axis=1))
+    np.testing.assert_array_equal(coll, (d.min(axis=1) <= 0.05).astype(np.int32))
+
+
+# -------------------------------------------------------------------- MLP
+
+def _numpy_forward(layers, X, act):
+    """Library-matmul formulation of the same network, for comparison."""
+    h = X
+    for W, b in layers[:-1]:
+        z = h @ W.T + b
+        h = np.maximum(z, 0) if act == 0 else z / (1 + np.exp(-z))
+    W, b = layers[-1]
+    return (h @ W.T + b)[:, 0]
+
+
+def test_mlp_hand_computed():
+    # width 1, one hidden layer: f = wo * relu(w2 * relu(w1 . x + b1) + b2) + bo
+    w1 = np.arange(1, 16, dtype=float) / 10.0
+    layers = [(w1[None, :], np.array([-1.0])), (np.array([[2.0]]), np.array([0.5])),
+              (np.array([[-3.0]]), np.array([0.25]))]
+    P = oracle.flatten_params(layers)
+    x = np.linspace(-1, 1, 15)
+    h1 = max(0.0, float(w1 @ x) - 1.0)
+    want = -3.0 * max(0.0, 2.0 * h1 + 0.5) + 0.25
+    assert oracle.mlp_forward(P, 1, 1, S.ACT_RELU, x[None, :])[0] == pytest.approx(want, abs=1e-15)
+    # all-zero weights: the output is the output bias
+    zero = [(np.zeros_like(W), np.zeros_like(b)) for W, b in S.xavier_weights(8, 2)]
+    zero[-1] = (zero[-1][0], np.array([0.75]))
+    assert np.all(oracle.mlp_forward(oracle.flatten_params(zero), 8, 2, 0, np.ones((3, 15))) == 0.75)
+
+
+@pytest.mark.parametrize("act", [S.ACT_RELU, S.ACT_SILU])
+def test_mlp_matches_library_matmul(act):
+    layers = S.xavier_weights(64, 3, seed=21)
+    layers = [(W.astype(np.float64), np.random.default_rng(0).normal(size=b.shape) * 0.1) for W, b in layers]
+    X = np.random.default_rng(1).uniform(-2, 2, (200, 15))
+    f = oracle.mlp_forward(oracle.flatten_params(layers), 64, 3, act, X)
+    np.testing.assert_allclose(f, _numpy_forward(layers, X, act), rtol=1e-12, atol=1e-12)
+
+
+def test_mlp_pairs_input_order(robot):
+    """Input row = [x, y, z, q0, q1] in that column order."""
+    layers = S.xavier_weights(16, 1, seed=3)
+    P = oracle.flatten_params(layers)
+    q0, q1 = S.uniform_motions(robot, 2, seed=1)
+    pts = S.cube_cloud(5, seed=1)
+    f = oracle.mlp_pairs(P, 16, 1, 0, q0, q1, pts)
+    for m in range(2):
+        X = np.concatenate([pts[:, :3].astype(np.float64), np.repeat(q0[m][None], 5, 0),
+                            np.repeat(q1[m][None], 5, 0)], axis=1)
+        np.testing.assert_allclose(f[m], _numpy_forward(layers, X, 0), rtol=1e-12, atol=1e-13)
+
+
+def test_mlp_gradient_finite_differences():
+    width, L, act = 8, 2, S.ACT_SILU
+    layers = S.xavier_weights(width, L, seed=31)
+    P = oracle.flatten_params(layers)
+    P = P + np.random.default_rng(2).normal(size=P.shape) * 0.05
+    X = np.random.default_rng(3).uniform(-1, 1, (16, 15))
+    target = oracle.mlp_forward(P, width, L, act, X) + np.random.default_rng(4).choice([-1, 1], 16) * 0.5
+    loss, G = oracle.mlp_loss_grad(P, width, L, act, X, target)
+    f = oracle.mlp_forward(P, width, L, act, X)
+    assert loss == pytest.approx(np.mean(np.abs(f - target)), rel=1e-14)
+    h = 1e-6
+    for i in range(P.shape[0]):
+        Pp, Pm = P.copy(), P.copy()
+        Pp[i] += h
+        Pm[i] -= h
+        lp = np.mean(np.abs(oracle.mlp_forward(Pp, width, L, act, X) - target))
+        lm = np.mean(np.abs(oracle.mlp_forward(Pm, width, L, act, X) - target))
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - G[i]) <= 1e-6 * max(1.0, abs(G[i])) + 1e-9, i
+
+
+def test_mlp_gradient_relu_finite_differences():
+    width, L, act = 6, 1, S.ACT_RELU
+    P = oracle.flatten_params(S.xavier_weights(width, L, seed=32))
+    P = P + np.random.default_rng(5).normal(size=P.shape) * 0.2
+    X = np.random.default_rng(6).uniform(-1, 1, (8, 15))
+    target = oracle.mlp_forward(P, width, L, act, X) - 1.0
+    _, G = oracle.mlp_loss_grad(P, width, L, act, X, target)
+    h = 1e-7
+    for i in range(P.shape[0]):
+        Pp, Pm = P.copy(), P.copy()
+        Pp[i] += h
+        Pm[i] -= h
+        fd = (np.mean(np.abs(oracle.mlp_forward(Pp, width, L, act, X) - target))
+              - np.mean(np.abs(oracle.mlp_forward(Pm, width, L, act, X) - target))) / (2 * h)
+        assert abs(fd - G[i]) <= 1e-6 * max(1.0, abs(G[i])), i
+
+
+def test_adam_first_step_closed_form():
+    """At t = 1 the bias-corrected moments are g and g^2, so each parameter
+    moves by -lr * g / (|g| + eps)."""
+    rng = np.random.default_rng(8)
+    P = rng.normal(size=100)
+    G = rng.normal(size=100)
+    P0 = P.copy()
+    m, v = np.zeros(100), np.zeros(100)
+    oracle.adam_step(P, G, m, v, 1, lr=1e-3)
+    np.testing.assert_allclose(P, P0 - 1e-3 * G / (np.abs(G) + 1e-8), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(m, 0.1 * G, rtol=1e-14)
+    np.testing.assert_allclose(v, 0.001 * G * G, rtol=1e-14)
+    # a constant gradient keeps moving by lr * sign(g) (bias correction exact)
+    for t in range(2, 6):
+        oracle.adam_step(P, G, m, v, t, lr=1e-3)
+    np.testing.assert_allclose(P, P0 - 5e-3 * G / (np.abs(G) + 1e-8), rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------- combined check
+
+def test_check_open_gate_reduces_to_gcc(robot):
+    """With the gate wide open every point is verified, so the combined check
+    is exactly the geometric check of Eq. 5 (GCC alone)."""
+    q0, q1 = S.uniform_motions(robot, 8, seed=15, max_step_deg=15)
+    pts = S.cube_cloud(64, seed=8)
+    P = oracle.flatten_params(S.xavier_weights(16, 1, seed=2))
+    r = oracle.check_motions(P, 16, 1, 0, robot, q0, q1, 32, pts, 0.05, np.inf)
+    dmin, coll = oracle.gcc_motion(robot, q0, q1, 32, pts, 0.05)
+    np.testing.assert_array_equal(r["collision"], coll)
+    np.testing.assert_array_equal(r["d_min"], dmin)
+    assert np.all(r["n_flagged"] == 64)
+    assert 0 < coll.sum() < 8     # both verdicts occur in this case
+
+
+def test_check_closed_gate_and_strict(robot):
+    q0, q1 = S.uniform_motions(robot, 6, seed=15, max_step_deg=15)
+    pts = S.cube_cloud(300, seed=8)
+    P = oracle.flatten_params(S.xavier_weights(16, 1, seed=2))
+    r = oracle.check_motions(P, 16, 1, 0, robot, q0, q1, 32, pts, 0.05, -np.inf)
+    assert np.all(r["collision"] == 0) and np.all(np.isinf(r["d_min"])) and np.all(r["n_flagged"] == 0)
+    # strict mode re-checks every point of a motion declared free
+    s = oracle.check_motions(P, 16, 1, 0, robot, q0, q1, 32, pts, 0.05, -np.inf, strict=True)
+    dmin, coll = oracle.gcc_motion(robot, q0, q1, 32, pts, 0.05)
+    np.testing.assert_array_equal(s["collision"], coll)
+    np.testing.assert_array_equal(s["d_min"], dmin)
+
+
+def test_check_gate_from_given_f(robot):
+    """Flagging is f <= gate with ties flagged; dhat is the minimum of f (Eq. 6)."""
+    q0, q1 = S.uniform_motions(robot, 2, seed=16, max_step_deg=10)
+    pts = S.cube_cloud(50, seed=9)
+    f = np.tile(np.linspace(-1, 1, 50), (2, 1))
+    r = oracle.check_motions(None, 1, 1, 0, robot, q0, q1, 8, pts, 0.05, f[0, 10], f=f)
+    assert np.all(r["n_flagged"] == 11)
+    assert np.all(r["dhat_min"] == -1.0)
+    d = oracle.swept_sdf_batch(robot, q0, q1, 8, pts)
+    np.testing.assert_array_equal(r["d_min"], d[:, :11].min(axis=1))
+
+
+# ------------------------------------------------------------- quantisers
+
+def test_bf16_matches_library_and_ties():
+    rng = np.random.default_rng(10)
+    v = np.concatenate([rng.normal(size=20000).astype(np.float32) * 3,
+                        np.array([1 + 2 ** -8, 1 + 3 * 2 ** -8, -(1 + 2 ** -8)], dtype=np.float32)])
+    torch = pytest.importorskip("torch")
+    lib = torch.from_numpy(v).to(torch.bfloat16).float().numpy()
+    np.testing.assert_array_equal(oracle.round_bf16(v), lib)
+    q = oracle.round_bf16(v[-3:])
+    assert list(q) == [1.0, 1.015625, -1.0]    # ties go to the even mantissa
+
+
+def _e4m3_table():
+    spec = json.load(open(os.path.join(GOLD, "e4m3_format.json")))
+    vals = []
+    for e in range(16):
+        for m in range(8):
+            if e == 15 and m == 7:
+                continue                             # NaN code
+            if e == 0:
+                vals.append(m * 2.0 ** (1 - spec["bias"] - spec["mantissa_bits"]))
+            else:
+                vals.append((1 + m / 8.0) * 2.0 ** (e - spec["bias"]))
+    vals = np.array(sorted(set(vals)))
+    assert vals.max() == spec["max_finite"] and vals[1] == spec["min_subnormal"]
+    return vals
+
+
+def test_e4m3_nearest_even_by_enumeration():
+    """Every result is the nearest code of the format table (built from the
+    OCP definition), ties to the code with an even mantissa, saturating."""
+    table = _e4m3_table()
+    rng = np.random.default_rng(11)
+    vs = np.concatenate([rng.normal(size=3000) * 10, rng.uniform(-0.02, 0.02, 2000),
+                         (table[:-1] + table[1:]) / 2, [500.0, -1e4, 448.0, 464.0]])
+    for v in vs:
+        r = oracle.round_e4m3(v)
+        a = min(abs(v), 448.0)
+        dist = np.abs(table - a)
+        cands = table[dist == dist.min()]
+        if len(cands) == 1:
+            assert abs(r) == cands[0], v
+        else:   # tie: the code whose own 3-bit mantissa field is even
+            def mant(c):
+                if c < 2 ** -6:
+                    return int(round(c / 2 ** -9))
+                e = math.floor(math.log2(c))
+                return int(round(c / 2.0 ** (e - 3))) - 8
+            even = [c for c in cands if mant(c) % 2 == 0]
+            assert len(even) == 1 and abs(r) == even[0], v
+        assert math.copysign(1.0, r) == math.copysign(1.0, v) or r == 0
+
+
+def test_e4m3_matches_library():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(12)
+    v = np.concatenate([rng.normal(size=20000) * 40, rng.uniform(-0.05, 0.05, 5000)])
+    v = v[np.abs(v) <= 448]
+    lib = torch.from_numpy(v.astype(np.float32)).to(torch.float8_e4m3fn).float().numpy()
+    ours = np.array([oracle.round_e4m3(float(np.float32(x))) for x in v])
+    np.testing.assert_array_equal(ours, lib.astype(np.float64))
+
+
+def test_quantize_e4m3_scale():
+    w = np.random.default_rng(13).normal(size=1000).astype(np.float32)
+    s, q = oracle.quantize_e4m3(w)
+    assert s == np.float32(np.abs(w).max()) / np.float32(448.0)
+    assert np.abs(q).max() == pytest.approx(np.abs(w).max(), rel=1e-6)
+    assert np.all(np.abs(q - w) <= np.abs(w) * 2 ** -4 + s * 2 ** -9 + 1e-12)
+
+
+# -------------------------------------------------------------------- RNG
+
+def test_splitmix64_published_vector():
+    gold = json.load(open(os.path.join(GOLD, "splitmix64.json")))
+    g = np.uint64(int(gold["gamma"], 16))
+    with np.errstate(over="ignore"):
+        z = np.arange(1, 5, dtype=np.uint64) * g
+    got = [hex(int(x)) for x in S._fin(z)]
+    assert got == [hex(int(h, 16)) for h in gold["outputs_from_state_0"]]
+
+
+def test_splitmix64_oracle_matches_generator():
+    r = S.Rng(17, 9)
+    u = r.uniform(50)
+    for i in range(50):
+        assert oracle.splitmix64_u01(17, 9, i) == u[i]
