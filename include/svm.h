@@ -1,0 +1,193 @@
+/*
+ * svm.h -- C ABI of libsvm: GPU collision checking of joint-space motions
+ * against a point cloud with a neural implicit swept-volume model and an
+ * exact geometric verifier.
+ *
+ * Method: Joho, Schwinn, Safronov, "Neural Implicit Swept Volume Models for
+ * Fast Collision Detection" (arXiv 2402.15281).
+ *   - the network f(x, q0, q1) approximates the signed distance of a point x
+ *     to the volume swept by the robot on the linear joint motion q0 -> q1
+ *     (Sec. III, Eqs. 1-4; network of Sec. IV-A);
+ *   - the minimum of the network over the cloud is the proxy d^(X, m) of
+ *     Eq. 6, the exact minimum d(X, m) of Eq. 5 is the geometric check, and a
+ *     motion is free iff d(X, m) > eps_S (Sec. IV-B, Algorithm 1).
+ * The library fuses both: the network flags the pairs whose prediction is
+ * under a gate g = margin + tau, and only those are checked exactly, so the
+ * verdict of a motion is decided by the geometric check.
+ *
+ * Conventions for every entry point:
+ *   - All calls return svm_status; no exception or abort crosses the ABI.
+ *     svm_last_error() gives a text for the last failing call on a model.
+ *   - Device pointers are CUDA global-memory addresses on the model's device.
+ *     The caller owns them; the library never frees them.  Host pointers are
+ *     read (or written) before the call returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued asynchronously on it; device results are
+ *     valid after the stream is synchronised.
+ *   - Points are float4 records (x, y, z, w) in metres, w ignored, 16-byte
+ *     aligned.  Joint angles are radians, 6 per configuration, row-major.
+ *   - A model is not thread safe: calls on one model must not overlap in
+ *     host threads; calls on one model are serialised in stream order.
+ */
+#ifndef SVM_H
+#define SVM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SVM_OK = 0,
+    SVM_E_INVALID = 1,      /* bad argument: size, pointer, NaN, layout        */
+    SVM_E_CUDA = 2,         /* a CUDA runtime or launch error                   */
+    SVM_E_OOM = 3,          /* device workspace could not be allocated          */
+    SVM_E_TIMEOUT = 4,      /* a bounded device wait expired (sticky per model) */
+    SVM_E_WEIGHTS = 5,      /* malformed weight blob or no weights loaded       */
+    SVM_E_UNSUPPORTED = 6   /* valid but not supported on this device/config    */
+} svm_status;
+
+typedef enum { SVM_FP32 = 0, SVM_BF16 = 1, SVM_FP8_E4M3 = 2 } svm_precision;
+typedef enum { SVM_RELU = 0, SVM_SILU = 1 } svm_act;
+
+/* Robot and network description; copied by svm_create_model.
+ * Robot: standard Denavit-Hartenberg chain of 6 revolute joints,
+ *   T_j = T_{j-1} Rz(q_j + theta_j) Tz(d_j) Tx(a_j) Rx(alpha_j), T_0 = I,
+ * dh[j] = {d_j, a_j, alpha_j, theta_j}.  Its geometry is 7 capsules: capsule
+ * j < 6 joins the origins of frames j and j+1, capsule 6 runs tool_len along
+ * the z axis of frame 6; radius[j] is capsule j's radius.
+ * Network: input [x, y, z, q0_1..q0_6, q1_1..q1_6] -> width (act) ->
+ * n_hidden x (width -> width, act) -> 1.  width must be 256 for the BF16 and
+ * FP8 tensor-core path; the FP32 path takes any width in [16, 512], a
+ * multiple of 16. */
+typedef struct {
+    double dh[6][4];
+    double radius[7];
+    double tool_len;
+    int32_t width;
+    int32_t n_hidden;
+    int32_t act;     /* svm_act       */
+    int32_t prec;    /* svm_precision */
+} svm_model_desc;
+
+/* Per-motion (or per-path) result, 32 bytes, written to device memory. */
+typedef struct {
+    uint8_t collision;      /* 1 iff some checked point has distance <= margin */
+    uint8_t early_exit;     /* 1 if checking stopped at the first collision     */
+    uint16_t reserved;
+    float d_min;            /* minimum exact distance over the checked points;
+                               +inf if none was checked; on early exit the first
+                               value found <= margin                            */
+    float dhat_min;         /* minimum network prediction over all points (Eq. 6);
+                               +inf when the network was not run                */
+    uint32_t n_flagged;     /* points whose prediction was <= the gate          */
+    uint32_t n_verified;    /* points checked exactly                           */
+    int32_t witness_point;  /* index of a colliding point, -1 if none           */
+    int32_t witness_step;   /* a sample k in [0, steps] where it collides, -1 if
+                               none; for paths: segment * (steps + 1) + k       */
+    uint32_t n_ambiguous;   /* checked points within 4e-6 m of the margin       */
+} svm_result;
+
+typedef struct svm_model svm_model;
+
+/* Flags of the check calls. */
+#define SVM_STRICT        1u  /* a motion without a flagged collision has every
+                                 point checked exactly: "free" is then always
+                                 confirmed by the geometric check (Algorithm 1)  */
+#define SVM_NO_EARLY_EXIT 2u  /* check every flagged point (exact d_min)         */
+#define SVM_VERIFY_ALL    4u  /* skip the network; check every pair exactly (the
+                                 geometric check alone, GCC_0 of Sec. V-B)       */
+#define SVM_PATHS3        8u  /* motions 3p, 3p+1, 3p+2 are the segments of path
+                                 p; one result per path (collision = OR), and a
+                                 path stops at its first colliding segment      */
+
+const char* svm_status_string(svm_status s);
+const char* svm_last_error(const svm_model* m);
+
+/* Create a model on CUDA device `device`.  Checks the description (finite
+ * DH values, radii >= 0, width/n_hidden/prec supported on this device).
+ * *out receives the handle; free it with svm_destroy_model. */
+svm_status svm_create_model(const svm_model_desc* desc, int device, svm_model** out);
+svm_status svm_destroy_model(svm_model* m);
+
+/* Load network weights from a little-endian blob:
+ *   char magic[4] = "SVMW"; uint32 version = 1; uint32 n_layers;
+ *   uint32 in_dim = 15; uint32 width; uint32 act; float tau;
+ *   then for each layer: uint32 out, uint32 in, float W[out][in] (row-major),
+ *   float b[out].
+ * Layers must be 15 -> width, n_hidden x (width -> width), width -> 1 as in
+ * the description.  The weights are rounded to the model precision on the
+ * device: BF16 rounds every weight to nearest-even bfloat16; FP8 rounds the
+ * hidden weights to E4M3 (nearest-even, saturating) with the per-layer scale
+ * s = max|W| / 448 (float) and the other layers to BF16.  Biases stay FP32.
+ * tau sets the gate offset (see svm_set_gate).  Returns SVM_E_WEIGHTS on a
+ * malformed blob. */
+svm_status svm_load_weights(svm_model* m, const void* blob, size_t bytes);
+
+/* Copy the weights as the model uses them (after rounding, dequantised to
+ * float) into host memory, in the blob's layer order (W then b per layer).
+ * `count` is the capacity of `out` in floats; the required count is written
+ * to *needed (may be NULL). */
+svm_status svm_export_weights(const svm_model* m, float* out, size_t count, size_t* needed);
+
+/* Gate offset tau >= 0 (metres): a pair is checked exactly iff its network
+ * prediction f <= margin + tau.  tau = +inf checks every pair. */
+svm_status svm_set_gate(svm_model* m, float tau);
+
+/* FP8 only: per-hidden-layer activation scales (n_hidden values > 0); the
+ * input of hidden layer l is stored as e4m3(h / scale[l]). */
+svm_status svm_set_act_scales(svm_model* m, const float* scales, int32_t n);
+
+/* Check n_motions linear motions q0[m] -> q1[m] against one point cloud.
+ *   q0, q1       host, n_motions x 6 doubles, finite.
+ *   points_dev   device, n_points float4 records.
+ *   margin       eps_S >= 0 in metres: collision iff distance <= margin.
+ *   steps        N >= 1: the motion is sampled at q_k = ((N-k) q0 + k q1) / N,
+ *                k = 0..N, and each sample is checked exactly.
+ *   results_dev  device, n_motions svm_result records (n_motions / 3 with
+ *                SVM_PATHS3, which needs n_motions % 3 == 0).
+ * The model's workspace grows on demand (cudaMalloc; SVM_E_OOM on failure). */
+svm_status svm_check_motions(svm_model* m, const double* q0, const double* q1,
+                             int32_t n_motions, const float* points_dev, int64_t n_points,
+                             float margin, int32_t steps, uint32_t flags,
+                             svm_result* results_dev, void* stream);
+
+/* Batched form over several scenes in one launch sequence.  Scene s owns the
+ * points [scene_offsets[s], scene_offsets[s+1]) of points_dev; motion m is
+ * checked against scene motion_scene[m].  scene_offsets (n_scenes + 1 int64)
+ * and motion_scene (n_motions int32) are host arrays. */
+svm_status svm_check_batch(svm_model* m, const double* q0, const double* q1,
+                           int32_t n_motions, const int32_t* motion_scene,
+                           const float* points_dev, const int64_t* scene_offsets,
+                           int32_t n_scenes, float margin, int32_t steps, uint32_t flags,
+                           svm_result* results_dev, void* stream);
+
+/* Network output for every (motion, point) pair: f_dev[m * n_points + i] =
+ * f(x_i, q0_m, q1_m) in the model precision (device, n_motions x n_points
+ * floats).  Same kernels as the check, with the output stored. */
+svm_status svm_eval_pairs(svm_model* m, const double* q0, const double* q1, int32_t n_motions,
+                          const float* points_dev, int64_t n_points, float* f_dev, void* stream);
+
+/* Exact sampled swept-volume distance (the verifier without gate or early
+ * exit) for every pair: delta_dev[m * n_points + i] = min over k = 0..steps
+ * and the 7 capsules of (distance to the capsule axis - radius). */
+svm_status svm_label_pairs(svm_model* m, const double* q0, const double* q1, int32_t n_motions,
+                           const float* points_dev, int64_t n_points, int32_t steps,
+                           float* delta_dev, void* stream);
+
+/* Phase timing.  With profiling on, every check call records CUDA events on
+ * its stream between its phases; svm_profile_read waits for the last call to
+ * finish and writes n <= 4 durations in milliseconds: ms[0] the per-call
+ * copy + prologue (FK, per-motion bias), ms[1] the network kernel (gate and
+ * compaction included), ms[2] the verifier (both passes in strict mode),
+ * ms[3] the finalize kernel.  Not part of the computation; off by default. */
+svm_status svm_profile_enable(svm_model* m, int on);
+svm_status svm_profile_read(svm_model* m, float* ms, int32_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SVM_H */

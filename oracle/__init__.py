@@ -189,6 +189,27 @@ def unflatten_params(P, width, n_hidden):
     return out
 
 
+def quantized_params(layers, prec) -> np.ndarray:
+    """Flat float64 parameters of [(W, b), ...] as a model of precision `prec`
+    uses them, rounded by the oracle's own quantisers: 0 = FP32 (unchanged);
+    1 = BF16 (every weight matrix to nearest-even bfloat16); 2 = FP8 (hidden
+    matrices to E4M3 with scale max|W| / 448, first and last layers BF16).
+    Biases are never rounded."""
+    out = []
+    n = len(layers)
+    for li, (W, b) in enumerate(layers):
+        W = np.ascontiguousarray(W, dtype=np.float32)
+        if prec == 1 or (prec == 2 and (li == 0 or li == n - 1)):
+            Wq = round_bf16(W)
+        elif prec == 2:
+            _, Wq = quantize_e4m3(W)
+            Wq = Wq.reshape(W.shape)
+        else:
+            Wq = W
+        out.append((Wq, np.asarray(b, dtype=np.float32)))
+    return flatten_params(out)
+
+
 def param_count(width, n_hidden) -> int:
     return int(lib().orc_param_count(width, n_hidden))
 

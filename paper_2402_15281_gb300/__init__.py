@@ -1,0 +1,222 @@
+"""Python binding of libsvm (include/svm.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and passes
+its arguments through ctypes: device buffers are torch CUDA tensors (their
+``data_ptr()``), host arrays are numpy arrays, the stream is a
+``torch.cuda.Stream`` (default: the current stream).  All computation runs in
+the library's CUDA kernels; there is no CPU fallback, and importing a
+function raises if ``libsvm.so`` has not been built (``build()``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import platform
+import struct
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", platform.machine(), "libsvm.so")
+
+SVM_OK, SVM_E_INVALID, SVM_E_CUDA, SVM_E_OOM, SVM_E_TIMEOUT, SVM_E_WEIGHTS, SVM_E_UNSUPPORTED = range(7)
+SVM_FP32, SVM_BF16, SVM_FP8_E4M3 = 0, 1, 2
+SVM_RELU, SVM_SILU = 0, 1
+SVM_STRICT, SVM_NO_EARLY_EXIT, SVM_VERIFY_ALL, SVM_PATHS3 = 1, 2, 4, 8
+
+RESULT_DTYPE = np.dtype([("collision", "u1"), ("early_exit", "u1"), ("reserved", "<u2"),
+                         ("d_min", "<f4"), ("dhat_min", "<f4"), ("n_flagged", "<u4"),
+                         ("n_verified", "<u4"), ("witness_point", "<i4"), ("witness_step", "<i4"),
+                         ("n_ambiguous", "<u4")])
+assert RESULT_DTYPE.itemsize == 32
+
+
+class svm_model_desc(C.Structure):
+    _fields_ = [("dh", (C.c_double * 4) * 6), ("radius", C.c_double * 7), ("tool_len", C.c_double),
+                ("width", C.c_int32), ("n_hidden", C.c_int32), ("act", C.c_int32), ("prec", C.c_int32)]
+
+
+class SvmError(RuntimeError):
+    def __init__(self, fn, status, text):
+        super().__init__(f"{fn} failed: status {status} ({text})")
+        self.status = status
+
+
+_lib = None
+
+
+def build() -> str:
+    """Compile libsvm.so for sm_103a (nvcc, in-tree)."""
+    from . import buildlib
+    return buildlib.build()
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libsvm.so not built ({LIB_PATH}); run paper_2402_15281_gb300.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, u32, f32, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_float, C.c_size_t
+        L.svm_status_string.argtypes = [C.c_int]
+        L.svm_status_string.restype = C.c_char_p
+        L.svm_last_error.argtypes = [vp]
+        L.svm_last_error.restype = C.c_char_p
+        L.svm_create_model.argtypes = [C.POINTER(svm_model_desc), C.c_int, C.POINTER(vp)]
+        L.svm_destroy_model.argtypes = [vp]
+        L.svm_load_weights.argtypes = [vp, C.c_char_p, sz]
+        L.svm_export_weights.argtypes = [vp, vp, sz, C.POINTER(sz)]
+        L.svm_set_gate.argtypes = [vp, f32]
+        L.svm_set_act_scales.argtypes = [vp, vp, i32]
+        L.svm_check_motions.argtypes = [vp, vp, vp, i32, vp, i64, f32, i32, u32, vp, vp]
+        L.svm_check_batch.argtypes = [vp, vp, vp, i32, vp, vp, vp, i32, f32, i32, u32, vp, vp]
+        L.svm_eval_pairs.argtypes = [vp, vp, vp, i32, vp, i64, vp, vp]
+        L.svm_label_pairs.argtypes = [vp, vp, vp, i32, vp, i64, i32, vp, vp]
+        L.svm_profile_enable.argtypes = [vp, C.c_int]
+        L.svm_profile_read.argtypes = [vp, vp, i32]
+        for f in ("svm_profile_enable", "svm_profile_read", "svm_create_model", "svm_destroy_model", "svm_load_weights", "svm_export_weights",
+                  "svm_set_gate", "svm_set_act_scales", "svm_check_motions", "svm_check_batch",
+                  "svm_eval_pairs", "svm_label_pairs"):
+            getattr(L, f).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(fn, status, model=None):
+    if status != SVM_OK:
+        text = lib().svm_status_string(status).decode()
+        if model is not None:
+            text += ": " + lib().svm_last_error(model).decode()
+        raise SvmError(fn, status, text)
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _host_f64(a, cols=6):
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1, cols)
+    return a, a.ctypes.data_as(C.c_void_p)
+
+
+def _dev(t):
+    if t is None:
+        return C.c_void_p(0)
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device arguments must be contiguous CUDA tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------ entry points
+
+def svm_create_model(robot, width=256, n_hidden=4, act=SVM_RELU, prec=SVM_FP32, device=0):
+    d = svm_model_desc()
+    for j in range(6):
+        for c in range(4):
+            d.dh[j][c] = float(robot.dh[j, c])
+    for j in range(7):
+        d.radius[j] = float(robot.radius[j])
+    d.tool_len = float(robot.tool_len)
+    d.width, d.n_hidden, d.act, d.prec = int(width), int(n_hidden), int(act), int(prec)
+    h = C.c_void_p()
+    _check("svm_create_model", lib().svm_create_model(C.byref(d), int(device), C.byref(h)))
+    return h
+
+
+def svm_destroy_model(model):
+    _check("svm_destroy_model", lib().svm_destroy_model(model))
+
+
+def make_blob(layers, act=SVM_RELU, tau=float("inf")) -> bytes:
+    """Serialise [(W, b), ...] (15 -> W, ..., W -> 1) in the blob format of svm_load_weights."""
+    width = layers[0][0].shape[0]
+    out = [b"SVMW", struct.pack("<IIIIIf", 1, len(layers), 15, width, act, tau)]
+    for W, b in layers:
+        W = np.ascontiguousarray(W, dtype="<f4")
+        b = np.ascontiguousarray(b, dtype="<f4")
+        out.append(struct.pack("<II", W.shape[0], W.shape[1]))
+        out.append(W.tobytes())
+        out.append(b.tobytes())
+    return b"".join(out)
+
+
+def svm_load_weights(model, blob: bytes):
+    _check("svm_load_weights", lib().svm_load_weights(model, blob, len(blob)), model)
+
+
+def svm_export_weights(model) -> np.ndarray:
+    need = C.c_size_t()
+    _check("svm_export_weights", lib().svm_export_weights(model, None, 0, C.byref(need)), model)
+    out = np.zeros(need.value, dtype=np.float32)
+    _check("svm_export_weights", lib().svm_export_weights(model, out.ctypes.data_as(C.c_void_p),
+                                                          out.shape[0], None), model)
+    return out
+
+
+def svm_set_gate(model, tau: float):
+    _check("svm_set_gate", lib().svm_set_gate(model, float(tau)), model)
+
+
+def svm_set_act_scales(model, scales):
+    s = np.ascontiguousarray(scales, dtype=np.float32)
+    _check("svm_set_act_scales", lib().svm_set_act_scales(model, s.ctypes.data_as(C.c_void_p), s.shape[0]), model)
+
+
+def svm_check_motions(model, q0, q1, points_dev, margin, steps, flags, results_dev, stream=None):
+    """q0, q1: host (M, 6); points_dev: CUDA float32 (P, 4); results_dev: CUDA uint8 (M, 32)."""
+    q0, p0 = _host_f64(q0)
+    q1, p1 = _host_f64(q1)
+    _check("svm_check_motions", lib().svm_check_motions(
+        model, p0, p1, q0.shape[0], _dev(points_dev), points_dev.shape[0], float(margin), int(steps),
+        int(flags), _dev(results_dev), _stream(stream)), model)
+
+
+def svm_check_batch(model, q0, q1, motion_scene, points_dev, scene_offsets, margin, steps, flags,
+                    results_dev, stream=None):
+    q0, p0 = _host_f64(q0)
+    q1, p1 = _host_f64(q1)
+    ms = np.ascontiguousarray(motion_scene, dtype=np.int32)
+    so = np.ascontiguousarray(scene_offsets, dtype=np.int64)
+    _check("svm_check_batch", lib().svm_check_batch(
+        model, p0, p1, q0.shape[0], ms.ctypes.data_as(C.c_void_p), _dev(points_dev),
+        so.ctypes.data_as(C.c_void_p), so.shape[0] - 1, float(margin), int(steps), int(flags),
+        _dev(results_dev), _stream(stream)), model)
+
+
+def svm_eval_pairs(model, q0, q1, points_dev, f_dev, stream=None):
+    q0, p0 = _host_f64(q0)
+    q1, p1 = _host_f64(q1)
+    _check("svm_eval_pairs", lib().svm_eval_pairs(model, p0, p1, q0.shape[0], _dev(points_dev),
+                                                  points_dev.shape[0], _dev(f_dev), _stream(stream)), model)
+
+
+def svm_label_pairs(model, q0, q1, points_dev, steps, delta_dev, stream=None):
+    q0, p0 = _host_f64(q0)
+    q1, p1 = _host_f64(q1)
+    _check("svm_label_pairs", lib().svm_label_pairs(model, p0, p1, q0.shape[0], _dev(points_dev),
+                                                    points_dev.shape[0], int(steps), _dev(delta_dev),
+                                                    _stream(stream)), model)
+
+
+def svm_profile_enable(model, on=True):
+    _check("svm_profile_enable", lib().svm_profile_enable(model, int(bool(on))), model)
+
+
+def svm_profile_read(model, n=4) -> np.ndarray:
+    """Phase durations (ms) of the last profiled check call."""
+    out = np.zeros(n, dtype=np.float32)
+    _check("svm_profile_read", lib().svm_profile_read(model, out.ctypes.data_as(C.c_void_p), n), model)
+    return out
+
+
+def results_to_numpy(results_dev) -> np.ndarray:
+    """Copy result records (CUDA uint8 tensor of n x 32 bytes) to a structured numpy array."""
+    raw = results_dev.cpu().numpy().reshape(-1)
+    return raw.view(RESULT_DTYPE)
+
+
+def new_results(n, device="cuda"):
+    import torch
+    return torch.empty((max(n, 1), 32), dtype=torch.uint8, device=device)

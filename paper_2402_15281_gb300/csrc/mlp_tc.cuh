@@ -1,0 +1,22 @@
+// mlp_tc.cuh -- host interface of the tcgen05 tensor-core network kernel.
+#pragma once
+#include "svm.h"
+#include "svm_internal.cuh"
+
+namespace svm {
+
+// Per-model state of the tensor-core path (TMA descriptors of the weights).
+struct TcModel {
+    bool ready = false;
+    int prec = 0;                       // SVM_BF16 or SVM_FP8_E4M3
+    alignas(64) unsigned char wmap[128];  // CUtensorMap of the hidden weights
+};
+
+int tc_tile_rows();                                    // pairs per tile
+size_t tc_workspace_bytes(int n_motions);              // extra workspace per call
+int tc_prepare(TcModel& t, const svm_model_desc& d, const DevWeights& w);
+void tc_release(TcModel& t);
+int tc_launch(TcModel& t, const CallArgs& a, const DevWeights& w, int n_tiles, void* ws, int n_sms,
+              cudaStream_t s);
+
+}  // namespace svm

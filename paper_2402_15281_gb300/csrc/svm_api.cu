@@ -1,0 +1,611 @@
+// svm_api.cu -- host side of libsvm: the C ABI declared in include/svm.h.
+//
+// The model owns its device weights, a workspace that grows on demand, a
+// pinned staging buffer for the per-call host arrays and the events that
+// guard them.  A check call validates its arguments on the host, copies the
+// small per-motion arrays (q0, q1, point ranges, tile prefix) in one
+// host-to-device copy, and enqueues the kernels on the caller's stream:
+// prologue (FK + per-motion bias) -> fused network + gate + compaction ->
+// verifier (-> strict second pass) -> finalize.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "svm.h"
+#include "svm_internal.cuh"
+#include "mlp_tc.cuh"
+
+using namespace svm;
+
+struct svm_model {
+    int device = 0;
+    int n_sms = 0;
+    int cc_major = 0, cc_minor = 0;
+    svm_model_desc desc{};
+    RobotParams rp{};
+    bool has_weights = false;
+    float tau = INFINITY;
+    std::vector<float> used;          // weights as used, blob order
+    std::vector<float> ascales;       // FP8 activation scales
+    void* d_weights = nullptr;        // one allocation for all weight arrays
+    DevWeights dw{};
+    TcModel tc{};                     // tensor-core path state (BF16 / FP8)
+    void* ws = nullptr;               // workspace
+    size_t ws_bytes = 0;
+    void* pinned = nullptr;           // host staging for per-call arrays
+    size_t pinned_bytes = 0;
+    cudaEvent_t staging_done = nullptr;
+    bool prof = false;
+    bool prof_valid = false;
+    cudaEvent_t ev[5] = {};
+    std::string last_error;
+};
+
+namespace {
+
+const char* kStatusText[] = {"ok", "invalid argument", "CUDA error", "out of device memory",
+                             "device wait timed out", "bad or missing weights", "unsupported"};
+
+svm_status fail(svm_model* m, svm_status s, const std::string& msg)
+{
+    if (m) m->last_error = msg;
+    return s;
+}
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(m, SVM_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+long long layer_count(const svm_model_desc& d) { return (long long)d.n_hidden + 2; }
+
+// Offsets of the layers in the flat blob-order parameter vector.
+struct Layout {
+    long long w1, b1, wh0, out_w, out_b, total;
+    long long hidden_stride;   // W*W + W
+};
+Layout layout_of(const svm_model_desc& d)
+{
+    Layout L{};
+    const long long W = d.width;
+    L.w1 = 0;
+    L.b1 = W * kInDim;
+    L.wh0 = L.b1 + W;
+    L.hidden_stride = W * W + W;
+    L.out_w = L.wh0 + (long long)d.n_hidden * L.hidden_stride;
+    L.out_b = L.out_w + W;
+    L.total = L.out_b + 1;
+    return L;
+}
+
+bool finite_all(const double* p, long long n)
+{
+    for (long long i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* svm_status_string(svm_status s)
+{
+    const int i = (int)s;
+    return (i >= 0 && i <= 6) ? kStatusText[i] : "unknown status";
+}
+
+const char* svm_last_error(const svm_model* m) { return m ? m->last_error.c_str() : "null model"; }
+
+svm_status svm_create_model(const svm_model_desc* desc, int device, svm_model** out)
+{
+    svm_model* m = nullptr;
+    if (!desc || !out) return SVM_E_INVALID;
+    *out = nullptr;
+    const svm_model_desc& d = *desc;
+    for (int j = 0; j < 6; ++j)
+        if (!finite_all(d.dh[j], 4)) return SVM_E_INVALID;
+    for (int j = 0; j < 7; ++j)
+        if (!std::isfinite(d.radius[j])) return SVM_E_INVALID;
+    if (!std::isfinite(d.tool_len) || d.tool_len < 0) return SVM_E_INVALID;
+    if (d.act != SVM_RELU && d.act != SVM_SILU) return SVM_E_INVALID;
+    if (d.prec < SVM_FP32 || d.prec > SVM_FP8_E4M3) return SVM_E_INVALID;
+    if (d.n_hidden < 0 || d.n_hidden > 16) return SVM_E_INVALID;
+    if (d.prec == SVM_FP32) {
+        if (!(d.width == 64 || d.width == 128 || d.width == 256 || d.width == 512)) return SVM_E_UNSUPPORTED;
+    } else {
+        if (d.width != 256 || d.n_hidden < 1) return SVM_E_UNSUPPORTED;
+    }
+    int n_dev = 0;
+    if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device < 0 || device >= n_dev) return SVM_E_INVALID;
+    m = new svm_model();
+    m->device = device;
+    m->desc = d;
+    DeviceGuard g(device);
+    cudaDeviceGetAttribute(&m->n_sms, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&m->cc_major, cudaDevAttrComputeCapabilityMajor, device);
+    cudaDeviceGetAttribute(&m->cc_minor, cudaDevAttrComputeCapabilityMinor, device);
+    if (d.prec != SVM_FP32 && !(m->cc_major == 10 && m->cc_minor == 3)) {
+        delete m;
+        return SVM_E_UNSUPPORTED;
+    }
+    for (int j = 0; j < 6; ++j) {
+        m->rp.d[j] = d.dh[j][0];
+        m->rp.a[j] = d.dh[j][1];
+        m->rp.ca[j] = std::cos(d.dh[j][2]);
+        m->rp.sa[j] = std::sin(d.dh[j][2]);
+        m->rp.th0[j] = d.dh[j][3];
+    }
+    m->rp.tool_len = d.tool_len;
+    for (int j = 0; j < 7; ++j) m->rp.radius[j] = (float)d.radius[j];
+    if (cudaEventCreateWithFlags(&m->staging_done, cudaEventDisableTiming) != cudaSuccess) {
+        delete m;
+        return SVM_E_CUDA;
+    }
+    m->ascales.assign(d.n_hidden, 1.0f);
+    *out = m;
+    return SVM_OK;
+}
+
+svm_status svm_destroy_model(svm_model* m)
+{
+    if (!m) return SVM_E_INVALID;
+    {
+        DeviceGuard g(m->device);
+        cudaDeviceSynchronize();
+        tc_release(m->tc);
+        if (m->d_weights) cudaFree(m->d_weights);
+        if (m->ws) cudaFree(m->ws);
+        if (m->pinned) cudaFreeHost(m->pinned);
+        if (m->staging_done) cudaEventDestroy(m->staging_done);
+        for (auto& e : m->ev)
+            if (e) cudaEventDestroy(e);
+    }
+    delete m;
+    return SVM_OK;
+}
+
+svm_status svm_set_gate(svm_model* m, float tau)
+{
+    if (!m) return SVM_E_INVALID;
+    if (std::isnan(tau) || tau < 0) return fail(m, SVM_E_INVALID, "tau must be >= 0");
+    m->tau = tau;
+    return SVM_OK;
+}
+
+svm_status svm_set_act_scales(svm_model* m, const float* scales, int32_t n)
+{
+    if (!m || !scales) return SVM_E_INVALID;
+    if (n != m->desc.n_hidden) return fail(m, SVM_E_INVALID, "need one activation scale per hidden layer");
+    for (int i = 0; i < n; ++i)
+        if (!(scales[i] > 0) || !std::isfinite(scales[i])) return fail(m, SVM_E_INVALID, "scale must be finite and > 0");
+    m->ascales.assign(scales, scales + n);
+    if (m->has_weights && m->dw.ascale) {
+        DeviceGuard g(m->device);
+        CK(cudaMemcpy(const_cast<float*>(m->dw.ascale), scales, n * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    return SVM_OK;
+}
+
+svm_status svm_load_weights(svm_model* m, const void* blob, size_t bytes)
+{
+    if (!m || !blob) return SVM_E_INVALID;
+    const svm_model_desc& d = m->desc;
+    const unsigned char* p = static_cast<const unsigned char*>(blob);
+    auto rd32 = [&](size_t off) { uint32_t v; std::memcpy(&v, p + off, 4); return v; };
+    if (bytes < 28 || std::memcmp(p, "SVMW", 4) != 0) return fail(m, SVM_E_WEIGHTS, "bad magic");
+    if (rd32(4) != 1) return fail(m, SVM_E_WEIGHTS, "unsupported blob version");
+    const uint32_t n_layers = rd32(8), in_dim = rd32(12), width = rd32(16), act = rd32(20);
+    float tau;
+    std::memcpy(&tau, p + 24, 4);
+    if ((long long)n_layers != layer_count(d) || in_dim != (uint32_t)kInDim || width != (uint32_t)d.width ||
+        act != (uint32_t)d.act)
+        return fail(m, SVM_E_WEIGHTS, "blob does not match the model description");
+    const Layout Lo = layout_of(d);
+    std::vector<float> orig(Lo.total);
+    size_t off = 28;
+    long long pos = 0;
+    for (uint32_t l = 0; l < n_layers; ++l) {
+        if (off + 8 > bytes) return fail(m, SVM_E_WEIGHTS, "truncated blob");
+        const uint32_t o = rd32(off), i = rd32(off + 4);
+        off += 8;
+        const uint32_t want_o = (l + 1 == n_layers) ? 1u : width;
+        const uint32_t want_i = (l == 0) ? (uint32_t)kInDim : width;
+        if (o != want_o || i != want_i) return fail(m, SVM_E_WEIGHTS, "layer shape mismatch");
+        const size_t nb = ((size_t)o * i + o) * 4;
+        if (off + nb > bytes) return fail(m, SVM_E_WEIGHTS, "truncated blob");
+        std::memcpy(orig.data() + pos, p + off, nb);
+        off += nb;
+        pos += (long long)o * i + o;
+    }
+    if (off != bytes) return fail(m, SVM_E_WEIGHTS, "trailing bytes in blob");
+    for (float v : orig)
+        if (!std::isfinite(v)) return fail(m, SVM_E_WEIGHTS, "non-finite weight");
+
+    DeviceGuard g(m->device);
+    CK(cudaDeviceSynchronize());
+    const long long W = d.width, L = d.n_hidden;
+    // 1) rounding to the model precision on the device
+    std::vector<uint8_t> e4(L * W * W);
+    std::vector<float> wscale(L, 1.0f);
+    {
+        float* tmp = nullptr;
+        uint8_t* tq = nullptr;
+        CK(cudaMalloc(&tmp, Lo.total * sizeof(float)));
+        CK(cudaMalloc(&tq, (size_t)std::max<long long>(1, L * W * W)));
+        CK(cudaMemcpy(tmp, orig.data(), Lo.total * sizeof(float), cudaMemcpyHostToDevice));
+        if (d.prec == SVM_BF16 || d.prec == SVM_FP8_E4M3) {
+            launch_round_bf16(tmp + Lo.w1, W * kInDim, 0);
+            launch_round_bf16(tmp + Lo.out_w, W, 0);
+        }
+        for (long long l = 0; l < L; ++l) {
+            float* wl = tmp + Lo.wh0 + l * Lo.hidden_stride;
+            if (d.prec == SVM_BF16) launch_round_bf16(wl, W * W, 0);
+            if (d.prec == SVM_FP8_E4M3) {
+                float mx = 0.f;
+                const float* hw = orig.data() + Lo.wh0 + l * Lo.hidden_stride;
+                for (long long i = 0; i < W * W; ++i) mx = std::max(mx, std::fabs(hw[i]));
+                const float s = mx > 0.f ? mx / 448.0f : 1.0f;
+                wscale[l] = s;
+                launch_quantize_e4m3(wl, tq + l * W * W, wl, W * W, s, 0);
+            }
+        }
+        CK(cudaGetLastError());
+        m->used.resize(Lo.total);
+        CK(cudaMemcpy(m->used.data(), tmp, Lo.total * sizeof(float), cudaMemcpyDeviceToHost));
+        if (d.prec == SVM_FP8_E4M3) CK(cudaMemcpy(e4.data(), tq, L * W * W, cudaMemcpyDeviceToHost));
+        cudaFree(tmp);
+        cudaFree(tq);
+    }
+    // 2) device layouts of the used values
+    const std::vector<float>& u = m->used;
+    std::vector<float> w1x(W * 3), w1q(W * 12), b1(W), wT(L * W * W), bh(L * W), wout(W);
+    for (long long o = 0; o < W; ++o) {
+        for (int c = 0; c < 3; ++c) w1x[o * 3 + c] = u[Lo.w1 + o * kInDim + c];
+        for (int c = 0; c < 12; ++c) w1q[o * 12 + c] = u[Lo.w1 + o * kInDim + 3 + c];
+        b1[o] = u[Lo.b1 + o];
+        wout[o] = u[Lo.out_w + o];
+    }
+    for (long long l = 0; l < L; ++l) {
+        const float* wl = u.data() + Lo.wh0 + l * Lo.hidden_stride;
+        for (long long o = 0; o < W; ++o)
+            for (long long i = 0; i < W; ++i) wT[(l * W + i) * W + o] = wl[o * W + i];
+        for (long long o = 0; o < W; ++o) bh[l * W + o] = wl[W * W + o];
+    }
+    // hidden weights for the tensor-core path, [L][W out][W in]
+    std::vector<uint16_t> bf(d.prec == SVM_BF16 ? L * W * W : 0);
+    if (d.prec == SVM_BF16)
+        for (long long l = 0; l < L; ++l) {
+            const float* wl = u.data() + Lo.wh0 + l * Lo.hidden_stride;
+            for (long long i = 0; i < W * W; ++i) {
+                uint32_t bits;
+                std::memcpy(&bits, wl + i, 4);
+                bf[l * W * W + i] = (uint16_t)(bits >> 16);   // exact: value is a bfloat16
+            }
+        }
+    const size_t n_w1x = align256(W * 3 * 4), n_w1q = align256(W * 12 * 4), n_b1 = align256(W * 4),
+                 n_wT = align256(L * W * W * 4), n_bh = align256(std::max<long long>(1, L * W) * 4),
+                 n_wout = align256(W * 4), n_wq = align256(std::max<long long>(1, L * W * W * 2)),
+                 n_sc = align256(std::max<long long>(1, L) * 4);
+    const size_t total = n_w1x + n_w1q + n_b1 + n_wT + n_bh + n_wout + n_wq + 2 * n_sc;
+    if (m->d_weights) { cudaFree(m->d_weights); m->d_weights = nullptr; }
+    if (cudaMalloc(&m->d_weights, total) != cudaSuccess) return fail(m, SVM_E_OOM, "weights allocation failed");
+    char* base = static_cast<char*>(m->d_weights);
+    size_t at = 0;
+    auto put = [&](const void* src, size_t nbytes, size_t slot) {
+        void* dst = base + at;
+        if (nbytes) cudaMemcpy(dst, src, nbytes, cudaMemcpyHostToDevice);
+        at += slot;
+        return dst;
+    };
+    DevWeights& dw = m->dw;
+    dw.w1x = (const float*)put(w1x.data(), W * 3 * 4, n_w1x);
+    dw.w1q = (const float*)put(w1q.data(), W * 12 * 4, n_w1q);
+    dw.b1 = (const float*)put(b1.data(), W * 4, n_b1);
+    dw.wT = (const float*)put(wT.data(), L * W * W * 4, n_wT);
+    dw.bh = (const float*)put(bh.data(), L * W * 4, n_bh);
+    dw.wout = (const float*)put(wout.data(), W * 4, n_wout);
+    if (d.prec == SVM_BF16) dw.wq = put(bf.data(), L * W * W * 2, n_wq);
+    else if (d.prec == SVM_FP8_E4M3) dw.wq = put(e4.data(), L * W * W, n_wq);
+    else dw.wq = put(nullptr, 0, n_wq);
+    dw.wscale = (const float*)put(wscale.data(), L * 4, n_sc);
+    dw.ascale = (const float*)put(m->ascales.data(), L * 4, n_sc);
+    dw.bout = u[Lo.out_b];
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+    if (d.prec != SVM_FP32) {
+        const int st = tc_prepare(m->tc, d, dw);
+        if (st != 0) return fail(m, SVM_E_CUDA, "tensor-core path set-up failed");
+    }
+    m->tau = std::isfinite(tau) && tau >= 0 ? tau : INFINITY;
+    m->has_weights = true;
+    return SVM_OK;
+}
+
+svm_status svm_export_weights(const svm_model* mc, float* out, size_t count, size_t* needed)
+{
+    svm_model* m = const_cast<svm_model*>(mc);
+    if (!m) return SVM_E_INVALID;
+    if (!m->has_weights) return fail(m, SVM_E_WEIGHTS, "no weights loaded");
+    if (needed) *needed = m->used.size();
+    if (!out) return SVM_OK;
+    if (count < m->used.size()) return fail(m, SVM_E_INVALID, "output too small");
+    std::memcpy(out, m->used.data(), m->used.size() * sizeof(float));
+    return SVM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+enum Mode { kCheck = 0, kEval = 1, kLabel = 2 };
+
+struct CallPlan {
+    int M, N;
+    long long P_total;       // sum of points over motions
+    int n_tiles;
+    int bm;
+    // offsets in the workspace
+    size_t o_q0, o_q1, o_pbeg, o_pend, o_toff, o_poff, header_bytes;
+    size_t o_caps, o_cbias, o_st, o_idx, o_chunk, total;
+};
+
+// Shared driver of the check, eval and label calls.
+svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1, int32_t M,
+                    const int32_t* motion_scene, const float* points_dev, const int64_t* scene_off,
+                    int32_t n_scenes, float margin, int32_t steps, uint32_t flags, void* results_dev,
+                    float* out_dev, cudaStream_t stream)
+{
+    const svm_model_desc& d = m->desc;
+    if (M < 0) return fail(m, SVM_E_INVALID, "n_motions < 0");
+    if (M > 0 && (!q0 || !q1)) return fail(m, SVM_E_INVALID, "null q0/q1");
+    if (n_scenes < 1 || !scene_off) return fail(m, SVM_E_INVALID, "no scene");
+    if (mode != kLabel && !m->has_weights && !(flags & SVM_VERIFY_ALL))
+        return fail(m, SVM_E_WEIGHTS, "no weights loaded");
+    if (mode == kCheck && M > 0 && !results_dev) return fail(m, SVM_E_INVALID, "null results");
+    if (mode != kCheck && M > 0 && !out_dev) return fail(m, SVM_E_INVALID, "null output");
+    if (!(margin >= 0) || !std::isfinite(margin)) return fail(m, SVM_E_INVALID, "margin must be finite and >= 0");
+    if (steps < 1 || steps > kMaxSteps) return fail(m, SVM_E_INVALID, "steps out of range");
+    if ((flags & SVM_PATHS3) && (M % 3) != 0) return fail(m, SVM_E_INVALID, "paths need n_motions % 3 == 0");
+    if (flags & ~(SVM_STRICT | SVM_NO_EARLY_EXIT | SVM_VERIFY_ALL | SVM_PATHS3))
+        return fail(m, SVM_E_INVALID, "unknown flag");
+    if (scene_off[0] != 0) return fail(m, SVM_E_INVALID, "scene_offsets[0] must be 0");
+    for (int s = 0; s < n_scenes; ++s)
+        if (scene_off[s + 1] < scene_off[s]) return fail(m, SVM_E_INVALID, "scene offsets decrease");
+    if (scene_off[n_scenes] > 0) {
+        if (!points_dev) return fail(m, SVM_E_INVALID, "null points");
+        if (reinterpret_cast<uintptr_t>(points_dev) % 16) return fail(m, SVM_E_INVALID, "points not 16-byte aligned");
+    }
+    if (scene_off[n_scenes] > (int64_t)0xffffffffLL) return fail(m, SVM_E_INVALID, "too many points");
+    if (M == 0) return SVM_OK;
+    if (!finite_all(q0, (long long)M * 6) || !finite_all(q1, (long long)M * 6))
+        return fail(m, SVM_E_INVALID, "non-finite joint angle");
+    for (int i = 0; i < M; ++i) {
+        const int s = motion_scene ? motion_scene[i] : 0;
+        if (s < 0 || s >= n_scenes) return fail(m, SVM_E_INVALID, "motion scene out of range");
+    }
+
+    const bool tc = d.prec != SVM_FP32;
+    CallPlan pl{};
+    pl.M = M;
+    pl.N = steps;
+    pl.bm = tc ? tc_tile_rows() : mlp_fp32_tile_rows();
+    pl.P_total = 0;
+    pl.n_tiles = 0;
+    for (int i = 0; i < M; ++i) {
+        const int s = motion_scene ? motion_scene[i] : 0;
+        const long long n = scene_off[s + 1] - scene_off[s];
+        pl.P_total += n;
+        pl.n_tiles += (int)((n + pl.bm - 1) / pl.bm);
+    }
+    size_t at = 0;
+    pl.o_q0 = at; at = align256(at + (size_t)M * 6 * 8);
+    pl.o_q1 = at; at = align256(at + (size_t)M * 6 * 8);
+    pl.o_pbeg = at; at = align256(at + (size_t)M * 8);
+    pl.o_pend = at; at = align256(at + (size_t)M * 8);
+    pl.o_toff = at; at = align256(at + (size_t)(M + 1) * 4);
+    pl.o_poff = at; at = align256(at + (size_t)(M + 1) * 8);
+    pl.header_bytes = at;
+    pl.o_caps = at; at = align256(at + (size_t)M * (steps + 1) * kCaps * sizeof(Capsule));
+    pl.o_cbias = at; at = align256(at + (size_t)M * d.width * 4);
+    pl.o_st = at; at = align256(at + (size_t)M * sizeof(MotionState));
+    pl.o_idx = at; at = align256(at + (size_t)std::max<long long>(1, pl.P_total) * 4);
+    pl.o_chunk = at; at = align256(at + (size_t)(M + 1) * 4);
+    at = align256(at + tc_workspace_bytes(M));
+    pl.total = at;
+
+    DeviceGuard g(m->device);
+    // grow the workspace and staging buffer (not inside a stream capture)
+    if (pl.total > m->ws_bytes) {
+        CK(cudaDeviceSynchronize());
+        if (m->ws) cudaFree(m->ws);
+        m->ws = nullptr;
+        m->ws_bytes = 0;
+        const size_t want = pl.total + pl.total / 4;
+        if (cudaMalloc(&m->ws, want) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(m, SVM_E_OOM, "workspace allocation failed");
+        }
+        m->ws_bytes = want;
+    }
+    if (pl.header_bytes > m->pinned_bytes) {
+        CK(cudaEventSynchronize(m->staging_done));
+        if (m->pinned) cudaFreeHost(m->pinned);
+        m->pinned = nullptr;
+        m->pinned_bytes = 0;
+        CK(cudaMallocHost(&m->pinned, pl.header_bytes * 2));
+        m->pinned_bytes = pl.header_bytes * 2;
+    }
+    // the previous call's header copy must have finished before the rewrite
+    CK(cudaEventSynchronize(m->staging_done));
+    char* h = static_cast<char*>(m->pinned);
+    std::memcpy(h + pl.o_q0, q0, (size_t)M * 48);
+    std::memcpy(h + pl.o_q1, q1, (size_t)M * 48);
+    long long* pbeg = reinterpret_cast<long long*>(h + pl.o_pbeg);
+    long long* pend = reinterpret_cast<long long*>(h + pl.o_pend);
+    int* toff = reinterpret_cast<int*>(h + pl.o_toff);
+    long long* poff = reinterpret_cast<long long*>(h + pl.o_poff);
+    toff[0] = 0;
+    poff[0] = 0;
+    for (int i = 0; i < M; ++i) {
+        const int s = motion_scene ? motion_scene[i] : 0;
+        pbeg[i] = scene_off[s];
+        pend[i] = scene_off[s + 1];
+        const long long n = pend[i] - pbeg[i];
+        toff[i + 1] = toff[i] + (int)((n + pl.bm - 1) / pl.bm);
+        poff[i + 1] = poff[i] + n;
+    }
+    char* ws = static_cast<char*>(m->ws);
+    const bool prof = m->prof && mode == kCheck;
+    m->prof_valid = false;
+    if (prof) CK(cudaEventRecord(m->ev[0], stream));
+    CK(cudaMemcpyAsync(ws, h, pl.header_bytes, cudaMemcpyHostToDevice, stream));
+    CK(cudaEventRecord(m->staging_done, stream));
+
+    CallArgs a{};
+    a.M = M;
+    a.N = steps;
+    a.W = d.width;
+    a.L = d.n_hidden;
+    a.act = d.act;
+    a.flags = flags;
+    a.margin = margin;
+    a.gate = (mode == kEval) ? -INFINITY : margin + m->tau;
+    a.q0 = reinterpret_cast<const double*>(ws + pl.o_q0);
+    a.q1 = reinterpret_cast<const double*>(ws + pl.o_q1);
+    a.pbeg = reinterpret_cast<const long long*>(ws + pl.o_pbeg);
+    a.pend = reinterpret_cast<const long long*>(ws + pl.o_pend);
+    a.tile_off = reinterpret_cast<const int*>(ws + pl.o_toff);
+    a.pair_off = reinterpret_cast<const long long*>(ws + pl.o_poff);
+    a.points = reinterpret_cast<const float4*>(points_dev);
+    a.caps = reinterpret_cast<Capsule*>(ws + pl.o_caps);
+    a.cbias = (mode == kLabel || (flags & SVM_VERIFY_ALL)) ? nullptr : reinterpret_cast<float*>(ws + pl.o_cbias);
+    a.st = reinterpret_cast<MotionState*>(ws + pl.o_st);
+    a.idx = reinterpret_cast<unsigned*>(ws + pl.o_idx);
+    a.chunk_off = reinterpret_cast<int*>(ws + pl.o_chunk);
+    a.f_out = (mode == kEval) ? out_dev : nullptr;
+    a.f_stride = (n_scenes == 1) ? scene_off[1] : 0;
+    a.paths3 = (flags & SVM_PATHS3) ? 1 : 0;
+    void* tc_ws = ws + pl.o_chunk + align256((size_t)(M + 1) * 4);
+
+    launch_prologue_fk(a, m->rp, m->dw, stream);
+    if (prof) CK(cudaEventRecord(m->ev[1], stream));
+    if (mode == kLabel) {
+        launch_label(a, out_dev, a.f_stride, stream);
+        CK(cudaGetLastError());
+        return SVM_OK;
+    }
+    if (!(flags & SVM_VERIFY_ALL)) {
+        if (tc) {
+            const int st = tc_launch(m->tc, a, m->dw, pl.n_tiles, tc_ws, m->n_sms, stream);
+            if (st != 0) return fail(m, SVM_E_CUDA, "tensor-core launch failed");
+        } else {
+            launch_mlp_fp32(a, m->dw, pl.n_tiles, pl.bm, stream);
+        }
+        if (mode == kEval) {
+            CK(cudaGetLastError());
+            return SVM_OK;
+        }
+        if (prof) CK(cudaEventRecord(m->ev[2], stream));
+        launch_verify(a, 0, 0, stream, m->n_sms);
+        if (flags & SVM_STRICT) launch_verify(a, 1, 1, stream, m->n_sms);
+    } else {
+        if (prof) CK(cudaEventRecord(m->ev[2], stream));
+        launch_verify(a, 1, 0, stream, m->n_sms);
+    }
+    if (prof) CK(cudaEventRecord(m->ev[3], stream));
+    launch_finalize(a, results_dev, stream);
+    if (prof) {
+        CK(cudaEventRecord(m->ev[4], stream));
+        m->prof_valid = true;
+    }
+    CK(cudaGetLastError());
+    return SVM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+svm_status svm_check_motions(svm_model* m, const double* q0, const double* q1, int32_t n_motions,
+                             const float* points_dev, int64_t n_points, float margin, int32_t steps,
+                             uint32_t flags, svm_result* results_dev, void* stream)
+{
+    if (!m) return SVM_E_INVALID;
+    if (n_points < 0) return fail(m, SVM_E_INVALID, "n_points < 0");
+    const int64_t off[2] = {0, n_points};
+    return run_call(m, kCheck, q0, q1, n_motions, nullptr, points_dev, off, 1, margin, steps, flags,
+                    results_dev, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+svm_status svm_check_batch(svm_model* m, const double* q0, const double* q1, int32_t n_motions,
+                           const int32_t* motion_scene, const float* points_dev, const int64_t* scene_offsets,
+                           int32_t n_scenes, float margin, int32_t steps, uint32_t flags,
+                           svm_result* results_dev, void* stream)
+{
+    if (!m) return SVM_E_INVALID;
+    if (n_motions > 0 && !motion_scene) return fail(m, SVM_E_INVALID, "null motion_scene");
+    return run_call(m, kCheck, q0, q1, n_motions, motion_scene, points_dev, scene_offsets, n_scenes, margin,
+                    steps, flags, results_dev, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+svm_status svm_eval_pairs(svm_model* m, const double* q0, const double* q1, int32_t n_motions,
+                          const float* points_dev, int64_t n_points, float* f_dev, void* stream)
+{
+    if (!m) return SVM_E_INVALID;
+    if (n_points < 0) return fail(m, SVM_E_INVALID, "n_points < 0");
+    const int64_t off[2] = {0, n_points};
+    return run_call(m, kEval, q0, q1, n_motions, nullptr, points_dev, off, 1, 0.0f, 1, 0u, nullptr, f_dev,
+                    static_cast<cudaStream_t>(stream));
+}
+
+svm_status svm_profile_enable(svm_model* m, int on)
+{
+    if (!m) return SVM_E_INVALID;
+    DeviceGuard g(m->device);
+    if (on && !m->ev[0])
+        for (auto& e : m->ev) CK(cudaEventCreate(&e));
+    m->prof = on != 0;
+    return SVM_OK;
+}
+
+svm_status svm_profile_read(svm_model* m, float* ms, int32_t n)
+{
+    if (!m || !ms || n < 0 || n > 4) return SVM_E_INVALID;
+    if (!m->prof_valid) return fail(m, SVM_E_INVALID, "no profiled call");
+    DeviceGuard g(m->device);
+    CK(cudaEventSynchronize(m->ev[4]));
+    for (int i = 0; i < n; ++i) CK(cudaEventElapsedTime(ms + i, m->ev[i], m->ev[i + 1]));
+    return SVM_OK;
+}
+
+svm_status svm_label_pairs(svm_model* m, const double* q0, const double* q1, int32_t n_motions,
+                           const float* points_dev, int64_t n_points, int32_t steps, float* delta_dev,
+                           void* stream)
+{
+    if (!m) return SVM_E_INVALID;
+    if (n_points < 0) return fail(m, SVM_E_INVALID, "n_points < 0");
+    const int64_t off[2] = {0, n_points};
+    return run_call(m, kLabel, q0, q1, n_motions, nullptr, points_dev, off, 1, 0.0f, steps, 0u, nullptr,
+                    delta_dev, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,135 @@
+// svm_internal.cuh -- device-side data layout shared by the kernels of libsvm.
+//
+// HBM layout of one check call (all owned by the model's workspace):
+//   q0, q1        [M][6] double     motion end configurations
+//   pbeg, pend    [M] int64         point range of motion m in the point array
+//   tile_off      [M+1] int32       prefix of MLP tiles (one motion per tile)
+//   pair_off      [M+1] int64       prefix of point counts: motion m's flagged
+//                                   indices live at idx[pair_off[m] ...]
+//   caps          [M][N+1][7] Capsule   FP32 capsule table (from FP64 FK)
+//   cbias         [M][W] float      per-motion first-layer bias c_m
+//   st            [M] MotionState   counters and running minima
+//   idx           [sum P_m] uint32  flagged point indices (compaction)
+//   chunk_off     [M+1] int32       verifier work prefix (written on device)
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace svm {
+
+constexpr int kDof = 6;
+constexpr int kCaps = 7;
+constexpr int kInDim = 15;
+constexpr int kMaxSteps = 900;        // capsule table of one motion fits in shared memory
+constexpr float kAmbiguousBand = 4e-6f;
+
+// One capsule at one sample: a = start point, r = radius; e = b - a and
+// inv_ee = 1 / |e|^2 (0 for a zero-length axis, which makes it a sphere).
+struct __align__(16) Capsule {
+    float4 a_r;    // a.x, a.y, a.z, r
+    float4 e_inv;  // e.x, e.y, e.z, inv_ee
+};
+
+// Per-motion device state, reset by the prologue of every call.
+struct MotionState {
+    unsigned int n_flagged;     // compaction counter (append position)
+    int collided;               // 0 / 1, set by the verifier
+    unsigned int dmin_key;      // ordered encoding of the exact minimum
+    unsigned int dhat_key;      // ordered encoding of the network minimum
+    unsigned int n_verified;
+    int witness_point;
+    int witness_step;
+    unsigned int n_ambiguous;
+};
+
+// Order-preserving float <-> uint32 map: unsigned comparison of keys equals
+// float comparison of values (for non-NaN values).
+__device__ __forceinline__ unsigned int float_key(float f) {
+    unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key_float(unsigned int k) {
+    unsigned int u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    return __uint_as_float(u);
+}
+
+// Everything a kernel of one call needs, passed by value.
+struct CallArgs {
+    int M;              // motions
+    int N;              // steps (N+1 samples)
+    int W;              // network width
+    int L;              // hidden layers
+    int act;            // 0 relu, 1 silu
+    uint32_t flags;
+    float margin;
+    float gate;         // margin + tau
+    const double* q0;
+    const double* q1;
+    const long long* pbeg;
+    const long long* pend;
+    const int* tile_off;
+    const long long* pair_off;
+    const float4* points;
+    Capsule* caps;
+    float* cbias;
+    MotionState* st;
+    unsigned int* idx;
+    int* chunk_off;
+    float* f_out;       // optional per-pair network output (eval mode)
+    long long f_stride; // row stride of f_out (points per motion row)
+    int paths3;         // motions form paths of 3 segments
+};
+
+// Model weights on the device.  FP32 copies are always present; the layer-1
+// and output weights hold the values of the model precision (BF16-rounded in
+// the BF16 and FP8 modes).
+struct DevWeights {
+    const float* w1x;     // [W][3]    layer-1 weights of x, y, z
+    const float* w1q;     // [W][12]   layer-1 weights of q0, q1
+    const float* b1;      // [W]
+    const float* wT;      // [L][W in][W out]  hidden weights, transposed (FP32 path)
+    const float* bh;      // [L][W]
+    const float* wout;    // [W]
+    float bout;
+    const void* wq;       // [L][W out][W in] BF16 or E4M3 hidden weights (tensor path)
+    const float* wscale;  // [L] per-layer weight scale (FP8), else 1
+    const float* ascale;  // [L] per-layer activation scale (FP8), else 1
+};
+
+__device__ __forceinline__ float act_fn(float z, int act) {
+    return act == 0 ? fmaxf(z, 0.0f) : z / (1.0f + __expf(-z));
+}
+
+// Motion index of tile t: the last m with tile_off[m] <= t.
+__device__ __forceinline__ int find_segment(const int* off, int n, int t) {
+    int lo = 0, hi = n;   // invariant: off[lo] <= t < off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------- launches
+void launch_prologue(const CallArgs& a, const DevWeights& w, cudaStream_t s);
+void launch_mlp_fp32(const CallArgs& a, const DevWeights& w, int n_tiles, int bm, cudaStream_t s);
+int  mlp_fp32_tile_rows();
+void launch_verify(const CallArgs& a, int range_mode, int strict_pass, cudaStream_t s, int n_sms);
+void launch_finalize(const CallArgs& a, void* results, cudaStream_t s);
+void launch_label(const CallArgs& a, float* delta, long long stride, cudaStream_t s);
+void launch_quantize_bf16(const float* in, uint16_t* out, long long n, cudaStream_t s);
+void launch_round_bf16(float* inout, long long n, cudaStream_t s);
+void launch_quantize_e4m3(const float* in, uint8_t* out, float* deq, long long n, float scale, cudaStream_t s);
+void launch_transpose(const float* in, float* out, int rows, int cols, int batches, cudaStream_t s);
+
+}  // namespace svm
+
+namespace svm {
+// Robot geometry as kernel parameters (FP64 kinematics, FP32 radii).
+struct RobotParams {
+    double d[kDof], a[kDof], ca[kDof], sa[kDof], th0[kDof];
+    double tool_len;
+    float radius[kCaps];
+};
+void launch_prologue_fk(const CallArgs& a, const RobotParams& rp, const DevWeights& w, cudaStream_t s);
+}  // namespace svm

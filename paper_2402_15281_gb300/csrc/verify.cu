@@ -1,0 +1,290 @@
+// verify.cu -- the exact geometric check of flagged pairs and the verdicts.
+//
+// For a point x and motion m the checked distance is the sampled swept-volume
+// distance  min_{k=0..N} min_{j<7} ( |x - seg_{m,k,j}| - r_j ),  the minimum
+// over the robot's capsules at the N+1 samples of the motion (Eqs. 1, 3-4 with
+// the union over s taken on the samples; the geometric checker of Sec. IV-B
+// discretises the motion in the same way).  Since r_j does not depend on k,
+// each thread keeps, per capsule j, the minimum squared axis distance over k
+// and takes 7 square roots at the end.
+//
+// Work: persistent CTAs walk a list of chunks (256 points of one motion).
+// The motion's capsule table is staged in shared memory and read as
+// broadcasts; points are read as float4.  A motion that has collided stops
+// its remaining chunks (early exit), as Algorithm 1 needs only the verdict.
+#include "svm_internal.cuh"
+
+namespace svm {
+
+namespace {
+
+constexpr int VT = 256;   // threads per CTA = points per chunk
+
+// chunk_off[m + 1] - chunk_off[m] = chunks of motion m; one CTA scans M.
+__global__ void plan_kernel(CallArgs A, int range_mode)
+{
+    __shared__ int carry;
+    __shared__ int warp_sums[32];
+    if (threadIdx.x == 0) { carry = 0; A.chunk_off[0] = 0; }
+    __syncthreads();
+    for (int base = 0; base < A.M; base += blockDim.x) {
+        const int m = base + threadIdx.x;
+        int c = 0;
+        if (m < A.M) {
+            const long long n = range_mode ? (A.pend[m] - A.pbeg[m]) : (long long)A.st[m].n_flagged;
+            c = (int)((n + VT - 1) / VT);
+        }
+        // block inclusive scan
+        int v = c;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        #pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, v, s);
+            if (lane >= s) v += t;
+        }
+        if (lane == 31) warp_sums[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            int w = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+            #pragma unroll
+            for (int s = 1; s < 32; s <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, w, s);
+                if (lane >= s) w += t;
+            }
+            warp_sums[lane] = w;
+        }
+        __syncthreads();
+        const int incl = v + (wid > 0 ? warp_sums[wid - 1] : 0) + carry;
+        if (m < A.M) A.chunk_off[m + 1] = incl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = incl;
+        __syncthreads();
+    }
+}
+
+// Squared distances from x to the 7 capsule axes, minimised over samples.
+__device__ __forceinline__ void scan_samples(const Capsule* cs, int n_samples, float3 x, float (&mn)[kCaps])
+{
+    #pragma unroll
+    for (int j = 0; j < kCaps; ++j) mn[j] = __int_as_float(0x7f800000);
+    for (int k = 0; k < n_samples; ++k) {
+        #pragma unroll
+        for (int j = 0; j < kCaps; ++j) {
+            const float4 ar = cs[k * kCaps + j].a_r;
+            const float4 ei = cs[k * kCaps + j].e_inv;
+            const float wx = x.x - ar.x, wy = x.y - ar.y, wz = x.z - ar.z;
+            const float t = __saturatef(fmaf(wz, ei.z, fmaf(wy, ei.y, wx * ei.x)) * ei.w);
+            const float dx = fmaf(-t, ei.x, wx), dy = fmaf(-t, ei.y, wy), dz = fmaf(-t, ei.z, wz);
+            mn[j] = fminf(mn[j], fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+        }
+    }
+}
+
+__device__ __forceinline__ float capsule_min(const float (&mn)[kCaps], const Capsule* cs)
+{
+    float d = __int_as_float(0x7f800000);
+    #pragma unroll
+    for (int j = 0; j < kCaps; ++j) d = fminf(d, sqrtf(mn[j]) - cs[j].a_r.w);
+    return d;
+}
+
+// First sample k at which x is within `margin` of the robot (witness).
+__device__ int witness_sample(const Capsule* cs, int n_samples, float3 x, float margin)
+{
+    for (int k = 0; k < n_samples; ++k) {
+        float mn[kCaps];
+        scan_samples(cs + k * kCaps, 1, x, mn);
+        if (capsule_min(mn, cs + k * kCaps) <= margin) return k;
+    }
+    return n_samples - 1;
+}
+
+template <int RANGE>
+__global__ void __launch_bounds__(VT) verify_kernel(CallArgs A, int strict_pass)
+{
+    extern __shared__ __align__(16) unsigned char vsm[];
+    Capsule* cs = reinterpret_cast<Capsule*>(vsm);
+    __shared__ int s_m;
+    __shared__ int s_skip;
+    __shared__ unsigned s_nver, s_namb;
+    __shared__ unsigned s_dkey;
+
+    const int n_samples = A.N + 1;
+    const int total = A.chunk_off[A.M];
+    const bool early = !(A.flags & 2u);
+    int cur_m = -1;
+
+    for (int c = blockIdx.x; c < total; c += gridDim.x) {
+        if (threadIdx.x == 0) {
+            const int m = find_segment(A.chunk_off, A.M, c);
+            s_m = m;
+            const int path_head = A.paths3 ? (m / 3) * 3 : m;
+            int skip = 0;
+            if (early && *(volatile int*)&A.st[path_head].collided) skip = 1;
+            // second pass of strict mode: only motions still without a collision
+            if (strict_pass && *(volatile int*)&A.st[m].collided) skip = 1;
+            s_skip = skip;
+            s_nver = 0;
+            s_namb = 0;
+            s_dkey = 0xffffffffu;
+        }
+        __syncthreads();
+        const int m = s_m;
+        if (s_skip) { __syncthreads(); continue; }
+        if (m != cur_m) {
+            const float4* src = reinterpret_cast<const float4*>(A.caps + (long long)m * n_samples * kCaps);
+            float4* dst = reinterpret_cast<float4*>(cs);
+            for (int i = threadIdx.x; i < n_samples * kCaps * 2; i += VT) dst[i] = __ldg(src + i);
+            cur_m = m;
+            __syncthreads();
+        }
+        const long long local = (long long)(c - A.chunk_off[m]) * VT + threadIdx.x;
+        const long long n = RANGE ? (A.pend[m] - A.pbeg[m]) : (long long)A.st[m].n_flagged;
+        bool hit = false;
+        if (local < n) {
+            const long long p = RANGE ? A.pbeg[m] + local : (long long)A.idx[A.pair_off[m] + local];
+            const float4 x4 = __ldg(A.points + p);
+            const float3 x = make_float3(x4.x, x4.y, x4.z);
+            float mn[kCaps];
+            scan_samples(cs, n_samples, x, mn);
+            const float d = capsule_min(mn, cs);
+            hit = d <= A.margin;
+            atomicAdd(&s_nver, 1u);
+            if (fabsf(d - A.margin) < kAmbiguousBand) atomicAdd(&s_namb, 1u);
+            atomicMin(&s_dkey, float_key(d));
+            if (hit) {
+                const int path_head = A.paths3 ? (m / 3) * 3 : m;
+                if (atomicCAS(&A.st[m].collided, 0, 1) == 0) {
+                    A.st[m].witness_point = (int)p;
+                    A.st[m].witness_step = witness_sample(cs, n_samples, x, A.margin);
+                }
+                if (path_head != m) atomicExch(&A.st[path_head].collided, 1);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (s_nver) atomicAdd(&A.st[m].n_verified, s_nver);
+            if (s_namb) atomicAdd(&A.st[m].n_ambiguous, s_namb);
+            if (s_dkey != 0xffffffffu) atomicMin(&A.st[m].dmin_key, s_dkey);
+        }
+        __syncthreads();
+    }
+}
+
+// Exact distance of every pair, no gate and no early exit (labels).
+__global__ void __launch_bounds__(VT) label_kernel(CallArgs A, float* delta, long long stride)
+{
+    extern __shared__ __align__(16) unsigned char vsm[];
+    Capsule* cs = reinterpret_cast<Capsule*>(vsm);
+    const int m = blockIdx.y;
+    const int n_samples = A.N + 1;
+    const float4* src = reinterpret_cast<const float4*>(A.caps + (long long)m * n_samples * kCaps);
+    float4* dst = reinterpret_cast<float4*>(cs);
+    for (int i = threadIdx.x; i < n_samples * kCaps * 2; i += VT) dst[i] = __ldg(src + i);
+    __syncthreads();
+    const long long n = A.pend[m] - A.pbeg[m];
+    for (long long local = (long long)blockIdx.x * VT + threadIdx.x; local < n; local += (long long)gridDim.x * VT) {
+        const float4 x4 = __ldg(A.points + A.pbeg[m] + local);
+        float mn[kCaps];
+        scan_samples(cs, n_samples, make_float3(x4.x, x4.y, x4.z), mn);
+        delta[(long long)m * stride + local] = capsule_min(mn, cs);
+    }
+}
+
+struct ResultRec {
+    uint8_t collision, early_exit;
+    uint16_t reserved;
+    float d_min, dhat_min;
+    uint32_t n_flagged, n_verified;
+    int32_t witness_point, witness_step;
+    uint32_t n_ambiguous;
+};
+static_assert(sizeof(ResultRec) == 32, "result record is 32 bytes");
+
+__global__ void finalize_kernel(CallArgs A, ResultRec* out)
+{
+    const int n_out = A.paths3 ? A.M / 3 : A.M;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_out) return;
+    const int seg = A.paths3 ? 3 : 1;
+    ResultRec o;
+    o.collision = 0;
+    o.early_exit = 0;
+    o.reserved = 0;
+    unsigned dk = 0xffffffffu, hk = 0xffffffffu;
+    o.n_flagged = 0;
+    o.n_verified = 0;
+    o.witness_point = -1;
+    o.witness_step = -1;
+    o.n_ambiguous = 0;
+    for (int s = 0; s < seg; ++s) {
+        const MotionState st = A.st[r * seg + s];
+        dk = min(dk, st.dmin_key);
+        hk = min(hk, st.dhat_key);
+        o.n_flagged += st.n_flagged;
+        o.n_verified += st.n_verified;
+        o.n_ambiguous += st.n_ambiguous;
+        if (st.collided && st.witness_point >= 0 && o.witness_point < 0) {
+            o.witness_point = st.witness_point;
+            o.witness_step = s * (A.N + 1) + st.witness_step;
+        }
+        if (st.collided) o.collision = 1;
+    }
+    const bool early = !(A.flags & 2u);
+    o.early_exit = (early && o.collision) ? 1 : 0;
+    o.d_min = key_float(dk);
+    o.dhat_min = key_float(hk);
+    out[r] = o;
+}
+
+}  // namespace
+
+namespace {
+// The capsule table of one motion can exceed the default 48 KB of dynamic
+// shared memory; raise the limit once per device for the kernels that stage it.
+void configure_smem()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    static bool configured[64] = {};
+    if (dev < 0 || dev >= 64 || configured[dev]) return;
+    const int mx = (kMaxSteps + 1) * kCaps * (int)sizeof(Capsule);
+    cudaFuncSetAttribute(verify_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(verify_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(label_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    configured[dev] = true;
+}
+}  // namespace
+
+void launch_verify(const CallArgs& a, int range_mode, int strict_pass, cudaStream_t s, int n_sms)
+{
+    if (a.M <= 0) return;
+    configure_smem();
+    plan_kernel<<<1, 1024, 0, s>>>(a, range_mode);
+    const size_t smem = (size_t)(a.N + 1) * kCaps * sizeof(Capsule);
+    // enough resident CTAs to fill the GPU: shared memory bounds CTAs per SM
+    int per_sm = (int)((200 * 1024) / (smem + 2048));
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 8) per_sm = 8;
+    const int grid = n_sms * per_sm;
+    if (range_mode) verify_kernel<1><<<grid, VT, smem, s>>>(a, strict_pass);
+    else verify_kernel<0><<<grid, VT, smem, s>>>(a, strict_pass);
+}
+
+void launch_label(const CallArgs& a, float* delta, long long stride, cudaStream_t s)
+{
+    if (a.M <= 0) return;
+    configure_smem();
+    const size_t smem = (size_t)(a.N + 1) * kCaps * sizeof(Capsule);
+    const int gx = 64;
+    label_kernel<<<dim3(gx, a.M), VT, smem, s>>>(a, delta, stride);
+}
+
+void launch_finalize(const CallArgs& a, void* results, cudaStream_t s)
+{
+    const int n_out = a.paths3 ? a.M / 3 : a.M;
+    if (n_out <= 0) return;
+    finalize_kernel<<<(n_out + 127) / 128, 128, 0, s>>>(a, reinterpret_cast<ResultRec*>(results));
+}
+
+}  // namespace svm
