@@ -76,7 +76,8 @@ typedef struct {
 typedef struct {
     uint8_t collision;      /* 1 iff some checked point has distance <= margin */
     uint8_t early_exit;     /* 1 if checking stopped at the first collision     */
-    uint16_t reserved;
+    uint16_t status;        /* 0 = valid; 1 = a bounded device wait expired during
+                               the call and this record is not valid           */
     float d_min;            /* minimum exact distance over the checked points;
                                +inf if none was checked; on early exit the first
                                value found <= margin                            */

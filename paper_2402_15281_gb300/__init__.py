@@ -24,7 +24,7 @@ SVM_FP32, SVM_BF16, SVM_FP8_E4M3 = 0, 1, 2
 SVM_RELU, SVM_SILU = 0, 1
 SVM_STRICT, SVM_NO_EARLY_EXIT, SVM_VERIFY_ALL, SVM_PATHS3 = 1, 2, 4, 8
 
-RESULT_DTYPE = np.dtype([("collision", "u1"), ("early_exit", "u1"), ("reserved", "<u2"),
+RESULT_DTYPE = np.dtype([("collision", "u1"), ("early_exit", "u1"), ("status", "<u2"),
                          ("d_min", "<f4"), ("dhat_min", "<f4"), ("n_flagged", "<u4"),
                          ("n_verified", "<u4"), ("witness_point", "<i4"), ("witness_step", "<i4"),
                          ("n_ambiguous", "<u4")])

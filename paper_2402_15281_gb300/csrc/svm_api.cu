@@ -505,6 +505,8 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
     a.f_stride = (n_scenes == 1) ? scene_off[1] : 0;
     a.paths3 = (flags & SVM_PATHS3) ? 1 : 0;
     void* tc_ws = ws + pl.o_chunk + align256((size_t)(M + 1) * 4);
+    a.dev_err = static_cast<unsigned int*>(tc_ws);
+    CK(cudaMemsetAsync(a.dev_err, 0, sizeof(unsigned int), stream));
 
     launch_prologue_fk(a, m->rp, m->dw, stream);
     if (prof) CK(cudaEventRecord(m->ev[1], stream));

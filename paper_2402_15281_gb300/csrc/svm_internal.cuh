@@ -78,6 +78,7 @@ struct CallArgs {
     float* f_out;       // optional per-pair network output (eval mode)
     long long f_stride; // row stride of f_out (points per motion row)
     int paths3;         // motions form paths of 3 segments
+    unsigned int* dev_err;  // per-call error word: nonzero if a bounded wait expired
 };
 
 // Model weights on the device.  FP32 copies are always present; the layer-1

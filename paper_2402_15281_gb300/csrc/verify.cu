@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(VT) label_kernel(CallArgs A, float* delta, lon
 
 struct ResultRec {
     uint8_t collision, early_exit;
-    uint16_t reserved;
+    uint16_t status;
     float d_min, dhat_min;
     uint32_t n_flagged, n_verified;
     int32_t witness_point, witness_step;
@@ -210,7 +210,7 @@ __global__ void finalize_kernel(CallArgs A, ResultRec* out)
     ResultRec o;
     o.collision = 0;
     o.early_exit = 0;
-    o.reserved = 0;
+    o.status = (A.dev_err != nullptr && *A.dev_err != 0u) ? 1 : 0;
     unsigned dk = 0xffffffffu, hk = 0xffffffffu;
     o.n_flagged = 0;
     o.n_verified = 0;

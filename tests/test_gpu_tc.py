@@ -1,0 +1,136 @@
+"""GPU parity of the tcgen05 network kernel (BF16, FP8 E4M3) against the FP64
+oracle evaluated on the same rounded weights.
+
+Per-pair tolerances: 2e-3 m (BF16) and 6e-3 m (FP8).  Verdicts must equal the
+oracle's combined check; flagged counts may differ only by pairs whose oracle
+prediction lies within the tolerance of the gate.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2402_15281_gb300 import synth as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {1: 2e-3, 2: 6e-3}
+DIST_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def svm():
+    import paper_2402_15281_gb300 as svm
+    svm.build()
+    return svm
+
+
+@pytest.fixture(scope="module")
+def robot():
+    return S.make_robot(1)
+
+
+def _layers(seed=2, bout=0.0, n_hidden=4):
+    layers = S.xavier_weights(256, n_hidden, seed=seed)
+    layers[-1] = (layers[-1][0], np.array([bout], dtype=np.float32))
+    return layers
+
+
+def _model(svm, robot, layers, prec, tau=float("inf"), act=0):
+    h = svm.svm_create_model(robot, 256, len(layers) - 2, act, prec, 0)
+    svm.svm_load_weights(h, svm.make_blob(layers, act=act, tau=tau))
+    if prec == 2:
+        svm.svm_set_act_scales(h, np.full(len(layers) - 2, 1.0 / 64, dtype=np.float32))
+    return h
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("n_motions,n_points", [(8, 4096), (3, 1000), (64, 4096), (1, 1), (5, 129)])
+def test_eval_pairs_tc(svm, robot, prec, n_motions, n_points):
+    """Several tile counts: fewer tiles than SMs (one slot per CTA), more
+    (both slots, odd and even counts per CTA), ragged last tiles."""
+    q0, q1 = S.uniform_motions(robot, n_motions, seed=n_motions)
+    pts = S.cube_cloud(n_points, seed=n_points)
+    layers = _layers()
+    h = _model(svm, robot, layers, prec)
+    try:
+        f = torch.empty((n_motions, n_points), device="cuda")
+        svm.svm_eval_pairs(h, q0, q1, _dev(pts), f)
+        torch.cuda.synchronize()
+        P = oracle.quantized_params(layers, prec)
+        ref = oracle.mlp_pairs(P, 256, 4, 0, q0, q1, pts)
+        err = np.abs(f.cpu().numpy() - ref)
+        assert np.isfinite(f.cpu().numpy()).all()
+        assert err.max() <= TOL[prec], err.max()
+    finally:
+        svm.svm_destroy_model(h)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_eval_pairs_tc_silu_and_depth(svm, robot, prec):
+    q0, q1 = S.uniform_motions(robot, 4, seed=3)
+    pts = S.cube_cloud(700, seed=3)
+    for n_hidden, act in ((1, 0), (2, 1), (6, 1)):
+        layers = _layers(seed=7, n_hidden=n_hidden)
+        h = _model(svm, robot, layers, prec, act=act)
+        try:
+            f = torch.empty((4, 700), device="cuda")
+            svm.svm_eval_pairs(h, q0, q1, _dev(pts), f)
+            torch.cuda.synchronize()
+            ref = oracle.mlp_pairs(oracle.quantized_params(layers, prec), 256, n_hidden, act, q0, q1, pts)
+            assert np.abs(f.cpu().numpy() - ref).max() <= TOL[prec]
+        finally:
+            svm.svm_destroy_model(h)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_check_tc_verdicts(svm, robot, prec):
+    """Balanced config-1 variant with a gate inside the prediction range."""
+    q0, q1 = S.uniform_motions(robot, 8, seed=15, max_step_deg=15)
+    pts = S.cube_cloud(4096, seed=8)
+    layers = _layers(bout=0.1)
+    eps, N = 0.05, 64
+    h = _model(svm, robot, layers, prec, tau=0.0)
+    try:
+        for flags in (svm.SVM_NO_EARLY_EXIT, svm.SVM_NO_EARLY_EXIT | svm.SVM_STRICT, 0):
+            res = svm.new_results(8)
+            svm.svm_check_motions(h, q0, q1, _dev(pts), eps, N, flags, res)
+            torch.cuda.synchronize()
+            r = svm.results_to_numpy(res)[:8]
+            P = oracle.quantized_params(layers, prec)
+            f = oracle.mlp_pairs(P, 256, 4, 0, q0, q1, pts)
+            strict = bool(flags & svm.SVM_STRICT)
+            ref = oracle.check_motions(P, 256, 4, 0, robot, q0, q1, N, pts, eps, eps, strict=strict, f=f)
+            assert np.all(r["status"] == 0)
+            near = (np.abs(f - eps) <= TOL[prec]).sum(axis=1)
+            assert np.all(np.abs(r["n_flagged"].astype(np.int64) - ref["n_flagged"]) <= near)
+            assert np.all(np.abs(r["dhat_min"] - ref["dhat_min"]) <= TOL[prec])
+            if strict or not near.any():
+                # with no pair near the gate the flagged sets agree, so the verdicts must too
+                np.testing.assert_array_equal(r["collision"], ref["collision"])
+            if flags & svm.SVM_NO_EARLY_EXIT and not near.any():
+                fin = np.isfinite(ref["d_min"])
+                assert np.all(np.abs(r["d_min"][fin] - ref["d_min"][fin]) <= DIST_TOL)
+    finally:
+        svm.svm_destroy_model(h)
+
+
+def test_bf16_open_gate_equals_geometric_check(svm, robot):
+    q0, q1 = S.bin_motions(robot, 16, seed=3)
+    pts = S.bin_cloud(20000, seed=3)
+    h = _model(svm, robot, _layers(), 1)
+    try:
+        res = svm.new_results(16)
+        svm.svm_check_motions(h, q0, q1, _dev(pts), 0.03, 128, svm.SVM_NO_EARLY_EXIT, res)
+        torch.cuda.synchronize()
+        r = svm.results_to_numpy(res)[:16]
+        dmin, coll = oracle.gcc_motion(robot, q0, q1, 128, pts, 0.03)
+        np.testing.assert_array_equal(r["collision"], coll)
+        assert np.abs(r["d_min"] - dmin).max() <= DIST_TOL
+        assert np.all(r["n_flagged"] == 20000)
+    finally:
+        svm.svm_destroy_model(h)
