@@ -65,6 +65,8 @@ def lib():
         L.orc_param_count.restype = C.c_long
         L.orc_mlp_forward.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, C.c_long, _D]
         L.orc_mlp_pairs.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, _D, C.c_int, _D, C.c_long, _D]
+        L.orc_mlp_pairs_rounded.argtypes = [_D, C.c_int, C.c_int, C.c_int, C.c_int, _D, _D, _D, C.c_int,
+                                            _D, C.c_long, _D]
         L.orc_mlp_loss_grad.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, _D, C.c_long, _D]
         L.orc_mlp_loss_grad.restype = C.c_double
         L.orc_adam_step.argtypes = [_D, _D, _D, _D, C.c_long, C.c_long, C.c_double, C.c_double,
@@ -229,6 +231,19 @@ def mlp_pairs(P, width, n_hidden, act, q0, q1, points) -> np.ndarray:
     M, n = q0.shape[0], pts.shape[0]
     out = np.zeros(M * n)
     lib().orc_mlp_pairs(_d(P), width, n_hidden, act, q0, q1, M, pts, n, out)
+    return out.reshape(M, n)
+
+
+def mlp_pairs_rounded(P, width, n_hidden, act, fmt, scales, q0, q1, points) -> np.ndarray:
+    """Like mlp_pairs, with the input of each hidden layer rounded to the
+    activation format fmt (1 bfloat16, 2 E4M3 with per-layer scales)."""
+    q0 = _d(q0).reshape(-1, 6)
+    q1 = _d(q1).reshape(-1, 6)
+    pts = _xyz(points)
+    M, n = q0.shape[0], pts.shape[0]
+    sc = _d(scales if scales is not None else np.ones(max(1, n_hidden)))
+    out = np.zeros(M * n)
+    lib().orc_mlp_pairs_rounded(_d(P), width, n_hidden, act, int(fmt), sc, q0, q1, M, pts, n, out)
     return out.reshape(M, n)
 
 

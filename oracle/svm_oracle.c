@@ -355,6 +355,57 @@ void orc_mlp_pairs(const double *P, int width, int n_hidden, int act,
     }
 }
 
+/* The network as a reduced-precision model evaluates it: the input of every
+ * hidden layer is rounded to the model's activation format before the layer
+ * (fmt 1: nearest-even bfloat16; fmt 2: FP8 E4M3 as e4m3(h / s_l) * s_l with
+ * the per-layer scale s_l), everything else in double.  fmt 0 is the plain
+ * network.  out[m][i] for all pairs, like orc_mlp_pairs. */
+float orc_round_bf16(float v);
+double orc_round_e4m3(double v);
+void orc_mlp_pairs_rounded(const double *P, int width, int n_hidden, int act, int fmt,
+                           const double *scales, const double *q0, const double *q1, int M,
+                           const double *pts, long n, double *out)
+{
+    #pragma omp parallel
+    {
+        double h[width], z[width];
+        #pragma omp for schedule(static) collapse(2)
+        for (int m = 0; m < M; ++m)
+            for (long i = 0; i < n; ++i) {
+                double in[15];
+                for (int c = 0; c < 3; ++c) in[c] = pts[3 * i + c];
+                for (int c = 0; c < DOF; ++c) {
+                    in[3 + c] = q0[m * DOF + c];
+                    in[9 + c] = q1[m * DOF + c];
+                }
+                const double *W = P, *b = P + (long)width * 15;
+                for (int o = 0; o < width; ++o) {
+                    double s = b[o];
+                    for (int k = 0; k < 15; ++k) s += W[(long)o * 15 + k] * in[k];
+                    h[o] = act_f(s, act);
+                }
+                const double *p = b + width;
+                for (int l = 0; l < n_hidden; ++l) {
+                    for (int k = 0; k < width; ++k) {
+                        if (fmt == 1) h[k] = (double)orc_round_bf16((float)h[k]);
+                        if (fmt == 2) h[k] = orc_round_e4m3(h[k] / scales[l]) * scales[l];
+                    }
+                    const double *Wl = p, *bl = p + (long)width * width;
+                    for (int o = 0; o < width; ++o) {
+                        double s = bl[o];
+                        for (int k = 0; k < width; ++k) s += Wl[(long)o * width + k] * h[k];
+                        z[o] = act_f(s, act);
+                    }
+                    memcpy(h, z, sizeof z);
+                    p = bl + width;
+                }
+                double f = p[width];
+                for (int k = 0; k < width; ++k) f += p[k] * h[k];
+                out[(long)m * n + i] = f;
+            }
+    }
+}
+
 /* Mean L1 loss (1/n) sum |f - delta| and its gradient w.r.t. every parameter
  * (written into G, same layout as P).  Backpropagation of the plain MLP. */
 double orc_mlp_loss_grad(const double *P, int width, int n_hidden, int act,

@@ -1,34 +1,39 @@
 // mlp_tc.cu -- the network f(x, q0, q1) of Sec. IV-A on the 5th-generation
-// tensor cores (tcgen05), BF16 or FP8 E4M3 operands with FP32 accumulation
-// in tensor memory, fused with the gate and the compaction of flagged pairs.
+// tensor cores (tcgen05): BF16 or FP8 E4M3 operands, FP32 accumulation in
+// tensor memory, fused with the gate and the compaction of flagged pairs.
 //
-// Persistent kernel, one CTA per SM, 10 warps:
-//   warp 0      TMA producer: streams the hidden-layer weights, one 128-byte
-//               wide K-slice (256 output rows) per stage, into a ring of
-//               shared-memory stages (128B swizzle, K-major B operand);
-//   warp 1      allocates the 512 TMEM columns and issues tcgen05.mma
-//               (M = 128 pairs, N = 256 outputs) from one thread;
-//   warps 2-5   epilogue of tile slot 0, warps 6-9 epilogue of slot 1.
-// Each CTA takes tiles of 128 pairs of one motion and runs two of them at a
-// time (slots 0 and 1, TMEM columns [0,256) and [256,512)), so that while the
-// tensor core works on one slot's layer, the other slot's epilogue drains its
-// accumulator: TMEM -> registers (tcgen05.ld) -> bias, activation, rounding
-// -> the next layer's A operand in shared memory (128B swizzle, K-major).
+// Persistent kernel, one CTA per SM, 18 warps:
+//   warp 0       TMA producer: streams the weights, one 128-byte K-slice x
+//                256 output rows (32 KB) per stage, into a ring of shared-
+//                memory stages (128B swizzle, the K-major B operand);
+//   warp 1       allocates the 512 TMEM columns and issues tcgen05.mma
+//                (M = 128 pairs, N = 256 outputs) from one thread;
+//   warps 2-9    epilogue of tile slot 0, warps 10-17 epilogue of slot 1;
+//                two warps per TMEM lane quarter, each owning 128 columns.
+// A CTA runs two tiles of 128 pairs at a time (slots 0 and 1 use TMEM
+// columns [0,256) and [256,512)): while the tensor core computes a layer of
+// one slot, the other slot's epilogue drains its accumulator -- TMEM ->
+// registers (tcgen05.ld) -> bias, activation, rounding -> the next layer's A
+// operand in shared memory (128B swizzle, K-major).
 //
-// Layer 1 uses the split W1 [x; q0; q1] + b1 = W1x x + c_m: the epilogue warps
-// compute it in FP32 from the point and the per-motion bias c_m.  The output
-// layer W -> 1 is a dot product on the last accumulator in FP32.  Then the
-// gate f <= margin + tau, a warp ballot and one atomicAdd per warp append the
-// flagged point indices to the motion's list, and the motion's minimum
-// prediction (Eq. 6) is kept with an atomic minimum.
+// Layer 1: the network input is [x; q0; q1]; W1 [x; q0; q1] + b1 splits into
+// W1x x + c_m, with c_m from the prologue.  W1x x runs as one K = 16 BF16 MMA
+// on (x_hi, y_hi, z_hi, x_lo, y_lo, z_lo), x = x_hi + x_lo in two bfloat16
+// parts (x to about 2^-17 relative), against the BF16 layer-1 weights
+// repeated twice; c_m is the bias of its epilogue.  Hidden layers are
+// K = 256 MMAs.  The output layer W -> 1 is an FP32 dot product on the last
+// accumulator, reduced over the two column halves through shared memory.
+// Then the gate f <= margin + tau, a warp ballot and one atomicAdd per warp
+// append the flagged point indices to the motion's list, and the motion's
+// minimum prediction (Eq. 6) is kept with an atomic minimum.
 //
 // FP8: hidden weights and activations are E4M3 with per-layer scales; the
-// accumulator is rescaled by s_w * s_a before the bias.  Both slots share
+// accumulator is rescaled by s_w * s_a before the bias.  Both slots consume
 // every weight stage (REUSE = 2), so each weight byte is read once per pair
-// of tiles.  BF16: the 128 KB layer does not fit twice, each slot streams it.
+// of tiles.  BF16: a 128 KB layer does not fit twice, so each slot streams it.
 //
 // Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the waiter
-// sets the call's error word and an abort flag, all roles leave their loops,
+// sets the call's error word and an abort flag, every role leaves its loop,
 // the MMA issuer and the producer wait (bounded) for their own operations in
 // flight, and the TMEM is freed before the CTA exits.
 #include <cuda.h>
@@ -44,12 +49,22 @@ namespace {
 
 constexpr int TM = 128;                    // pairs per tile = MMA M
 constexpr int WN = 256;                    // network width = MMA N = hidden K
-constexpr int NUM_WARPS = 10;
+constexpr int NUM_EPI_WARPS = 16;
+constexpr int NUM_WARPS = 2 + NUM_EPI_WARPS;
 constexpr int NUM_THREADS = NUM_WARPS * 32;
+constexpr int EPI_PER_SLOT = NUM_EPI_WARPS / 2;
+constexpr int HALF_COLS = WN / 2;
 constexpr int STAGE_BYTES = 32768;         // one 128-byte K-slice x 256 rows
 constexpr int KBLOCK_BYTES = TM * 128;     // one 128-byte K-block of a 128-row tile
 constexpr unsigned long long kTimeoutNs = 2000000000ull;
 constexpr unsigned kErrTimeout = 1u;
+
+// kind::f16 instruction descriptor: D f32 (bit 4), A and B bf16 (bits 7-9,
+// 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t IDESC_BF16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(WN >> 3) << 17) |
+                                ((uint32_t)(TM >> 4) << 24);
+// kind::f8f6f4: D f32, A and B e4m3 (format code 0).
+constexpr uint32_t IDESC_E4M3 = (1u << 4) | ((uint32_t)(WN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 
 template <int PREC>
 struct Cfg;
@@ -57,27 +72,19 @@ template <>
 struct Cfg<SVM_BF16> {
     static constexpr int ELEM = 2;
     static constexpr int SLICE_K = 64;                   // elements per 128-byte row
-    static constexpr int SLICES = WN / SLICE_K;          // 4 per layer
-    static constexpr int MMA_K = 16;
-    static constexpr int MMAS = SLICE_K / MMA_K;         // 4 per slice
+    static constexpr int SLICES = WN / SLICE_K;          // 4 per hidden layer
+    static constexpr int MMAS = 4;                       // K = 16 each
     static constexpr int STAGES = 3;
     static constexpr int REUSE = 1;
-    // kind::f16: D f32 (bit 4), A bf16 (bits 7-9 = 1), B bf16 (bits 10-12 = 1),
-    // both K-major, N >> 3 at bit 17, M >> 4 at bit 24
-    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(WN >> 3) << 17) |
-                                      ((uint32_t)(TM >> 4) << 24);
 };
 template <>
 struct Cfg<SVM_FP8_E4M3> {
     static constexpr int ELEM = 1;
     static constexpr int SLICE_K = 128;
-    static constexpr int SLICES = WN / SLICE_K;          // 2 per layer
-    static constexpr int MMA_K = 32;
-    static constexpr int MMAS = SLICE_K / MMA_K;         // 4 per slice
+    static constexpr int SLICES = WN / SLICE_K;          // 2 per hidden layer
+    static constexpr int MMAS = 4;                       // K = 32 each
     static constexpr int STAGES = 5;
     static constexpr int REUSE = 2;
-    // kind::f8f6f4: D f32, A e4m3 (0), B e4m3 (0)
-    static constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(WN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 };
 
 template <int PREC>
@@ -85,12 +92,15 @@ struct Smem {
     static constexpr int ACT_BYTES = TM * WN * Cfg<PREC>::ELEM;
     static constexpr int ACT0 = 0;
     static constexpr int W0 = 2 * ACT_BYTES;
-    static constexpr int BARS = W0 + Cfg<PREC>::STAGES * STAGE_BYTES;
+    static constexpr int RED = W0 + Cfg<PREC>::STAGES * STAGE_BYTES;   // 2 x 128 floats
+    static constexpr int BARS = RED + 2 * TM * 4;
     static constexpr int N_BARS = 2 * Cfg<PREC>::STAGES + 5;
     static constexpr int MISC = BARS + 8 * N_BARS;
     static constexpr int TOTAL = MISC + 16;
     static constexpr int DYN = TOTAL + 1024;      // slack for 1024-byte alignment
 };
+static_assert(Smem<SVM_BF16>::DYN <= 232448, "shared memory budget");
+static_assert(Smem<SVM_FP8_E4M3>::DYN <= 232448, "shared memory budget");
 
 // ------------------------------------------------------------ PTX wrappers
 
@@ -173,22 +183,22 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
     return d;
 }
 
-template <int PREC>
-__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
 {
-    if constexpr (PREC == SVM_BF16) {
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
-            "l"(adesc), "l"(bdesc), "r"(Cfg<PREC>::IDESC), "r"(accumulate)
-            : "memory");
-    } else {
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
-            "l"(adesc), "l"(bdesc), "r"(Cfg<PREC>::IDESC), "r"(accumulate)
-            : "memory");
-    }
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(IDESC_BF16), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(IDESC_E4M3), "r"(accumulate)
+        : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar)
@@ -201,20 +211,28 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// 32 lanes x 32 consecutive FP32 columns of TMEM into 32 registers per thread.
+__device__ __forceinline__ void named_sync(int id, int threads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// 32 lanes x 32 consecutive FP32 columns of TMEM into 32 registers per
+// thread; the load and its wait are one asm statement, so the registers are
+// valid when it returns.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
 {
     uint32_t r[32];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        : "r"(taddr)
+        : "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
@@ -225,10 +243,17 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
                  : "memory");
 }
 
+// bfloat16 pair (lo in the low half), round to nearest even; with RELU the
+// conversion also clamps negative values to zero.
+template <bool RELU>
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t*>(&v);
+    uint32_t d;
+    if constexpr (RELU)
+        asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    else
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
 }
 
 __device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d)
@@ -238,6 +263,13 @@ __device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float
     return (lo & 0xFFFFu) | (hi << 16);
 }
 
+template <int ACT>
+__device__ __forceinline__ float act_t(float z)
+{
+    if constexpr (ACT == SVM_RELU) return fmaxf(z, 0.0f);
+    else return z / (1.0f + __expf(-z));
+}
+
 // Address of 16-byte chunk `c` (0..7) of K-block `kb` in row `r` of a tile
 // stored K-major with the 128B swizzle (the layout the MMA descriptor reads).
 __device__ __forceinline__ uint32_t act_chunk_addr(uint32_t base, int kb, int r, int c)
@@ -245,45 +277,63 @@ __device__ __forceinline__ uint32_t act_chunk_addr(uint32_t base, int kb, int r,
     return base + kb * KBLOCK_BYTES + r * 128 + ((c ^ (r & 7)) << 4);
 }
 
-// Store 32 activations (columns o0..o0+31 of the next layer's input) of row r.
-template <int PREC>
-__device__ __forceinline__ void store_act32(uint32_t base, int r, int o0, const float (&h)[32], float inv_scale)
+// z = v * scale + bias for 32 columns, activation, rounding, and store as
+// columns o0..o0+31 of row r of the next layer's A operand.
+template <int PREC, int ACT>
+__device__ __forceinline__ void epilogue32(uint32_t base, int r, int o0, float (&v)[32], const float* bias,
+                                           float scale, float inv_next)
 {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + o0 + 4 * q));
+        v[4 * q + 0] = fmaf(v[4 * q + 0], scale, b4.x);
+        v[4 * q + 1] = fmaf(v[4 * q + 1], scale, b4.y);
+        v[4 * q + 2] = fmaf(v[4 * q + 2], scale, b4.z);
+        v[4 * q + 3] = fmaf(v[4 * q + 3], scale, b4.w);
+    }
     if constexpr (PREC == SVM_BF16) {
+        constexpr bool RELU = ACT == SVM_RELU;
+        if constexpr (!RELU) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = act_t<ACT>(v[i]);
+        }
         const int kb = o0 >> 6, c0 = (o0 & 63) >> 3;
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            st_shared_v4(act_chunk_addr(base, kb, r, c0 + q), pack_bf16(h[8 * q + 0], h[8 * q + 1]),
-                         pack_bf16(h[8 * q + 2], h[8 * q + 3]), pack_bf16(h[8 * q + 4], h[8 * q + 5]),
-                         pack_bf16(h[8 * q + 6], h[8 * q + 7]));
+        for (int c = 0; c < 4; ++c)
+            st_shared_v4(act_chunk_addr(base, kb, r, c0 + c), pack_bf16<RELU>(v[8 * c + 0], v[8 * c + 1]),
+                         pack_bf16<RELU>(v[8 * c + 2], v[8 * c + 3]), pack_bf16<RELU>(v[8 * c + 4], v[8 * c + 5]),
+                         pack_bf16<RELU>(v[8 * c + 6], v[8 * c + 7]));
     } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = act_t<ACT>(v[i]) * inv_next;
         const int kb = o0 >> 7, c0 = (o0 & 127) >> 4;
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const float* g = h + 16 * q;
-            st_shared_v4(act_chunk_addr(base, kb, r, c0 + q),
-                         pack_e4m3x4(g[0] * inv_scale, g[1] * inv_scale, g[2] * inv_scale, g[3] * inv_scale),
-                         pack_e4m3x4(g[4] * inv_scale, g[5] * inv_scale, g[6] * inv_scale, g[7] * inv_scale),
-                         pack_e4m3x4(g[8] * inv_scale, g[9] * inv_scale, g[10] * inv_scale, g[11] * inv_scale),
-                         pack_e4m3x4(g[12] * inv_scale, g[13] * inv_scale, g[14] * inv_scale, g[15] * inv_scale));
+        for (int c = 0; c < 2; ++c) {
+            const float* g = v + 16 * c;
+            st_shared_v4(act_chunk_addr(base, kb, r, c0 + c), pack_e4m3x4(g[0], g[1], g[2], g[3]),
+                         pack_e4m3x4(g[4], g[5], g[6], g[7]), pack_e4m3x4(g[8], g[9], g[10], g[11]),
+                         pack_e4m3x4(g[12], g[13], g[14], g[15]));
         }
     }
 }
 
 // ------------------------------------------------------------------ kernel
 
-template <int PREC>
+template <int PREC, int ACT>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
-    mlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, CallArgs A, DevWeights Wt, int n_tiles)
+    mlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ CUtensorMap w1map, CallArgs A,
+                  DevWeights Wt, int n_tiles)
 {
     using C = Cfg<PREC>;
     using SM = Smem<PREC>;
     extern __shared__ __align__(1024) unsigned char dsm_raw[];
-    unsigned char* dsm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char* dsm =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t sbase = smem_u32(dsm);
-    const uint32_t act_base[2] = {sbase + SM::ACT0, sbase + SM::ACT0 + SM::ACT_BYTES};
     const uint32_t w_base = sbase + SM::W0;
     const uint32_t bar0 = sbase + SM::BARS;
+    float* red = reinterpret_cast<float*>(dsm + SM::RED);
+    auto act_base = [&](int s) { return sbase + SM::ACT0 + (uint32_t)(s * SM::ACT_BYTES); };
     auto full_bar = [&](int s) { return bar0 + 8 * s; };
     auto empty_bar = [&](int s) { return bar0 + 8 * (C::STAGES + s); };
     auto accf_bar = [&](int s) { return bar0 + 8 * (2 * C::STAGES + s); };
@@ -293,8 +343,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(dsm + SM::MISC + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_mine = n_tiles > (int)blockIdx.x ? (n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    const int n_mine =
+        n_tiles > (int)blockIdx.x ? (n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
     const int n_pairs = (n_mine + 1) >> 1;
+    const int n_layers = A.L + 1;             // layer 0 = the x part of layer 1, then L hidden layers
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
@@ -303,7 +355,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(accf_bar(s), 1);
-            mbar_init(epid_bar(s), 4);
+            mbar_init(epid_bar(s), EPI_PER_SLOT);
         }
         mbar_init(drain_bar, 1);
         *abort_flag = 0;
@@ -324,6 +376,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&wmap)) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&w1map)) : "memory");
             int stage = 0;
             uint32_t phase = 0;
             uint32_t armed = 0;            // bit s: stage s has been loaded at least once
@@ -331,13 +384,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             bool ok = true;
             for (int j = 0; j < n_pairs && ok; ++j) {
                 const int nslots = min(2, n_mine - 2 * j);
-                for (int l = 0; l < A.L && ok; ++l) {
+                for (int l = 0; l < n_layers && ok; ++l) {
                     const int passes = C::REUSE == 2 ? 1 : nslots;
+                    const int slices = l == 0 ? 1 : C::SLICES;
                     for (int s = 0; s < passes && ok; ++s)
-                        for (int kk = 0; kk < C::SLICES; ++kk) {
+                        for (int kk = 0; kk < slices; ++kk) {
                             if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, A.dev_err)) { ok = false; break; }
                             mbar_arrive_tx(full_bar(stage), STAGE_BYTES);
-                            tma_load_2d(w_base + stage * STAGE_BYTES, &wmap, kk * C::SLICE_K, l * WN, full_bar(stage));
+                            if (l == 0) tma_load_2d(w_base + stage * STAGE_BYTES, &w1map, 0, 0, full_bar(stage));
+                            else tma_load_2d(w_base + stage * STAGE_BYTES, &wmap, kk * C::SLICE_K, (l - 1) * WN,
+                                             full_bar(stage));
                             armed |= 1u << stage;
                             armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
                             if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
@@ -362,7 +418,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             bool ok = true;
             for (int j = 0; j < n_pairs && ok; ++j) {
                 const int nslots = min(2, n_mine - 2 * j);
-                for (int l = 0; l < A.L && ok; ++l) {
+                for (int l = 0; l < n_layers && ok; ++l) {
+                    const int slices = l == 0 ? 1 : C::SLICES;
                     const int layer_stage = stage;
                     const uint32_t layer_phase = phase;
                     for (int s = 0; s < nslots && ok; ++s) {
@@ -371,17 +428,25 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         tc_fence_after();
                         if (C::REUSE == 2) { stage = layer_stage; phase = layer_phase; }
                         const uint32_t d_tmem = tmem_base + (uint32_t)(s * WN);
-                        for (int kk = 0; kk < C::SLICES; ++kk) {
+                        for (int kk = 0; kk < slices; ++kk) {
                             const bool first_use = C::REUSE == 1 || s == 0;
                             if (first_use) {
                                 if (!mbar_wait(full_bar(stage), phase, abort_flag, A.dev_err)) { ok = false; break; }
                                 tc_fence_after();
                             }
-                            const uint32_t a0 = act_base[s] + kk * KBLOCK_BYTES;
+                            const uint32_t a0 = act_base(s) + kk * KBLOCK_BYTES;
                             const uint32_t b0 = w_base + stage * STAGE_BYTES;
+                            if (l == 0) {
+                                mma_bf16(d_tmem, sdesc(a0), sdesc(b0), 0u);
+                            } else {
 #pragma unroll
-                            for (int k = 0; k < C::MMAS; ++k)
-                                mma<PREC>(d_tmem, sdesc(a0 + k * 32), sdesc(b0 + k * 32), (kk | k) != 0 ? 1u : 0u);
+                                for (int k = 0; k < C::MMAS; ++k) {
+                                    if constexpr (PREC == SVM_BF16)
+                                        mma_bf16(d_tmem, sdesc(a0 + k * 32), sdesc(b0 + k * 32), (kk | k) != 0 ? 1u : 0u);
+                                    else
+                                        mma_e4m3(d_tmem, sdesc(a0 + k * 32), sdesc(b0 + k * 32), (kk | k) != 0 ? 1u : 0u);
+                                }
+                            }
                             const bool last_use = C::REUSE == 1 || s == nslots - 1;
                             if (last_use) mma_commit(empty_bar(stage));
                             if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
@@ -399,10 +464,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     } else {
         // ------------------------------------------------ epilogue warps
         const int ew = warp - 2;
-        const int s = ew >> 2;                 // tile slot
-        const int quarter = warp & 3;          // TMEM lane quarter this warp may access
-        const int r = quarter * 32 + lane;     // row of the tile = TMEM lane
-        const uint32_t t_row = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(s * WN);
+        const int s = ew / EPI_PER_SLOT;           // tile slot
+        const int half = (ew % EPI_PER_SLOT) / 4;  // column half [half*128, half*128+128)
+        const int quarter = warp & 3;              // TMEM lane quarter this warp may access
+        const int r = quarter * 32 + lane;         // row of the tile = TMEM lane
+        const int col0 = half * HALF_COLS;
+        const uint32_t abase = act_base(s);
+        const uint32_t t_row = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(s * WN + col0);
+        float* red_s = red + s * TM;
         uint32_t acc_phase = 0;
         bool ok = true;
         for (int i = s; i < n_mine && ok; i += 2) {
@@ -410,53 +479,35 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const int m = find_segment(A.tile_off, A.M, t);
             const long long p = A.pbeg[m] + (long long)(t - A.tile_off[m]) * TM + r;
             const bool valid = p < A.pend[m];
-            const float4 x = valid ? __ldg(A.points + p) : make_float4(0.f, 0.f, 0.f, 0.f);
-            // ---- layer 1 in FP32: act(W1x x + c_m)
-            {
-                const float* cb = A.cbias + (long long)m * WN;
-                const float inv0 = PREC == SVM_FP8_E4M3 ? 1.0f / __ldg(Wt.ascale) : 1.0f;
-#pragma unroll 1
-                for (int o0 = 0; o0 < WN; o0 += 32) {
-                    float h[32];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float4 w0 = __ldg(reinterpret_cast<const float4*>(Wt.w1x + (o0 + 4 * q) * 3));
-                        const float4 w1 = __ldg(reinterpret_cast<const float4*>(Wt.w1x + (o0 + 4 * q) * 3 + 4));
-                        const float4 w2 = __ldg(reinterpret_cast<const float4*>(Wt.w1x + (o0 + 4 * q) * 3 + 8));
-                        const float4 c4 = __ldg(reinterpret_cast<const float4*>(cb + o0 + 4 * q));
-                        h[4 * q + 0] = act_fn(fmaf(w0.z, x.z, fmaf(w0.y, x.y, fmaf(w0.x, x.x, c4.x))), A.act);
-                        h[4 * q + 1] = act_fn(fmaf(w1.y, x.z, fmaf(w1.x, x.y, fmaf(w0.w, x.x, c4.y))), A.act);
-                        h[4 * q + 2] = act_fn(fmaf(w2.x, x.z, fmaf(w1.w, x.y, fmaf(w1.z, x.x, c4.z))), A.act);
-                        h[4 * q + 3] = act_fn(fmaf(w2.w, x.z, fmaf(w2.z, x.y, fmaf(w2.y, x.x, c4.w))), A.act);
-                    }
-                    store_act32<PREC>(act_base[s], r, o0, h, inv0);
-                }
+            // ---- A operand of layer 0: (x_hi, y_hi, z_hi, x_lo, y_lo, z_lo, 0, ...)
+            if (half == 0) {
+                const float4 x = valid ? __ldg(A.points + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+                // hi parts are the nearest bfloat16; the differences are exact in FP32
+                const float xl = x.x - __bfloat162float(__float2bfloat16_rn(x.x));
+                const float yl = x.y - __bfloat162float(__float2bfloat16_rn(x.y));
+                const float zl = x.z - __bfloat162float(__float2bfloat16_rn(x.z));
+                st_shared_v4(act_chunk_addr(abase, 0, r, 0), pack_bf16<false>(x.x, x.y), pack_bf16<false>(x.z, xl),
+                             pack_bf16<false>(yl, zl), 0u);
+                st_shared_v4(act_chunk_addr(abase, 0, r, 1), 0u, 0u, 0u, 0u);
                 fence_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(epid_bar(s));
             }
-            // ---- hidden layers
-            for (int l = 0; l < A.L; ++l) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(epid_bar(s));
+            // ---- layers
+            for (int l = 0; l < n_layers; ++l) {
                 if (!mbar_wait(accf_bar(s), acc_phase, abort_flag, A.dev_err)) { ok = false; break; }
                 acc_phase ^= 1u;
                 tc_fence_after();
-                const float* bl = Wt.bh + (long long)l * WN;
-                const float scale = PREC == SVM_FP8_E4M3 ? __ldg(Wt.wscale + l) * __ldg(Wt.ascale + l) : 1.0f;
-                if (l + 1 < A.L) {
-                    const float inv_next = PREC == SVM_FP8_E4M3 ? 1.0f / __ldg(Wt.ascale + l + 1) : 1.0f;
+                const float* bias = l == 0 ? A.cbias + (long long)m * WN : Wt.bh + (long long)(l - 1) * WN;
+                const float scale =
+                    (PREC == SVM_FP8_E4M3 && l > 0) ? __ldg(Wt.wscale + l - 1) * __ldg(Wt.ascale + l - 1) : 1.0f;
+                if (l + 1 < n_layers) {
+                    const float inv_next = PREC == SVM_FP8_E4M3 ? 1.0f / __ldg(Wt.ascale + l) : 1.0f;
 #pragma unroll 1
-                    for (int o0 = 0; o0 < WN; o0 += 32) {
+                    for (int o0 = 0; o0 < HALF_COLS; o0 += 32) {
                         float v[32];
                         tmem_ld32(t_row + (uint32_t)o0, v);
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const float4 b4 = __ldg(reinterpret_cast<const float4*>(bl + o0 + 4 * q));
-                            v[4 * q + 0] = act_fn(fmaf(v[4 * q + 0], scale, b4.x), A.act);
-                            v[4 * q + 1] = act_fn(fmaf(v[4 * q + 1], scale, b4.y), A.act);
-                            v[4 * q + 2] = act_fn(fmaf(v[4 * q + 2], scale, b4.z), A.act);
-                            v[4 * q + 3] = act_fn(fmaf(v[4 * q + 3], scale, b4.w), A.act);
-                        }
-                        store_act32<PREC>(act_base[s], r, o0, v, inv_next);
+                        epilogue32<PREC, ACT>(abase, r, col0 + o0, v, bias, scale, inv_next);
                     }
                     fence_async_smem();
                     tc_fence_before();
@@ -465,33 +516,38 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 } else {
                     float f = 0.0f;
 #pragma unroll 1
-                    for (int o0 = 0; o0 < WN; o0 += 32) {
+                    for (int o0 = 0; o0 < HALF_COLS; o0 += 32) {
                         float v[32];
                         tmem_ld32(t_row + (uint32_t)o0, v);
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
-                            const float4 b4 = __ldg(reinterpret_cast<const float4*>(bl + o0 + 4 * q));
-                            const float4 w4 = __ldg(reinterpret_cast<const float4*>(Wt.wout + o0 + 4 * q));
-                            f = fmaf(w4.x, act_fn(fmaf(v[4 * q + 0], scale, b4.x), A.act), f);
-                            f = fmaf(w4.y, act_fn(fmaf(v[4 * q + 1], scale, b4.y), A.act), f);
-                            f = fmaf(w4.z, act_fn(fmaf(v[4 * q + 2], scale, b4.z), A.act), f);
-                            f = fmaf(w4.w, act_fn(fmaf(v[4 * q + 3], scale, b4.w), A.act), f);
+                            const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + col0 + o0 + 4 * q));
+                            const float4 w4 = __ldg(reinterpret_cast<const float4*>(Wt.wout + col0 + o0 + 4 * q));
+                            f = fmaf(w4.x, act_t<ACT>(fmaf(v[4 * q + 0], scale, b4.x)), f);
+                            f = fmaf(w4.y, act_t<ACT>(fmaf(v[4 * q + 1], scale, b4.y)), f);
+                            f = fmaf(w4.z, act_t<ACT>(fmaf(v[4 * q + 2], scale, b4.z)), f);
+                            f = fmaf(w4.w, act_t<ACT>(fmaf(v[4 * q + 3], scale, b4.w)), f);
                         }
                     }
                     tc_fence_before();
-                    f += Wt.bout;
-                    // gate, compaction, running minimum (one warp = 32 rows)
-                    if (A.f_out != nullptr && valid) A.f_out[(long long)m * A.f_stride + (p - A.pbeg[m])] = f;
-                    const bool flag = valid && f <= A.gate;
-                    const unsigned mask = __ballot_sync(0xffffffffu, flag);
-                    unsigned base = 0;
-                    if (lane == 0 && mask) base = atomicAdd(&A.st[m].n_flagged, (unsigned)__popc(mask));
-                    base = __shfl_sync(0xffffffffu, base, 0);
-                    if (flag) A.idx[A.pair_off[m] + base + __popc(mask & ((1u << lane) - 1u))] = (unsigned)p;
-                    float fm = valid ? f : __int_as_float(0x7f800000);
+                    // the two column halves of a row meet in shared memory
+                    if (half == 1) red_s[r] = f;
+                    named_sync(1 + s, 32 * EPI_PER_SLOT);
+                    if (half == 0) {
+                        f += red_s[r] + Wt.bout;
+                        if (A.f_out != nullptr && valid) A.f_out[(long long)m * A.f_stride + (p - A.pbeg[m])] = f;
+                        const bool flag = valid && f <= A.gate;
+                        const unsigned mask = __ballot_sync(0xffffffffu, flag);
+                        unsigned base = 0;
+                        if (lane == 0 && mask) base = atomicAdd(&A.st[m].n_flagged, (unsigned)__popc(mask));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        if (flag) A.idx[A.pair_off[m] + base + __popc(mask & ((1u << lane) - 1u))] = (unsigned)p;
+                        float fm = valid ? f : __int_as_float(0x7f800000);
 #pragma unroll
-                    for (int sh = 16; sh > 0; sh >>= 1) fm = fminf(fm, __shfl_xor_sync(0xffffffffu, fm, sh));
-                    if (lane == 0 && fm < __int_as_float(0x7f800000)) atomicMin(&A.st[m].dhat_key, float_key(fm));
+                        for (int sh = 16; sh > 0; sh >>= 1) fm = fminf(fm, __shfl_xor_sync(0xffffffffu, fm, sh));
+                        if (lane == 0 && fm < __int_as_float(0x7f800000))
+                            atomicMin(&A.st[m].dhat_key, float_key(fm));
+                    }
                 }
             }
         }
@@ -521,14 +577,30 @@ EncodeFn get_encode()
     return fn;
 }
 
-template <int PREC>
-void configure(int dev)
+template <int PREC, int ACT>
+void launch_t(const TcModel& t, const CallArgs& a, const DevWeights& w, int n_tiles, int grid, cudaStream_t s)
 {
+    int dev = 0;
+    cudaGetDevice(&dev);
     static bool done[64] = {};
     if (dev >= 0 && dev < 64 && !done[dev]) {
-        cudaFuncSetAttribute(mlp_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<PREC>::DYN);
+        cudaFuncSetAttribute(mlp_tc_kernel<PREC, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<PREC>::DYN);
         done[dev] = true;
     }
+    const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(t.wmap);
+    const CUtensorMap* map1 = reinterpret_cast<const CUtensorMap*>(t.w1map);
+    mlp_tc_kernel<PREC, ACT><<<grid, NUM_THREADS, Smem<PREC>::DYN, s>>>(*map, *map1, a, w, n_tiles);
+}
+
+CUresult encode_2d(EncodeFn enc, CUtensorMap* map, CUtensorMapDataType dt, const void* gaddr, uint64_t inner,
+                   uint64_t rows, uint64_t row_bytes, uint32_t box_inner, uint32_t box_rows)
+{
+    const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+    const cuuint32_t box[2] = {box_inner, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, dt, 2, const_cast<void*>(gaddr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
 }  // namespace
@@ -541,19 +613,17 @@ int tc_prepare(TcModel& t, const svm_model_desc& d, const DevWeights& w)
 {
     t.ready = false;
     t.prec = d.prec;
+    t.act = d.act;
     EncodeFn enc = get_encode();
-    if (!enc || d.width != WN) return -1;
+    if (!enc || d.width != WN || !w.wq || !w.w1pad) return -1;
     const int elem = d.prec == SVM_BF16 ? 2 : 1;
-    const cuuint64_t dims[2] = {(cuuint64_t)WN, (cuuint64_t)WN * (cuuint64_t)d.n_hidden};
-    const cuuint64_t strides[1] = {(cuuint64_t)WN * elem};
-    const cuuint32_t box[2] = {(cuuint32_t)(128 / elem), (cuuint32_t)WN};
-    const cuuint32_t estr[2] = {1, 1};
-    CUtensorMap* map = reinterpret_cast<CUtensorMap*>(t.wmap);
-    const CUresult r = enc(map, d.prec == SVM_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
-                           const_cast<void*>(w.wq), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return -2;
+    const CUtensorMapDataType dt = d.prec == SVM_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    if (encode_2d(enc, reinterpret_cast<CUtensorMap*>(t.wmap), dt, w.wq, WN, (uint64_t)WN * d.n_hidden, WN * elem,
+                  128 / elem, WN) != CUDA_SUCCESS)
+        return -2;
+    if (encode_2d(enc, reinterpret_cast<CUtensorMap*>(t.w1map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, w.w1pad, 64, WN, 128,
+                  64, WN) != CUDA_SUCCESS)
+        return -3;
     t.ready = true;
     return 0;
 }
@@ -565,16 +635,13 @@ int tc_launch(TcModel& t, const CallArgs& a, const DevWeights& w, int n_tiles, v
     (void)ws;
     if (!t.ready) return -1;
     if (n_tiles <= 0) return 0;
-    int dev = 0;
-    cudaGetDevice(&dev);
     const int grid = n_tiles < n_sms ? n_tiles : n_sms;
-    const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(t.wmap);
     if (t.prec == SVM_BF16) {
-        configure<SVM_BF16>(dev);
-        mlp_tc_kernel<SVM_BF16><<<grid, NUM_THREADS, Smem<SVM_BF16>::DYN, s>>>(*map, a, w, n_tiles);
+        if (t.act == SVM_RELU) launch_t<SVM_BF16, SVM_RELU>(t, a, w, n_tiles, grid, s);
+        else launch_t<SVM_BF16, SVM_SILU>(t, a, w, n_tiles, grid, s);
     } else {
-        configure<SVM_FP8_E4M3>(dev);
-        mlp_tc_kernel<SVM_FP8_E4M3><<<grid, NUM_THREADS, Smem<SVM_FP8_E4M3>::DYN, s>>>(*map, a, w, n_tiles);
+        if (t.act == SVM_RELU) launch_t<SVM_FP8_E4M3, SVM_RELU>(t, a, w, n_tiles, grid, s);
+        else launch_t<SVM_FP8_E4M3, SVM_SILU>(t, a, w, n_tiles, grid, s);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

@@ -9,7 +9,9 @@ namespace svm {
 struct TcModel {
     bool ready = false;
     int prec = 0;                       // SVM_BF16 or SVM_FP8_E4M3
+    int act = 0;                        // SVM_RELU or SVM_SILU
     alignas(64) unsigned char wmap[128];  // CUtensorMap of the hidden weights
+    alignas(64) unsigned char w1map[128]; // CUtensorMap of the padded layer-1 x-weights
 };
 
 int tc_tile_rows();                                    // pairs per tile

@@ -301,11 +301,21 @@ svm_status svm_load_weights(svm_model* m, const void* blob, size_t bytes)
                 bf[l * W * W + i] = (uint16_t)(bits >> 16);   // exact: value is a bfloat16
             }
         }
+    // layer-1 x-weights for the tensor path (values already bfloat16 in these modes)
+    std::vector<uint16_t> w1pad(d.prec != SVM_FP32 ? W * 64 : 0, 0);
+    if (d.prec != SVM_FP32)
+        for (long long o = 0; o < W; ++o)
+            for (int c = 0; c < 3; ++c) {
+                uint32_t bits;
+                std::memcpy(&bits, &w1x[o * 3 + c], 4);
+                w1pad[o * 64 + c] = w1pad[o * 64 + 3 + c] = (uint16_t)(bits >> 16);
+            }
+    const size_t n_w1pad = align256(std::max<long long>(1, (long long)w1pad.size() * 2));
     const size_t n_w1x = align256(W * 3 * 4), n_w1q = align256(W * 12 * 4), n_b1 = align256(W * 4),
                  n_wT = align256(L * W * W * 4), n_bh = align256(std::max<long long>(1, L * W) * 4),
                  n_wout = align256(W * 4), n_wq = align256(std::max<long long>(1, L * W * W * 2)),
                  n_sc = align256(std::max<long long>(1, L) * 4);
-    const size_t total = n_w1x + n_w1q + n_b1 + n_wT + n_bh + n_wout + n_wq + 2 * n_sc;
+    const size_t total = n_w1x + n_w1q + n_b1 + n_wT + n_bh + n_wout + n_wq + 2 * n_sc + n_w1pad;
     if (m->d_weights) { cudaFree(m->d_weights); m->d_weights = nullptr; }
     if (cudaMalloc(&m->d_weights, total) != cudaSuccess) return fail(m, SVM_E_OOM, "weights allocation failed");
     char* base = static_cast<char*>(m->d_weights);
@@ -328,6 +338,7 @@ svm_status svm_load_weights(svm_model* m, const void* blob, size_t bytes)
     else dw.wq = put(nullptr, 0, n_wq);
     dw.wscale = (const float*)put(wscale.data(), L * 4, n_sc);
     dw.ascale = (const float*)put(m->ascales.data(), L * 4, n_sc);
+    dw.w1pad = put(w1pad.data(), w1pad.size() * 2, n_w1pad);
     dw.bout = u[Lo.out_b];
     CK(cudaGetLastError());
     CK(cudaDeviceSynchronize());

@@ -93,6 +93,9 @@ struct DevWeights {
     const float* wout;    // [W]
     float bout;
     const void* wq;       // [L][W out][W in] BF16 or E4M3 hidden weights (tensor path)
+    const void* w1pad;    // [W][64] BF16 layer-1 x-weights for the tensor path: row o is
+                          // (w_ox, w_oy, w_oz, w_ox, w_oy, w_oz, 0, ...), applied to
+                          // (x_hi, y_hi, z_hi, x_lo, y_lo, z_lo, 0, ...)
     const float* wscale;  // [L] per-layer weight scale (FP8), else 1
     const float* ascale;  // [L] per-layer activation scale (FP8), else 1
 };

@@ -1,9 +1,16 @@
 """GPU parity of the tcgen05 network kernel (BF16, FP8 E4M3) against the FP64
 oracle evaluated on the same rounded weights.
 
-Per-pair tolerances: 2e-3 m (BF16) and 6e-3 m (FP8).  Verdicts must equal the
-oracle's combined check; flagged counts may differ only by pairs whose oracle
-prediction lies within the tolerance of the gate.
+Per-pair tolerances: 2e-3 m (BF16) and 6e-3 m (FP8).  BF16 meets 2e-3 m
+against the plain FP64 network on the same weights.  FP8 is held to 6e-3 m
+against the oracle that also rounds each hidden layer's input to E4M3 with
+the same scales (same weights, same activation format): E4M3 activations
+alone move the output by up to ~0.03 m on these random networks, which the
+test reports.  Against its own rounding emulation each path must also agree
+on almost every pair to FP32 accumulation error (the median check), since
+rounding decisions only flip where FP32 and FP64 straddle a boundary.
+Verdicts must equal the oracle's combined check; flagged counts may differ
+only by pairs whose oracle prediction lies within the tolerance of the gate.
 """
 import numpy as np
 import pytest
@@ -15,6 +22,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = {1: 2e-3, 2: 6e-3}
+ASCALE = 1.0 / 64
 DIST_TOL = 1e-5
 
 
@@ -40,7 +48,7 @@ def _model(svm, robot, layers, prec, tau=float("inf"), act=0):
     h = svm.svm_create_model(robot, 256, len(layers) - 2, act, prec, 0)
     svm.svm_load_weights(h, svm.make_blob(layers, act=act, tau=tau))
     if prec == 2:
-        svm.svm_set_act_scales(h, np.full(len(layers) - 2, 1.0 / 64, dtype=np.float32))
+        svm.svm_set_act_scales(h, np.full(len(layers) - 2, ASCALE, dtype=np.float32))
     return h
 
 
@@ -62,10 +70,18 @@ def test_eval_pairs_tc(svm, robot, prec, n_motions, n_points):
         svm.svm_eval_pairs(h, q0, q1, _dev(pts), f)
         torch.cuda.synchronize()
         P = oracle.quantized_params(layers, prec)
+        got = f.cpu().numpy()
+        assert np.isfinite(got).all()
+        emu = oracle.mlp_pairs_rounded(P, 256, 4, 0, prec, np.full(4, ASCALE), q0, q1, pts)
+        e_emu = np.abs(got - emu)
+        assert e_emu.max() <= TOL[prec], e_emu.max()
+        assert np.median(e_emu) <= 1e-5, np.median(e_emu)
         ref = oracle.mlp_pairs(P, 256, 4, 0, q0, q1, pts)
-        err = np.abs(f.cpu().numpy() - ref)
-        assert np.isfinite(f.cpu().numpy()).all()
-        assert err.max() <= TOL[prec], err.max()
+        e_ref = np.abs(got - ref)
+        print(f"prec {prec}: max |f - f64| = {e_ref.max():.2e}, mean {e_ref.mean():.2e}; "
+              f"vs rounding emulation max {e_emu.max():.2e}")
+        if prec == 1:
+            assert e_ref.max() <= TOL[prec], e_ref.max()
     finally:
         svm.svm_destroy_model(h)
 
@@ -81,8 +97,9 @@ def test_eval_pairs_tc_silu_and_depth(svm, robot, prec):
             f = torch.empty((4, 700), device="cuda")
             svm.svm_eval_pairs(h, q0, q1, _dev(pts), f)
             torch.cuda.synchronize()
-            ref = oracle.mlp_pairs(oracle.quantized_params(layers, prec), 256, n_hidden, act, q0, q1, pts)
-            assert np.abs(f.cpu().numpy() - ref).max() <= TOL[prec]
+            P = oracle.quantized_params(layers, prec)
+            emu = oracle.mlp_pairs_rounded(P, 256, n_hidden, act, prec, np.full(n_hidden, ASCALE), q0, q1, pts)
+            assert np.abs(f.cpu().numpy() - emu).max() <= TOL[prec]
         finally:
             svm.svm_destroy_model(h)
 
@@ -102,7 +119,7 @@ def test_check_tc_verdicts(svm, robot, prec):
             torch.cuda.synchronize()
             r = svm.results_to_numpy(res)[:8]
             P = oracle.quantized_params(layers, prec)
-            f = oracle.mlp_pairs(P, 256, 4, 0, q0, q1, pts)
+            f = oracle.mlp_pairs_rounded(P, 256, 4, 0, prec, np.full(4, ASCALE), q0, q1, pts)
             strict = bool(flags & svm.SVM_STRICT)
             ref = oracle.check_motions(P, 256, 4, 0, robot, q0, q1, N, pts, eps, eps, strict=strict, f=f)
             assert np.all(r["status"] == 0)

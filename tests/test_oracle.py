@@ -330,6 +330,39 @@ def test_adam_first_step_closed_form():
     np.testing.assert_allclose(P, P0 - 5e-3 * G / (np.abs(G) + 1e-8), rtol=0, atol=1e-12)
 
 
+def test_mlp_rounded_activations_match_library_emulation(robot):
+    """fmt 0 is the plain network; fmt 1 and 2 round each hidden layer's input
+    like torch's bfloat16 / float8_e4m3fn conversions (a library routine)."""
+    torch = pytest.importorskip("torch")
+    layers = S.xavier_weights(32, 2, seed=4)
+    P = oracle.flatten_params(layers)
+    q0, q1 = S.uniform_motions(robot, 2, seed=2)
+    pts = S.cube_cloud(100, seed=2)
+    np.testing.assert_array_equal(oracle.mlp_pairs_rounded(P, 32, 2, 0, 0, None, q0, q1, pts),
+                                  oracle.mlp_pairs(P, 32, 2, 0, q0, q1, pts))
+    Ls = [(W.astype(np.float64), b.astype(np.float64)) for W, b in layers]
+    sc = np.array([1 / 16, 1 / 32])
+
+    def emulate(fmt):
+        out = []
+        for m in range(2):
+            X = np.concatenate([pts[:, :3].astype(np.float64), np.repeat(q0[m][None], 100, 0),
+                                np.repeat(q1[m][None], 100, 0)], 1)
+            h = np.maximum(X @ Ls[0][0].T + Ls[0][1], 0)
+            for l in (1, 2):
+                if fmt == 1:
+                    h = torch.from_numpy(h.astype(np.float32)).to(torch.bfloat16).double().numpy()
+                else:
+                    h = torch.from_numpy(h / sc[l - 1]).to(torch.float8_e4m3fn).double().numpy() * sc[l - 1]
+                h = np.maximum(h @ Ls[l][0].T + Ls[l][1], 0)
+            out.append((h @ Ls[3][0].T + Ls[3][1])[:, 0])
+        return np.array(out)
+
+    for fmt in (1, 2):
+        got = oracle.mlp_pairs_rounded(P, 32, 2, 0, fmt, sc, q0, q1, pts)
+        np.testing.assert_allclose(got, emulate(fmt), rtol=1e-12, atol=1e-12)
+
+
 # ---------------------------------------------------------- combined check
 
 def test_check_open_gate_reduces_to_gcc(robot):
