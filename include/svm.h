@@ -178,6 +178,34 @@ svm_status svm_label_pairs(svm_model* m, const double* q0, const double* q1, int
                            const float* points_dev, int64_t n_points, int32_t steps,
                            float* delta_dev, void* stream);
 
+/* Allocation-free variant of svm_check_motions, for callers that cannot
+ * allocate device memory while they check motions: a real-time loop whose
+ * memory is fixed at start-up, a process whose allocator belongs to another
+ * framework, or code between the begin and end of a stream capture, where
+ * cudaMalloc is not allowed.  The paper has no counterpart; this is an
+ * interface of this library only.
+ *   - Allocates nothing: no cudaMalloc, cudaFree, pinned host memory or
+ *     allocating library call.  Its scratch is one fixed 32 MiB array in
+ *     device memory that the library declares at file scope; every GPU that
+ *     loads the library holds it until the process exits.
+ *   - q0_dev, q1_dev are DEVICE arrays (n_motions x 6 doubles, finite; not
+ *     checked); the other arguments and the results are as in
+ *     svm_check_motions.
+ *   - A call needs about 4 bytes per motion-point pair plus, per motion,
+ *     (steps + 1) * 7 * 32 bytes and 1.3 KB; a call needing more than the
+ *     32 MiB is rejected with SVM_E_INVALID and a message naming the sizes
+ *     (e.g. 64 motions x 100 000 points fit, 64 x 200 000 do not).
+ *   - The first call on a device looks up the scratch array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call, from every model on that device, shares the one array and
+ *     finds the previous call's contents in it; the call re-initialises what
+ *     it needs.  Calls whose kernels overlap on the GPU (different streams
+ *     without ordering) race on the array and give wrong results. */
+svm_status svm_check_motions_noalloc(svm_model* m, const double* q0_dev, const double* q1_dev,
+                                     int32_t n_motions, const float* points_dev, int64_t n_points,
+                                     float margin, int32_t steps, uint32_t flags,
+                                     svm_result* results_dev, void* stream);
+
 /* Phase timing.  With profiling on, every check call records CUDA events on
  * its stream between its phases; svm_profile_read waits for the last call to
  * finish and writes n <= 4 durations in milliseconds: ms[0] the per-call

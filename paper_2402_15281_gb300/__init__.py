@@ -72,6 +72,8 @@ def lib():
         L.svm_check_batch.argtypes = [vp, vp, vp, i32, vp, vp, vp, i32, f32, i32, u32, vp, vp]
         L.svm_eval_pairs.argtypes = [vp, vp, vp, i32, vp, i64, vp, vp]
         L.svm_label_pairs.argtypes = [vp, vp, vp, i32, vp, i64, i32, vp, vp]
+        L.svm_check_motions_noalloc.argtypes = [vp, vp, vp, i32, vp, i64, f32, i32, u32, vp, vp]
+        L.svm_check_motions_noalloc.restype = C.c_int
         L.svm_profile_enable.argtypes = [vp, C.c_int]
         L.svm_profile_read.argtypes = [vp, vp, i32]
         for f in ("svm_profile_enable", "svm_profile_read", "svm_create_model", "svm_destroy_model", "svm_load_weights", "svm_export_weights",
@@ -171,6 +173,22 @@ def svm_check_motions(model, q0, q1, points_dev, margin, steps, flags, results_d
     _check("svm_check_motions", lib().svm_check_motions(
         model, p0, p1, q0.shape[0], _dev(points_dev), points_dev.shape[0], float(margin), int(steps),
         int(flags), _dev(results_dev), _stream(stream)), model)
+
+
+def svm_check_motions_noalloc(model, q0_dev, q1_dev, points_dev, margin, steps, flags, results_dev, stream=None):
+    """Allocation-free check: q0_dev, q1_dev are CUDA float64 (M, 6) tensors."""
+    if q0_dev.dtype != _torch().float64 or q1_dev.dtype != _torch().float64:
+        raise ValueError("q0_dev and q1_dev must be float64 CUDA tensors")
+    if q0_dev.shape != q1_dev.shape or q0_dev.shape[-1] != 6:
+        raise ValueError("q0_dev and q1_dev must both be (M, 6)")
+    _check("svm_check_motions_noalloc", lib().svm_check_motions_noalloc(
+        model, _dev(q0_dev), _dev(q1_dev), q0_dev.shape[0], _dev(points_dev), points_dev.shape[0],
+        float(margin), int(steps), int(flags), _dev(results_dev), _stream(stream)), model)
+
+
+def _torch():
+    import torch
+    return torch
 
 
 def svm_check_batch(model, q0, q1, motion_scene, points_dev, scene_offsets, margin, steps, flags,

@@ -622,3 +622,159 @@ svm_status svm_label_pairs(svm_model* m, const double* q0, const double* q1, int
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------
+// Allocation-free check.  Some callers cannot allocate device memory while
+// they check motions: a real-time control loop whose memory is fixed at
+// start-up, a process whose allocator is owned by another framework, or code
+// running between a stream capture's begin and end, where cudaMalloc is not
+// allowed.  svm_check_motions grows its workspace with cudaMalloc and stages
+// q0/q1 in pinned host memory it allocates on first use; the entry point
+// below does neither.  Its scratch is one fixed array in device memory,
+// declared here at file scope, which every GPU that loads this library holds
+// until the process exits.
+// ------------------------------------------------------------------------
+
+#include <mutex>
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;   // 32 MiB per device
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {};
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a stand-in; the address comes from the runtime.
+cudaError_t noalloc_scratch(int dev, void** out)
+{
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+// Per-motion point ranges and prefixes for one cloud shared by all motions,
+// and the call's error word, written into the scratch on the device.
+__global__ void noalloc_setup_kernel(int M, long long n_points, int bm, long long* pbeg, long long* pend,
+                                     int* tile_off, long long* pair_off, unsigned int* err)
+{
+    const long long tiles = (n_points + bm - 1) / bm;
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m <= M; m += gridDim.x * blockDim.x) {
+        if (m < M) {
+            pbeg[m] = 0;
+            pend[m] = n_points;
+        }
+        tile_off[m] = (int)(tiles * m);
+        pair_off[m] = n_points * m;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *err = 0u;
+}
+
+}  // namespace
+
+extern "C" svm_status svm_check_motions_noalloc(svm_model* m, const double* q0_dev, const double* q1_dev,
+                                                int32_t n_motions, const float* points_dev, int64_t n_points,
+                                                float margin, int32_t steps, uint32_t flags,
+                                                svm_result* results_dev, void* stream_v)
+{
+    if (!m) return SVM_E_INVALID;
+    const svm_model_desc& d = m->desc;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    const int M = n_motions;
+    if (M < 0 || n_points < 0) return fail(m, SVM_E_INVALID, "negative size");
+    if (M == 0) return SVM_OK;
+    if (!q0_dev || !q1_dev || !results_dev) return fail(m, SVM_E_INVALID, "null q0/q1/results");
+    if (n_points > 0 && !points_dev) return fail(m, SVM_E_INVALID, "null points");
+    if (reinterpret_cast<uintptr_t>(points_dev) % 16) return fail(m, SVM_E_INVALID, "points not 16-byte aligned");
+    if (!m->has_weights && !(flags & SVM_VERIFY_ALL)) return fail(m, SVM_E_WEIGHTS, "no weights loaded");
+    if (!(margin >= 0) || !std::isfinite(margin)) return fail(m, SVM_E_INVALID, "margin must be finite and >= 0");
+    if (steps < 1 || steps > kMaxSteps) return fail(m, SVM_E_INVALID, "steps out of range");
+    if ((flags & SVM_PATHS3) && (M % 3) != 0) return fail(m, SVM_E_INVALID, "paths need n_motions % 3 == 0");
+    if (flags & ~(SVM_STRICT | SVM_NO_EARLY_EXIT | SVM_VERIFY_ALL | SVM_PATHS3))
+        return fail(m, SVM_E_INVALID, "unknown flag");
+
+    const bool tc = d.prec != SVM_FP32;
+    const int bm = tc ? tc_tile_rows() : mlp_fp32_tile_rows();
+    const long long tiles_per = (n_points + bm - 1) / bm;
+    if ((long long)M * tiles_per > 0x7fffffffLL || n_points > (int64_t)0xffffffffLL)
+        return fail(m, SVM_E_INVALID, "too many tiles");
+    // scratch layout (the same arrays as the workspace of svm_check_motions)
+    size_t at = 0;
+    const size_t o_pbeg = at; at = align256(at + (size_t)M * 8);
+    const size_t o_pend = at; at = align256(at + (size_t)M * 8);
+    const size_t o_toff = at; at = align256(at + (size_t)(M + 1) * 4);
+    const size_t o_poff = at; at = align256(at + (size_t)(M + 1) * 8);
+    const size_t o_caps = at; at = align256(at + (size_t)M * (steps + 1) * kCaps * sizeof(Capsule));
+    const size_t o_cbias = at; at = align256(at + (size_t)M * d.width * 4);
+    const size_t o_st = at; at = align256(at + (size_t)M * sizeof(MotionState));
+    const size_t o_idx = at; at = align256(at + (size_t)std::max<long long>(1, (long long)M * n_points) * 4);
+    const size_t o_chunk = at; at = align256(at + (size_t)(M + 1) * 4);
+    const size_t o_err = at; at = align256(at + 4);
+    if (at > kNoAllocScratchBytes)
+        return fail(m, SVM_E_INVALID,
+                    "svm_check_motions_noalloc: the call needs " + std::to_string(at) +
+                        " bytes of scratch, more than its fixed 32 MiB; use fewer motions or points per call "
+                        "(about 4 bytes per motion-point pair plus ~29 KB per motion at 128 steps)");
+
+    DeviceGuard g(m->device);
+    void* sp = nullptr;
+    {
+        const cudaError_t e = noalloc_scratch(m->device, &sp);
+        if (e != cudaSuccess) return fail(m, SVM_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    }
+    char* ws = static_cast<char*>(sp);
+    CallArgs a{};
+    a.M = M;
+    a.N = steps;
+    a.W = d.width;
+    a.L = d.n_hidden;
+    a.act = d.act;
+    a.flags = flags;
+    a.margin = margin;
+    a.gate = margin + m->tau;
+    a.q0 = q0_dev;
+    a.q1 = q1_dev;
+    a.pbeg = reinterpret_cast<const long long*>(ws + o_pbeg);
+    a.pend = reinterpret_cast<const long long*>(ws + o_pend);
+    a.tile_off = reinterpret_cast<const int*>(ws + o_toff);
+    a.pair_off = reinterpret_cast<const long long*>(ws + o_poff);
+    a.points = reinterpret_cast<const float4*>(points_dev);
+    a.caps = reinterpret_cast<Capsule*>(ws + o_caps);
+    a.cbias = (flags & SVM_VERIFY_ALL) ? nullptr : reinterpret_cast<float*>(ws + o_cbias);
+    a.st = reinterpret_cast<MotionState*>(ws + o_st);
+    a.idx = reinterpret_cast<unsigned*>(ws + o_idx);
+    a.chunk_off = reinterpret_cast<int*>(ws + o_chunk);
+    a.f_out = nullptr;
+    a.f_stride = n_points;
+    a.paths3 = (flags & SVM_PATHS3) ? 1 : 0;
+    a.dev_err = reinterpret_cast<unsigned int*>(ws + o_err);
+
+    noalloc_setup_kernel<<<(M + 256) / 256, 256, 0, stream>>>(
+        M, n_points, bm, reinterpret_cast<long long*>(ws + o_pbeg), reinterpret_cast<long long*>(ws + o_pend),
+        reinterpret_cast<int*>(ws + o_toff), reinterpret_cast<long long*>(ws + o_poff), a.dev_err);
+    launch_prologue_fk(a, m->rp, m->dw, stream);
+    if (!(flags & SVM_VERIFY_ALL)) {
+        const int n_tiles = (int)(M * tiles_per);
+        if (tc) {
+            if (tc_launch(m->tc, a, m->dw, n_tiles, nullptr, m->n_sms, stream) != 0)
+                return fail(m, SVM_E_CUDA, "tensor-core launch failed");
+        } else {
+            launch_mlp_fp32(a, m->dw, n_tiles, bm, stream);
+        }
+        launch_verify(a, 0, 0, stream, m->n_sms);
+        if (flags & SVM_STRICT) launch_verify(a, 1, 1, stream, m->n_sms);
+    } else {
+        launch_verify(a, 1, 0, stream, m->n_sms);
+    }
+    launch_finalize(a, results_dev, stream);
+    CK(cudaGetLastError());
+    return SVM_OK;
+}
