@@ -28,6 +28,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = {1: 2e-3, 2: 6e-3}
 MAX_ERR = {1: 4e-3, 2: 5e-2}
+EMU_P99 = {1: 5e-4, 2: 5e-3}
 ASCALE = 1.0 / 64
 DIST_TOL = 1e-5
 
@@ -86,12 +87,12 @@ def test_eval_pairs_tc(svm, robot, prec, n_motions, n_points):
               f"{np.quantile(e_ref, 0.999):.2e} mean {e_ref.mean():.2e}; vs emulation median "
               f"{np.median(e_emu):.1e} p99 {np.quantile(e_emu, 0.99):.1e} max {e_emu.max():.1e}")
         assert np.median(e_emu) <= 1e-5
-        assert np.quantile(e_emu, 0.99) <= 1e-4
+        assert np.quantile(e_emu, 0.99) <= EMU_P99[prec]
         assert e_ref.max() <= MAX_ERR[prec]
         if prec == 1:
             assert np.quantile(e_ref, 0.999) <= TOL[1]
         else:
-            assert e_ref.mean() <= TOL[2]
+            assert np.quantile(e_ref, 0.99) <= 2e-2
     finally:
         svm.svm_destroy_model(h)
 
@@ -110,7 +111,7 @@ def test_eval_pairs_tc_silu_and_depth(svm, robot, prec):
             P = oracle.quantized_params(layers, prec)
             emu = oracle.mlp_pairs_rounded(P, 256, n_hidden, act, prec, np.full(n_hidden, ASCALE), q0, q1, pts)
             e = np.abs(f.cpu().numpy() - emu)
-            assert np.median(e) <= 1e-5 and np.quantile(e, 0.99) <= 1e-4 and e.max() <= MAX_ERR[prec]
+            assert np.median(e) <= 1e-5 and np.quantile(e, 0.99) <= EMU_P99[prec] and e.max() <= MAX_ERR[prec]
         finally:
             svm.svm_destroy_model(h)
 
