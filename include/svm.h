@@ -206,6 +206,62 @@ svm_status svm_check_motions_noalloc(svm_model* m, const double* q0_dev, const d
                                      float margin, int32_t steps, uint32_t flags,
                                      svm_result* results_dev, void* stream);
 
+/* ---------------------------------------------------------------- training
+ * The network is trained on the GPU on tuples (x, q0, q1, delta) (Sec. IV-C)
+ * whose labels come from the exact geometric check, with mean absolute error
+ * as the loss (the paper reports MAE) and Adam (betas 0.9 / 0.999, eps 1e-8,
+ * Sec. V).  Hidden layers run as BF16 tensor-core GEMMs with FP32
+ * accumulation and FP32 master weights; layer 1 and the output layer in FP32.
+ * A trainer owns its parameters, Adam moments, activations for one batch and
+ * its data; calls are synchronous (they return after the GPU work). */
+typedef struct svm_trainer svm_trainer;
+
+/* width 256 or 512, n_hidden 1..16, act ReLU or SiLU; batch a multiple of
+ * 256 (>= 256).  Parameters start at zero: load initial weights with
+ * svm_train_set_weights.  Needs a GPU of compute capability 10.3. */
+svm_status svm_train_create(const svm_model_desc* desc, int device, int32_t batch, svm_trainer** out);
+svm_status svm_train_destroy(svm_trainer* t);
+const char* svm_train_last_error(const svm_trainer* t);
+int64_t svm_train_param_count(const svm_trainer* t);
+
+/* Weights in the blob format of svm_load_weights (tau ignored).  Setting
+ * weights resets the Adam moments and the step count. */
+svm_status svm_train_set_weights(svm_trainer* t, const void* blob, size_t bytes);
+svm_status svm_train_get_weights(svm_trainer* t, void* blob, size_t capacity, size_t* needed);
+
+/* Generate n_motions * samples_per_motion labelled samples on the GPU for
+ * the host motions q0, q1 (n_motions x 6): for motion m and local index j the
+ * SplitMix64 stream (seed, m) gives draws u_0..u_6 at counters 8j..8j+6;
+ * with u_0 < 0.7 the point is near capsule floor(u_2 * 7) at sample
+ * floor(u_1 * (steps + 1)): a + u_3 e + (r + off) d with d the unit vector of
+ * (z = 2 u_4 - 1, phi = 2 pi u_5) and off = -0.1 + 0.2 u_6; otherwise it is
+ * uniform in [-0.75,0.75]^2 x [0,1.5] from u_1..u_3.  The label is the exact
+ * sampled swept-volume distance with `steps` steps.  Sample s = m *
+ * samples_per_motion + j. */
+svm_status svm_train_make_data(svm_trainer* t, const double* q0, const double* q1, int32_t n_motions,
+                               int32_t samples_per_motion, int32_t steps, uint64_t seed);
+/* Explicit samples: x4 (n x 4 floats: x, y, z, delta) and motion indices. */
+svm_status svm_train_set_samples(svm_trainer* t, const double* q0, const double* q1, int32_t n_motions,
+                                 const float* x4, const int32_t* motion, int64_t n);
+svm_status svm_train_copy_samples(svm_trainer* t, float* x4_out, int32_t* motion_out, int64_t n);
+
+/* Loss and gradient (blob order, param_count floats, host) of the batch of
+ * samples [sample_begin, sample_begin + batch); no update. */
+svm_status svm_train_gradient(svm_trainer* t, int64_t sample_begin, float* grad_out, float* loss_out);
+/* One Adam step with the gradient held by the trainer. */
+svm_status svm_train_adam(svm_trainer* t, float lr);
+/* One epoch over the samples [begin, end): floor((end-begin)/batch) batches,
+ * batch i holding the samples begin + o_i + r * n_batches (r < batch) with a
+ * random permutation o of the batch offsets drawn from shuffle_seed. */
+svm_status svm_train_epoch(svm_trainer* t, int64_t sample_begin, int64_t sample_end, float lr,
+                           uint64_t shuffle_seed, float* mean_loss);
+/* Mean absolute error over the whole batches of [begin, end). */
+svm_status svm_train_evaluate(svm_trainer* t, int64_t sample_begin, int64_t sample_end, float* mae);
+/* Checkpoint: parameters, Adam moments (param_count floats each) and step. */
+svm_status svm_train_state(svm_trainer* t, float* params, float* m1, float* m2, int64_t* step, int64_t n);
+svm_status svm_train_restore(svm_trainer* t, const float* params, const float* m1, const float* m2, int64_t step,
+                             int64_t n);
+
 /* Phase timing.  With profiling on, every check call records CUDA events on
  * its stream between its phases; svm_profile_read waits for the last call to
  * finish and writes n <= 4 durations in milliseconds: ms[0] the per-call

@@ -81,6 +81,7 @@ def lib():
         L.orc_round_e4m3.restype = C.c_double
         L.orc_quantize_e4m3.argtypes = [_F, C.c_long, _F]
         L.orc_quantize_e4m3.restype = C.c_float
+        L.orc_training_points.argtypes = [_D, C.c_double, _D, _D, _D, C.c_int, C.c_uint64, C.c_int, C.c_int, _D]
         L.orc_splitmix64_u01.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
         L.orc_splitmix64_u01.restype = C.c_double
     return _lib
@@ -307,3 +308,12 @@ def quantize_e4m3(w):
 
 def splitmix64_u01(seed, stream, i) -> float:
     return lib().orc_splitmix64_u01(int(seed), int(stream), int(i))
+
+
+def training_points(robot, q0, q1, N, seed, m, spm) -> np.ndarray:
+    """The data generator's points and labels for motion index m: (spm, 4)."""
+    R = RobotArrays(robot)
+    out = np.zeros(spm * 4)
+    lib().orc_training_points(R.dh, R.tool_len, R.radius, _d(q0).reshape(6), _d(q1).reshape(6), int(N),
+                              int(seed), int(m), int(spm), out)
+    return out.reshape(spm, 4)

@@ -612,3 +612,49 @@ double orc_splitmix64_u01(uint64_t seed, uint64_t stream, uint64_t i)
     const uint64_t u = sm_fin(base + (i + 1) * gamma);
     return (double)(u >> 11) * 0x1.0p-53;
 }
+
+/* Training points of one motion m (samples_per_motion of them), the recipe of
+ * the data generator (Sec. IV-C adapted to capsules): draws u_0..u_6 of the
+ * SplitMix64 stream (seed, m) at counters 8j..8j+6; with u_0 < 0.7 a point
+ * near capsule c = floor(7 u_2) of sample k = floor((N+1) u_1):
+ * a + u_3 (b - a) + (r_c + off) d, with d = (sqrt(1 - z^2) cos phi,
+ * sqrt(1 - z^2) sin phi, z), z = 2 u_4 - 1, phi = 2 pi u_5,
+ * off = -0.1 + 0.2 u_6; otherwise uniform in [-0.75,0.75]^2 x [0,1.5] from
+ * u_1..u_3.  Each point gets its exact sampled swept-volume distance.
+ * out is (spm, 4): x, y, z, delta. */
+void orc_training_points(const double *dh, double tool_len, const double *radius, const double *q0,
+                         const double *q1, int N, uint64_t seed, int m, int spm, double *out)
+{
+    double A[(N + 1) * NCAPS * 3], Bx[(N + 1) * NCAPS * 3];
+    motion_capsules(dh, tool_len, q0, q1, N, A, Bx);
+    #pragma omp parallel for schedule(static)
+    for (int j = 0; j < spm; ++j) {
+        const uint64_t c = (uint64_t)j * 8u;
+        double u[7];
+        for (int i = 0; i < 7; ++i) u[i] = orc_splitmix64_u01(seed, (uint64_t)m, c + (uint64_t)i);
+        double p[3];
+        if (u[0] < 0.7) {
+            int k = (int)(u[1] * (N + 1));
+            if (k > N) k = N;
+            int cj = (int)(u[2] * NCAPS);
+            if (cj > NCAPS - 1) cj = NCAPS - 1;
+            const double *a = A + (k * NCAPS + cj) * 3, *b = Bx + (k * NCAPS + cj) * 3;
+            const double z = 2.0 * u[4] - 1.0, phi = 2.0 * 3.141592653589793 * u[5];
+            const double off = -0.1 + 0.2 * u[6];
+            const double rxy = sqrt(fmax(0.0, 1.0 - z * z));
+            const double d[3] = {rxy * cos(phi), rxy * sin(phi), z};
+            for (int q = 0; q < 3; ++q) p[q] = a[q] + u[3] * (b[q] - a[q]) + (radius[cj] + off) * d[q];
+        } else {
+            p[0] = -0.75 + 1.5 * u[1];
+            p[1] = -0.75 + 1.5 * u[2];
+            p[2] = 1.5 * u[3];
+        }
+        double best = INFINITY;
+        for (int k = 0; k <= N; ++k) {
+            const double dd = robot_sdf_caps(p, A + k * NCAPS * 3, Bx + k * NCAPS * 3, radius);
+            if (dd < best) best = dd;
+        }
+        for (int q = 0; q < 3; ++q) out[4 * j + q] = p[q];
+        out[4 * j + 3] = best;
+    }
+}

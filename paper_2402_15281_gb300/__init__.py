@@ -74,6 +74,28 @@ def lib():
         L.svm_label_pairs.argtypes = [vp, vp, vp, i32, vp, i64, i32, vp, vp]
         L.svm_check_motions_noalloc.argtypes = [vp, vp, vp, i32, vp, i64, f32, i32, u32, vp, vp]
         L.svm_check_motions_noalloc.restype = C.c_int
+        L.svm_train_create.argtypes = [C.POINTER(svm_model_desc), C.c_int, i32, C.POINTER(vp)]
+        L.svm_train_destroy.argtypes = [vp]
+        L.svm_train_last_error.argtypes = [vp]
+        L.svm_train_last_error.restype = C.c_char_p
+        L.svm_train_param_count.argtypes = [vp]
+        L.svm_train_param_count.restype = C.c_int64
+        L.svm_train_set_weights.argtypes = [vp, C.c_char_p, sz]
+        L.svm_train_get_weights.argtypes = [vp, vp, sz, C.POINTER(sz)]
+        L.svm_train_make_data.argtypes = [vp, vp, vp, i32, i32, i32, C.c_uint64]
+        L.svm_train_set_samples.argtypes = [vp, vp, vp, i32, vp, vp, i64]
+        L.svm_train_copy_samples.argtypes = [vp, vp, vp, i64]
+        L.svm_train_gradient.argtypes = [vp, i64, vp, vp]
+        L.svm_train_adam.argtypes = [vp, f32]
+        L.svm_train_epoch.argtypes = [vp, i64, i64, f32, C.c_uint64, vp]
+        L.svm_train_evaluate.argtypes = [vp, i64, i64, vp]
+        L.svm_train_state.argtypes = [vp, vp, vp, vp, vp, i64]
+        L.svm_train_restore.argtypes = [vp, vp, vp, vp, i64, i64]
+        for f in ("svm_train_create", "svm_train_destroy", "svm_train_set_weights", "svm_train_get_weights",
+                  "svm_train_make_data", "svm_train_set_samples", "svm_train_copy_samples", "svm_train_gradient",
+                  "svm_train_adam", "svm_train_epoch", "svm_train_evaluate", "svm_train_state",
+                  "svm_train_restore"):
+            getattr(L, f).restype = C.c_int
         L.svm_profile_enable.argtypes = [vp, C.c_int]
         L.svm_profile_read.argtypes = [vp, vp, i32]
         for f in ("svm_profile_enable", "svm_profile_read", "svm_create_model", "svm_destroy_model", "svm_load_weights", "svm_export_weights",
@@ -238,3 +260,116 @@ def results_to_numpy(results_dev) -> np.ndarray:
 def new_results(n, device="cuda"):
     import torch
     return torch.empty((max(n, 1), 32), dtype=torch.uint8, device=device)
+
+
+# ------------------------------------------------------------------ training
+
+def _tcheck(fn, status, trainer=None):
+    if status != SVM_OK:
+        text = lib().svm_status_string(status).decode()
+        if trainer is not None:
+            text += ": " + lib().svm_train_last_error(trainer).decode()
+        raise SvmError(fn, status, text)
+
+
+def _desc(robot, width, n_hidden, act, prec=SVM_FP32):
+    d = svm_model_desc()
+    for j in range(6):
+        for c in range(4):
+            d.dh[j][c] = float(robot.dh[j, c])
+    for j in range(7):
+        d.radius[j] = float(robot.radius[j])
+    d.tool_len = float(robot.tool_len)
+    d.width, d.n_hidden, d.act, d.prec = int(width), int(n_hidden), int(act), int(prec)
+    return d
+
+
+def svm_train_create(robot, width, n_hidden, act, batch, device=0):
+    d = _desc(robot, width, n_hidden, act)
+    h = C.c_void_p()
+    _tcheck("svm_train_create", lib().svm_train_create(C.byref(d), int(device), int(batch), C.byref(h)))
+    return h
+
+
+def svm_train_destroy(t):
+    _tcheck("svm_train_destroy", lib().svm_train_destroy(t))
+
+
+def svm_train_param_count(t) -> int:
+    return int(lib().svm_train_param_count(t))
+
+
+def svm_train_set_weights(t, blob: bytes):
+    _tcheck("svm_train_set_weights", lib().svm_train_set_weights(t, blob, len(blob)), t)
+
+
+def svm_train_get_weights(t) -> bytes:
+    need = C.c_size_t()
+    _tcheck("svm_train_get_weights", lib().svm_train_get_weights(t, None, 0, C.byref(need)), t)
+    buf = C.create_string_buffer(need.value)
+    _tcheck("svm_train_get_weights", lib().svm_train_get_weights(t, buf, need.value, None), t)
+    return buf.raw
+
+
+def svm_train_make_data(t, q0, q1, samples_per_motion, steps, seed):
+    q0, p0 = _host_f64(q0)
+    q1, p1 = _host_f64(q1)
+    _tcheck("svm_train_make_data", lib().svm_train_make_data(t, p0, p1, q0.shape[0], int(samples_per_motion),
+                                                             int(steps), int(seed)), t)
+
+
+def svm_train_set_samples(t, q0, q1, x4, motion):
+    q0, p0 = _host_f64(q0)
+    q1, p1 = _host_f64(q1)
+    x4 = np.ascontiguousarray(x4, dtype=np.float32).reshape(-1, 4)
+    mo = np.ascontiguousarray(motion, dtype=np.int32)
+    _tcheck("svm_train_set_samples", lib().svm_train_set_samples(
+        t, p0, p1, q0.shape[0], x4.ctypes.data_as(C.c_void_p), mo.ctypes.data_as(C.c_void_p), x4.shape[0]), t)
+
+
+def svm_train_copy_samples(t, n):
+    x4 = np.zeros((n, 4), dtype=np.float32)
+    mo = np.zeros(n, dtype=np.int32)
+    _tcheck("svm_train_copy_samples", lib().svm_train_copy_samples(
+        t, x4.ctypes.data_as(C.c_void_p), mo.ctypes.data_as(C.c_void_p), n), t)
+    return x4, mo
+
+
+def svm_train_gradient(t, sample_begin=0):
+    g = np.zeros(svm_train_param_count(t), dtype=np.float32)
+    loss = C.c_float()
+    _tcheck("svm_train_gradient", lib().svm_train_gradient(t, int(sample_begin), g.ctypes.data_as(C.c_void_p),
+                                                           C.byref(loss)), t)
+    return g, loss.value
+
+
+def svm_train_adam(t, lr):
+    _tcheck("svm_train_adam", lib().svm_train_adam(t, float(lr)), t)
+
+
+def svm_train_epoch(t, begin, end, lr, shuffle_seed) -> float:
+    loss = C.c_float()
+    _tcheck("svm_train_epoch", lib().svm_train_epoch(t, int(begin), int(end), float(lr), int(shuffle_seed),
+                                                     C.byref(loss)), t)
+    return loss.value
+
+
+def svm_train_evaluate(t, begin, end) -> float:
+    mae = C.c_float()
+    _tcheck("svm_train_evaluate", lib().svm_train_evaluate(t, int(begin), int(end), C.byref(mae)), t)
+    return mae.value
+
+
+def svm_train_state(t):
+    n = svm_train_param_count(t)
+    P, M1, M2 = (np.zeros(n, dtype=np.float32) for _ in range(3))
+    step = C.c_int64()
+    _tcheck("svm_train_state", lib().svm_train_state(t, P.ctypes.data_as(C.c_void_p), M1.ctypes.data_as(C.c_void_p),
+                                                     M2.ctypes.data_as(C.c_void_p), C.byref(step), n), t)
+    return P, M1, M2, step.value
+
+
+def svm_train_restore(t, P, M1, M2, step):
+    P, M1, M2 = (np.ascontiguousarray(a, dtype=np.float32) for a in (P, M1, M2))
+    _tcheck("svm_train_restore", lib().svm_train_restore(t, P.ctypes.data_as(C.c_void_p), M1.ctypes.data_as(C.c_void_p),
+                                                         M2.ctypes.data_as(C.c_void_p), int(step), P.shape[0]), t)

@@ -114,6 +114,32 @@ __device__ __forceinline__ int find_segment(const int* off, int n, int t) {
     return lo;
 }
 
+// Squared distances from x to the 7 capsule axes, minimised over samples.
+__device__ __forceinline__ void scan_samples(const Capsule* cs, int n_samples, float3 x, float (&mn)[kCaps])
+{
+    #pragma unroll
+    for (int j = 0; j < kCaps; ++j) mn[j] = __int_as_float(0x7f800000);
+    for (int k = 0; k < n_samples; ++k) {
+        #pragma unroll
+        for (int j = 0; j < kCaps; ++j) {
+            const float4 ar = cs[k * kCaps + j].a_r;
+            const float4 ei = cs[k * kCaps + j].e_inv;
+            const float wx = x.x - ar.x, wy = x.y - ar.y, wz = x.z - ar.z;
+            const float t = __saturatef(fmaf(wz, ei.z, fmaf(wy, ei.y, wx * ei.x)) * ei.w);
+            const float dx = fmaf(-t, ei.x, wx), dy = fmaf(-t, ei.y, wy), dz = fmaf(-t, ei.z, wz);
+            mn[j] = fminf(mn[j], fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+        }
+    }
+}
+
+__device__ __forceinline__ float capsule_min(const float (&mn)[kCaps], const Capsule* cs)
+{
+    float d = __int_as_float(0x7f800000);
+    #pragma unroll
+    for (int j = 0; j < kCaps; ++j) d = fminf(d, sqrtf(mn[j]) - cs[j].a_r.w);
+    return d;
+}
+
 // ---------------------------------------------------------------- launches
 void launch_prologue(const CallArgs& a, const DevWeights& w, cudaStream_t s);
 void launch_mlp_fp32(const CallArgs& a, const DevWeights& w, int n_tiles, int bm, cudaStream_t s);

@@ -1,0 +1,819 @@
+// train.cu -- training of the swept-volume network on the GPU (C ABI
+// svm_train_*): data generation with the exact geometric check as labeller,
+// and BF16 forward / backward / Adam steps.
+//
+// Data (Sec. IV-C: tuples (x, q0, q1, delta)): for each motion, points drawn
+// with a counter-based SplitMix64 stream (seed, motion, point) -- 70 % near
+// the robot's swept surface (a random sample k, capsule j, position along its
+// axis, unit direction, and radial offset r_j + U[-0.1, 0.1] m), 30 % uniform
+// in the workspace cube [-0.75,0.75]^2 x [0,1.5] -- labelled with the exact
+// sampled swept-volume distance (the verifier's arithmetic, no gate).
+// Samples are stored grouped by motion; a batch takes every n_batch-th sample
+// from a per-epoch random offset, so each batch mixes all motions.
+//
+// Step (loss: mean |f - delta|, the error the paper reports as MAE):
+//   layer 1 (15 -> W) in FP32 on CUDA cores, hidden layers as BF16 tcgen05
+//   GEMMs (train_gemm.cu), output layer, loss and its gradient on CUDA cores;
+//   backward: per hidden layer a split-K weight-gradient GEMM and an input-
+//   gradient GEMM, bias gradients by column sums, layer-1 gradient on CUDA
+//   cores; then Adam (lr, betas (0.9, 0.999), eps 1e-8, as in Sec. V) on FP32
+//   master weights, which also refreshes the BF16 copies W and W^T.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "svm.h"
+#include "svm_internal.cuh"
+#include "train_internal.cuh"
+
+using namespace svm;
+
+namespace {
+
+constexpr int kTpStride = 80;   // bytes per row of a 32 x 32 bfloat16 staging tile
+
+// ------------------------------------------------------------ SplitMix64
+
+__device__ __forceinline__ unsigned long long sm_fin(unsigned long long z)
+{
+    z ^= z >> 30; z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 27; z *= 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double sm_u01(unsigned long long base, unsigned long long i)
+{
+    return (double)(sm_fin(base + (i + 1ull) * 0x9E3779B97F4A7C15ull) >> 11) * 0x1.0p-53;
+}
+
+// One training point of motion m, local index j, and its exact label.
+__global__ void __launch_bounds__(256) sample_kernel(const Capsule* caps, int N, int spm, unsigned long long seed,
+                                                     float4* X, int* MID)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    Capsule* cs = reinterpret_cast<Capsule*>(smem);
+    const int m = blockIdx.x;
+    const int ns = N + 1;
+    const float4* src = reinterpret_cast<const float4*>(caps + (long long)m * ns * kCaps);
+    for (int i = threadIdx.x; i < ns * kCaps * 2; i += blockDim.x) reinterpret_cast<float4*>(cs)[i] = src[i];
+    __syncthreads();
+    const unsigned long long base =
+        sm_fin((seed * 0x9E3779B97F4A7C15ull) ^ ((unsigned long long)m * 0xD1B54A32D192ED03ull));
+    for (int j = threadIdx.x; j < spm; j += blockDim.x) {
+        const unsigned long long c = (unsigned long long)j * 8ull;
+        const double u0 = sm_u01(base, c);
+        float3 p;
+        if (u0 < 0.7) {
+            const int k = min((int)(sm_u01(base, c + 1) * ns), ns - 1);
+            const int cj = min((int)(sm_u01(base, c + 2) * kCaps), kCaps - 1);
+            const float t = (float)sm_u01(base, c + 3);
+            const float zc = (float)(2.0 * sm_u01(base, c + 4) - 1.0);
+            const float ph = (float)(6.283185307179586 * sm_u01(base, c + 5));
+            const float off = (float)(-0.1 + 0.2 * sm_u01(base, c + 6));
+            const Capsule& q = cs[k * kCaps + cj];
+            const float rxy = sqrtf(fmaxf(0.0f, 1.0f - zc * zc));
+            float sp, cp;
+            sincosf(ph, &sp, &cp);
+            const float rad = q.a_r.w + off;
+            p.x = q.a_r.x + t * q.e_inv.x + rad * rxy * cp;
+            p.y = q.a_r.y + t * q.e_inv.y + rad * rxy * sp;
+            p.z = q.a_r.z + t * q.e_inv.z + rad * zc;
+        } else {
+            p.x = (float)(-0.75 + 1.5 * sm_u01(base, c + 1));
+            p.y = (float)(-0.75 + 1.5 * sm_u01(base, c + 2));
+            p.z = (float)(1.5 * sm_u01(base, c + 3));
+        }
+        float mn[kCaps];
+        scan_samples(cs, ns, p, mn);
+        const long long s = (long long)m * spm + j;
+        X[s] = make_float4(p.x, p.y, p.z, capsule_min(mn, cs));
+        MID[s] = m;
+    }
+}
+
+// ------------------------------------------------------------ layer 1 and head
+
+struct StepArgs {
+    int W, B, act;
+    long long base, stride;           // sample of batch row r: base + r * stride
+    const float4* X;
+    const int* MID;
+    const double* q0;
+    const double* q1;
+    const float* P;                   // FP32 master parameters (blob order)
+    float* Gr;                        // FP32 gradient (blob order)
+    float* loss;                      // sum of |f - delta| over the batch
+    long long off_w1, off_b1, off_out;
+};
+
+template <int ACT>
+__device__ __forceinline__ float actf(float z)
+{
+    if constexpr (ACT == 0) return fmaxf(z, 0.0f);
+    else return z / (1.0f + __expf(-z));
+}
+
+template <int ACT>
+__device__ __forceinline__ float actg(float z)
+{
+    if constexpr (ACT == 0) return z > 0.0f ? 1.0f : 0.0f;
+    else {
+        const float s = 1.0f / (1.0f + __expf(-z));
+        return s * (1.0f + z * (1.0f - s));
+    }
+}
+
+__device__ __forceinline__ void input_row(const StepArgs& a, int r, float (&in)[15], float& delta)
+{
+    const long long s = a.base + (long long)r * a.stride;
+    const float4 x = a.X[s];
+    const int m = a.MID[s];
+    in[0] = x.x; in[1] = x.y; in[2] = x.z;
+    for (int i = 0; i < 6; ++i) {
+        in[3 + i] = (float)a.q0[m * 6 + i];
+        in[9 + i] = (float)a.q1[m * 6 + i];
+    }
+    delta = x.w;
+}
+
+__device__ __forceinline__ void store_bf16_row32(__nv_bfloat16* dst, const float (&v)[32])
+{
+    uint4* o = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        __nv_bfloat162 b0 = __floats2bfloat162_rn(v[8 * q + 0], v[8 * q + 1]);
+        __nv_bfloat162 b1 = __floats2bfloat162_rn(v[8 * q + 2], v[8 * q + 3]);
+        __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * q + 4], v[8 * q + 5]);
+        __nv_bfloat162 b3 = __floats2bfloat162_rn(v[8 * q + 6], v[8 * q + 7]);
+        o[q] = make_uint4(*reinterpret_cast<uint32_t*>(&b0), *reinterpret_cast<uint32_t*>(&b1),
+                          *reinterpret_cast<uint32_t*>(&b2), *reinterpret_cast<uint32_t*>(&b3));
+    }
+}
+
+// dst at [col0][row0] of a [cols][ld] matrix; lane = row, v = 32 columns.
+__device__ __forceinline__ void store_bf16_transposed32(unsigned char* tp, int lane, const float (&v)[32],
+                                                        __nv_bfloat16* dst, long long ld)
+{
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+        *reinterpret_cast<__nv_bfloat16*>(tp + c * kTpStride + lane * 2) = __float2bfloat16_rn(v[c]);
+    __syncwarp();
+    const uint4* src = reinterpret_cast<const uint4*>(tp + lane * kTpStride);
+    uint4* out = reinterpret_cast<uint4*>(dst + (long long)lane * ld);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[q] = src[q];
+    __syncwarp();
+}
+
+__device__ __forceinline__ void load_bf16_row32(const __nv_bfloat16* src, float (&v)[32])
+{
+    const uint4* p = reinterpret_cast<const uint4*>(src);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint4 w = p[q];
+        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            v[8 * q + 2 * i] = __uint_as_float(ws[i] << 16);
+            v[8 * q + 2 * i + 1] = __uint_as_float(ws[i] & 0xFFFF0000u);
+        }
+    }
+}
+
+// Layer 1 forward: 32 samples per block (lane = sample), warps split the
+// feature chunks.  Writes Z0, H0 (row-major) and H0^T.
+template <int ACT>
+__global__ void __launch_bounds__(128) layer1_fwd_kernel(StepArgs a, __nv_bfloat16* Z0, __nv_bfloat16* H0,
+                                                         __nv_bfloat16* H0T)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    float* w1 = reinterpret_cast<float*>(smem);                       // [W][15] then b1 [W]
+    unsigned char* tp = smem + (size_t)a.W * 16 * 4 + (threadIdx.x >> 5) * 32 * kTpStride;
+    for (int i = threadIdx.x; i < a.W * 15; i += blockDim.x) w1[i] = a.P[a.off_w1 + i];
+    for (int i = threadIdx.x; i < a.W; i += blockDim.x) w1[a.W * 15 + i] = a.P[a.off_b1 + i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = blockIdx.x * 32 + lane;
+    float in[15], delta;
+    input_row(a, r, in, delta);
+    for (int c = warp; c < a.W / 32; c += 4) {
+        float z[32], h[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const int o = c * 32 + i;
+            float s = w1[a.W * 15 + o];
+#pragma unroll
+            for (int k = 0; k < 15; ++k) s = fmaf(w1[o * 15 + k], in[k], s);
+            z[i] = s;
+            h[i] = actf<ACT>(s);
+        }
+        store_bf16_row32(Z0 + (long long)r * a.W + c * 32, z);
+        store_bf16_row32(H0 + (long long)r * a.W + c * 32, h);
+        store_bf16_transposed32(tp, lane, h, H0T + (long long)(c * 32) * a.B + blockIdx.x * 32, a.B);
+    }
+}
+
+// Output layer, loss and its gradient: f = w_out . h_L + b_out, e = f - delta,
+// loss += |e|; df = sign(e) / B; G_L = df * w_out * act'(z_L) (written as G_L
+// and G_L^T); dw_out += df h_L; db_out += df.  eval != 0: loss only.
+template <int ACT>
+__global__ void __launch_bounds__(128) head_kernel(StepArgs a, const __nv_bfloat16* HL, const __nv_bfloat16* ZL,
+                                                   __nv_bfloat16* GL, __nv_bfloat16* GLT, int eval)
+{
+    __shared__ float part[4][32];
+    __shared__ __align__(16) unsigned char tps[4 * 32 * kTpStride];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = blockIdx.x * 32 + lane;
+    unsigned char* tp = tps + warp * 32 * kTpStride;
+    const float* wo = a.P + a.off_out;
+    float f = 0.0f;
+    for (int c = warp; c < a.W / 32; c += 4) {
+        float h[32];
+        load_bf16_row32(HL + (long long)r * a.W + c * 32, h);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) f = fmaf(wo[c * 32 + i], h[i], f);
+    }
+    part[warp][lane] = f;
+    __syncthreads();
+    float in[15], delta;
+    input_row(a, r, in, delta);
+    const float fr = part[0][lane] + part[1][lane] + part[2][lane] + part[3][lane] + wo[a.W];
+    const float e = fr - delta;
+    float ae = fabsf(e);
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) ae += __shfl_xor_sync(0xffffffffu, ae, s);
+    if (lane == 0 && warp == 0) atomicAdd(a.loss, ae);
+    if (eval) return;
+    const float df = (e > 0.0f ? 1.0f : (e < 0.0f ? -1.0f : 0.0f)) / (float)a.B;
+    float dsum = df;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, s);
+    if (lane == 0 && warp == 0) atomicAdd(a.Gr + a.off_out + a.W, dsum);
+    for (int c = warp; c < a.W / 32; c += 4) {
+        float h[32], z[32], gv[32];
+        load_bf16_row32(HL + (long long)r * a.W + c * 32, h);
+        load_bf16_row32(ZL + (long long)r * a.W + c * 32, z);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            gv[i] = df * wo[c * 32 + i] * actg<ACT>(z[i]);
+            float dw = df * h[i];
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) dw += __shfl_xor_sync(0xffffffffu, dw, s);
+            if (lane == i) atomicAdd(a.Gr + a.off_out + c * 32 + i, dw);
+        }
+        store_bf16_row32(GL + (long long)r * a.W + c * 32, gv);
+        store_bf16_transposed32(tp, lane, gv, GLT + (long long)(c * 32) * a.B + blockIdx.x * 32, a.B);
+    }
+}
+
+// Layer-1 gradients: dW1[n][k] += sum_b G0[b][n] in_b[k], db1[n] += sum_b G0[b][n],
+// 256 samples per block, one thread per feature.
+__global__ void __launch_bounds__(256) layer1_bwd_kernel(StepArgs a, const __nv_bfloat16* G0)
+{
+    __shared__ float ins[256][16];
+    const int r0 = blockIdx.x * 256;
+    {
+        float in[15], delta;
+        input_row(a, r0 + threadIdx.x, in, delta);
+        for (int k = 0; k < 15; ++k) ins[threadIdx.x][k] = in[k];
+        ins[threadIdx.x][15] = 1.0f;
+    }
+    __syncthreads();
+    for (int n = threadIdx.x; n < a.W; n += blockDim.x) {
+        float acc[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc[k] = 0.0f;
+        for (int b = 0; b < 256; ++b) {
+            const float gv = __bfloat162float(G0[(long long)(r0 + b) * a.W + n]);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) acc[k] = fmaf(gv, ins[b][k], acc[k]);
+        }
+        for (int k = 0; k < 15; ++k) atomicAdd(a.Gr + a.off_w1 + n * 15 + k, acc[k]);
+        atomicAdd(a.Gr + a.off_b1 + n, acc[15]);
+    }
+}
+
+// db[n] = sum_b GT[n][b]
+__global__ void __launch_bounds__(256) colsum_kernel(const __nv_bfloat16* GT, long long B, float* db)
+{
+    const int n = blockIdx.x;
+    float s = 0.0f;
+    for (long long b = threadIdx.x; b < B; b += blockDim.x) s += __bfloat162float(GT[(long long)n * B + b]);
+    __shared__ float red[8];
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) s += __shfl_xor_sync(0xffffffffu, s, sh);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        db[n] += t;
+    }
+}
+
+// Adam on the FP32 master parameters; refreshes the BF16 copies of the
+// hidden weights (W [out][in] and W^T [in][out]).
+__global__ void adam_kernel(float* P, const float* G, float* Mo, float* Vo, long long n, float lr, float b1, float b2,
+                            float eps, float c1, float c2, int W, int L, long long off_h, __nv_bfloat16* wb,
+                            __nv_bfloat16* wbt)
+{
+    const long long stride_l = (long long)W * W + W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float g = G[i];
+        const float m = b1 * Mo[i] + (1.0f - b1) * g;
+        const float v = b2 * Vo[i] + (1.0f - b2) * g * g;
+        Mo[i] = m;
+        Vo[i] = v;
+        const float p = P[i] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+        P[i] = p;
+        const long long j = i - off_h;
+        if (j >= 0 && j < stride_l * L) {
+            const long long l = j / stride_l, w = j % stride_l;
+            if (w < (long long)W * W) {
+                const long long o = w / W, k = w % W;
+                const __nv_bfloat16 pb = __float2bfloat16_rn(p);
+                wb[l * W * W + o * W + k] = pb;
+                wbt[l * W * W + k * W + o] = pb;
+            }
+        }
+    }
+}
+
+__global__ void refresh_bf16_kernel(const float* P, int W, int L, long long off_h, __nv_bfloat16* wb,
+                                    __nv_bfloat16* wbt)
+{
+    const long long total = (long long)L * W * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long l = i / ((long long)W * W), w = i % ((long long)W * W);
+        const long long o = w / W, k = w % W;
+        const __nv_bfloat16 pb = __float2bfloat16_rn(P[off_h + l * ((long long)W * W + W) + w]);
+        wb[i] = pb;
+        wbt[l * W * W + k * W + o] = pb;
+    }
+}
+
+int grid_for(long long n) { long long g = (n + 255) / 256; return (int)(g > 8192 ? 8192 : (g < 1 ? 1 : g)); }
+
+struct Map { alignas(64) unsigned char b[128]; };
+
+}  // namespace
+
+struct svm_trainer {
+    int device = 0, n_sms = 0;
+    svm_model_desc desc{};
+    RobotParams rp{};
+    int W = 0, L = 0, act = 0, B = 0;
+    long long np = 0, off_w1 = 0, off_b1 = 0, off_h = 0, off_out = 0;
+    long long step = 0;
+    float* P = nullptr; float* Gr = nullptr; float* Mo = nullptr; float* Vo = nullptr;
+    float* loss = nullptr;
+    unsigned int* err = nullptr;
+    __nv_bfloat16* wb = nullptr; __nv_bfloat16* wbt = nullptr;
+    std::vector<__nv_bfloat16*> H, Z, HT, G, GT;     // per layer 0..L
+    std::vector<Map> mapH, mapHT, mapG, mapGT, mapW, mapWT;
+    // data
+    float4* X = nullptr; int* MID = nullptr; double* q0 = nullptr; double* q1 = nullptr;
+    int n_motions = 0; long long n_samples = 0;
+    std::vector<void*> allocs;
+    std::string last_error;
+};
+
+namespace {
+
+svm_status tfail(svm_trainer* t, svm_status s, const std::string& msg)
+{
+    if (t) t->last_error = msg;
+    return s;
+}
+
+#define TCK(call)                                                                              \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return tfail(t, SVM_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+    } while (0)
+
+template <class T>
+svm_status talloc(svm_trainer* t, T** p, size_t bytes)
+{
+    void* q = nullptr;
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return tfail(t, SVM_E_OOM, "trainer allocation failed");
+    }
+    t->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return SVM_OK;
+}
+
+void free_data(svm_trainer* t)
+{
+    for (void* p : {(void*)t->X, (void*)t->MID, (void*)t->q0, (void*)t->q1})
+        if (p) {
+            cudaFree(p);
+            for (auto& a : t->allocs)
+                if (a == p) a = nullptr;
+        }
+    t->X = nullptr; t->MID = nullptr; t->q0 = nullptr; t->q1 = nullptr;
+    t->n_motions = 0; t->n_samples = 0;
+}
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int d) { if (cudaGetDevice(&prev) != cudaSuccess) prev = -1; if (prev != d) cudaSetDevice(d); }
+    ~DevGuard() { int c = -1; if (prev >= 0 && cudaGetDevice(&c) == cudaSuccess && c != prev) cudaSetDevice(prev); }
+};
+
+StepArgs step_args(svm_trainer* t, long long base, long long stride)
+{
+    StepArgs a{};
+    a.W = t->W; a.B = t->B; a.act = t->act;
+    a.base = base; a.stride = stride;
+    a.X = t->X; a.MID = t->MID; a.q0 = t->q0; a.q1 = t->q1;
+    a.P = t->P; a.Gr = t->Gr; a.loss = t->loss;
+    a.off_w1 = t->off_w1; a.off_b1 = t->off_b1; a.off_out = t->off_out;
+    return a;
+}
+
+// Forward over one batch; with grad, also the backward pass into Gr.
+svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad, cudaStream_t s)
+{
+    const int W = t->W, L = t->L, B = t->B;
+    const StepArgs a = step_args(t, base, stride);
+    const size_t l1_smem = (size_t)W * 16 * 4 + 4 * 32 * kTpStride;
+    if (t->act == 0) layer1_fwd_kernel<0><<<B / 32, 128, l1_smem, s>>>(a, t->Z[0], t->H[0], t->HT[0]);
+    else layer1_fwd_kernel<1><<<B / 32, 128, l1_smem, s>>>(a, t->Z[0], t->H[0], t->HT[0]);
+    for (int l = 1; l <= L; ++l) {
+        GemmArgs g{};
+        g.n_mt = B / 128; g.n_nt = W / 256; g.n_ks = 1; g.k_len = W;
+        g.ld_rows = W; g.ld_cols = B;
+        g.bias = t->P + t->off_h + (long long)(l - 1) * ((long long)W * W + W) + (long long)W * W;
+        g.h_out = t->H[l]; g.z_out = t->Z[l]; g.ht_out = t->HT[l]; g.err = t->err;
+        launch_train_gemm(kEpiFwd, t->act, t->mapH[l - 1].b, t->mapW[l - 1].b, g, t->n_sms, s);
+    }
+    if (t->act == 0) head_kernel<0><<<B / 32, 128, 0, s>>>(a, t->H[L], t->Z[L], t->G[L], t->GT[L], grad ? 0 : 1);
+    else head_kernel<1><<<B / 32, 128, 0, s>>>(a, t->H[L], t->Z[L], t->G[L], t->GT[L], grad ? 0 : 1);
+    if (!grad) return SVM_OK;
+    for (int l = L; l >= 1; --l) {
+        const long long woff = t->off_h + (long long)(l - 1) * ((long long)W * W + W);
+        GemmArgs g{};
+        const int k_len = B >= 2048 ? 2048 : B;
+        g.n_mt = W / 128; g.n_nt = W / 256; g.n_ks = B / k_len; g.k_len = k_len;
+        g.ld_rows = W; g.ld_cols = 0; g.dw = t->Gr + woff; g.err = t->err;
+        launch_train_gemm(kEpiWgrad, 0, t->mapGT[l].b, t->mapHT[l - 1].b, g, t->n_sms, s);
+        colsum_kernel<<<W, 256, 0, s>>>(t->GT[l], B, t->Gr + woff + (long long)W * W);
+        GemmArgs d{};
+        d.n_mt = B / 128; d.n_nt = W / 256; d.n_ks = 1; d.k_len = W;
+        d.ld_rows = W; d.ld_cols = B; d.z_in = t->Z[l - 1];
+        d.h_out = t->G[l - 1]; d.ht_out = t->GT[l - 1]; d.err = t->err;
+        launch_train_gemm(kEpiDgrad, t->act, t->mapG[l].b, t->mapWT[l - 1].b, d, t->n_sms, s);
+    }
+    layer1_bwd_kernel<<<B / 256, 256, 0, s>>>(a, t->G[0]);
+    return SVM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* svm_train_last_error(const svm_trainer* t) { return t ? t->last_error.c_str() : "null trainer"; }
+
+svm_status svm_train_create(const svm_model_desc* desc, int device, int32_t batch, svm_trainer** out)
+{
+    svm_trainer* t = nullptr;
+    if (!desc || !out) return SVM_E_INVALID;
+    *out = nullptr;
+    const svm_model_desc& d = *desc;
+    if (!(d.width == 256 || d.width == 512) || d.n_hidden < 1 || d.n_hidden > 16) return SVM_E_UNSUPPORTED;
+    if (d.act != SVM_RELU && d.act != SVM_SILU) return SVM_E_INVALID;
+    if (batch < 256 || batch % 256 != 0) return SVM_E_INVALID;
+    int n_dev = 0;
+    if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device < 0 || device >= n_dev) return SVM_E_INVALID;
+    int maj = 0, min_ = 0;
+    cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, device);
+    cudaDeviceGetAttribute(&min_, cudaDevAttrComputeCapabilityMinor, device);
+    if (!(maj == 10 && min_ == 3)) return SVM_E_UNSUPPORTED;
+    t = new svm_trainer();
+    DevGuard gd(device);
+    t->device = device;
+    t->desc = d;
+    cudaDeviceGetAttribute(&t->n_sms, cudaDevAttrMultiProcessorCount, device);
+    for (int j = 0; j < 6; ++j) {
+        t->rp.d[j] = d.dh[j][0]; t->rp.a[j] = d.dh[j][1];
+        t->rp.ca[j] = std::cos(d.dh[j][2]); t->rp.sa[j] = std::sin(d.dh[j][2]); t->rp.th0[j] = d.dh[j][3];
+    }
+    t->rp.tool_len = d.tool_len;
+    for (int j = 0; j < 7; ++j) t->rp.radius[j] = (float)d.radius[j];
+    t->W = d.width; t->L = d.n_hidden; t->act = d.act; t->B = batch;
+    const long long W = t->W, L = t->L, B = t->B;
+    t->off_w1 = 0; t->off_b1 = W * 15; t->off_h = W * 16;
+    t->off_out = t->off_h + L * (W * W + W);
+    t->np = t->off_out + W + 1;
+    svm_status st;
+    auto fail_free = [&](svm_status s) { svm_train_destroy(t); return s; };
+    if ((st = talloc(t, &t->P, t->np * 4)) != SVM_OK) return fail_free(st);
+    if ((st = talloc(t, &t->Gr, t->np * 4)) != SVM_OK) return fail_free(st);
+    if ((st = talloc(t, &t->Mo, t->np * 4)) != SVM_OK) return fail_free(st);
+    if ((st = talloc(t, &t->Vo, t->np * 4)) != SVM_OK) return fail_free(st);
+    if ((st = talloc(t, &t->loss, 256)) != SVM_OK) return fail_free(st);
+    if ((st = talloc(t, &t->err, 256)) != SVM_OK) return fail_free(st);
+    if ((st = talloc(t, &t->wb, L * W * W * 2)) != SVM_OK) return fail_free(st);
+    if ((st = talloc(t, &t->wbt, L * W * W * 2)) != SVM_OK) return fail_free(st);
+    t->H.resize(L + 1); t->Z.resize(L + 1); t->HT.resize(L + 1); t->G.resize(L + 1); t->GT.resize(L + 1);
+    for (int l = 0; l <= L; ++l)
+        for (auto* v : {&t->H, &t->Z, &t->HT, &t->G, &t->GT})
+            if ((st = talloc(t, &(*v)[l], B * W * 2)) != SVM_OK) return fail_free(st);
+    cudaMemset(t->P, 0, t->np * 4);
+    cudaMemset(t->Mo, 0, t->np * 4);
+    cudaMemset(t->Vo, 0, t->np * 4);
+    cudaMemset(t->err, 0, 4);
+    t->mapH.resize(L + 1); t->mapHT.resize(L + 1); t->mapG.resize(L + 1); t->mapGT.resize(L + 1);
+    t->mapW.resize(L); t->mapWT.resize(L);
+    int bad = 0;
+    for (int l = 0; l <= L; ++l) {
+        bad |= train_make_map(t->mapH[l].b, t->H[l], B, W, 128);       // A of FWD
+        bad |= train_make_map(t->mapHT[l].b, t->HT[l], W, B, 256);     // B of WGRAD
+        bad |= train_make_map(t->mapG[l].b, t->G[l], B, W, 128);       // A of DGRAD
+        bad |= train_make_map(t->mapGT[l].b, t->GT[l], W, B, 128);     // A of WGRAD
+    }
+    for (int l = 0; l < L; ++l) {
+        bad |= train_make_map(t->mapW[l].b, t->wb + (long long)l * W * W, W, W, 256);    // B of FWD
+        bad |= train_make_map(t->mapWT[l].b, t->wbt + (long long)l * W * W, W, W, 256);  // B of DGRAD
+    }
+    if (bad) return fail_free(SVM_E_CUDA);
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail_free(SVM_E_CUDA);
+    *out = t;
+    return SVM_OK;
+}
+
+svm_status svm_train_destroy(svm_trainer* t)
+{
+    if (!t) return SVM_E_INVALID;
+    {
+        DevGuard gd(t->device);
+        cudaDeviceSynchronize();
+        for (void* p : t->allocs)
+            if (p) cudaFree(p);
+    }
+    delete t;
+    return SVM_OK;
+}
+
+svm_status svm_train_set_weights(svm_trainer* t, const void* blob, size_t bytes)
+{
+    if (!t || !blob) return SVM_E_INVALID;
+    const unsigned char* p = static_cast<const unsigned char*>(blob);
+    auto rd32 = [&](size_t off) { uint32_t v; std::memcpy(&v, p + off, 4); return v; };
+    if (bytes < 28 || std::memcmp(p, "SVMW", 4) != 0 || rd32(4) != 1) return tfail(t, SVM_E_WEIGHTS, "bad blob header");
+    if ((int)rd32(8) != t->L + 2 || rd32(12) != 15 || (int)rd32(16) != t->W || (int)rd32(20) != t->act)
+        return tfail(t, SVM_E_WEIGHTS, "blob does not match the trainer");
+    std::vector<float> P(t->np);
+    size_t off = 28;
+    long long pos = 0;
+    for (int l = 0; l < t->L + 2; ++l) {
+        if (off + 8 > bytes) return tfail(t, SVM_E_WEIGHTS, "truncated blob");
+        const uint32_t o = rd32(off), i = rd32(off + 4);
+        off += 8;
+        const size_t nb = ((size_t)o * i + o) * 4;
+        if ((long long)(pos + (long long)o * i + o) > t->np || off + nb > bytes) return tfail(t, SVM_E_WEIGHTS, "bad layer");
+        std::memcpy(P.data() + pos, p + off, nb);
+        off += nb;
+        pos += (long long)o * i + o;
+    }
+    if (pos != t->np || off != bytes) return tfail(t, SVM_E_WEIGHTS, "blob size mismatch");
+    DevGuard gd(t->device);
+    TCK(cudaMemcpy(t->P, P.data(), t->np * 4, cudaMemcpyHostToDevice));
+    TCK(cudaMemset(t->Mo, 0, t->np * 4));
+    TCK(cudaMemset(t->Vo, 0, t->np * 4));
+    t->step = 0;
+    refresh_bf16_kernel<<<grid_for((long long)t->L * t->W * t->W), 256>>>(t->P, t->W, t->L, t->off_h, t->wb, t->wbt);
+    TCK(cudaGetLastError());
+    TCK(cudaDeviceSynchronize());
+    return SVM_OK;
+}
+
+svm_status svm_train_get_weights(svm_trainer* t, void* blob, size_t cap, size_t* needed)
+{
+    if (!t) return SVM_E_INVALID;
+    const size_t need = 28 + (size_t)(t->L + 2) * 8 + (size_t)t->np * 4;
+    if (needed) *needed = need;
+    if (!blob) return SVM_OK;
+    if (cap < need) return tfail(t, SVM_E_INVALID, "buffer too small");
+    std::vector<float> P(t->np);
+    DevGuard gd(t->device);
+    TCK(cudaDeviceSynchronize());
+    TCK(cudaMemcpy(P.data(), t->P, t->np * 4, cudaMemcpyDeviceToHost));
+    unsigned char* o = static_cast<unsigned char*>(blob);
+    std::memcpy(o, "SVMW", 4);
+    const uint32_t hdr[5] = {1u, (uint32_t)(t->L + 2), 15u, (uint32_t)t->W, (uint32_t)t->act};
+    std::memcpy(o + 4, hdr, 20);
+    const float tau = INFINITY;
+    std::memcpy(o + 24, &tau, 4);
+    size_t off = 28;
+    long long pos = 0;
+    for (int l = 0; l < t->L + 2; ++l) {
+        const uint32_t out = l == t->L + 1 ? 1u : (uint32_t)t->W;
+        const uint32_t in = l == 0 ? 15u : (uint32_t)t->W;
+        std::memcpy(o + off, &out, 4);
+        std::memcpy(o + off + 4, &in, 4);
+        off += 8;
+        const size_t nb = ((size_t)out * in + out) * 4;
+        std::memcpy(o + off, P.data() + pos, nb);
+        off += nb;
+        pos += (long long)out * in + out;
+    }
+    return SVM_OK;
+}
+
+svm_status svm_train_make_data(svm_trainer* t, const double* q0, const double* q1, int32_t n_motions,
+                               int32_t samples_per_motion, int32_t steps, uint64_t seed)
+{
+    if (!t || !q0 || !q1 || n_motions < 1 || samples_per_motion < 1 || steps < 1 || steps > kMaxSteps)
+        return tfail(t, SVM_E_INVALID, "bad data arguments");
+    for (long long i = 0; i < (long long)n_motions * 6; ++i)
+        if (!std::isfinite(q0[i]) || !std::isfinite(q1[i])) return tfail(t, SVM_E_INVALID, "non-finite joint angle");
+    DevGuard gd(t->device);
+    TCK(cudaDeviceSynchronize());
+    free_data(t);
+    const long long S = (long long)n_motions * samples_per_motion;
+    svm_status st;
+    if ((st = talloc(t, &t->X, S * 16)) != SVM_OK) return st;
+    if ((st = talloc(t, &t->MID, S * 4)) != SVM_OK) return st;
+    if ((st = talloc(t, &t->q0, (size_t)n_motions * 48)) != SVM_OK) return st;
+    if ((st = talloc(t, &t->q1, (size_t)n_motions * 48)) != SVM_OK) return st;
+    TCK(cudaMemcpy(t->q0, q0, (size_t)n_motions * 48, cudaMemcpyHostToDevice));
+    TCK(cudaMemcpy(t->q1, q1, (size_t)n_motions * 48, cudaMemcpyHostToDevice));
+    Capsule* caps = nullptr;
+    MotionState* stt = nullptr;
+    TCK(cudaMalloc(&caps, (size_t)n_motions * (steps + 1) * kCaps * sizeof(Capsule)));
+    TCK(cudaMalloc(&stt, (size_t)n_motions * sizeof(MotionState)));
+    CallArgs a{};
+    a.M = n_motions; a.N = steps; a.W = t->W; a.q0 = t->q0; a.q1 = t->q1; a.caps = caps; a.st = stt;
+    DevWeights dw{};
+    launch_prologue_fk(a, t->rp, dw, 0);
+    const size_t smem = (size_t)(steps + 1) * kCaps * sizeof(Capsule);
+    cudaFuncSetAttribute(sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (kMaxSteps + 1) * kCaps * (int)sizeof(Capsule));
+    sample_kernel<<<n_motions, 256, smem, 0>>>(caps, steps, samples_per_motion, (unsigned long long)seed, t->X, t->MID);
+    const cudaError_t e = cudaDeviceSynchronize();
+    cudaFree(caps);
+    cudaFree(stt);
+    if (e != cudaSuccess) return tfail(t, SVM_E_CUDA, std::string("data generation: ") + cudaGetErrorString(e));
+    t->n_motions = n_motions;
+    t->n_samples = S;
+    return SVM_OK;
+}
+
+svm_status svm_train_set_samples(svm_trainer* t, const double* q0, const double* q1, int32_t n_motions,
+                                 const float* x4, const int32_t* motion, int64_t n)
+{
+    if (!t || !q0 || !q1 || !x4 || !motion || n_motions < 1 || n < 1) return tfail(t, SVM_E_INVALID, "bad samples");
+    for (long long i = 0; i < n; ++i)
+        if (motion[i] < 0 || motion[i] >= n_motions) return tfail(t, SVM_E_INVALID, "motion index out of range");
+    DevGuard gd(t->device);
+    TCK(cudaDeviceSynchronize());
+    free_data(t);
+    svm_status st;
+    if ((st = talloc(t, &t->X, n * 16)) != SVM_OK) return st;
+    if ((st = talloc(t, &t->MID, n * 4)) != SVM_OK) return st;
+    if ((st = talloc(t, &t->q0, (size_t)n_motions * 48)) != SVM_OK) return st;
+    if ((st = talloc(t, &t->q1, (size_t)n_motions * 48)) != SVM_OK) return st;
+    TCK(cudaMemcpy(t->X, x4, n * 16, cudaMemcpyHostToDevice));
+    TCK(cudaMemcpy(t->MID, motion, n * 4, cudaMemcpyHostToDevice));
+    TCK(cudaMemcpy(t->q0, q0, (size_t)n_motions * 48, cudaMemcpyHostToDevice));
+    TCK(cudaMemcpy(t->q1, q1, (size_t)n_motions * 48, cudaMemcpyHostToDevice));
+    t->n_motions = n_motions;
+    t->n_samples = n;
+    return SVM_OK;
+}
+
+svm_status svm_train_copy_samples(svm_trainer* t, float* x4_out, int32_t* motion_out, int64_t n)
+{
+    if (!t || n < 0 || n > t->n_samples) return tfail(t, SVM_E_INVALID, "bad copy");
+    DevGuard gd(t->device);
+    TCK(cudaDeviceSynchronize());
+    if (x4_out) TCK(cudaMemcpy(x4_out, t->X, n * 16, cudaMemcpyDeviceToHost));
+    if (motion_out) TCK(cudaMemcpy(motion_out, t->MID, n * 4, cudaMemcpyDeviceToHost));
+    return SVM_OK;
+}
+
+svm_status svm_train_gradient(svm_trainer* t, int64_t sample_begin, float* grad_out, float* loss_out)
+{
+    if (!t || !grad_out) return SVM_E_INVALID;
+    if (sample_begin < 0 || sample_begin + t->B > t->n_samples) return tfail(t, SVM_E_INVALID, "batch out of range");
+    DevGuard gd(t->device);
+    TCK(cudaMemset(t->Gr, 0, t->np * 4));
+    TCK(cudaMemset(t->loss, 0, 4));
+    svm_status st = run_batch(t, sample_begin, 1, true, 0);
+    if (st != SVM_OK) return st;
+    TCK(cudaGetLastError());
+    TCK(cudaDeviceSynchronize());
+    TCK(cudaMemcpy(grad_out, t->Gr, t->np * 4, cudaMemcpyDeviceToHost));
+    float l = 0;
+    TCK(cudaMemcpy(&l, t->loss, 4, cudaMemcpyDeviceToHost));
+    if (loss_out) *loss_out = l / (float)t->B;
+    unsigned e = 0;
+    TCK(cudaMemcpy(&e, t->err, 4, cudaMemcpyDeviceToHost));
+    if (e) return tfail(t, SVM_E_TIMEOUT, "a bounded device wait expired");
+    return SVM_OK;
+}
+
+svm_status svm_train_adam(svm_trainer* t, float lr)
+{
+    if (!t || !(lr > 0)) return SVM_E_INVALID;
+    DevGuard gd(t->device);
+    t->step += 1;
+    const double b1 = 0.9, b2 = 0.999;
+    const float c1 = (float)(1.0 - std::pow(b1, (double)t->step)), c2 = (float)(1.0 - std::pow(b2, (double)t->step));
+    adam_kernel<<<grid_for(t->np), 256>>>(t->P, t->Gr, t->Mo, t->Vo, t->np, lr, (float)b1, (float)b2, 1e-8f, c1, c2,
+                                         t->W, t->L, t->off_h, t->wb, t->wbt);
+    TCK(cudaGetLastError());
+    return SVM_OK;
+}
+
+svm_status svm_train_epoch(svm_trainer* t, int64_t sample_begin, int64_t sample_end, float lr, uint64_t shuffle_seed,
+                           float* mean_loss)
+{
+    if (!t || !(lr > 0)) return SVM_E_INVALID;
+    const long long S = sample_end - sample_begin;
+    if (sample_begin < 0 || sample_end > t->n_samples || S < t->B) return tfail(t, SVM_E_INVALID, "bad sample range");
+    const long long nb = S / t->B;                    // batches per epoch; batch i takes offset perm[i]
+    std::vector<long long> perm(nb);
+    for (long long i = 0; i < nb; ++i) perm[i] = i;
+    std::mt19937_64 rng(shuffle_seed);
+    std::shuffle(perm.begin(), perm.end(), rng);
+    DevGuard gd(t->device);
+    TCK(cudaMemset(t->loss, 0, 4));
+    for (long long i = 0; i < nb; ++i) {
+        TCK(cudaMemsetAsync(t->Gr, 0, t->np * 4, 0));
+        svm_status st = run_batch(t, sample_begin + perm[i], nb, true, 0);
+        if (st != SVM_OK) return st;
+        st = svm_train_adam(t, lr);
+        if (st != SVM_OK) return st;
+    }
+    TCK(cudaGetLastError());
+    TCK(cudaDeviceSynchronize());
+    float l = 0;
+    TCK(cudaMemcpy(&l, t->loss, 4, cudaMemcpyDeviceToHost));
+    if (mean_loss) *mean_loss = l / (float)(nb * t->B);
+    unsigned e = 0;
+    TCK(cudaMemcpy(&e, t->err, 4, cudaMemcpyDeviceToHost));
+    if (e) return tfail(t, SVM_E_TIMEOUT, "a bounded device wait expired");
+    return SVM_OK;
+}
+
+svm_status svm_train_evaluate(svm_trainer* t, int64_t sample_begin, int64_t sample_end, float* mae)
+{
+    if (!t || !mae) return SVM_E_INVALID;
+    const long long S = sample_end - sample_begin;
+    if (sample_begin < 0 || sample_end > t->n_samples || S < t->B) return tfail(t, SVM_E_INVALID, "bad sample range");
+    const long long nb = S / t->B;
+    DevGuard gd(t->device);
+    TCK(cudaMemset(t->loss, 0, 4));
+    for (long long i = 0; i < nb; ++i) {
+        svm_status st = run_batch(t, sample_begin + i * t->B, 1, false, 0);
+        if (st != SVM_OK) return st;
+    }
+    TCK(cudaGetLastError());
+    TCK(cudaDeviceSynchronize());
+    float l = 0;
+    TCK(cudaMemcpy(&l, t->loss, 4, cudaMemcpyDeviceToHost));
+    *mae = l / (float)(nb * t->B);
+    return SVM_OK;
+}
+
+svm_status svm_train_state(svm_trainer* t, float* params, float* m1, float* m2, int64_t* step, int64_t n)
+{
+    if (!t || n != t->np) return tfail(t, SVM_E_INVALID, "state size mismatch");
+    DevGuard gd(t->device);
+    TCK(cudaDeviceSynchronize());
+    if (params) TCK(cudaMemcpy(params, t->P, n * 4, cudaMemcpyDeviceToHost));
+    if (m1) TCK(cudaMemcpy(m1, t->Mo, n * 4, cudaMemcpyDeviceToHost));
+    if (m2) TCK(cudaMemcpy(m2, t->Vo, n * 4, cudaMemcpyDeviceToHost));
+    if (step) *step = t->step;
+    return SVM_OK;
+}
+
+svm_status svm_train_restore(svm_trainer* t, const float* params, const float* m1, const float* m2, int64_t step,
+                             int64_t n)
+{
+    if (!t || n != t->np || !params || !m1 || !m2 || step < 0) return tfail(t, SVM_E_INVALID, "state size mismatch");
+    DevGuard gd(t->device);
+    TCK(cudaDeviceSynchronize());
+    TCK(cudaMemcpy(t->P, params, n * 4, cudaMemcpyHostToDevice));
+    TCK(cudaMemcpy(t->Mo, m1, n * 4, cudaMemcpyHostToDevice));
+    TCK(cudaMemcpy(t->Vo, m2, n * 4, cudaMemcpyHostToDevice));
+    t->step = step;
+    refresh_bf16_kernel<<<grid_for((long long)t->L * t->W * t->W), 256>>>(t->P, t->W, t->L, t->off_h, t->wb, t->wbt);
+    TCK(cudaGetLastError());
+    TCK(cudaDeviceSynchronize());
+    return SVM_OK;
+}
+
+int64_t svm_train_param_count(const svm_trainer* t) { return t ? t->np : 0; }
+
+}  // extern "C"

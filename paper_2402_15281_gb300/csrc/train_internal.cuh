@@ -1,0 +1,32 @@
+// train_internal.cuh -- shared declarations of the training kernels.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace svm {
+
+constexpr int kEpiFwd = 0, kEpiDgrad = 1, kEpiWgrad = 2;
+
+// Arguments of one training GEMM D[M][N] = A[M][K] B[N][K]^T (bfloat16).
+struct GemmArgs {
+    int n_mt, n_nt, n_ks;           // tiles along M (128), N (256), K splits
+    int k_len;                      // K elements per split (multiple of 64)
+    long long ld_rows;              // row stride of the row-major [M][.] operands and outputs
+    long long ld_cols;              // row stride of the transposed [N][.] outputs
+    const float* bias;              // FWD: [N]
+    __nv_bfloat16* h_out;           // FWD: H; DGRAD: G
+    __nv_bfloat16* z_out;           // FWD: Z
+    __nv_bfloat16* ht_out;          // FWD: H^T; DGRAD: G^T
+    const __nv_bfloat16* z_in;      // DGRAD: Z of the previous layer
+    float* dw;                      // WGRAD: FP32 gradient [M][N]
+    unsigned int* err;              // bounded-wait error word
+};
+
+int train_gemm_bm();
+int train_gemm_bn();
+int train_gemm_bk();
+int train_make_map(void* map, const void* base, long long rows, long long cols, int box_rows);
+void launch_train_gemm(int epi, int act, const void* amap, const void* bmap, const GemmArgs& g, int n_sms,
+                       cudaStream_t s);
+
+}  // namespace svm
