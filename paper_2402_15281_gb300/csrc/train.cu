@@ -18,6 +18,9 @@
 //   gradient GEMM, bias gradients by column sums, layer-1 gradient on CUDA
 //   cores; then Adam (lr, betas (0.9, 0.999), eps 1e-8, as in Sec. V) on FP32
 //   master weights, which also refreshes the BF16 copies W and W^T.
+//   Every sum over the batch is formed from per-block (or per-split)
+//   partials reduced in a fixed order -- no floating-point atomics -- so a
+//   step, an epoch and a resumed run are bitwise reproducible.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -105,7 +108,8 @@ struct StepArgs {
     const double* q1;
     const float* P;                   // FP32 master parameters (blob order)
     float* Gr;                        // FP32 gradient (blob order)
-    float* loss;                      // sum of |f - delta| over the batch
+    float* loss;                      // per-block partial sums of |f - delta|
+    float* part;                      // per-block partial gradients
     long long off_w1, off_b1, off_out;
 };
 
@@ -216,9 +220,11 @@ __global__ void __launch_bounds__(128) layer1_fwd_kernel(StepArgs a, __nv_bfloat
     }
 }
 
-// Output layer, loss and its gradient: f = w_out . h_L + b_out, e = f - delta,
-// loss += |e|; df = sign(e) / B; G_L = df * w_out * act'(z_L) (written as G_L
-// and G_L^T); dw_out += df h_L; db_out += df.  eval != 0: loss only.
+// Output layer, loss and its gradient: f = w_out . h_L + b_out, e = f - delta;
+// block b writes its sum of |e| to loss[b]; with eval == 0 also df = sign(e)/B,
+// G_L = df * w_out * act'(z_L) (as G_L and G_L^T), and the block's partial
+// gradients of w_out and b_out to part[b][0..W].  Sums over blocks follow in
+// a fixed order (reduce_kernel), so the step is deterministic.
 template <int ACT>
 __global__ void __launch_bounds__(128) head_kernel(StepArgs a, const __nv_bfloat16* HL, const __nv_bfloat16* ZL,
                                                    __nv_bfloat16* GL, __nv_bfloat16* GLT, int eval)
@@ -245,13 +251,14 @@ __global__ void __launch_bounds__(128) head_kernel(StepArgs a, const __nv_bfloat
     float ae = fabsf(e);
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) ae += __shfl_xor_sync(0xffffffffu, ae, s);
-    if (lane == 0 && warp == 0) atomicAdd(a.loss, ae);
+    if (lane == 0 && warp == 0) a.loss[blockIdx.x] = ae;
     if (eval) return;
+    float* pb = a.part + (long long)blockIdx.x * (a.W + 1);
     const float df = (e > 0.0f ? 1.0f : (e < 0.0f ? -1.0f : 0.0f)) / (float)a.B;
     float dsum = df;
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, s);
-    if (lane == 0 && warp == 0) atomicAdd(a.Gr + a.off_out + a.W, dsum);
+    if (lane == 0 && warp == 0) pb[a.W] = dsum;
     for (int c = warp; c < a.W / 32; c += 4) {
         float h[32], z[32], gv[32];
         load_bf16_row32(HL + (long long)r * a.W + c * 32, h);
@@ -262,15 +269,16 @@ __global__ void __launch_bounds__(128) head_kernel(StepArgs a, const __nv_bfloat
             float dw = df * h[i];
 #pragma unroll
             for (int s = 16; s > 0; s >>= 1) dw += __shfl_xor_sync(0xffffffffu, dw, s);
-            if (lane == i) atomicAdd(a.Gr + a.off_out + c * 32 + i, dw);
+            if (lane == i) pb[c * 32 + i] = dw;
         }
         store_bf16_row32(GL + (long long)r * a.W + c * 32, gv);
         store_bf16_transposed32(tp, lane, gv, GLT + (long long)(c * 32) * a.B + blockIdx.x * 32, a.B);
     }
 }
 
-// Layer-1 gradients: dW1[n][k] += sum_b G0[b][n] in_b[k], db1[n] += sum_b G0[b][n],
-// 256 samples per block, one thread per feature.
+// Layer-1 gradients of 256 samples per block (one thread per feature):
+// part[b][n * 15 + k] = sum G0[r][n] in_r[k], part[b][15 W + n] = sum G0[r][n]
+// -- the layout of W1 and b1 in the parameter vector.
 __global__ void __launch_bounds__(256) layer1_bwd_kernel(StepArgs a, const __nv_bfloat16* G0)
 {
     __shared__ float ins[256][16];
@@ -291,8 +299,9 @@ __global__ void __launch_bounds__(256) layer1_bwd_kernel(StepArgs a, const __nv_
 #pragma unroll
             for (int k = 0; k < 16; ++k) acc[k] = fmaf(gv, ins[b][k], acc[k]);
         }
-        for (int k = 0; k < 15; ++k) atomicAdd(a.Gr + a.off_w1 + n * 15 + k, acc[k]);
-        atomicAdd(a.Gr + a.off_b1 + n, acc[15]);
+        float* pb = a.part + (long long)blockIdx.x * a.W * 16;
+        for (int k = 0; k < 15; ++k) pb[n * 15 + k] = acc[k];
+        pb[15 * a.W + n] = acc[15];
     }
 }
 
@@ -311,6 +320,16 @@ __global__ void __launch_bounds__(256) colsum_kernel(const __nv_bfloat16* GT, lo
         float t = 0.0f;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
         db[n] += t;
+    }
+}
+
+// dst[j] += sum_{p < P} part[p * n + j], summed in the order p = 0, 1, ...
+__global__ void reduce_kernel(const float* part, int P, long long n, float* dst)
+{
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+        float s = 0.0f;
+        for (int p = 0; p < P; ++p) s += part[(long long)p * n + j];
+        dst[j] += s;
     }
 }
 
@@ -370,7 +389,10 @@ struct svm_trainer {
     long long np = 0, off_w1 = 0, off_b1 = 0, off_h = 0, off_out = 0;
     long long step = 0;
     float* P = nullptr; float* Gr = nullptr; float* Mo = nullptr; float* Vo = nullptr;
-    float* loss = nullptr;
+    float* loss = nullptr;            // per-block loss partials (B / 32)
+    float* loss_sum = nullptr;        // batch-summed losses of the current call
+    float* part = nullptr;            // partial gradients (largest of the three uses)
+    long long part_n = 0;
     unsigned int* err = nullptr;
     __nv_bfloat16* wb = nullptr; __nv_bfloat16* wbt = nullptr;
     std::vector<__nv_bfloat16*> H, Z, HT, G, GT;     // per layer 0..L
@@ -434,7 +456,7 @@ StepArgs step_args(svm_trainer* t, long long base, long long stride)
     a.W = t->W; a.B = t->B; a.act = t->act;
     a.base = base; a.stride = stride;
     a.X = t->X; a.MID = t->MID; a.q0 = t->q0; a.q1 = t->q1;
-    a.P = t->P; a.Gr = t->Gr; a.loss = t->loss;
+    a.P = t->P; a.Gr = t->Gr; a.loss = t->loss; a.part = t->part;
     a.off_w1 = t->off_w1; a.off_b1 = t->off_b1; a.off_out = t->off_out;
     return a;
 }
@@ -457,14 +479,17 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
     }
     if (t->act == 0) head_kernel<0><<<B / 32, 128, 0, s>>>(a, t->H[L], t->Z[L], t->G[L], t->GT[L], grad ? 0 : 1);
     else head_kernel<1><<<B / 32, 128, 0, s>>>(a, t->H[L], t->Z[L], t->G[L], t->GT[L], grad ? 0 : 1);
+    reduce_kernel<<<1, 1, 0, s>>>(t->loss, B / 32, 1, t->loss_sum);
     if (!grad) return SVM_OK;
+    reduce_kernel<<<grid_for(W + 1), 256, 0, s>>>(t->part, B / 32, W + 1, t->Gr + t->off_out);
     for (int l = L; l >= 1; --l) {
         const long long woff = t->off_h + (long long)(l - 1) * ((long long)W * W + W);
         GemmArgs g{};
         const int k_len = B >= 2048 ? 2048 : B;
         g.n_mt = W / 128; g.n_nt = W / 256; g.n_ks = B / k_len; g.k_len = k_len;
-        g.ld_rows = W; g.ld_cols = 0; g.dw = t->Gr + woff; g.err = t->err;
+        g.ld_rows = W; g.ld_cols = 0; g.dw = t->part; g.split_stride = (long long)W * W; g.err = t->err;
         launch_train_gemm(kEpiWgrad, 0, t->mapGT[l].b, t->mapHT[l - 1].b, g, t->n_sms, s);
+        reduce_kernel<<<grid_for((long long)W * W), 256, 0, s>>>(t->part, g.n_ks, (long long)W * W, t->Gr + woff);
         colsum_kernel<<<W, 256, 0, s>>>(t->GT[l], B, t->Gr + woff + (long long)W * W);
         GemmArgs d{};
         d.n_mt = B / 128; d.n_nt = W / 256; d.n_ks = 1; d.k_len = W;
@@ -473,6 +498,7 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
         launch_train_gemm(kEpiDgrad, t->act, t->mapG[l].b, t->mapWT[l - 1].b, d, t->n_sms, s);
     }
     layer1_bwd_kernel<<<B / 256, 256, 0, s>>>(a, t->G[0]);
+    reduce_kernel<<<grid_for((long long)W * 16), 256, 0, s>>>(t->part, B / 256, (long long)W * 16, t->Gr + t->off_w1);
     return SVM_OK;
 }
 
@@ -519,7 +545,13 @@ svm_status svm_train_create(const svm_model_desc* desc, int device, int32_t batc
     if ((st = talloc(t, &t->Gr, t->np * 4)) != SVM_OK) return fail_free(st);
     if ((st = talloc(t, &t->Mo, t->np * 4)) != SVM_OK) return fail_free(st);
     if ((st = talloc(t, &t->Vo, t->np * 4)) != SVM_OK) return fail_free(st);
-    if ((st = talloc(t, &t->loss, 256)) != SVM_OK) return fail_free(st);
+    if ((st = talloc(t, &t->loss, (B / 32) * 4)) != SVM_OK) return fail_free(st);
+    if ((st = talloc(t, &t->loss_sum, 256)) != SVM_OK) return fail_free(st);
+    {
+        const long long k_len = B >= 2048 ? 2048 : B;
+        t->part_n = std::max({(B / k_len) * W * W, (B / 32) * (W + 1), (B / 256) * W * 16});
+    }
+    if ((st = talloc(t, &t->part, t->part_n * 4)) != SVM_OK) return fail_free(st);
     if ((st = talloc(t, &t->err, 256)) != SVM_OK) return fail_free(st);
     if ((st = talloc(t, &t->wb, L * W * W * 2)) != SVM_OK) return fail_free(st);
     if ((st = talloc(t, &t->wbt, L * W * W * 2)) != SVM_OK) return fail_free(st);
@@ -707,14 +739,14 @@ svm_status svm_train_gradient(svm_trainer* t, int64_t sample_begin, float* grad_
     if (sample_begin < 0 || sample_begin + t->B > t->n_samples) return tfail(t, SVM_E_INVALID, "batch out of range");
     DevGuard gd(t->device);
     TCK(cudaMemset(t->Gr, 0, t->np * 4));
-    TCK(cudaMemset(t->loss, 0, 4));
+    TCK(cudaMemset(t->loss_sum, 0, 4));
     svm_status st = run_batch(t, sample_begin, 1, true, 0);
     if (st != SVM_OK) return st;
     TCK(cudaGetLastError());
     TCK(cudaDeviceSynchronize());
     TCK(cudaMemcpy(grad_out, t->Gr, t->np * 4, cudaMemcpyDeviceToHost));
     float l = 0;
-    TCK(cudaMemcpy(&l, t->loss, 4, cudaMemcpyDeviceToHost));
+    TCK(cudaMemcpy(&l, t->loss_sum, 4, cudaMemcpyDeviceToHost));
     if (loss_out) *loss_out = l / (float)t->B;
     unsigned e = 0;
     TCK(cudaMemcpy(&e, t->err, 4, cudaMemcpyDeviceToHost));
@@ -747,7 +779,7 @@ svm_status svm_train_epoch(svm_trainer* t, int64_t sample_begin, int64_t sample_
     std::mt19937_64 rng(shuffle_seed);
     std::shuffle(perm.begin(), perm.end(), rng);
     DevGuard gd(t->device);
-    TCK(cudaMemset(t->loss, 0, 4));
+    TCK(cudaMemset(t->loss_sum, 0, 4));
     for (long long i = 0; i < nb; ++i) {
         TCK(cudaMemsetAsync(t->Gr, 0, t->np * 4, 0));
         svm_status st = run_batch(t, sample_begin + perm[i], nb, true, 0);
@@ -758,7 +790,7 @@ svm_status svm_train_epoch(svm_trainer* t, int64_t sample_begin, int64_t sample_
     TCK(cudaGetLastError());
     TCK(cudaDeviceSynchronize());
     float l = 0;
-    TCK(cudaMemcpy(&l, t->loss, 4, cudaMemcpyDeviceToHost));
+    TCK(cudaMemcpy(&l, t->loss_sum, 4, cudaMemcpyDeviceToHost));
     if (mean_loss) *mean_loss = l / (float)(nb * t->B);
     unsigned e = 0;
     TCK(cudaMemcpy(&e, t->err, 4, cudaMemcpyDeviceToHost));
@@ -773,7 +805,7 @@ svm_status svm_train_evaluate(svm_trainer* t, int64_t sample_begin, int64_t samp
     if (sample_begin < 0 || sample_end > t->n_samples || S < t->B) return tfail(t, SVM_E_INVALID, "bad sample range");
     const long long nb = S / t->B;
     DevGuard gd(t->device);
-    TCK(cudaMemset(t->loss, 0, 4));
+    TCK(cudaMemset(t->loss_sum, 0, 4));
     for (long long i = 0; i < nb; ++i) {
         svm_status st = run_batch(t, sample_begin + i * t->B, 1, false, 0);
         if (st != SVM_OK) return st;
@@ -781,7 +813,7 @@ svm_status svm_train_evaluate(svm_trainer* t, int64_t sample_begin, int64_t samp
     TCK(cudaGetLastError());
     TCK(cudaDeviceSynchronize());
     float l = 0;
-    TCK(cudaMemcpy(&l, t->loss, 4, cudaMemcpyDeviceToHost));
+    TCK(cudaMemcpy(&l, t->loss_sum, 4, cudaMemcpyDeviceToHost));
     *mae = l / (float)(nb * t->B);
     return SVM_OK;
 }

@@ -8,7 +8,9 @@
 //   DGRAD  input gradient, rows = samples:  g = acc * act'(z_prev);
 //          writes G [M][N] and G^T [N][M] (bfloat16).
 //   WGRAD  weight gradient dW = G^T H over a slice of the batch (split-K):
-//          adds the FP32 partial tile into dW [M][N] with vector atomics.
+//          stores the FP32 partial of split s into dW + s * M * N ([M][N]);
+//          the splits are summed afterwards in a fixed order, so the result
+//          does not depend on the order in which CTAs finish.
 //
 // Persistent kernel, one CTA per SM, 10 warps: warp 0 streams A and B tiles
 // (128 x 64 and 256 x 64 bfloat16, 128B swizzle) with TMA into a 4-stage
@@ -272,11 +274,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                     store_row32(g.h_out + m * g.ld_rows + n0, v);
                     store_transposed32(tp, lane, v, g.ht_out + (long long)n0 * g.ld_cols + m0, g.ld_cols);
                 } else {
-                    float* dst = g.dw + m * g.ld_rows + n0;
+                    float4* dst = reinterpret_cast<float4*>(g.dw + (long long)ks * g.split_stride + m * g.ld_rows + n0);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        atomicAdd(reinterpret_cast<float4*>(dst + 4 * q),
-                                  make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+                    for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
                 }
             }
             tc_fence_before();

@@ -18,7 +18,8 @@ struct GemmArgs {
     __nv_bfloat16* z_out;           // FWD: Z
     __nv_bfloat16* ht_out;          // FWD: H^T; DGRAD: G^T
     const __nv_bfloat16* z_in;      // DGRAD: Z of the previous layer
-    float* dw;                      // WGRAD: FP32 gradient [M][N]
+    float* dw;                      // WGRAD: FP32 partials [n_ks][M][N]
+    long long split_stride;         // WGRAD: elements between the partials of two splits
     unsigned int* err;              // bounded-wait error word
 };
 

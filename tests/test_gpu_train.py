@@ -9,8 +9,8 @@
   batch with cancellation, such as the layer-1 weight gradient, show the
   largest relative error, ~5 %); a wrong operand or a dropped term fails both;
 * Adam: the first step moves every parameter by -lr g / (|g| + eps);
-* training lowers the held-out error, and a checkpoint resumes the run (to
-  within the non-deterministic order of FP32 atomic sums).
+* training lowers the held-out error, and a checkpoint resumes the run
+  bit for bit (every batch sum is reduced in a fixed order).
 """
 import numpy as np
 import pytest
@@ -92,6 +92,9 @@ def test_gradient_matches_oracle(svm, robot, width, n_hidden, act):
                 print(f"layer {li} {name}: rel L2 {err:.3e} cos {cos:.6f}")
                 assert err <= 8e-2 and cos >= 0.995, (li, name, err, cos)
         assert off == g.size
+        g2, loss2 = svm.svm_train_gradient(t, 0)      # deterministic: same batch, same bits
+        np.testing.assert_array_equal(g, g2)
+        assert loss == loss2
     finally:
         svm.svm_train_destroy(t)
 
@@ -134,16 +137,15 @@ def test_training_lowers_heldout_error_and_resumes(svm, robot):
         print(f"held-out MAE {before:.4f} -> {after:.4f} m; epoch losses {np.round(losses, 4)}")
         assert losses[-1] < losses[0]
         assert after < 0.5 * before
-        # checkpoint and resume: the continued run matches the uninterrupted one up to
-        # the summation order of the FP32 atomics in the batch reductions (not bitwise)
+        # checkpoint and resume: the continued run equals the uninterrupted one bitwise
         state = svm.svm_train_state(t)
         la = svm.svm_train_epoch(t, 0, n_train, 1e-3, 99)
         Pa = svm.svm_train_state(t)[0]
         svm.svm_train_restore(t, *state)
         lb = svm.svm_train_epoch(t, 0, n_train, 1e-3, 99)
         Pb = svm.svm_train_state(t)[0]
-        assert abs(la - lb) <= 1e-2 * la
-        assert np.abs(Pa - Pb).max() <= 1e-2 * np.abs(Pa).max()
+        assert la == lb
+        np.testing.assert_array_equal(Pa, Pb)
         # the exported weights load into an inference model
         blob = svm.svm_train_get_weights(t)
         h = svm.svm_create_model(robot, 256, 4, 0, svm.SVM_BF16, 0)
