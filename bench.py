@@ -4,8 +4,12 @@
 Workload (one step = one svm_check_motions call over the whole batch):
 64 linear joint motions x a 200 000-point depth-camera cloud of a bin with 30
 objects, margin 0.03 m, 128 steps per motion, network 15 -> 256 x 4 ReLU -> 1
-in the chosen precision, gate calibrated on separate motions.  Every (motion,
-point) pair covered by a verdict counts as one query.
+in the chosen precision.  Before timing, the network is trained on the GPU on
+data the library generates and labels itself (1024 motions like the
+workload's, 4096 samples each), and the gate is calibrated on 16 separate
+motions.  Every (motion, point) pair covered by a verdict counts as one query.
+The same step through the plain FP32 path (SIMT network, same verifier) is
+timed too and reported beside the value.
 
 Timing: W warm-up steps, then K steps each bracketed by CUDA events on the
 launching stream; an L2 flush (a 256 MiB write) runs between steps, outside
@@ -57,12 +61,30 @@ def weights():
     return S.xavier_weights(WIDTH, HIDDEN, seed=2)
 
 
-def workload_config(prec):
+def workload_config(prec, weights="trained"):
+    w = ("trained on GPU-generated, exactly labelled data (1024 motions x 4096 samples, 30 epochs), "
+         "gate calibrated on 16 separate motions") if weights == "trained" else \
+        "Glorot-uniform seed 2, gate calibrated on 16 separate motions"
     return {"workload": "bin-picking: 64 linear motions x 200k-point bin cloud, margin 0.03 m, 128 steps, "
                         "MLP 15-256x4-1 ReLU",
             "motions": N_MOTIONS, "points": N_POINTS, "steps": STEPS, "margin_m": EPS,
-            "precision": prec, "l2": "flushed between steps (256 MiB write)",
-            "weights": "Glorot-uniform seed 2, gate calibrated on 16 separate motions"}
+            "precision": prec, "l2": "flushed between steps (256 MiB write)", "weights": w}
+
+
+def blob_layers(blob):
+    """[(W, b), ...] of a weight blob (format of svm_load_weights)."""
+    import struct
+    n_layers = struct.unpack("<I", blob[8:12])[0]
+    off, out = 28, []
+    for _ in range(n_layers):
+        o, i = struct.unpack("<II", blob[off:off + 8])
+        off += 8
+        W = np.frombuffer(blob, "<f4", o * i, off).reshape(o, i).copy()
+        off += 4 * o * i
+        b = np.frombuffer(blob, "<f4", o, off).copy()
+        off += 4 * o
+        out.append((W, b))
+    return out
 
 
 # --------------------------------------------------------------------- clocks
@@ -161,19 +183,6 @@ def run_reference(args):
 
 # --------------------------------------------------------------------- GPU arm
 
-def calibrate_tau(svm, model, robot, pts_d, torch):
-    """tau = 1.25 x max(f - delta) over calibration pairs with delta <= margin + 0.05
-    (16 motions of the same distribution, seed 1000), never below 0."""
-    q0, q1 = S.bin_motions(robot, 16, seed=1000)
-    f = torch.empty((16, pts_d.shape[0]), device=pts_d.device)
-    d = torch.empty_like(f)
-    svm.svm_eval_pairs(model, q0, q1, pts_d, f)
-    svm.svm_label_pairs(model, q0, q1, pts_d, STEPS, d)
-    near = d <= EPS + 0.05
-    over = torch.where(near, f - d, torch.full_like(f, -float("inf"))).max().item()
-    return max(0.0, 1.25 * over) if np.isfinite(over) else 0.0
-
-
 def run_gpu(args):
     import torch
     import paper_2402_15281_gb300 as svm
@@ -189,14 +198,30 @@ def run_gpu(args):
     svm.build() if rank == 0 or world == 1 else None
     if world > 1:
         torch.distributed.barrier()
+    from paper_2402_15281_gb300 import training
     robot, pts, q0, q1 = workload(seed=rank)
-    layers = weights()
     prec = PREC_NAMES[args.prec]
-    model = svm.svm_create_model(robot, WIDTH, HIDDEN, svm.SVM_RELU, prec, local)
-    svm.svm_load_weights(model, svm.make_blob(layers))
+    train_info = None
+    if args.weights == "trained":
+        tq0, tq1 = training.bin_training_motions(robot, 1024, seed=41)
+        blob, hist = training.train_model(svm, robot, tq0, tq1, samples_per_motion=4096, steps=STEPS,
+                                          batch=65536, epochs=30, patience=10, device=local)
+        train_info = {"val_mae_m": hist["best_val_mae"], "train_samples": hist["train_samples"],
+                      "train_samples_per_s": hist["samples_per_s"], "seconds": round(hist["seconds"], 2)}
+    else:
+        blob = svm.make_blob(weights())
+    layers = blob_layers(blob)
     pts_d = torch.from_numpy(pts).to(dev)
-    tau = calibrate_tau(svm, model, robot, pts_d, torch)
-    svm.svm_set_gate(model, tau)
+    cq0, cq1 = S.bin_motions(robot, 16, seed=1000)
+
+    def make_model(p):
+        h = svm.svm_create_model(robot, WIDTH, HIDDEN, svm.SVM_RELU, p, local)
+        svm.svm_load_weights(h, blob)
+        t = training.calibrate_tau(svm, h, robot, pts_d, EPS, STEPS, cq0, cq1)
+        svm.svm_set_gate(h, t)
+        return h, t
+
+    model, tau = make_model(prec)
     svm.svm_profile_enable(model, True)
     res = svm.new_results(N_MOTIONS, dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -292,11 +317,33 @@ def run_gpu(args):
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
 
+    # the plain FP32 path on the same workload and weights (SIMT network, same verifier)
+    fp32 = None
+    if args.prec != "fp32" and not args.no_fp32_path:
+        m32, tau32 = make_model(svm.SVM_FP32)
+        for _ in range(2):
+            svm.svm_check_motions(m32, q0, q1, pts_d, EPS, STEPS, flags, res, stream)
+        flush.fill_(0.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k32 = 3
+        e0.record(stream)
+        for _ in range(k32):
+            svm.svm_check_motions(m32, q0, q1, pts_d, EPS, STEPS, flags, res, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms32 = e0.elapsed_time(e1) / k32
+        r32 = svm.results_to_numpy(res)[:N_MOTIONS]
+        fp32 = {"value": pairs_step / (ms32 / 1e3), "ms_per_step": ms32, "tau_m": tau32,
+                "collisions": int(r32["collision"].sum()),
+                "verdicts_equal": bool(np.array_equal(r32["collision"], r["collision"]))}
+        svm.svm_destroy_model(m32)
+
     launches_per_step = 5 + (2 if flags & svm.SVM_STRICT else 0)
     line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAMES[args.prec], "data": "synthetic",
-            "config": workload_config(args.prec), "clocks": clocks,
+            "config": workload_config(args.prec, args.weights), "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": "queries/s",
                     "h2d_bytes_per_step": int(pts.nbytes + 2 * q0.nbytes),
                     "d2h_bytes_per_step": int(res.numel())},
@@ -305,6 +352,8 @@ def run_gpu(args):
             "phases_ms": {"prologue": float(phases[0]), "network": float(phases[1]),
                           "verify": float(phases[2]), "finalize": float(phases[3])},
             "tau_m": tau, "collisions": int(r["collision"].sum()),
+            "fp32_path": fp32, "speedup_vs_fp32_path": (value / fp32["value"]) if fp32 else None,
+            "training": train_info,
             "flagged_fraction": float(r["n_flagged"].sum()) / pairs_step,
             "verified_fraction": n_verified / pairs_step}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -326,6 +375,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--prec", choices=list(PREC_NAMES), default="bf16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32-path", action="store_true")
+    ap.add_argument("--weights", choices=["trained", "random"], default="trained")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
