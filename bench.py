@@ -71,22 +71,6 @@ def workload_config(prec, weights="trained"):
             "precision": prec, "l2": "flushed between steps (256 MiB write)", "weights": w}
 
 
-def blob_layers(blob):
-    """[(W, b), ...] of a weight blob (format of svm_load_weights)."""
-    import struct
-    n_layers = struct.unpack("<I", blob[8:12])[0]
-    off, out = 28, []
-    for _ in range(n_layers):
-        o, i = struct.unpack("<II", blob[off:off + 8])
-        off += 8
-        W = np.frombuffer(blob, "<f4", o * i, off).reshape(o, i).copy()
-        off += 4 * o * i
-        b = np.frombuffer(blob, "<f4", o, off).copy()
-        off += 4 * o
-        out.append((W, b))
-    return out
-
-
 # --------------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -210,7 +194,7 @@ def run_gpu(args):
                       "train_samples_per_s": hist["samples_per_s"], "seconds": round(hist["seconds"], 2)}
     else:
         blob = svm.make_blob(weights())
-    layers = blob_layers(blob)
+    layers = svm.parse_blob(blob)
     pts_d = torch.from_numpy(pts).to(dev)
     cq0, cq1 = S.bin_motions(robot, 16, seed=1000)
 

@@ -141,6 +141,17 @@ svm_status svm_set_gate(svm_model* m, float tau);
  * input of hidden layer l is stored as e4m3(h / scale[l]). */
 svm_status svm_set_act_scales(svm_model* m, const float* scales, int32_t n);
 
+/* FP8 only: choose the activation scales from data.  The network is run in
+ * FP32 on the model's rounded weights over every (motion, point) pair given
+ * (host q0/q1, device points), recording the largest magnitude entering each
+ * hidden layer; scale[l] = headroom * max[l] / 448 (headroom >= 1 keeps
+ * unseen larger activations below the E4M3 saturation).  Sets the scales and
+ * writes them to scales_out (n_hidden floats, may be NULL).  Synchronous;
+ * allocates temporary device memory. */
+svm_status svm_calibrate_act_scales(svm_model* m, const double* q0, const double* q1, int32_t n_motions,
+                                    const float* points_dev, int64_t n_points, float headroom,
+                                    float* scales_out);
+
 /* Check n_motions linear motions q0[m] -> q1[m] against one point cloud.
  *   q0, q1       host, n_motions x 6 doubles, finite.
  *   points_dev   device, n_points float4 records.

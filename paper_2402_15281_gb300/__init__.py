@@ -72,6 +72,8 @@ def lib():
         L.svm_check_batch.argtypes = [vp, vp, vp, i32, vp, vp, vp, i32, f32, i32, u32, vp, vp]
         L.svm_eval_pairs.argtypes = [vp, vp, vp, i32, vp, i64, vp, vp]
         L.svm_label_pairs.argtypes = [vp, vp, vp, i32, vp, i64, i32, vp, vp]
+        L.svm_calibrate_act_scales.argtypes = [vp, vp, vp, i32, vp, i64, f32, vp]
+        L.svm_calibrate_act_scales.restype = C.c_int
         L.svm_check_motions_noalloc.argtypes = [vp, vp, vp, i32, vp, i64, f32, i32, u32, vp, vp]
         L.svm_check_motions_noalloc.restype = C.c_int
         L.svm_train_create.argtypes = [C.POINTER(svm_model_desc), C.c_int, i32, C.POINTER(vp)]
@@ -166,6 +168,21 @@ def make_blob(layers, act=SVM_RELU, tau=float("inf")) -> bytes:
     return b"".join(out)
 
 
+def parse_blob(blob: bytes):
+    """[(W, b), ...] of a weight blob (inverse of make_blob)."""
+    n_layers = struct.unpack("<I", blob[8:12])[0]
+    off, out = 28, []
+    for _ in range(n_layers):
+        o, i = struct.unpack("<II", blob[off:off + 8])
+        off += 8
+        W = np.frombuffer(blob, "<f4", o * i, off).reshape(o, i).copy()
+        off += 4 * o * i
+        b = np.frombuffer(blob, "<f4", o, off).copy()
+        off += 4 * o
+        out.append((W, b))
+    return out
+
+
 def svm_load_weights(model, blob: bytes):
     _check("svm_load_weights", lib().svm_load_weights(model, blob, len(blob)), model)
 
@@ -186,6 +203,17 @@ def svm_set_gate(model, tau: float):
 def svm_set_act_scales(model, scales):
     s = np.ascontiguousarray(scales, dtype=np.float32)
     _check("svm_set_act_scales", lib().svm_set_act_scales(model, s.ctypes.data_as(C.c_void_p), s.shape[0]), model)
+
+
+def svm_calibrate_act_scales(model, q0, q1, points_dev, headroom=2.0) -> np.ndarray:
+    """FP8: set (and return) the per-layer activation scales from data."""
+    q0, p0 = _host_f64(q0)
+    q1, p1 = _host_f64(q1)
+    out = np.zeros(64, dtype=np.float32)
+    _check("svm_calibrate_act_scales", lib().svm_calibrate_act_scales(
+        model, p0, p1, q0.shape[0], _dev(points_dev), points_dev.shape[0], float(headroom),
+        out.ctypes.data_as(C.c_void_p)), model)
+    return out
 
 
 def svm_check_motions(model, q0, q1, points_dev, margin, steps, flags, results_dev, stream=None):

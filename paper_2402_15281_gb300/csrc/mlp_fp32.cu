@@ -85,6 +85,19 @@ __global__ void __launch_bounds__(NT, 1) mlp_fp32_kernel(CallArgs A, DevWeights 
             }
         }
     }
+    // calibration: the largest magnitude entering each hidden layer (valid rows only)
+    auto record_amax = [&](int layer) {
+        float mx = 0.0f;
+        for (int r = 0; r < 4; ++r) {
+            if (p0 + ty * 4 + r >= pe) continue;
+            for (int c = 0; c < CG; ++c)
+                for (int i = 0; i < 4; ++i) mx = fmaxf(mx, fabsf(H[(ty * 4 + r) * HS + tx * 4 + 64 * c + i]));
+        }
+        #pragma unroll
+        for (int s = 16; s > 0; s >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, s));
+        if ((tid & 31) == 0) atomicMax(A.amax + layer, __float_as_uint(mx));
+    };
+    if (A.amax != nullptr && A.L > 0) { __syncthreads(); record_amax(0); }
 
     float acc[4][CPT];
     float fpart[4] = {0.f, 0.f, 0.f, 0.f};
@@ -146,6 +159,7 @@ __global__ void __launch_bounds__(NT, 1) mlp_fp32_kernel(CallArgs A, DevWeights 
                 }
             }
             __syncthreads();
+            if (A.amax != nullptr) record_amax(l + 1);
         } else {
             // last hidden layer: fold the output layer into the epilogue
             #pragma unroll

@@ -40,6 +40,7 @@ struct svm_model {
     bool prof = false;
     bool prof_valid = false;
     cudaEvent_t ev[5] = {};
+    unsigned int* calib_amax = nullptr;   // set only on a calibration model
     std::string last_error;
 };
 
@@ -515,6 +516,7 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
     a.f_out = (mode == kEval) ? out_dev : nullptr;
     a.f_stride = (n_scenes == 1) ? scene_off[1] : 0;
     a.paths3 = (flags & SVM_PATHS3) ? 1 : 0;
+    a.amax = m->calib_amax;
     void* tc_ws = ws + pl.o_chunk + align256((size_t)(M + 1) * 4);
     a.dev_err = static_cast<unsigned int*>(tc_ws);
     CK(cudaMemsetAsync(a.dev_err, 0, sizeof(unsigned int), stream));
@@ -588,6 +590,80 @@ svm_status svm_eval_pairs(svm_model* m, const double* q0, const double* q1, int3
     const int64_t off[2] = {0, n_points};
     return run_call(m, kEval, q0, q1, n_motions, nullptr, points_dev, off, 1, 0.0f, 1, 0u, nullptr, f_dev,
                     static_cast<cudaStream_t>(stream));
+}
+
+svm_status svm_calibrate_act_scales(svm_model* m, const double* q0, const double* q1, int32_t n_motions,
+                                    const float* points_dev, int64_t n_points, float headroom, float* scales_out)
+{
+    if (!m) return SVM_E_INVALID;
+    const svm_model_desc& d = m->desc;
+    if (d.prec != SVM_FP8_E4M3) return fail(m, SVM_E_INVALID, "activation scales apply to FP8 models only");
+    if (!(headroom >= 1.0f) || !std::isfinite(headroom)) return fail(m, SVM_E_INVALID, "headroom must be >= 1");
+    if (n_motions < 1 || n_points < 1) return fail(m, SVM_E_INVALID, "empty calibration set");
+    // the FP32 network on the model's rounded weights records the largest
+    // activation entering each hidden layer; scale = headroom * max / 448
+    svm_model_desc d32 = d;
+    d32.prec = SVM_FP32;
+    svm_model* c = nullptr;
+    svm_status st = svm_create_model(&d32, m->device, &c);
+    if (st != SVM_OK) return fail(m, st, "calibration model");
+    c->used = m->used;
+    {
+        // load the rounded weights as FP32 weights (they round to themselves)
+        const Layout Lo = layout_of(d);
+        std::vector<unsigned char> blob(28 + (size_t)(d.n_hidden + 2) * 8 + Lo.total * 4);
+        unsigned char* o = blob.data();
+        std::memcpy(o, "SVMW", 4);
+        const uint32_t hdr[5] = {1u, (uint32_t)(d.n_hidden + 2), 15u, (uint32_t)d.width, (uint32_t)d.act};
+        std::memcpy(o + 4, hdr, 20);
+        const float inf = INFINITY;
+        std::memcpy(o + 24, &inf, 4);
+        size_t off = 28;
+        long long pos = 0;
+        for (int l = 0; l < d.n_hidden + 2; ++l) {
+            const uint32_t out = l == d.n_hidden + 1 ? 1u : (uint32_t)d.width;
+            const uint32_t in = l == 0 ? 15u : (uint32_t)d.width;
+            std::memcpy(o + off, &out, 4);
+            std::memcpy(o + off + 4, &in, 4);
+            off += 8;
+            std::memcpy(o + off, m->used.data() + pos, ((size_t)out * in + out) * 4);
+            off += ((size_t)out * in + out) * 4;
+            pos += (long long)out * in + out;
+        }
+        st = svm_load_weights(c, blob.data(), blob.size());
+        if (st != SVM_OK) { svm_destroy_model(c); return fail(m, st, "calibration weights"); }
+    }
+    DeviceGuard g(m->device);
+    unsigned int* amax = nullptr;
+    if (cudaMalloc(&amax, sizeof(unsigned int) * d.n_hidden) != cudaSuccess) {
+        svm_destroy_model(c);
+        return fail(m, SVM_E_OOM, "calibration buffer");
+    }
+    cudaMemset(amax, 0, sizeof(unsigned int) * d.n_hidden);
+    c->calib_amax = amax;
+    float* fdev = nullptr;
+    if (cudaMalloc(&fdev, sizeof(float) * (size_t)n_motions * n_points) != cudaSuccess) {
+        cudaFree(amax);
+        svm_destroy_model(c);
+        return fail(m, SVM_E_OOM, "calibration buffer");
+    }
+    st = svm_eval_pairs(c, q0, q1, n_motions, points_dev, n_points, fdev, nullptr);
+    std::vector<unsigned int> h(d.n_hidden);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), amax, sizeof(unsigned int) * d.n_hidden, cudaMemcpyDeviceToHost);
+    cudaFree(fdev);
+    cudaFree(amax);
+    svm_destroy_model(c);
+    if (st != SVM_OK) return fail(m, st, "calibration run");
+    if (e != cudaSuccess) return fail(m, SVM_E_CUDA, cudaGetErrorString(e));
+    std::vector<float> sc(d.n_hidden);
+    for (int l = 0; l < d.n_hidden; ++l) {
+        float mx;
+        std::memcpy(&mx, &h[l], 4);
+        sc[l] = mx > 0.0f ? headroom * mx / 448.0f : 1.0f;
+    }
+    if (scales_out) std::memcpy(scales_out, sc.data(), sizeof(float) * d.n_hidden);
+    return svm_set_act_scales(m, sc.data(), d.n_hidden);
 }
 
 svm_status svm_profile_enable(svm_model* m, int on)

@@ -79,6 +79,7 @@ struct CallArgs {
     long long f_stride; // row stride of f_out (points per motion row)
     int paths3;         // motions form paths of 3 segments
     unsigned int* dev_err;  // per-call error word: nonzero if a bounded wait expired
+    unsigned int* amax;     // optional [L]: bit patterns of max |input of hidden layer l| (calibration)
 };
 
 // Model weights on the device.  FP32 copies are always present; the layer-1

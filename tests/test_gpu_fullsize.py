@@ -1,0 +1,90 @@
+"""Parity at the benchmark's full size, in the configuration bench.py times:
+64 bin-picking motions x the 200 000-point bin cloud, margin 0.03 m, 128
+steps, the network trained on GPU-generated data, gate calibrated on
+separate motions.
+
+The exact FP64 oracle over the whole workload is too slow for a test, so:
+  * every verdict is compared with the library's exact check of every pair
+    (the geometric check alone, SVM_VERIFY_ALL), and four motions spread over
+    the batch are checked against the FP64 oracle (Eq. 5) in full;
+  * the network output is compared with the FP64 oracle (same rounded
+    weights) on 20 000 pairs drawn at random from the 12.8 M.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2402_15281_gb300 import synth as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS, N, M, P = 0.03, 128, 64, 200_000
+SAMPLED = [0, 21, 42, 63]
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import paper_2402_15281_gb300 as svm
+    from paper_2402_15281_gb300 import training
+    svm.build()
+    robot = S.make_robot(1)
+    tq0, tq1 = training.bin_training_motions(robot, 1024, seed=41)
+    blob, hist = training.train_model(svm, robot, tq0, tq1, samples_per_motion=4096, steps=N, batch=65536,
+                                      epochs=30, patience=10)
+    pts = S.bin_cloud(P, seed=0)
+    q0, q1 = S.bin_motions(robot, M, seed=0)
+    pts_d = torch.from_numpy(pts).cuda()
+    dmin, coll = oracle.gcc_motion(robot, q0[SAMPLED], q1[SAMPLED], N, pts, EPS)
+    return svm, training, robot, blob, hist, pts, pts_d, q0, q1, dmin, coll
+
+
+def _check(svm, h, q0, q1, pts_d, flags):
+    res = svm.new_results(M)
+    svm.svm_check_motions(h, q0, q1, pts_d, EPS, N, flags, res)
+    torch.cuda.synchronize()
+    return svm.results_to_numpy(res)[:M]
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_full_size_verdicts_and_outputs(setup, prec):
+    svm, training, robot, blob, hist, pts, pts_d, q0, q1, dmin, coll = setup
+    h = svm.svm_create_model(robot, 256, 4, 0, prec, 0)
+    try:
+        svm.svm_load_weights(h, blob)
+        cq0, cq1 = S.bin_motions(robot, 16, seed=1000)
+        scales = None
+        if prec == 2:
+            scales = svm.svm_calibrate_act_scales(h, cq0, cq1, pts_d, 2.0)[:4].astype(np.float64)
+        tau = training.calibrate_tau(svm, h, robot, pts_d, EPS, N, cq0, cq1)
+        svm.svm_set_gate(h, tau)
+        r = _check(svm, h, q0, q1, pts_d, 0)                      # the bench's call
+        g = _check(svm, h, q0, q1, pts_d, svm.SVM_VERIFY_ALL | svm.SVM_NO_EARLY_EXIT)
+        assert np.all(r["status"] == 0) and np.all(g["status"] == 0)
+        np.testing.assert_array_equal(r["collision"], g["collision"])
+        np.testing.assert_array_equal(r["collision"][SAMPLED], coll)
+        assert np.abs(g["d_min"][SAMPLED] - dmin).max() <= 1e-5
+        frac = r["n_flagged"].sum() / (M * P)
+        print(f"prec {prec}: tau {tau:.4f} m, flagged {frac:.2%}, collisions {r['collision'].sum()}/{M}")
+        # per-pair network output on random pairs
+        f = torch.empty((M, P), device="cuda")
+        svm.svm_eval_pairs(h, q0, q1, pts_d, f)
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(prec)
+        mi, pi = rng.integers(0, M, 20000), rng.integers(0, P, 20000)
+        got = f[torch.from_numpy(mi).cuda(), torch.from_numpy(pi).cuda()].cpu().numpy().astype(np.float64)
+        del f
+        Pq = oracle.quantized_params(svm.parse_blob(blob), prec)
+        X = np.concatenate([pts[pi, :3].astype(np.float64), q0[mi], q1[mi]], axis=1)
+        ref = oracle.mlp_forward(Pq, 256, 4, 0, X)
+        err = np.abs(got - ref)
+        band = np.abs(ref - EPS) <= 0.1
+        print(f"prec {prec}: |f - f64| max {err.max():.2e} p99.9 {np.quantile(err, 0.999):.2e} "
+              f"mean {err.mean():.2e}; in the gate band (|f - eps| <= 0.1 m, {band.mean():.1%} of pairs) "
+              f"max {err[band].max() if band.any() else 0:.2e}")
+        if prec == 1:
+            assert np.quantile(err, 0.999) <= 2e-3 and err.max() <= 4e-3
+        else:
+            assert np.quantile(err[band], 0.99) <= 6e-3 and err.max() <= 5e-2
+    finally:
+        svm.svm_destroy_model(h)
