@@ -59,9 +59,9 @@ typedef enum { SVM_RELU = 0, SVM_SILU = 1 } svm_act;
  * j < 6 joins the origins of frames j and j+1, capsule 6 runs tool_len along
  * the z axis of frame 6; radius[j] is capsule j's radius.
  * Network: input [x, y, z, q0_1..q0_6, q1_1..q1_6] -> width (act) ->
- * n_hidden x (width -> width, act) -> 1.  width must be 256 for the BF16 and
- * FP8 tensor-core path; the FP32 path takes any width in [16, 512], a
- * multiple of 16. */
+ * n_hidden x (width -> width, act) -> 1.  The BF16 and FP8 tensor-core path
+ * needs width 256 and 1 <= n_hidden <= 8; the FP32 path takes width 64, 128,
+ * 256 or 512 and 0 <= n_hidden <= 16. */
 typedef struct {
     double dh[6][4];
     double radius[7];
