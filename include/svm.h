@@ -60,7 +60,7 @@ typedef enum { SVM_RELU = 0, SVM_SILU = 1 } svm_act;
  * the z axis of frame 6; radius[j] is capsule j's radius.
  * Network: input [x, y, z, q0_1..q0_6, q1_1..q1_6] -> width (act) ->
  * n_hidden x (width -> width, act) -> 1.  The BF16 and FP8 tensor-core path
- * needs width 256 and 1 <= n_hidden <= 8; the FP32 path takes width 64, 128,
+ * needs width 256 and 1 <= n_hidden <= 16; the FP32 path takes width 64, 128,
  * 256 or 512 and 0 <= n_hidden <= 16. */
 typedef struct {
     double dh[6][4];

@@ -131,13 +131,13 @@ __device__ __forceinline__ uint32_t act_chunk_addr(uint32_t base, int kb, int r,
 
 // z = v * scale + bias for 32 columns, activation, rounding, and store as
 // columns o0..o0+31 of row r of the next layer's A operand.
-template <int PREC, int ACT, class BiasFn>
-__device__ __forceinline__ void epilogue32(uint32_t base, int r, int o0, float (&v)[32], BiasFn bias4,
+template <int PREC, int ACT>
+__device__ __forceinline__ void epilogue32(uint32_t base, int r, int o0, float (&v)[32], const float* bias,
                                            float scale, float inv_next)
 {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        const float4 b4 = bias4(q);
+        const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + o0 + 4 * q));
         v[4 * q + 0] = fmaf(v[4 * q + 0], scale, b4.x);
         v[4 * q + 1] = fmaf(v[4 * q + 1], scale, b4.y);
         v[4 * q + 2] = fmaf(v[4 * q + 2], scale, b4.z);
@@ -174,7 +174,7 @@ __device__ __forceinline__ void epilogue32(uint32_t base, int r, int o0, float (
 template <int PREC, int ACT>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     mlp_tc_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ CUtensorMap w1map, CallArgs A,
-                  DevWeights Wt, const __grid_constant__ TcConst kc, int n_tiles)
+                  DevWeights Wt, int n_tiles)
 {
     using C = Cfg<PREC>;
     using SM = Smem<PREC>;
@@ -350,27 +350,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 if (!mbar_wait(accf_bar(s), acc_phase, abort_flag, A.dev_err)) { ok = false; break; }
                 acc_phase ^= 1u;
                 tc_fence_after();
-                const float* cb = A.cbias + (long long)m * WN;
-                const float* bl = kc.bh[l > 0 ? l - 1 : 0];
-                const float scale = (PREC == SVM_FP8_E4M3 && l > 0) ? kc.wscale[l - 1] * kc.ascale[l - 1] : 1.0f;
+                const float* bias = l == 0 ? A.cbias + (long long)m * WN : Wt.bh + (long long)(l - 1) * WN;
+                const float scale =
+                    (PREC == SVM_FP8_E4M3 && l > 0) ? __ldg(Wt.wscale + l - 1) * __ldg(Wt.ascale + l - 1) : 1.0f;
                 if (l + 1 < n_layers) {
-                    const float inv_next = PREC == SVM_FP8_E4M3 ? 1.0f / kc.ascale[l] : 1.0f;
+                    const float inv_next = PREC == SVM_FP8_E4M3 ? 1.0f / __ldg(Wt.ascale + l) : 1.0f;
 #pragma unroll 1
                     for (int o0 = 0; o0 < HALF_COLS; o0 += 32) {
                         float v[32];
                         tmem_ld32(t_row + (uint32_t)o0, v);
-                        const int c0 = col0 + o0;
-                        if (l == 0)
-                            epilogue32<PREC, ACT>(abase, r, c0, v,
-                                                  [&](int q) { return __ldg(reinterpret_cast<const float4*>(cb + c0 + 4 * q)); },
-                                                  scale, inv_next);
-                        else
-                            epilogue32<PREC, ACT>(abase, r, c0, v,
-                                                  [&](int q) {
-                                                      const float* b = bl + c0 + 4 * q;
-                                                      return make_float4(b[0], b[1], b[2], b[3]);
-                                                  },
-                                                  scale, inv_next);
+                        epilogue32<PREC, ACT>(abase, r, col0 + o0, v, bias, scale, inv_next);
                     }
                     fence_async_smem();
                     tc_fence_before();
@@ -382,11 +371,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     for (int o0 = 0; o0 < HALF_COLS; o0 += 32) {
                         float v[32];
                         tmem_ld32(t_row + (uint32_t)o0, v);
-                        const int c0 = col0 + o0;
 #pragma unroll
-                        for (int q = 0; q < 32; ++q) {
-                            const float bq = l == 0 ? __ldg(cb + c0 + q) : bl[c0 + q];
-                            f = fmaf(kc.wout[c0 + q], act_t<ACT>(fmaf(v[q], scale, bq)), f);
+                        for (int q = 0; q < 8; ++q) {
+                            const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + col0 + o0 + 4 * q));
+                            const float4 w4 = __ldg(reinterpret_cast<const float4*>(Wt.wout + col0 + o0 + 4 * q));
+                            f = fmaf(w4.x, act_t<ACT>(fmaf(v[4 * q + 0], scale, b4.x)), f);
+                            f = fmaf(w4.y, act_t<ACT>(fmaf(v[4 * q + 1], scale, b4.y)), f);
+                            f = fmaf(w4.z, act_t<ACT>(fmaf(v[4 * q + 2], scale, b4.z)), f);
+                            f = fmaf(w4.w, act_t<ACT>(fmaf(v[4 * q + 3], scale, b4.w)), f);
                         }
                     }
                     tc_fence_before();
@@ -394,7 +386,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     if (half == 1) red_s[r] = f;
                     named_sync(1 + s, 32 * EPI_PER_SLOT);
                     if (half == 0) {
-                        f += red_s[r] + kc.bout;
+                        f += red_s[r] + Wt.bout;
                         if (A.f_out != nullptr && valid) A.f_out[(long long)m * A.f_stride + (p - A.pbeg[m])] = f;
                         const bool flag = valid && f <= A.gate;
                         const unsigned mask = __ballot_sync(0xffffffffu, flag);
@@ -449,7 +441,7 @@ void launch_t(const TcModel& t, const CallArgs& a, const DevWeights& w, int n_ti
     }
     const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(t.wmap);
     const CUtensorMap* map1 = reinterpret_cast<const CUtensorMap*>(t.w1map);
-    mlp_tc_kernel<PREC, ACT><<<grid, NUM_THREADS, Smem<PREC>::DYN, s>>>(*map, *map1, a, w, t.kc, n_tiles);
+    mlp_tc_kernel<PREC, ACT><<<grid, NUM_THREADS, Smem<PREC>::DYN, s>>>(*map, *map1, a, w, n_tiles);
 }
 
 CUresult encode_2d(EncodeFn enc, CUtensorMap* map, CUtensorMapDataType dt, const void* gaddr, uint64_t inner,
@@ -469,27 +461,11 @@ int tc_tile_rows() { return TM; }
 
 size_t tc_workspace_bytes(int) { return 256; }
 
-int tc_prepare(TcModel& t, const svm_model_desc& d, const DevWeights& w, const float* used, const float* wscale,
-               const float* ascale)
+int tc_prepare(TcModel& t, const svm_model_desc& d, const DevWeights& w)
 {
     t.ready = false;
     t.prec = d.prec;
     t.act = d.act;
-    if (d.n_hidden < 1 || d.n_hidden > kTcMaxHidden) return -4;
-    {
-        // blob order: W1 [W][15], b1 [W], then per hidden layer W [W][W], b [W], then w_out [W], b_out
-        const long long W = WN;
-        long long off = W * 15 + W;
-        for (int l = 0; l < d.n_hidden; ++l) {
-            off += W * W;
-            for (int o = 0; o < WN; ++o) t.kc.bh[l][o] = used[off + o];
-            off += W;
-            t.kc.wscale[l] = d.prec == SVM_FP8_E4M3 ? wscale[l] : 1.0f;
-            t.kc.ascale[l] = d.prec == SVM_FP8_E4M3 ? ascale[l] : 1.0f;
-        }
-        for (int o = 0; o < WN; ++o) t.kc.wout[o] = used[off + o];
-        t.kc.bout = used[off + W];
-    }
     EncodeFn enc = get_encode();
     if (!enc || d.width != WN || !w.wq || !w.w1pad) return -1;
     const int elem = d.prec == SVM_BF16 ? 2 : 1;
@@ -505,11 +481,6 @@ int tc_prepare(TcModel& t, const svm_model_desc& d, const DevWeights& w, const f
 }
 
 void tc_release(TcModel& t) { t.ready = false; }
-
-void tc_set_act_scales(TcModel& t, const float* ascale, int n)
-{
-    for (int l = 0; l < n && l < kTcMaxHidden; ++l) t.kc.ascale[l] = ascale[l];
-}
 
 int tc_launch(TcModel& t, const CallArgs& a, const DevWeights& w, int n_tiles, void* ws, int n_sms, cudaStream_t s)
 {

@@ -133,7 +133,7 @@ svm_status svm_create_model(const svm_model_desc* desc, int device, svm_model** 
     if (d.prec == SVM_FP32) {
         if (!(d.width == 64 || d.width == 128 || d.width == 256 || d.width == 512)) return SVM_E_UNSUPPORTED;
     } else {
-        if (d.width != 256 || d.n_hidden < 1 || d.n_hidden > kTcMaxHidden) return SVM_E_UNSUPPORTED;
+        if (d.width != 256 || d.n_hidden < 1) return SVM_E_UNSUPPORTED;
     }
     int n_dev = 0;
     if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device < 0 || device >= n_dev) return SVM_E_INVALID;
@@ -199,7 +199,6 @@ svm_status svm_set_act_scales(svm_model* m, const float* scales, int32_t n)
     for (int i = 0; i < n; ++i)
         if (!(scales[i] > 0) || !std::isfinite(scales[i])) return fail(m, SVM_E_INVALID, "scale must be finite and > 0");
     m->ascales.assign(scales, scales + n);
-    tc_set_act_scales(m->tc, scales, n);
     if (m->has_weights && m->dw.ascale) {
         DeviceGuard g(m->device);
         CK(cudaMemcpy(const_cast<float*>(m->dw.ascale), scales, n * sizeof(float), cudaMemcpyHostToDevice));
@@ -345,7 +344,7 @@ svm_status svm_load_weights(svm_model* m, const void* blob, size_t bytes)
     CK(cudaGetLastError());
     CK(cudaDeviceSynchronize());
     if (d.prec != SVM_FP32) {
-        const int st = tc_prepare(m->tc, d, dw, m->used.data(), wscale.data(), m->ascales.data());
+        const int st = tc_prepare(m->tc, d, dw);
         if (st != 0) return fail(m, SVM_E_CUDA, "tensor-core path set-up failed");
     }
     m->tau = std::isfinite(tau) && tau >= 0 ? tau : INFINITY;
