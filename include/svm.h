@@ -176,6 +176,34 @@ svm_status svm_check_batch(svm_model* m, const double* q0, const double* q1,
                            int32_t n_scenes, float margin, int32_t steps, uint32_t flags,
                            svm_result* results_dev, void* stream);
 
+/* ------------------------------------------------------------ prepared batches
+ * A plan holds a fixed batch (motions, their scenes, margin, steps, flags)
+ * validated and uploaded once, with its own workspace (cudaMalloc at
+ * creation).  svm_plan_launch then only enqueues the kernels of one check
+ * (no host synchronisation, no allocation): it may be captured in a CUDA
+ * graph.  Results as in svm_check_batch; the model must outlive the plan.
+ * Weights or gate changed after creation apply to later launches, except
+ * that an instantiated graph keeps the gate it was captured with. */
+typedef struct svm_plan svm_plan;
+svm_status svm_plan_create(svm_model* m, const double* q0, const double* q1, int32_t n_motions,
+                           const int32_t* motion_scene, const int64_t* scene_offsets, int32_t n_scenes,
+                           float margin, int32_t steps, uint32_t flags, svm_plan** out);
+svm_status svm_plan_destroy(svm_plan* p);
+svm_status svm_plan_launch(svm_plan* p, const float* points_dev, svm_result* results_dev, void* stream);
+/* Replay the plan as a CUDA graph on `stream` (a created stream, not the
+ * default one).  The first call, and any call with other points or results
+ * pointers, runs one plain launch and captures the graph for the next calls. */
+svm_status svm_plan_graph_launch(svm_plan* p, const float* points_dev, svm_result* results_dev, void* stream);
+/* Verifier launch shape: points per thread (1, 2 or 4: one shared-memory read
+ * of a capsule serves that many points) and CTAs per SM (0 = all that fit). */
+svm_status svm_plan_set_verify_shape(svm_plan* p, int32_t points_per_thread, int32_t ctas_per_sm);
+/* Time every launch shape on the plan's data (3 launches each, CUDA events,
+ * synchronous), keep the fastest, and write a JSON report of all timings and
+ * the choice to `report` (may be NULL).  The report can be stored and the
+ * choice re-applied later with svm_plan_set_verify_shape. */
+svm_status svm_plan_autotune(svm_plan* p, const float* points_dev, svm_result* results_dev, void* stream,
+                             char* report, size_t capacity);
+
 /* Network output for every (motion, point) pair: f_dev[m * n_points + i] =
  * f(x_i, q0_m, q1_m) in the model precision (device, n_motions x n_points
  * floats).  Same kernels as the check, with the output stored. */

@@ -72,6 +72,15 @@ def lib():
         L.svm_check_batch.argtypes = [vp, vp, vp, i32, vp, vp, vp, i32, f32, i32, u32, vp, vp]
         L.svm_eval_pairs.argtypes = [vp, vp, vp, i32, vp, i64, vp, vp]
         L.svm_label_pairs.argtypes = [vp, vp, vp, i32, vp, i64, i32, vp, vp]
+        L.svm_plan_create.argtypes = [vp, vp, vp, i32, vp, vp, i32, f32, i32, u32, C.POINTER(vp)]
+        L.svm_plan_destroy.argtypes = [vp]
+        L.svm_plan_launch.argtypes = [vp, vp, vp, vp]
+        L.svm_plan_graph_launch.argtypes = [vp, vp, vp, vp]
+        L.svm_plan_set_verify_shape.argtypes = [vp, i32, i32]
+        L.svm_plan_autotune.argtypes = [vp, vp, vp, vp, C.c_char_p, sz]
+        for f in ("svm_plan_create", "svm_plan_destroy", "svm_plan_launch", "svm_plan_graph_launch",
+                  "svm_plan_set_verify_shape", "svm_plan_autotune"):
+            getattr(L, f).restype = C.c_int
         L.svm_calibrate_act_scales.argtypes = [vp, vp, vp, i32, vp, i64, f32, vp]
         L.svm_calibrate_act_scales.restype = C.c_int
         L.svm_check_motions_noalloc.argtypes = [vp, vp, vp, i32, vp, i64, f32, i32, u32, vp, vp]
@@ -251,6 +260,44 @@ def svm_check_batch(model, q0, q1, motion_scene, points_dev, scene_offsets, marg
         model, p0, p1, q0.shape[0], ms.ctypes.data_as(C.c_void_p), _dev(points_dev),
         so.ctypes.data_as(C.c_void_p), so.shape[0] - 1, float(margin), int(steps), int(flags),
         _dev(results_dev), _stream(stream)), model)
+
+
+class Plan:
+    """A prepared batch (svm_plan_*); `model` must stay alive."""
+
+    def __init__(self, model, q0, q1, motion_scene, scene_offsets, margin, steps, flags):
+        q0, p0 = _host_f64(q0)
+        q1, p1 = _host_f64(q1)
+        ms = np.ascontiguousarray(motion_scene, dtype=np.int32)
+        so = np.ascontiguousarray(scene_offsets, dtype=np.int64)
+        self.model = model
+        self.h = C.c_void_p()
+        _check("svm_plan_create", lib().svm_plan_create(
+            model, p0, p1, q0.shape[0], ms.ctypes.data_as(C.c_void_p), so.ctypes.data_as(C.c_void_p),
+            so.shape[0] - 1, float(margin), int(steps), int(flags), C.byref(self.h)), model)
+
+    def launch(self, points_dev, results_dev, stream=None):
+        _check("svm_plan_launch", lib().svm_plan_launch(self.h, _dev(points_dev), _dev(results_dev),
+                                                        _stream(stream)), self.model)
+
+    def graph_launch(self, points_dev, results_dev, stream):
+        _check("svm_plan_graph_launch", lib().svm_plan_graph_launch(self.h, _dev(points_dev), _dev(results_dev),
+                                                                    _stream(stream)), self.model)
+
+    def set_verify_shape(self, points_per_thread, ctas_per_sm):
+        _check("svm_plan_set_verify_shape", lib().svm_plan_set_verify_shape(self.h, int(points_per_thread),
+                                                                            int(ctas_per_sm)), self.model)
+
+    def autotune(self, points_dev, results_dev, stream=None) -> str:
+        buf = C.create_string_buffer(4096)
+        _check("svm_plan_autotune", lib().svm_plan_autotune(self.h, _dev(points_dev), _dev(results_dev),
+                                                            _stream(stream), buf, 4096), self.model)
+        return buf.value.decode()
+
+    def close(self):
+        if self.h:
+            _check("svm_plan_destroy", lib().svm_plan_destroy(self.h))
+            self.h = C.c_void_p()
 
 
 def svm_eval_pairs(model, q0, q1, points_dev, f_dev, stream=None):

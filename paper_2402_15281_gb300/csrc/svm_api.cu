@@ -16,33 +16,10 @@
 #include "svm.h"
 #include "svm_internal.cuh"
 #include "mlp_tc.cuh"
+#include "svm_model.h"
 
 using namespace svm;
 
-struct svm_model {
-    int device = 0;
-    int n_sms = 0;
-    int cc_major = 0, cc_minor = 0;
-    svm_model_desc desc{};
-    RobotParams rp{};
-    bool has_weights = false;
-    float tau = INFINITY;
-    std::vector<float> used;          // weights as used, blob order
-    std::vector<float> ascales;       // FP8 activation scales
-    void* d_weights = nullptr;        // one allocation for all weight arrays
-    DevWeights dw{};
-    TcModel tc{};                     // tensor-core path state (BF16 / FP8)
-    void* ws = nullptr;               // workspace
-    size_t ws_bytes = 0;
-    void* pinned = nullptr;           // host staging for per-call arrays
-    size_t pinned_bytes = 0;
-    cudaEvent_t staging_done = nullptr;
-    bool prof = false;
-    bool prof_valid = false;
-    cudaEvent_t ev[5] = {};
-    unsigned int* calib_amax = nullptr;   // set only on a calibration model
-    std::string last_error;
-};
 
 namespace {
 

@@ -145,7 +145,15 @@ __device__ __forceinline__ float capsule_min(const float (&mn)[kCaps], const Cap
 void launch_prologue(const CallArgs& a, const DevWeights& w, cudaStream_t s);
 void launch_mlp_fp32(const CallArgs& a, const DevWeights& w, int n_tiles, int bm, cudaStream_t s);
 int  mlp_fp32_tile_rows();
+// Verifier launch shape: points each thread checks per chunk (1, 2 or 4) and
+// resident CTAs per SM (0 = as many as shared memory allows, at most 8).
+struct VerifyConfig {
+    int points_per_thread = 2;
+    int ctas_per_sm = 0;
+};
 void launch_verify(const CallArgs& a, int range_mode, int strict_pass, cudaStream_t s, int n_sms);
+void launch_verify_cfg(const CallArgs& a, int range_mode, int strict_pass, cudaStream_t s, int n_sms,
+                       const VerifyConfig& cfg);
 void launch_finalize(const CallArgs& a, void* results, cudaStream_t s);
 void launch_label(const CallArgs& a, float* delta, long long stride, cudaStream_t s);
 void launch_quantize_bf16(const float* in, uint16_t* out, long long n, cudaStream_t s);

@@ -1,0 +1,37 @@
+// svm_model.h -- the model object behind the opaque svm_model handle (host).
+#pragma once
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "svm.h"
+#include "svm_internal.cuh"
+#include "mlp_tc.cuh"
+
+// The model owns its device weights, a workspace that grows on demand, a
+// pinned staging buffer for the per-call host arrays and the events that
+// guard them.
+struct svm_model {
+    int device = 0;
+    int n_sms = 0;
+    int cc_major = 0, cc_minor = 0;
+    svm_model_desc desc{};
+    svm::RobotParams rp{};
+    bool has_weights = false;
+    float tau = INFINITY;
+    std::vector<float> used;          // weights as used, blob order
+    std::vector<float> ascales;       // FP8 activation scales
+    void* d_weights = nullptr;        // one allocation for all weight arrays
+    svm::DevWeights dw{};
+    svm::TcModel tc{};                     // tensor-core path state (BF16 / FP8)
+    void* ws = nullptr;               // workspace
+    size_t ws_bytes = 0;
+    void* pinned = nullptr;           // host staging for per-call arrays
+    size_t pinned_bytes = 0;
+    cudaEvent_t staging_done = nullptr;
+    bool prof = false;
+    bool prof_valid = false;
+    cudaEvent_t ev[5] = {};
+    unsigned int* calib_amax = nullptr;   // set only on a calibration model
+    std::string last_error;
+};

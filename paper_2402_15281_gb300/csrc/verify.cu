@@ -20,8 +20,9 @@ namespace {
 
 constexpr int VT = 256;   // threads per CTA = points per chunk
 
-// chunk_off[m + 1] - chunk_off[m] = chunks of motion m; one CTA scans M.
-__global__ void plan_kernel(CallArgs A, int range_mode)
+// chunk_off[m + 1] - chunk_off[m] = chunks of `chunk` points of motion m;
+// one CTA scans the M motions.
+__global__ void plan_kernel(CallArgs A, int range_mode, int chunk)
 {
     __shared__ int carry;
     __shared__ int warp_sums[32];
@@ -32,7 +33,7 @@ __global__ void plan_kernel(CallArgs A, int range_mode)
         int c = 0;
         if (m < A.M) {
             const long long n = range_mode ? (A.pend[m] - A.pbeg[m]) : (long long)A.st[m].n_flagged;
-            c = (int)((n + VT - 1) / VT);
+            c = (int)((n + chunk - 1) / chunk);
         }
         // block inclusive scan
         int v = c;
@@ -73,7 +74,9 @@ __device__ int witness_sample(const Capsule* cs, int n_samples, float3 x, float 
     return n_samples - 1;
 }
 
-template <int RANGE>
+// One chunk = VT * PPT points of one motion; thread t checks points
+// t, t + VT, ..., so each capsule read from shared memory serves PPT points.
+template <int RANGE, int PPT>
 __global__ void __launch_bounds__(VT) verify_kernel(CallArgs A, int strict_pass)
 {
     extern __shared__ __align__(16) unsigned char vsm[];
@@ -112,25 +115,56 @@ __global__ void __launch_bounds__(VT) verify_kernel(CallArgs A, int strict_pass)
             cur_m = m;
             __syncthreads();
         }
-        const long long local = (long long)(c - A.chunk_off[m]) * VT + threadIdx.x;
+        const long long base = (long long)(c - A.chunk_off[m]) * VT * PPT + threadIdx.x;
         const long long n = RANGE ? (A.pend[m] - A.pbeg[m]) : (long long)A.st[m].n_flagged;
-        bool hit = false;
-        if (local < n) {
-            const long long p = RANGE ? A.pbeg[m] + local : (long long)A.idx[A.pair_off[m] + local];
-            const float4 x4 = __ldg(A.points + p);
-            const float3 x = make_float3(x4.x, x4.y, x4.z);
-            float mn[kCaps];
-            scan_samples(cs, n_samples, x, mn);
-            const float d = capsule_min(mn, cs);
-            hit = d <= A.margin;
+        float3 x[PPT];
+        long long pidx[PPT];
+        bool valid[PPT];
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+            const long long local = base + (long long)j * VT;
+            valid[j] = local < n;
+            pidx[j] = 0;
+            x[j] = make_float3(0.f, 0.f, 0.f);
+            if (valid[j]) {
+                pidx[j] = RANGE ? A.pbeg[m] + local : (long long)A.idx[A.pair_off[m] + local];
+                const float4 x4 = __ldg(A.points + pidx[j]);
+                x[j] = make_float3(x4.x, x4.y, x4.z);
+            }
+        }
+        float mn[PPT][kCaps];
+#pragma unroll
+        for (int j = 0; j < PPT; ++j)
+#pragma unroll
+            for (int q = 0; q < kCaps; ++q) mn[j][q] = __int_as_float(0x7f800000);
+        for (int k = 0; k < n_samples; ++k) {
+#pragma unroll
+            for (int q = 0; q < kCaps; ++q) {
+                const float4 ar = cs[k * kCaps + q].a_r;
+                const float4 ei = cs[k * kCaps + q].e_inv;
+#pragma unroll
+                for (int j = 0; j < PPT; ++j) {
+                    const float wx = x[j].x - ar.x, wy = x[j].y - ar.y, wz = x[j].z - ar.z;
+                    const float t = __saturatef(fmaf(wz, ei.z, fmaf(wy, ei.y, wx * ei.x)) * ei.w);
+                    const float dx = fmaf(-t, ei.x, wx), dy = fmaf(-t, ei.y, wy), dz = fmaf(-t, ei.z, wz);
+                    mn[j][q] = fminf(mn[j][q], fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+            if (!valid[j]) continue;
+            float d = __int_as_float(0x7f800000);
+#pragma unroll
+            for (int q = 0; q < kCaps; ++q) d = fminf(d, sqrtf(mn[j][q]) - cs[q].a_r.w);
             atomicAdd(&s_nver, 1u);
             if (fabsf(d - A.margin) < kAmbiguousBand) atomicAdd(&s_namb, 1u);
             atomicMin(&s_dkey, float_key(d));
-            if (hit) {
+            if (d <= A.margin) {
                 const int path_head = A.paths3 ? (m / 3) * 3 : m;
                 if (atomicCAS(&A.st[m].collided, 0, 1) == 0) {
-                    A.st[m].witness_point = (int)p;
-                    A.st[m].witness_step = witness_sample(cs, n_samples, x, A.margin);
+                    A.st[m].witness_point = (int)pidx[j];
+                    A.st[m].witness_step = witness_sample(cs, n_samples, x[j], A.margin);
                 }
                 if (path_head != m) atomicExch(&A.st[path_head].collided, 1);
             }
@@ -223,26 +257,46 @@ void configure_smem()
     static bool configured[64] = {};
     if (dev < 0 || dev >= 64 || configured[dev]) return;
     const int mx = (kMaxSteps + 1) * kCaps * (int)sizeof(Capsule);
-    cudaFuncSetAttribute(verify_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(verify_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(verify_kernel<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(verify_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(verify_kernel<0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(verify_kernel<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(verify_kernel<0, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(verify_kernel<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(label_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     configured[dev] = true;
 }
 }  // namespace
 
-void launch_verify(const CallArgs& a, int range_mode, int strict_pass, cudaStream_t s, int n_sms)
+void launch_verify_cfg(const CallArgs& a, int range_mode, int strict_pass, cudaStream_t s, int n_sms,
+                       const VerifyConfig& cfg)
 {
     if (a.M <= 0) return;
     configure_smem();
-    plan_kernel<<<1, 1024, 0, s>>>(a, range_mode);
+    const int ppt = (cfg.points_per_thread == 1 || cfg.points_per_thread == 4) ? cfg.points_per_thread : 2;
+    plan_kernel<<<1, 1024, 0, s>>>(a, range_mode, VT * ppt);
     const size_t smem = (size_t)(a.N + 1) * kCaps * sizeof(Capsule);
     // enough resident CTAs to fill the GPU: shared memory bounds CTAs per SM
     int per_sm = (int)((200 * 1024) / (smem + 2048));
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 8) per_sm = 8;
+    if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < per_sm) per_sm = cfg.ctas_per_sm;
     const int grid = n_sms * per_sm;
-    if (range_mode) verify_kernel<1><<<grid, VT, smem, s>>>(a, strict_pass);
-    else verify_kernel<0><<<grid, VT, smem, s>>>(a, strict_pass);
+    if (ppt == 1) {
+        if (range_mode) verify_kernel<1, 1><<<grid, VT, smem, s>>>(a, strict_pass);
+        else verify_kernel<0, 1><<<grid, VT, smem, s>>>(a, strict_pass);
+    } else if (ppt == 2) {
+        if (range_mode) verify_kernel<1, 2><<<grid, VT, smem, s>>>(a, strict_pass);
+        else verify_kernel<0, 2><<<grid, VT, smem, s>>>(a, strict_pass);
+    } else {
+        if (range_mode) verify_kernel<1, 4><<<grid, VT, smem, s>>>(a, strict_pass);
+        else verify_kernel<0, 4><<<grid, VT, smem, s>>>(a, strict_pass);
+    }
+}
+
+void launch_verify(const CallArgs& a, int range_mode, int strict_pass, cudaStream_t s, int n_sms)
+{
+    launch_verify_cfg(a, range_mode, strict_pass, s, n_sms, VerifyConfig{});
 }
 
 void launch_label(const CallArgs& a, float* delta, long long stride, cudaStream_t s)

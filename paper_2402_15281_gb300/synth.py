@@ -219,8 +219,8 @@ def _hit_box(o, d, c, R, half):
     with np.errstate(divide="ignore", invalid="ignore"):
         t1 = (-half[None, :] - ol[None, :]) / dl
         t2 = (half[None, :] - ol[None, :]) / dl
-    tn = np.nanmax(np.minimum(t1, t2), axis=1)
-    tf = np.nanmin(np.maximum(t1, t2), axis=1)
+    tn = np.fmax.reduce(np.minimum(t1, t2), axis=1)
+    tf = np.fmin.reduce(np.maximum(t1, t2), axis=1)
     ok = (tn <= tf) & (tn > 0)
     return np.where(ok, tn, np.inf)
 
@@ -253,16 +253,21 @@ def bin_cloud(n: int, seed: int = 0, noise: float = 0.002, scene: BinScene | Non
     looks straight down (60 x 45 deg field of view); rays at uniform image
     coordinates hit the bin's floor and four walls (with Gaussian range noise
     of ``noise`` metres) or one of the objects (no noise).  Rays that hit
-    nothing are dropped and more are cast until n hits are found."""
+    nothing are dropped and more are cast until n hits are found.  Only the
+    part of the image that can see the bin is sampled (every ray outside it
+    misses), which leaves the distribution of the hits unchanged."""
     sc = scene if scene is not None else make_bin_scene(seed)
     r = Rng(seed, S_CLOUD)
     lo = BIN_CENTER - BIN_SIZE / 2
     hi = BIN_CENTER + BIN_SIZE / 2
     got = []
     total = 0
-    batch = max(4 * n, 4096)
+    # image window that contains the bin seen from the camera (margin included)
+    ux = min(1.0, 1.1 * (BIN_SIZE[0] / 2) / (CAMERA[2] - hi[2]) / math.tan(FOV_X / 2))
+    uy = min(1.0, 1.1 * (BIN_SIZE[1] / 2) / (CAMERA[2] - hi[2]) / math.tan(FOV_Y / 2))
+    batch = max(2 * n, 4096)
     while total < n:
-        u = r.uniform(2 * batch, -1.0, 1.0).reshape(batch, 2)
+        u = r.uniform(2 * batch, -1.0, 1.0).reshape(batch, 2) * np.array([ux, uy])
         d = np.stack([u[:, 0] * math.tan(FOV_X / 2), u[:, 1] * math.tan(FOV_Y / 2),
                       -np.ones(batch)], axis=1)
         d /= np.linalg.norm(d, axis=1, keepdims=True)

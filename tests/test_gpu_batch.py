@@ -1,0 +1,139 @@
+"""Config 3: a batch of uneven scenes in one launch sequence.
+
+32 bin scenes with log-uniform cloud sizes in [10k, 500k] points (about
+4 M points), 16 motions per scene (512 motions, ~64 M pairs), checked with
+the plain FP32 path, BF16 and FP8 (trained network, calibrated gates), and
+as a prepared plan replayed through a CUDA graph with an autotuned verifier.
+
+Parity: every verdict of every precision equals the library's exact check of
+every pair (SVM_VERIFY_ALL), whose distances are compared with the FP64
+oracle (Eq. 5) on four motions in full; plan, graph replay and autotuned
+launches give the same records as svm_check_batch.
+"""
+import json
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2402_15281_gb300 import synth as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS, N, SCENES, PER = 0.03, 128, 32, 16
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import paper_2402_15281_gb300 as svm
+    from paper_2402_15281_gb300 import training
+    svm.build()
+    robot = S.make_robot(1)
+    sizes = np.round(np.exp(S.Rng(3, 77).uniform(SCENES, np.log(10_000), np.log(500_000)))).astype(np.int64)
+    clouds = [S.bin_cloud(int(n), seed=200 + s) for s, n in enumerate(sizes)]
+    pts = np.concatenate(clouds)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    q0s, q1s = [], []
+    for s in range(SCENES):
+        a, b = S.bin_motions(robot, PER, seed=300 + s)
+        q0s.append(a)
+        q1s.append(b)
+    q0, q1 = np.concatenate(q0s), np.concatenate(q1s)
+    scene = np.repeat(np.arange(SCENES, dtype=np.int32), PER)
+    tq0, tq1 = training.bin_training_motions(robot, 1024, seed=41)
+    blob, _ = training.train_model(svm, robot, tq0, tq1, samples_per_motion=4096, steps=N, batch=65536,
+                                   epochs=30, patience=10)
+    return svm, training, robot, sizes, clouds, torch.from_numpy(pts).cuda(), off, q0, q1, scene, blob
+
+
+DETERMINISTIC = ("status", "collision", "d_min", "dhat_min", "n_flagged", "n_verified", "n_ambiguous")
+
+
+def _same(a, b):
+    """Records agree on every field that does not depend on thread order
+    (the witness is whichever collision was found first)."""
+    for k in DETERMINISTIC:
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+def _batch(svm, h, s, flags):
+    svm_, training, robot, sizes, clouds, pts_d, off, q0, q1, scene, blob = s
+    res = svm.new_results(len(q0))
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    svm.svm_check_batch(h, q0, q1, scene, pts_d, off, EPS, N, flags, res)
+    torch.cuda.synchronize()
+    return svm.results_to_numpy(res)[:len(q0)].copy(), 1e3 * (time.perf_counter() - t)
+
+
+def test_uneven_batch_all_precisions(setup):
+    svm, training, robot, sizes, clouds, pts_d, off, q0, q1, scene, blob = setup
+    M = len(q0)
+    cq0, cq1 = S.bin_motions(robot, 16, seed=1000)
+    cal_pts = pts_d[off[0]:off[1]]
+    ref = None
+    for prec in (0, 1, 2):
+        h = svm.svm_create_model(robot, 256, 4, 0, prec, 0)
+        try:
+            svm.svm_load_weights(h, blob)
+            if prec == 2:
+                svm.svm_calibrate_act_scales(h, cq0, cq1, cal_pts, 2.0)
+            svm.svm_set_gate(h, training.calibrate_tau(svm, h, robot, cal_pts, EPS, N, cq0, cq1))
+            if ref is None:
+                ref, _ = _batch(svm, h, setup, svm.SVM_VERIFY_ALL | svm.SVM_NO_EARLY_EXIT)
+            _batch(svm, h, setup, 0)                                   # warm-up
+            r, ms = _batch(svm, h, setup, 0)
+            assert np.all(r["status"] == 0)
+            np.testing.assert_array_equal(r["collision"], ref["collision"])
+            print(f"prec {prec}: {M} motions, {int(sizes.sum()) * PER / 1e6:.1f} M pairs in {ms:.1f} ms "
+                  f"(wall), flagged {r['n_flagged'].sum() / (sizes.sum() * PER):.2%}")
+        finally:
+            svm.svm_destroy_model(h)
+    assert 0 < ref["collision"].sum() < M
+    # the exact check against the FP64 oracle on four motions of the smallest scenes
+    small = np.argsort(sizes)[:4]
+    for s in small:
+        m = s * PER
+        dmin, coll = oracle.gcc_motion(robot, q0[m:m + 1], q1[m:m + 1], N, clouds[s], EPS)
+        assert ref["collision"][m] == coll[0]
+        assert abs(ref["d_min"][m] - dmin[0]) <= 1e-5
+
+
+def test_plan_graph_and_autotune(setup):
+    svm, training, robot, sizes, clouds, pts_d, off, q0, q1, scene, blob = setup
+    M = len(q0)
+    h = svm.svm_create_model(robot, 256, 4, 0, svm.SVM_BF16, 0)
+    plan = None
+    try:
+        svm.svm_load_weights(h, blob)
+        cq0, cq1 = S.bin_motions(robot, 16, seed=1000)
+        svm.svm_set_gate(h, training.calibrate_tau(svm, h, robot, pts_d[off[0]:off[1]], EPS, N, cq0, cq1))
+        flags = svm.SVM_NO_EARLY_EXIT
+        want, _ = _batch(svm, h, setup, flags)
+        plan = svm.Plan(h, q0, q1, scene, off, EPS, N, flags)
+        stream = torch.cuda.Stream()
+        res = svm.new_results(M)
+        with torch.cuda.stream(stream):
+            plan.launch(pts_d, res, stream)
+            stream.synchronize()
+            _same(svm.results_to_numpy(res)[:M], want)
+            report = json.loads(plan.autotune(pts_d, res, stream))
+            assert len(report["candidates"]) == 9 and report["best"]["ms"] > 0
+            for _ in range(3):                 # capture, then two replays
+                res.zero_()
+                plan.graph_launch(pts_d, res, stream)
+                stream.synchronize()
+                _same(svm.results_to_numpy(res)[:M], want)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(5):
+                plan.graph_launch(pts_d, res, stream)
+            ev1.record(stream)
+            stream.synchronize()
+        print(f"autotune best {report['best']}; graph replay {ev0.elapsed_time(ev1) / 5:.2f} ms per batch")
+    finally:
+        if plan is not None:
+            plan.close()
+        svm.svm_destroy_model(h)
