@@ -169,6 +169,99 @@ __device__ __forceinline__ void epilogue32(uint32_t base, int r, int o0, float (
     }
 }
 
+// ---- packed FP32 pairs (sm_100+): two values per instruction
+__device__ __forceinline__ uint64_t f2(float lo, float hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+// max(v, 0) of both halves rounded to bfloat16, low half first
+__device__ __forceinline__ uint32_t relu_bf16x2(uint64_t v)
+{
+    uint32_t d;
+    asm("{\n .reg .f32 lo, hi;\n mov.b64 {lo, hi}, %1;\n cvt.rn.relu.bf16x2.f32 %0, hi, lo;\n}" : "=r"(d) : "l"(v));
+    return d;
+}
+// max(v, 0) of both halves rounded to E4M3 (saturating), low byte first
+__device__ __forceinline__ uint32_t relu_e4m3x2(uint64_t v)
+{
+    uint16_t d;
+    asm("{\n .reg .f32 lo, hi;\n mov.b64 {lo, hi}, %1;\n cvt.rn.satfinite.relu.e4m3x2.f32 %0, hi, lo;\n}"
+        : "=h"(d)
+        : "l"(v));
+    return d;
+}
+
+// Epilogue of 32 columns (o0..o0+31) of row r with ReLU, packed arithmetic:
+//   BF16:        h = relu(acc + b)                  -> bfloat16
+//   FP8 hidden:  h = relu(acc * c + b)  with c = s_w s_a / s_next and b
+//                already divided by s_next          -> E4M3
+//   FP8 layer 0: h = relu((acc + b) * c), c = 1 / s_next
+template <int PREC, bool LAYER0>
+__device__ __forceinline__ void epilogue32_relu(uint32_t base, int r, int o0, const float (&v)[32],
+                                                const float* bias, float c)
+{
+    const uint64_t c2 = f2(c, c);
+    uint32_t out[16];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + o0 + 4 * q));
+        const uint64_t a0 = f2(v[4 * q + 0], v[4 * q + 1]), a1 = f2(v[4 * q + 2], v[4 * q + 3]);
+        const uint64_t b0 = f2(b4.x, b4.y), b1 = f2(b4.z, b4.w);
+        uint64_t z0, z1;
+        if constexpr (PREC == SVM_BF16) {
+            z0 = f2_add(a0, b0);
+            z1 = f2_add(a1, b1);
+            out[2 * q + 0] = relu_bf16x2(z0);
+            out[2 * q + 1] = relu_bf16x2(z1);
+        } else {
+            if constexpr (LAYER0) {
+                z0 = f2_mul(f2_add(a0, b0), c2);
+                z1 = f2_mul(f2_add(a1, b1), c2);
+            } else {
+                z0 = f2_fma(a0, c2, b0);
+                z1 = f2_fma(a1, c2, b1);
+            }
+            out[2 * q + 0] = relu_e4m3x2(z0);
+            out[2 * q + 1] = relu_e4m3x2(z1);
+        }
+    }
+    if constexpr (PREC == SVM_BF16) {
+        const int kb = o0 >> 6, c0 = (o0 & 63) >> 3;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            st_shared_v4(act_chunk_addr(base, kb, r, c0 + k), out[4 * k + 0], out[4 * k + 1], out[4 * k + 2],
+                         out[4 * k + 3]);
+    } else {
+        // 16 E4M3 pairs (16 bits each) -> 8 words -> two 16-byte chunks
+        uint32_t w[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) w[k] = (out[2 * k] & 0xFFFFu) | (out[2 * k + 1] << 16);
+        const int kb = o0 >> 7, c0 = (o0 & 127) >> 4;
+        st_shared_v4(act_chunk_addr(base, kb, r, c0), w[0], w[1], w[2], w[3]);
+        st_shared_v4(act_chunk_addr(base, kb, r, c0 + 1), w[4], w[5], w[6], w[7]);
+    }
+}
+
 // ------------------------------------------------------------------ kernel
 
 template <int PREC, int ACT>
@@ -359,7 +452,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     for (int o0 = 0; o0 < HALF_COLS; o0 += 32) {
                         float v[32];
                         tmem_ld32(t_row + (uint32_t)o0, v);
-                        epilogue32<PREC, ACT>(abase, r, col0 + o0, v, bias, scale, inv_next);
+                        if constexpr (ACT == SVM_RELU) {
+                            if (PREC == SVM_FP8_E4M3 && l == 0)
+                                epilogue32_relu<PREC, true>(abase, r, col0 + o0, v, bias, inv_next);
+                            else if (PREC == SVM_FP8_E4M3)
+                                epilogue32_relu<PREC, false>(abase, r, col0 + o0, v,
+                                                             Wt.bhs + (long long)(l - 1) * WN, scale * inv_next);
+                            else
+                                epilogue32_relu<PREC, false>(abase, r, col0 + o0, v, bias, 1.0f);
+                        } else {
+                            epilogue32<PREC, ACT>(abase, r, col0 + o0, v, bias, scale, inv_next);
+                        }
                     }
                     fence_async_smem();
                     tc_fence_before();
@@ -367,6 +470,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     if (lane == 0) mbar_arrive(epid_bar(s));
                 } else {
                     float f = 0.0f;
+                    uint64_t f2acc = f2(0.0f, 0.0f);
+                    const uint64_t s2 = f2(scale, scale);
 #pragma unroll 1
                     for (int o0 = 0; o0 < HALF_COLS; o0 += 32) {
                         float v[32];
@@ -375,11 +480,26 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         for (int q = 0; q < 8; ++q) {
                             const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + col0 + o0 + 4 * q));
                             const float4 w4 = __ldg(reinterpret_cast<const float4*>(Wt.wout + col0 + o0 + 4 * q));
-                            f = fmaf(w4.x, act_t<ACT>(fmaf(v[4 * q + 0], scale, b4.x)), f);
-                            f = fmaf(w4.y, act_t<ACT>(fmaf(v[4 * q + 1], scale, b4.y)), f);
-                            f = fmaf(w4.z, act_t<ACT>(fmaf(v[4 * q + 2], scale, b4.z)), f);
-                            f = fmaf(w4.w, act_t<ACT>(fmaf(v[4 * q + 3], scale, b4.w)), f);
+                            if constexpr (ACT == SVM_RELU) {
+                                uint64_t z0 = f2_fma(f2(v[4 * q + 0], v[4 * q + 1]), s2, f2(b4.x, b4.y));
+                                uint64_t z1 = f2_fma(f2(v[4 * q + 2], v[4 * q + 3]), s2, f2(b4.z, b4.w));
+                                float z0l, z0h, z1l, z1h;
+                                asm("mov.b64 {%0, %1}, %2;" : "=f"(z0l), "=f"(z0h) : "l"(z0));
+                                asm("mov.b64 {%0, %1}, %2;" : "=f"(z1l), "=f"(z1h) : "l"(z1));
+                                f2acc = f2_fma(f2(w4.x, w4.y), f2(fmaxf(z0l, 0.0f), fmaxf(z0h, 0.0f)), f2acc);
+                                f2acc = f2_fma(f2(w4.z, w4.w), f2(fmaxf(z1l, 0.0f), fmaxf(z1h, 0.0f)), f2acc);
+                            } else {
+                                f = fmaf(w4.x, act_t<ACT>(fmaf(v[4 * q + 0], scale, b4.x)), f);
+                                f = fmaf(w4.y, act_t<ACT>(fmaf(v[4 * q + 1], scale, b4.y)), f);
+                                f = fmaf(w4.z, act_t<ACT>(fmaf(v[4 * q + 2], scale, b4.z)), f);
+                                f = fmaf(w4.w, act_t<ACT>(fmaf(v[4 * q + 3], scale, b4.w)), f);
+                            }
                         }
+                    }
+                    {
+                        float lo, hi;
+                        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(f2acc));
+                        f += lo + hi;
                     }
                     tc_fence_before();
                     // the two column halves of a row meet in shared memory

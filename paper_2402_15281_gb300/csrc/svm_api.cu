@@ -81,6 +81,21 @@ bool finite_all(const double* p, long long n)
     return true;
 }
 
+// FP8: hidden biases divided by the activation scale of the layer they feed
+// (b_l / ascale[l] for hidden layers l < L-1, 0-based), the form the packed
+// epilogue adds after its single rescaling multiply.
+svm_status upload_scaled_biases(svm_model* m)
+{
+    const long long W = m->desc.width, L = m->desc.n_hidden;
+    if (!m->dw.bhs || (long long)m->bh_host.size() != L * W) return SVM_OK;
+    std::vector<float> bhs(L * W, 0.0f);
+    for (long long l = 0; l + 1 < L; ++l)
+        for (long long o = 0; o < W; ++o) bhs[l * W + o] = m->bh_host[l * W + o] / m->ascales[l + 1];
+    const cudaError_t e = cudaMemcpy(const_cast<float*>(m->dw.bhs), bhs.data(), L * W * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(m, SVM_E_CUDA, std::string("bias upload: ") + cudaGetErrorString(e));
+    return SVM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -179,6 +194,8 @@ svm_status svm_set_act_scales(svm_model* m, const float* scales, int32_t n)
     if (m->has_weights && m->dw.ascale) {
         DeviceGuard g(m->device);
         CK(cudaMemcpy(const_cast<float*>(m->dw.ascale), scales, n * sizeof(float), cudaMemcpyHostToDevice));
+        const svm_status st = upload_scaled_biases(m);
+        if (st != SVM_OK) return st;
     }
     return SVM_OK;
 }
@@ -293,7 +310,7 @@ svm_status svm_load_weights(svm_model* m, const void* blob, size_t bytes)
                  n_wT = align256(L * W * W * 4), n_bh = align256(std::max<long long>(1, L * W) * 4),
                  n_wout = align256(W * 4), n_wq = align256(std::max<long long>(1, L * W * W * 2)),
                  n_sc = align256(std::max<long long>(1, L) * 4);
-    const size_t total = n_w1x + n_w1q + n_b1 + n_wT + n_bh + n_wout + n_wq + 2 * n_sc + n_w1pad;
+    const size_t total = n_w1x + n_w1q + n_b1 + n_wT + n_bh + n_wout + n_wq + 2 * n_sc + n_w1pad + n_bh;
     if (m->d_weights) { cudaFree(m->d_weights); m->d_weights = nullptr; }
     if (cudaMalloc(&m->d_weights, total) != cudaSuccess) return fail(m, SVM_E_OOM, "weights allocation failed");
     char* base = static_cast<char*>(m->d_weights);
@@ -317,6 +334,12 @@ svm_status svm_load_weights(svm_model* m, const void* blob, size_t bytes)
     dw.wscale = (const float*)put(wscale.data(), L * 4, n_sc);
     dw.ascale = (const float*)put(m->ascales.data(), L * 4, n_sc);
     dw.w1pad = put(w1pad.data(), w1pad.size() * 2, n_w1pad);
+    m->bh_host = bh;
+    dw.bhs = (const float*)put(nullptr, 0, n_bh);
+    {
+        const svm_status st2 = upload_scaled_biases(m);
+        if (st2 != SVM_OK) return st2;
+    }
     dw.bout = u[Lo.out_b];
     CK(cudaGetLastError());
     CK(cudaDeviceSynchronize());

@@ -99,6 +99,8 @@ struct DevWeights {
                           // (x_hi, y_hi, z_hi, x_lo, y_lo, z_lo, 0, ...)
     const float* wscale;  // [L] per-layer weight scale (FP8), else 1
     const float* ascale;  // [L] per-layer activation scale (FP8), else 1
+    const float* bhs;     // FP8: [L][W] hidden biases divided by the next layer's
+                          // activation scale (b_l / ascale[l], l < L-1)
 };
 
 __device__ __forceinline__ float act_fn(float z, int act) {

@@ -21,6 +21,7 @@ struct svm_model {
     float tau = INFINITY;
     std::vector<float> used;          // weights as used, blob order
     std::vector<float> ascales;       // FP8 activation scales
+    std::vector<float> bh_host;       // hidden biases [L][W] (for the FP8 scaled copy)
     void* d_weights = nullptr;        // one allocation for all weight arrays
     svm::DevWeights dw{};
     svm::TcModel tc{};                     // tensor-core path state (BF16 / FP8)
