@@ -356,56 +356,63 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
-        if (lane == 0) {
-            int stage = 0;
-            uint32_t phase = 0;
-            uint32_t epi_phase[2] = {0u, 0u};
-            bool ok = true;
-            for (int j = 0; j < n_pairs && ok; ++j) {
-                const int nslots = min(2, n_mine - 2 * j);
-                for (int l = 0; l < n_layers && ok; ++l) {
-                    const int slices = l == 0 ? 1 : C::SLICES;
-                    const int layer_stage = stage;
-                    const uint32_t layer_phase = phase;
-                    for (int s = 0; s < nslots && ok; ++s) {
-                        if (!mbar_wait(epid_bar(s), epi_phase[s], abort_flag, A.dev_err)) { ok = false; break; }
-                        epi_phase[s] ^= 1u;
-                        tc_fence_after();
-                        if (C::REUSE == 2) { stage = layer_stage; phase = layer_phase; }
-                        const uint32_t d_tmem = tmem_base + (uint32_t)(s * WN);
-                        for (int kk = 0; kk < slices; ++kk) {
-                            const bool first_use = C::REUSE == 1 || s == 0;
-                            if (first_use) {
-                                if (!mbar_wait(full_bar(stage), phase, abort_flag, A.dev_err)) { ok = false; break; }
-                                tc_fence_after();
-                            }
-                            const uint32_t a0 = act_base(s) + kk * KBLOCK_BYTES;
-                            const uint32_t b0 = w_base + stage * STAGE_BYTES;
-                            if (l == 0) {
-                                mma_bf16(d_tmem, sdesc(a0), sdesc(b0), 0u);
-                            } else {
-#pragma unroll
-                                for (int k = 0; k < C::MMAS; ++k) {
-                                    if constexpr (PREC == SVM_BF16)
-                                        mma_bf16(d_tmem, sdesc(a0 + k * 32), sdesc(b0 + k * 32), (kk | k) != 0 ? 1u : 0u);
-                                    else
-                                        mma_e4m3(d_tmem, sdesc(a0 + k * 32), sdesc(b0 + k * 32), (kk | k) != 0 ? 1u : 0u);
-                                }
-                            }
-                            const bool last_use = C::REUSE == 1 || s == nslots - 1;
-                            if (last_use) mma_commit(empty_bar(stage));
-                            if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
+        // The whole warp runs the loop (warp-uniform control flow); one
+        // elected lane issues each MMA and commit.  Descriptors are built
+        // once: advancing K by 32 bytes inside a swizzle atom adds 2 to the
+        // start-address field, a 128-byte K-block of the activations adds
+        // KBLOCK_BYTES >> 4.
+        const uint64_t a_desc[2] = {sdesc(act_base(0)), sdesc(act_base(1))};
+        const uint64_t b_desc0 = sdesc(w_base);
+        constexpr uint32_t IDESC = PREC == SVM_BF16 ? IDESC_BF16 : IDESC_E4M3;
+        int stage = 0;
+        uint32_t phase = 0;
+        uint32_t epi_phase[2] = {0u, 0u};
+        bool ok = true;
+        for (int j = 0; j < n_pairs && ok; ++j) {
+            const int nslots = min(2, n_mine - 2 * j);
+            for (int l = 0; l < n_layers && ok; ++l) {
+                const int slices = l == 0 ? 1 : C::SLICES;
+                const int layer_stage = stage;
+                const uint32_t layer_phase = phase;
+                for (int s = 0; s < nslots && ok; ++s) {
+                    if (!mbar_wait_warp(epid_bar(s), epi_phase[s], abort_flag, A.dev_err)) { ok = false; break; }
+                    epi_phase[s] ^= 1u;
+                    tc_fence_after();
+                    if (C::REUSE == 2) { stage = layer_stage; phase = layer_phase; }
+                    const uint32_t d_tmem = tmem_base + (uint32_t)(s * WN);
+                    for (int kk = 0; kk < slices; ++kk) {
+                        const bool first_use = C::REUSE == 1 || s == 0;
+                        if (first_use) {
+                            if (!mbar_wait_warp(full_bar(stage), phase, abort_flag, A.dev_err)) { ok = false; break; }
+                            tc_fence_after();
                         }
-                        if (ok) mma_commit(accf_bar(s));
+                        const uint64_t ad = a_desc[s] + (uint64_t)(kk * (KBLOCK_BYTES >> 4));
+                        const uint64_t bd = b_desc0 + (uint64_t)(stage * (STAGE_BYTES >> 4));
+                        if (l == 0) {
+                            mma_f16_warp(d_tmem, ad, bd, IDESC_BF16, 0u);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < C::MMAS; ++k) {
+                                if constexpr (PREC == SVM_BF16)
+                                    mma_f16_warp(d_tmem, ad + 2 * k, bd + 2 * k, IDESC, (kk | k) != 0 ? 1u : 0u);
+                                else
+                                    mma_f8f6f4_warp(d_tmem, ad + 2 * k, bd + 2 * k, IDESC, (kk | k) != 0 ? 1u : 0u);
+                            }
+                        }
+                        const bool last_use = C::REUSE == 1 || s == nslots - 1;
+                        if (last_use) mma_commit_warp(empty_bar(stage));
+                        if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
                     }
+                    if (ok) mma_commit_warp(accf_bar(s));
                 }
             }
-            // every MMA issued by this thread has completed before TMEM is freed
-            mma_commit(drain_bar);
-            const uint64_t t0 = globaltimer();
-            while (!mbar_try(drain_bar, 0u) && globaltimer() - t0 < kTimeoutNs) {
-            }
         }
+        // every MMA issued by this warp has completed before TMEM is freed
+        mma_commit_warp(drain_bar);
+        const uint64_t t0 = globaltimer();
+        while (!mbar_try(drain_bar, 0u) && globaltimer() - t0 < kTimeoutNs) {
+        }
+        __syncwarp();
     } else {
         // ------------------------------------------------ epilogue warps
         const int ew = warp - 2;

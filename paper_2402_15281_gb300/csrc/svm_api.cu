@@ -612,6 +612,7 @@ svm_status svm_calibrate_act_scales(svm_model* m, const double* q0, const double
         // load the rounded weights as FP32 weights (they round to themselves)
         const Layout Lo = layout_of(d);
         std::vector<unsigned char> blob(28 + (size_t)(d.n_hidden + 2) * 8 + Lo.total * 4);
+        if (blob.size() < 28) { svm_destroy_model(c); return fail(m, SVM_E_INVALID, "calibration blob size"); }
         unsigned char* o = blob.data();
         std::memcpy(o, "SVMW", 4);
         const uint32_t hdr[5] = {1u, (uint32_t)(d.n_hidden + 2), 15u, (uint32_t)d.width, (uint32_t)d.act};

@@ -53,10 +53,11 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
 
 // Bounded wait for the phase of `parity` to complete.  On expiry: record the
 // error, raise the CTA's abort flag, return false.  Also returns false as
-// soon as another role has aborted.
-static __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, unsigned* err)
+// soon as another role has aborted.  The first test is inline (a completed
+// phase costs one try_wait); the polling loop is out of line.
+static __device__ __noinline__ bool mbar_wait_poll(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                                   unsigned* err)
 {
-    if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try(bar, parity)) return true;
@@ -69,6 +70,20 @@ static __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, vol
             }
         }
     }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, unsigned* err)
+{
+    if (mbar_try(bar, parity)) return true;
+    return mbar_wait_poll(bar, parity, abort_flag, err);
+}
+
+// The same wait taken by all 32 lanes of a warp; the warp agrees on the
+// outcome (any lane that gave up makes it false for all).
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, volatile int* abort_flag, unsigned* err)
+{
+    const bool ok = mbar_wait(bar, parity, abort_flag, err);
+    return __all_sync(0xffffffffu, ok);
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar)
@@ -113,6 +128,37 @@ __device__ __forceinline__ void mma_f8f6f4(uint32_t tmem_d, uint64_t adesc, uint
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Warp-wide forms: all 32 lanes execute them with the same operands and one
+// lane, chosen by elect.sync, issues the instruction.  Keeping the issuing
+// loop warp-uniform lets its address arithmetic stay on the uniform datapath.
+__device__ __forceinline__ void mma_f16_warp(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                             uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred e, p;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_f8f6f4_warp(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                                uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred e, p;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit_warp(uint32_t bar)
+{
+    asm volatile(
+        "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+        " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}" ::"r"(bar)
         : "memory");
 }
 
