@@ -169,6 +169,16 @@ __device__ __forceinline__ void epilogue32(uint32_t base, int r, int o0, float (
     }
 }
 
+// 16-byte global load that does not allocate in L1
+__device__ __forceinline__ float4 ld_stream_f4(const float4* p)
+{
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+
 // ---- packed FP32 pairs (sm_100+): two values per instruction
 __device__ __forceinline__ uint64_t f2(float lo, float hi)
 {
@@ -253,6 +263,45 @@ __device__ __forceinline__ void epilogue32_relu(uint32_t base, int r, int o0, co
                          out[4 * k + 3]);
     } else {
         // 16 E4M3 pairs (16 bits each) -> 8 words -> two 16-byte chunks
+        uint32_t w[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) w[k] = (out[2 * k] & 0xFFFFu) | (out[2 * k + 1] << 16);
+        const int kb = o0 >> 7, c0 = (o0 & 127) >> 4;
+        st_shared_v4(act_chunk_addr(base, kb, r, c0), w[0], w[1], w[2], w[3]);
+        st_shared_v4(act_chunk_addr(base, kb, r, c0 + 1), w[4], w[5], w[6], w[7]);
+    }
+}
+
+// The same with the 32 biases of the chunk held one per lane (lane i holds
+// the bias of column o0 + i) and broadcast by shuffles: no memory access on
+// the path from the accumulator to the stores.
+template <int PREC, bool LAYER0>
+__device__ __forceinline__ void epilogue32_relu_lane(uint32_t base, int r, int o0, const float (&v)[32], float bl,
+                                                     float c)
+{
+    const uint64_t c2 = f2(c, c);
+    uint32_t out[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const uint64_t a = f2(v[2 * q], v[2 * q + 1]);
+        const uint64_t b = f2(__shfl_sync(0xffffffffu, bl, 2 * q), __shfl_sync(0xffffffffu, bl, 2 * q + 1));
+        uint64_t z;
+        if constexpr (PREC == SVM_BF16) {
+            z = f2_add(a, b);
+            out[q] = relu_bf16x2(z);
+        } else {
+            if constexpr (LAYER0) z = f2_mul(f2_add(a, b), c2);
+            else z = f2_fma(a, c2, b);
+            out[q] = relu_e4m3x2(z);
+        }
+    }
+    if constexpr (PREC == SVM_BF16) {
+        const int kb = o0 >> 6, c0 = (o0 & 63) >> 3;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            st_shared_v4(act_chunk_addr(base, kb, r, c0 + k), out[4 * k + 0], out[4 * k + 1], out[4 * k + 2],
+                         out[4 * k + 3]);
+    } else {
         uint32_t w[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) w[k] = (out[2 * k] & 0xFFFFu) | (out[2 * k + 1] << 16);
@@ -361,7 +410,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         // once: advancing K by 32 bytes inside a swizzle atom adds 2 to the
         // start-address field, a 128-byte K-block of the activations adds
         // KBLOCK_BYTES >> 4.
-        const uint64_t a_desc[2] = {sdesc(act_base(0)), sdesc(act_base(1))};
+        const uint64_t a_desc0 = sdesc(act_base(0)), a_desc1 = sdesc(act_base(1));
         const uint64_t b_desc0 = sdesc(w_base);
         constexpr uint32_t IDESC = PREC == SVM_BF16 ? IDESC_BF16 : IDESC_E4M3;
         int stage = 0;
@@ -386,7 +435,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                             if (!mbar_wait_warp(full_bar(stage), phase, abort_flag, A.dev_err)) { ok = false; break; }
                             tc_fence_after();
                         }
-                        const uint64_t ad = a_desc[s] + (uint64_t)(kk * (KBLOCK_BYTES >> 4));
+                        const uint64_t ad = (s == 0 ? a_desc0 : a_desc1) + (uint64_t)(kk * (KBLOCK_BYTES >> 4));
                         const uint64_t bd = b_desc0 + (uint64_t)(stage * (STAGE_BYTES >> 4));
                         if (l == 0) {
                             mma_f16_warp(d_tmem, ad, bd, IDESC_BF16, 0u);
@@ -433,7 +482,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const bool valid = p < A.pend[m];
             // ---- A operand of layer 0: (x_hi, y_hi, z_hi, x_lo, y_lo, z_lo, 0, ...)
             if (half == 0) {
-                const float4 x = valid ? __ldg(A.points + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+                // streamed once per tile: kept out of L1 so that the bias vectors stay there
+                const float4 x = valid ? ld_stream_f4(A.points + p) : make_float4(0.f, 0.f, 0.f, 0.f);
                 // hi parts are the nearest bfloat16; the differences are exact in FP32
                 const float xl = x.x - __bfloat162float(__float2bfloat16_rn(x.x));
                 const float yl = x.y - __bfloat162float(__float2bfloat16_rn(x.y));
@@ -447,10 +497,29 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             if (lane == 0) mbar_arrive(epid_bar(s));
             // ---- layers
             for (int l = 0; l < n_layers; ++l) {
+                const float* bias = l == 0 ? A.cbias + (long long)m * WN : Wt.bh + (long long)(l - 1) * WN;
+                // ReLU hidden layers: the 128 biases of this warp's columns, one
+                // per lane per 32-column chunk, loaded before the accumulator wait
+                // (the output layer also takes its output weights the same way)
+                float bl0 = 0.0f, bl1 = 0.0f, bl2 = 0.0f, bl3 = 0.0f;
+                float wl0 = 0.0f, wl1 = 0.0f, wl2 = 0.0f, wl3 = 0.0f;
+                if (ACT == SVM_RELU) {
+                    const float* bsrc =
+                        (PREC == SVM_FP8_E4M3 && l > 0 && l + 1 < n_layers) ? Wt.bhs + (long long)(l - 1) * WN : bias;
+                    bl0 = __ldg(bsrc + col0 + lane);
+                    bl1 = __ldg(bsrc + col0 + 32 + lane);
+                    bl2 = __ldg(bsrc + col0 + 64 + lane);
+                    bl3 = __ldg(bsrc + col0 + 96 + lane);
+                    if (l + 1 == n_layers) {
+                        wl0 = __ldg(Wt.wout + col0 + lane);
+                        wl1 = __ldg(Wt.wout + col0 + 32 + lane);
+                        wl2 = __ldg(Wt.wout + col0 + 64 + lane);
+                        wl3 = __ldg(Wt.wout + col0 + 96 + lane);
+                    }
+                }
                 if (!mbar_wait(accf_bar(s), acc_phase, abort_flag, A.dev_err)) { ok = false; break; }
                 acc_phase ^= 1u;
                 tc_fence_after();
-                const float* bias = l == 0 ? A.cbias + (long long)m * WN : Wt.bh + (long long)(l - 1) * WN;
                 const float scale =
                     (PREC == SVM_FP8_E4M3 && l > 0) ? __ldg(Wt.wscale + l - 1) * __ldg(Wt.ascale + l - 1) : 1.0f;
                 if (l + 1 < n_layers) {
@@ -461,12 +530,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         tmem_ld32(t_row + (uint32_t)o0, v);
                         if constexpr (ACT == SVM_RELU) {
                             if (PREC == SVM_FP8_E4M3 && l == 0)
-                                epilogue32_relu<PREC, true>(abase, r, col0 + o0, v, bias, inv_next);
+                                epilogue32_relu_lane<PREC, true>(abase, r, col0 + o0, v, bl0, inv_next);
                             else if (PREC == SVM_FP8_E4M3)
-                                epilogue32_relu<PREC, false>(abase, r, col0 + o0, v,
-                                                             Wt.bhs + (long long)(l - 1) * WN, scale * inv_next);
+                                epilogue32_relu_lane<PREC, false>(abase, r, col0 + o0, v, bl0, scale * inv_next);
                             else
-                                epilogue32_relu<PREC, false>(abase, r, col0 + o0, v, bias, 1.0f);
+                                epilogue32_relu_lane<PREC, false>(abase, r, col0 + o0, v, bl0, 1.0f);
+                            bl0 = bl1;
+                            bl1 = bl2;
+                            bl2 = bl3;
                         } else {
                             epilogue32<PREC, ACT>(abase, r, col0 + o0, v, bias, scale, inv_next);
                         }
@@ -483,19 +554,31 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     for (int o0 = 0; o0 < HALF_COLS; o0 += 32) {
                         float v[32];
                         tmem_ld32(t_row + (uint32_t)o0, v);
+                        if constexpr (ACT == SVM_RELU) {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) {
+                                const uint64_t b = f2(__shfl_sync(0xffffffffu, bl0, 2 * q),
+                                                      __shfl_sync(0xffffffffu, bl0, 2 * q + 1));
+                                const uint64_t w = f2(__shfl_sync(0xffffffffu, wl0, 2 * q),
+                                                      __shfl_sync(0xffffffffu, wl0, 2 * q + 1));
+                                const uint64_t z = f2_fma(f2(v[2 * q], v[2 * q + 1]), s2, b);
+                                float zl, zh;
+                                asm("mov.b64 {%0, %1}, %2;" : "=f"(zl), "=f"(zh) : "l"(z));
+                                f2acc = f2_fma(w, f2(fmaxf(zl, 0.0f), fmaxf(zh, 0.0f)), f2acc);
+                            }
+                            bl0 = bl1;
+                            bl1 = bl2;
+                            bl2 = bl3;
+                            wl0 = wl1;
+                            wl1 = wl2;
+                            wl2 = wl3;
+                            continue;
+                        }
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
                             const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + col0 + o0 + 4 * q));
                             const float4 w4 = __ldg(reinterpret_cast<const float4*>(Wt.wout + col0 + o0 + 4 * q));
-                            if constexpr (ACT == SVM_RELU) {
-                                uint64_t z0 = f2_fma(f2(v[4 * q + 0], v[4 * q + 1]), s2, f2(b4.x, b4.y));
-                                uint64_t z1 = f2_fma(f2(v[4 * q + 2], v[4 * q + 3]), s2, f2(b4.z, b4.w));
-                                float z0l, z0h, z1l, z1h;
-                                asm("mov.b64 {%0, %1}, %2;" : "=f"(z0l), "=f"(z0h) : "l"(z0));
-                                asm("mov.b64 {%0, %1}, %2;" : "=f"(z1l), "=f"(z1h) : "l"(z1));
-                                f2acc = f2_fma(f2(w4.x, w4.y), f2(fmaxf(z0l, 0.0f), fmaxf(z0h, 0.0f)), f2acc);
-                                f2acc = f2_fma(f2(w4.z, w4.w), f2(fmaxf(z1l, 0.0f), fmaxf(z1h, 0.0f)), f2acc);
-                            } else {
+                            {
                                 f = fmaf(w4.x, act_t<ACT>(fmaf(v[4 * q + 0], scale, b4.x)), f);
                                 f = fmaf(w4.y, act_t<ACT>(fmaf(v[4 * q + 1], scale, b4.y)), f);
                                 f = fmaf(w4.z, act_t<ACT>(fmaf(v[4 * q + 2], scale, b4.z)), f);
