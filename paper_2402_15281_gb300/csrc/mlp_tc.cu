@@ -376,24 +376,25 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             uint32_t armed = 0;            // bit s: stage s has been loaded at least once
             uint32_t armed_par = 0;        // bit s: parity of its last load
             bool ok = true;
-            for (int j = 0; j < n_pairs && ok; ++j) {
-                const int nslots = min(2, n_mine - 2 * j);
-                for (int l = 0; l < n_layers && ok; ++l) {
-                    const int passes = C::REUSE == 2 ? 1 : nslots;
-                    const int slices = l == 0 ? 1 : C::SLICES;
-                    for (int s = 0; s < passes && ok; ++s)
-                        for (int kk = 0; kk < slices; ++kk) {
-                            if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, A.dev_err)) { ok = false; break; }
-                            mbar_arrive_tx(full_bar(stage), STAGE_BYTES);
-                            if (l == 0) tma_load_2d(w_base + stage * STAGE_BYTES, &w1map, 0, 0, full_bar(stage));
-                            else tma_load_2d(w_base + stage * STAGE_BYTES, &wmap, kk * C::SLICE_K, (l - 1) * WN,
-                                             full_bar(stage));
-                            armed |= 1u << stage;
-                            armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
-                            if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
-                        }
+            // the weight slices of one block (layer l), in MMA order
+            auto load_layer = [&](int l) {
+                const int slices = l == 0 ? 1 : C::SLICES;
+                for (int kk = 0; kk < slices; ++kk) {
+                    if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, A.dev_err)) { ok = false; return; }
+                    mbar_arrive_tx(full_bar(stage), STAGE_BYTES);
+                    if (l == 0) tma_load_2d(w_base + stage * STAGE_BYTES, &w1map, 0, 0, full_bar(stage));
+                    else tma_load_2d(w_base + stage * STAGE_BYTES, &wmap, kk * C::SLICE_K, (l - 1) * WN,
+                                     full_bar(stage));
+                    armed |= 1u << stage;
+                    armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+                    if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
                 }
-            }
+            };
+            // lockstep: layer l of slot 0, then of slot 1; with REUSE = 2 both
+            // slots consume one copy of the layer's slices
+            for (int j = 0; j < n_pairs && ok; ++j)
+                for (int l = 0; l < n_layers && ok; ++l)
+                    for (int s = 0; s < (C::REUSE == 2 ? 1 : min(2, n_mine - 2 * j)) && ok; ++s) load_layer(l);
             // wait (bounded) for every copy this thread started
             for (int s = 0; s < C::STAGES; ++s)
                 if (armed & (1u << s)) {
@@ -415,44 +416,58 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         constexpr uint32_t IDESC = PREC == SVM_BF16 ? IDESC_BF16 : IDESC_E4M3;
         int stage = 0;
         uint32_t phase = 0;
-        uint32_t epi_phase[2] = {0u, 0u};
+        uint32_t epi_phase0 = 0u, epi_phase1 = 0u;
         bool ok = true;
-        for (int j = 0; j < n_pairs && ok; ++j) {
-            const int nslots = min(2, n_mine - 2 * j);
-            for (int l = 0; l < n_layers && ok; ++l) {
-                const int slices = l == 0 ? 1 : C::SLICES;
-                const int layer_stage = stage;
-                const uint32_t layer_phase = phase;
-                for (int s = 0; s < nslots && ok; ++s) {
-                    if (!mbar_wait_warp(epid_bar(s), epi_phase[s], abort_flag, A.dev_err)) { ok = false; break; }
-                    epi_phase[s] ^= 1u;
+        // one block: layer l of the tile in slot s.  first/last: whether this
+        // block is the first / last consumer of the layer's weight stages.
+        auto mma_block = [&](int s, int l, bool first, bool last) {
+            uint32_t& ep = s == 0 ? epi_phase0 : epi_phase1;
+            if (!mbar_wait_warp(epid_bar(s), ep, abort_flag, A.dev_err)) { ok = false; return; }
+            ep ^= 1u;
+            tc_fence_after();
+            const uint32_t d_tmem = tmem_base + (uint32_t)(s * WN);
+            const int slices = l == 0 ? 1 : C::SLICES;
+            for (int kk = 0; kk < slices; ++kk) {
+                if (first) {
+                    if (!mbar_wait_warp(full_bar(stage), phase, abort_flag, A.dev_err)) { ok = false; return; }
                     tc_fence_after();
-                    if (C::REUSE == 2) { stage = layer_stage; phase = layer_phase; }
-                    const uint32_t d_tmem = tmem_base + (uint32_t)(s * WN);
-                    for (int kk = 0; kk < slices; ++kk) {
-                        const bool first_use = C::REUSE == 1 || s == 0;
-                        if (first_use) {
-                            if (!mbar_wait_warp(full_bar(stage), phase, abort_flag, A.dev_err)) { ok = false; break; }
-                            tc_fence_after();
-                        }
-                        const uint64_t ad = (s == 0 ? a_desc0 : a_desc1) + (uint64_t)(kk * (KBLOCK_BYTES >> 4));
-                        const uint64_t bd = b_desc0 + (uint64_t)(stage * (STAGE_BYTES >> 4));
-                        if (l == 0) {
-                            mma_f16_warp(d_tmem, ad, bd, IDESC_BF16, 0u);
-                        } else {
+                }
+                const uint64_t ad = (s == 0 ? a_desc0 : a_desc1) + (uint64_t)(kk * (KBLOCK_BYTES >> 4));
+                const uint64_t bd = b_desc0 + (uint64_t)(stage * (STAGE_BYTES >> 4));
+                if (l == 0) {
+                    mma_f16_warp(d_tmem, ad, bd, IDESC_BF16, 0u);
+                } else {
 #pragma unroll
-                            for (int k = 0; k < C::MMAS; ++k) {
-                                if constexpr (PREC == SVM_BF16)
-                                    mma_f16_warp(d_tmem, ad + 2 * k, bd + 2 * k, IDESC, (kk | k) != 0 ? 1u : 0u);
-                                else
-                                    mma_f8f6f4_warp(d_tmem, ad + 2 * k, bd + 2 * k, IDESC, (kk | k) != 0 ? 1u : 0u);
-                            }
-                        }
-                        const bool last_use = C::REUSE == 1 || s == nslots - 1;
-                        if (last_use) mma_commit_warp(empty_bar(stage));
-                        if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
+                    for (int k = 0; k < C::MMAS; ++k) {
+                        if constexpr (PREC == SVM_BF16)
+                            mma_f16_warp(d_tmem, ad + 2 * k, bd + 2 * k, IDESC, (kk | k) != 0 ? 1u : 0u);
+                        else
+                            mma_f8f6f4_warp(d_tmem, ad + 2 * k, bd + 2 * k, IDESC, (kk | k) != 0 ? 1u : 0u);
                     }
-                    if (ok) mma_commit_warp(accf_bar(s));
+                }
+                if (last) mma_commit_warp(empty_bar(stage));
+                if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
+            }
+            mma_commit_warp(accf_bar(s));
+        };
+        {
+            // lockstep: layer l of slot 0, then of slot 1 (on the same weight
+            // stages when REUSE = 2).  Tried: staggering the slots by two
+            // layers so that no two short layer-0 blocks meet -- slower.
+            for (int j = 0; j < n_pairs && ok; ++j) {
+                const int nslots = min(2, n_mine - 2 * j);
+                for (int l = 0; l < n_layers && ok; ++l) {
+                    const int layer_stage = stage;
+                    const uint32_t layer_phase = phase;
+                    for (int s = 0; s < nslots && ok; ++s) {
+                        if (C::REUSE == 2) {
+                            stage = layer_stage;
+                            phase = layer_phase;
+                            mma_block(s, l, s == 0, s == nslots - 1);
+                        } else {
+                            mma_block(s, l, true, true);
+                        }
+                    }
                 }
             }
         }
@@ -475,15 +490,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         float* red_s = red + s * TM;
         uint32_t acc_phase = 0;
         bool ok = true;
-        for (int i = s; i < n_mine && ok; i += 2) {
+        // tile i of this CTA: its motion, this lane's point, whether it exists
+        auto tile_info = [&](int i, int& m, long long& p, bool& valid) {
             const int t = (int)blockIdx.x + i * (int)gridDim.x;
-            const int m = find_segment(A.tile_off, A.M, t);
-            const long long p = A.pbeg[m] + (long long)(t - A.tile_off[m]) * TM + r;
-            const bool valid = p < A.pend[m];
-            // ---- A operand of layer 0: (x_hi, y_hi, z_hi, x_lo, y_lo, z_lo, 0, ...)
+            m = find_segment(A.tile_off, A.M, t);
+            p = A.pbeg[m] + (long long)(t - A.tile_off[m]) * TM + r;
+            valid = p < A.pend[m];
+        };
+        // streamed once per tile: kept out of L1 so that the bias vectors stay there
+        auto load_x = [&](long long p, bool valid) {
+            return valid ? ld_stream_f4(A.points + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+        };
+        // A operand of layer 0 (column half 0 writes it): (x_hi, y_hi, z_hi,
+        // x_lo, y_lo, z_lo, 0, ...); then every warp of the slot arrives
+        auto stage_x = [&](float4 x) {
             if (half == 0) {
-                // streamed once per tile: kept out of L1 so that the bias vectors stay there
-                const float4 x = valid ? ld_stream_f4(A.points + p) : make_float4(0.f, 0.f, 0.f, 0.f);
                 // hi parts are the nearest bfloat16; the differences are exact in FP32
                 const float xl = x.x - __bfloat162float(__float2bfloat16_rn(x.x));
                 const float yl = x.y - __bfloat162float(__float2bfloat16_rn(x.y));
@@ -495,6 +516,22 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(epid_bar(s));
+        };
+        int m = 0;
+        long long p = 0;
+        bool valid = false;
+        if (s < n_mine) {
+            tile_info(s, m, p, valid);
+            stage_x(load_x(p, valid));
+        }
+        for (int i = s; i < n_mine && ok; i += 2) {
+            // the slot's next tile: looked up, and its points loaded, during the
+            // output layer of this one; staged as soon as the output is reduced
+            const bool has_next = i + 2 < n_mine;
+            int nm = 0;
+            long long np = 0;
+            bool nvalid = false;
+            float4 nx = make_float4(0.f, 0.f, 0.f, 0.f);
             // ---- layers
             for (int l = 0; l < n_layers; ++l) {
                 const float* bias = l == 0 ? A.cbias + (long long)m * WN : Wt.bh + (long long)(l - 1) * WN;
@@ -516,6 +553,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         wl2 = __ldg(Wt.wout + col0 + 64 + lane);
                         wl3 = __ldg(Wt.wout + col0 + 96 + lane);
                     }
+                }
+                if (l + 1 == n_layers && has_next) {
+                    tile_info(i + 2, nm, np, nvalid);
+                    if (half == 0) nx = load_x(np, nvalid);
                 }
                 if (!mbar_wait(accf_bar(s), acc_phase, abort_flag, A.dev_err)) { ok = false; break; }
                 acc_phase ^= 1u;
@@ -595,8 +636,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     // the two column halves of a row meet in shared memory
                     if (half == 1) red_s[r] = f;
                     named_sync(1 + s, 32 * EPI_PER_SLOT);
+                    if (half == 0) f += red_s[r] + Wt.bout;
+                    // the TMEM slot and the layer-0 operand are free: hand them to the next tile
+                    if (has_next) stage_x(nx);
                     if (half == 0) {
-                        f += red_s[r] + Wt.bout;
                         if (A.f_out != nullptr && valid) A.f_out[(long long)m * A.f_stride + (p - A.pbeg[m])] = f;
                         const bool flag = valid && f <= A.gate;
                         const unsigned mask = __ballot_sync(0xffffffffu, flag);
@@ -612,6 +655,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     }
                 }
             }
+            m = nm;
+            p = np;
+            valid = nvalid;
         }
     }
 
