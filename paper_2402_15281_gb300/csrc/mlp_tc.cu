@@ -82,9 +82,20 @@ struct Cfg<SVM_FP8_E4M3> {
     static constexpr int SLICE_K = 128;
     static constexpr int SLICES = WN / SLICE_K;          // 2 per hidden layer
     static constexpr int MMAS = 4;                       // K = 32 each
-    static constexpr int STAGES = 5;
+    static constexpr int STAGES = 4;
     static constexpr int REUSE = 2;
 };
+
+// FP8 keeps its hidden biases (already divided by the next activation
+// scale), the output layer's bias and the output weights in shared memory,
+// read as broadcast 16-byte loads; BF16 has no room left and broadcasts them
+// from registers with shuffles.
+constexpr int MAX_HIDDEN = 16;
+template <int PREC>
+__host__ __device__ constexpr int bias_smem_bytes()
+{
+    return PREC == SVM_FP8_E4M3 ? (MAX_HIDDEN + 1) * WN * 4 : 0;
+}
 
 template <int PREC>
 struct Smem {
@@ -95,25 +106,18 @@ struct Smem {
     static constexpr int BARS = RED + 2 * TM * 4;
     static constexpr int N_BARS = 2 * Cfg<PREC>::STAGES + 5;
     static constexpr int MISC = BARS + 8 * N_BARS;
-    static constexpr int TOTAL = MISC + 16;
+    // [L-1 hidden][W], [output bias][W], [w_out][W]; 16-byte loads need 16-byte alignment
+    static constexpr int BIAS = (MISC + 16 + 127) / 128 * 128;
+    static constexpr int TOTAL = BIAS + bias_smem_bytes<PREC>();
     static constexpr int DYN = TOTAL + 1024;      // slack for 1024-byte alignment
 };
 static_assert(Smem<SVM_BF16>::DYN <= 232448, "shared memory budget");
+static_assert(Smem<SVM_FP8_E4M3>::BIAS % 16 == 0, "bias table alignment");
 static_assert(Smem<SVM_FP8_E4M3>::DYN <= 232448, "shared memory budget");
 
 // ------------------------------------------------------------ PTX wrappers
 
 using namespace ptx;
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
-{
-    mma_f16(tmem_d, adesc, bdesc, IDESC_BF16, accumulate);
-}
-
-__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
-{
-    mma_f8f6f4(tmem_d, adesc, bdesc, IDESC_E4M3, accumulate);
-}
 
 template <int ACT>
 __device__ __forceinline__ float act_t(float z)
@@ -311,6 +315,34 @@ __device__ __forceinline__ void epilogue32_relu_lane(uint32_t base, int r, int o
     }
 }
 
+__device__ __forceinline__ float4 ld_shared_f4(uint32_t addr)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+    return v;
+}
+
+// FP8 hidden layer with the 32 biases (divided by the next activation scale)
+// read from shared memory at `brow` (broadcast loads): h = relu(acc * c + b).
+__device__ __forceinline__ void epilogue32_relu_e4m3_sm(uint32_t base, int r, int o0, const float (&v)[32],
+                                                        uint32_t brow, float c)
+{
+    const uint64_t c2 = f2(c, c);
+    uint32_t out[16];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float4 b4 = ld_shared_f4(brow + 16 * q);
+        out[2 * q + 0] = relu_e4m3x2(f2_fma(f2(v[4 * q + 0], v[4 * q + 1]), c2, f2(b4.x, b4.y)));
+        out[2 * q + 1] = relu_e4m3x2(f2_fma(f2(v[4 * q + 2], v[4 * q + 3]), c2, f2(b4.z, b4.w)));
+    }
+    uint32_t w[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) w[k] = (out[2 * k] & 0xFFFFu) | (out[2 * k + 1] << 16);
+    const int kb = o0 >> 7, c0 = (o0 & 127) >> 4;
+    st_shared_v4(act_chunk_addr(base, kb, r, c0), w[0], w[1], w[2], w[3]);
+    st_shared_v4(act_chunk_addr(base, kb, r, c0 + 1), w[4], w[5], w[6], w[7]);
+}
+
 // ------------------------------------------------------------------ kernel
 
 template <int PREC, int ACT>
@@ -360,6 +392,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                      "r"(512)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if constexpr (bias_smem_bytes<PREC>() > 0) {
+        // rows 0..L-2: hidden biases / next activation scale; row L-1: the
+        // output layer's bias; row L: w_out
+        float4* dst = reinterpret_cast<float4*>(dsm + SM::BIAS);
+        const int L = A.L, q = WN / 4;
+        for (int i = threadIdx.x; i < (L + 1) * q; i += blockDim.x) {
+            const int row = i / q, c4 = i % q;
+            const float* src = row < L - 1 ? Wt.bhs + (long long)row * WN
+                                            : (row == L - 1 ? Wt.bh + (long long)(L - 1) * WN : Wt.wout);
+            dst[i] = __ldg(reinterpret_cast<const float4*>(src) + c4);
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -538,9 +582,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 // ReLU hidden layers: the 128 biases of this warp's columns, one
                 // per lane per 32-column chunk, loaded before the accumulator wait
                 // (the output layer also takes its output weights the same way)
+                // (FP8 layers after the first read them from the shared-memory table)
+                constexpr bool kSmemBias = bias_smem_bytes<PREC>() > 0 && ACT == SVM_RELU;
+                const bool sm_bias = kSmemBias && l > 0;
+                const uint32_t sb = smem_u32(dsm + SM::BIAS);
                 float bl0 = 0.0f, bl1 = 0.0f, bl2 = 0.0f, bl3 = 0.0f;
                 float wl0 = 0.0f, wl1 = 0.0f, wl2 = 0.0f, wl3 = 0.0f;
-                if (ACT == SVM_RELU) {
+                if (ACT == SVM_RELU && !sm_bias) {
                     const float* bsrc =
                         (PREC == SVM_FP8_E4M3 && l > 0 && l + 1 < n_layers) ? Wt.bhs + (long long)(l - 1) * WN : bias;
                     bl0 = __ldg(bsrc + col0 + lane);
@@ -572,6 +620,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         if constexpr (ACT == SVM_RELU) {
                             if (PREC == SVM_FP8_E4M3 && l == 0)
                                 epilogue32_relu_lane<PREC, true>(abase, r, col0 + o0, v, bl0, inv_next);
+                            else if (sm_bias)
+                                epilogue32_relu_e4m3_sm(abase, r, col0 + o0, v,
+                                                        sb + (uint32_t)(((l - 1) * WN + col0 + o0) * 4),
+                                                        scale * inv_next);
                             else if (PREC == SVM_FP8_E4M3)
                                 epilogue32_relu_lane<PREC, false>(abase, r, col0 + o0, v, bl0, scale * inv_next);
                             else
@@ -595,6 +647,22 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     for (int o0 = 0; o0 < HALF_COLS; o0 += 32) {
                         float v[32];
                         tmem_ld32(t_row + (uint32_t)o0, v);
+                        if (sm_bias) {
+                            const uint32_t brow = sb + (uint32_t)(((A.L - 1) * WN + col0 + o0) * 4);
+                            const uint32_t wrow = sb + (uint32_t)((A.L * WN + col0 + o0) * 4);
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) {
+                                const float4 b4 = ld_shared_f4(brow + 16 * q), w4 = ld_shared_f4(wrow + 16 * q);
+                                const uint64_t z0 = f2_fma(f2(v[4 * q + 0], v[4 * q + 1]), s2, f2(b4.x, b4.y));
+                                const uint64_t z1 = f2_fma(f2(v[4 * q + 2], v[4 * q + 3]), s2, f2(b4.z, b4.w));
+                                float z0l, z0h, z1l, z1h;
+                                asm("mov.b64 {%0, %1}, %2;" : "=f"(z0l), "=f"(z0h) : "l"(z0));
+                                asm("mov.b64 {%0, %1}, %2;" : "=f"(z1l), "=f"(z1h) : "l"(z1));
+                                f2acc = f2_fma(f2(w4.x, w4.y), f2(fmaxf(z0l, 0.0f), fmaxf(z0h, 0.0f)), f2acc);
+                                f2acc = f2_fma(f2(w4.z, w4.w), f2(fmaxf(z1l, 0.0f), fmaxf(z1h, 0.0f)), f2acc);
+                            }
+                            continue;
+                        }
                         if constexpr (ACT == SVM_RELU) {
 #pragma unroll
                             for (int q = 0; q < 16; ++q) {
@@ -613,13 +681,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                             wl0 = wl1;
                             wl1 = wl2;
                             wl2 = wl3;
-                            continue;
-                        }
+                        } else {
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + col0 + o0 + 4 * q));
-                            const float4 w4 = __ldg(reinterpret_cast<const float4*>(Wt.wout + col0 + o0 + 4 * q));
-                            {
+                            for (int q = 0; q < 8; ++q) {
+                                const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + col0 + o0 + 4 * q));
+                                const float4 w4 = __ldg(reinterpret_cast<const float4*>(Wt.wout + col0 + o0 + 4 * q));
                                 f = fmaf(w4.x, act_t<ACT>(fmaf(v[4 * q + 0], scale, b4.x)), f);
                                 f = fmaf(w4.y, act_t<ACT>(fmaf(v[4 * q + 1], scale, b4.y)), f);
                                 f = fmaf(w4.z, act_t<ACT>(fmaf(v[4 * q + 2], scale, b4.z)), f);
