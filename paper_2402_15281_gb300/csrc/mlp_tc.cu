@@ -561,6 +561,35 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(epid_bar(s));
         };
+        // gate and compaction of a finished tile (column half 0): flag f <= margin + tau,
+        // append the flagged points to the motion's list, keep the minimum prediction
+        bool pend = false, pvalid = false;
+        float pf = 0.0f;
+        int pm = 0;
+        long long pp = 0;
+        // In two parts: gate() reserves the list space (the atomic is left in
+        // flight), gate_store() -- one layer later -- writes the indices.
+        unsigned pmask = 0, pbase = 0;
+        bool pstore = false;
+        auto gate = [&]() {
+            pend = false;
+            if (A.f_out != nullptr && pvalid) A.f_out[(long long)pm * A.f_stride + (pp - A.pbeg[pm])] = pf;
+            const bool flag = pvalid && pf <= A.gate;
+            pmask = __ballot_sync(0xffffffffu, flag);
+            pbase = 0;
+            if (lane == 0 && pmask) pbase = atomicAdd(&A.st[pm].n_flagged, (unsigned)__popc(pmask));
+            pstore = true;
+            float fm = pvalid ? pf : __int_as_float(0x7f800000);
+#pragma unroll
+            for (int sh = 16; sh > 0; sh >>= 1) fm = fminf(fm, __shfl_xor_sync(0xffffffffu, fm, sh));
+            if (lane == 0 && fm < __int_as_float(0x7f800000)) atomicMin(&A.st[pm].dhat_key, float_key(fm));
+        };
+        auto gate_store = [&]() {
+            pstore = false;
+            const unsigned base = __shfl_sync(0xffffffffu, pbase, 0);
+            if ((pmask >> lane) & 1u)
+                A.idx[A.pair_off[pm] + base + __popc(pmask & ((1u << lane) - 1u))] = (unsigned)pp;
+        };
         int m = 0;
         long long p = 0;
         bool valid = false;
@@ -602,6 +631,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         wl3 = __ldg(Wt.wout + col0 + 96 + lane);
                     }
                 }
+                if (l == 1 && pend) {         // the previous tile's gate, after this tile's layer 0
+                    gate();
+                    if (n_layers < 3) gate_store();
+                }
+                if (l == 2 && pstore) gate_store();
                 if (l + 1 == n_layers && has_next) {
                     tile_info(i + 2, nm, np, nvalid);
                     if (half == 0) nx = load_x(np, nvalid);
@@ -705,19 +739,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     if (half == 0) f += red_s[r] + Wt.bout;
                     // the TMEM slot and the layer-0 operand are free: hand them to the next tile
                     if (has_next) stage_x(nx);
+                    // FP8: the gate of this tile waits until the next tile's layer-0
+                    // epilogue is done (its atomics would delay that epilogue; FP8's
+                    // short MMA blocks leave no slack for them).  Measured slower
+                    // for BF16, which gates at once.
+                    constexpr bool kDeferGate = PREC == SVM_FP8_E4M3;
                     if (half == 0) {
-                        if (A.f_out != nullptr && valid) A.f_out[(long long)m * A.f_stride + (p - A.pbeg[m])] = f;
-                        const bool flag = valid && f <= A.gate;
-                        const unsigned mask = __ballot_sync(0xffffffffu, flag);
-                        unsigned base = 0;
-                        if (lane == 0 && mask) base = atomicAdd(&A.st[m].n_flagged, (unsigned)__popc(mask));
-                        base = __shfl_sync(0xffffffffu, base, 0);
-                        if (flag) A.idx[A.pair_off[m] + base + __popc(mask & ((1u << lane) - 1u))] = (unsigned)p;
-                        float fm = valid ? f : __int_as_float(0x7f800000);
-#pragma unroll
-                        for (int sh = 16; sh > 0; sh >>= 1) fm = fminf(fm, __shfl_xor_sync(0xffffffffu, fm, sh));
-                        if (lane == 0 && fm < __int_as_float(0x7f800000))
-                            atomicMin(&A.st[m].dhat_key, float_key(fm));
+                        pend = true;
+                        pf = f;
+                        pm = m;
+                        pp = p;
+                        pvalid = valid;
+                        if (!has_next || !kDeferGate) {
+                            gate();
+                            gate_store();
+                        }
                     }
                 }
             }
