@@ -48,6 +48,9 @@ DTYPE_NAMES = {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}
 METRIC = "verified motion-point queries/s"
 FLOP_PER_PAIR = 2 * (3 * WIDTH + HIDDEN * WIDTH * WIDTH + WIDTH)   # 526 336
 FLOP_PER_CAPSULE_TEST = 20
+# DRAM bytes (read + write) of one launch of the tensor-core network kernel on this workload, from
+# one-pass ncu captures of a full-size launch; to be reset to None whenever that kernel changes.
+TC_TRAFFIC_BYTES = {"bf16": 3.90e6, "fp8": 3.62e6}
 
 
 def workload(seed=0):
@@ -68,7 +71,9 @@ def workload_config(prec, weights="trained"):
     return {"workload": "bin-picking: 64 linear motions x 200k-point bin cloud, margin 0.03 m, 128 steps, "
                         "MLP 15-256x4-1 ReLU",
             "motions": N_MOTIONS, "points": N_POINTS, "steps": STEPS, "margin_m": EPS,
-            "precision": prec, "l2": "flushed between steps (256 MiB write)", "weights": w}
+            "precision": prec, "l2": "flushed between steps (256 MiB write)", "weights": w,
+            **({"fp8_scales": "per-layer activation scales calibrated on the same 16 motions (2x headroom)"}
+               if prec == "fp8" else {})}
 
 
 # --------------------------------------------------------------------- clocks
@@ -225,6 +230,9 @@ def run_gpu(args):
     def make_model(p):
         h = svm.svm_create_model(robot, WIDTH, HIDDEN, svm.SVM_RELU, p, local)
         svm.svm_load_weights(h, blob)
+        if p == svm.SVM_FP8_E4M3:
+            # per-layer activation scales from the calibration motions (2x headroom)
+            svm.svm_calibrate_act_scales(h, cq0, cq1, pts_d, 2.0)
         t = training.calibrate_tau(svm, h, robot, pts_d, EPS, STEPS, cq0, cq1)
         svm.svm_set_gate(h, t)
         return h, t
@@ -315,7 +323,7 @@ def run_gpu(args):
         roof = {"kernel": "verify", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = TC_TRAFFIC_BYTES.get(args.prec) if roof["kernel"].startswith("mlp_tc") else None
 
     # the plain FP32 path on the same workload and weights (SIMT network, same verifier)
     fp32 = None
@@ -367,6 +375,40 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
+def profile_call(args):
+    """One check call for an external profiler.  With --weights random: Glorot weights and the
+    blob's gate, no other network launch (ncu -k regex:mlp_tc -c 1).  With --weights trained:
+    the bench's training and gate calibration first, which launch the network kernel once
+    (ncu -k regex:mlp_tc -s 1 -c 1)."""
+    import torch
+    import paper_2402_15281_gb300 as svm
+    from paper_2402_15281_gb300 import training
+    svm.build()
+    robot, pts, q0, q1 = workload()
+    m = min(args.profile_call, N_MOTIONS)
+    pts_d = torch.from_numpy(pts).cuda()
+    h = svm.svm_create_model(robot, WIDTH, HIDDEN, svm.SVM_RELU, PREC_NAMES[args.prec], 0)
+    if args.weights == "trained":
+        tq0, tq1 = training.bin_training_motions(robot, 1024, seed=41)
+        blob, _ = training.train_model(svm, robot, tq0, tq1, samples_per_motion=4096, steps=STEPS,
+                                       batch=65536, epochs=30, patience=10)
+        svm.svm_load_weights(h, blob)
+        cq0, cq1 = S.bin_motions(robot, 16, seed=1000)
+        if args.prec == "fp8":
+            svm.svm_calibrate_act_scales(h, cq0, cq1, pts_d, 2.0)
+        svm.svm_set_gate(h, training.calibrate_tau(svm, h, robot, pts_d, EPS, STEPS, cq0, cq1))
+    else:
+        svm.svm_load_weights(h, svm.make_blob(weights()))
+        if args.prec == "fp8":
+            svm.svm_set_act_scales(h, np.full(HIDDEN, 1 / 64, np.float32))
+    res = svm.new_results(m)
+    svm.svm_check_motions(h, q0[:m], q1[:m], pts_d, EPS, STEPS, 0, res)
+    torch.cuda.synchronize()
+    r = svm.results_to_numpy(res)[:m]
+    print("profile call:", m, "motions,", int(r["collision"].sum()), "collisions, status", int(r["status"].max()))
+    svm.svm_destroy_model(h)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -377,8 +419,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-path", action="store_true")
     ap.add_argument("--weights", choices=["trained", "random"], default="trained")
+    ap.add_argument("--profile-call", type=int, default=0, metavar="M",
+                    help="for profilers: one svm_check_motions call on the first M bench motions (weights "
+                         "as --weights), then exit (no timing, no JSON line)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_call > 0:
+        profile_call(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
