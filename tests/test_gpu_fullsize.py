@@ -93,3 +93,59 @@ def test_full_size_verdicts_and_outputs(setup, prec):
             assert np.quantile(err[band], 0.99) <= 2.5e-2 and err.max() <= 5e-2
     finally:
         svm.svm_destroy_model(h)
+
+
+def test_config4_paths_full_size(setup):
+    """Three-segment paths at full size: 128 paths q_start -> q_inVia ->
+    q_outVia -> q_end (Sec. V-C) against a 300 000-point bin cloud, BF16,
+    trained network, early exit on the first colliding segment.  The gate is
+    calibrated on the segments of 16 separate paths: the network was trained
+    on grasp motions into the bin, and the reversed and via segments of a path
+    come from another distribution, for which a gate calibrated on grasp
+    motions alone misses collisions.  Verdicts (default and SVM_STRICT) equal
+    the exact check of every pair (OR over segments, free iff d > eps); two
+    paths are checked against the FP64 oracle (Eq. 5) in full.  The call is
+    timed."""
+    import time
+    svm, training, robot, blob, hist, _, _, _, _, _, _ = setup
+    paths = S.bin_paths(robot, 128, seed=4)
+    q0 = np.ascontiguousarray(paths[:, :3].reshape(-1, 6))
+    q1 = np.ascontiguousarray(paths[:, 1:].reshape(-1, 6))
+    pts = S.bin_cloud(300_000, seed=4)
+    pts_d = torch.from_numpy(pts).cuda()
+    h = svm.svm_create_model(robot, 256, 4, 0, 1, 0)
+    try:
+        svm.svm_load_weights(h, blob)
+        cpaths = S.bin_paths(robot, 16, seed=1000)
+        cq0 = np.ascontiguousarray(cpaths[:, :3].reshape(-1, 6))
+        cq1 = np.ascontiguousarray(cpaths[:, 1:].reshape(-1, 6))
+        tau = training.calibrate_tau(svm, h, robot, pts_d, EPS, N, cq0, cq1)
+        svm.svm_set_gate(h, tau)
+
+        def run(flags):
+            res = svm.new_results(128)
+            svm.svm_check_motions(h, q0, q1, pts_d, EPS, N, flags | svm.SVM_PATHS3, res)
+            torch.cuda.synchronize()
+            return svm.results_to_numpy(res)[:128]
+
+        run(0)                                                     # warm-up
+        t = time.perf_counter()
+        r = run(0)
+        ms = 1e3 * (time.perf_counter() - t)
+        g = run(svm.SVM_VERIFY_ALL | svm.SVM_NO_EARLY_EXIT)
+        st = run(svm.SVM_STRICT)
+        assert np.all(r["status"] == 0) and np.all(g["status"] == 0) and np.all(st["status"] == 0)
+        np.testing.assert_array_equal(st["collision"], g["collision"])
+        np.testing.assert_array_equal(r["collision"], g["collision"])
+        assert 0 < r["collision"].sum() < 128
+        pick = [int(np.argmax(r["collision"])), int(np.argmin(r["collision"]))]   # one colliding, one free
+        seg = np.concatenate([np.arange(3 * k, 3 * k + 3) for k in pick])
+        dmin, coll = oracle.gcc_motion(robot, q0[seg], q1[seg], N, pts, EPS)
+        np.testing.assert_array_equal(r["collision"][pick], coll.reshape(-1, 3).max(axis=1))
+        assert np.abs(g["d_min"][pick] - dmin.reshape(-1, 3).min(axis=1)).max() <= 1e-5
+        pairs = 3 * 128 * len(pts)
+        print(f"config 4: 128 paths x 3 segments x {len(pts)} points = {pairs / 1e6:.0f} M pairs in {ms:.1f} ms "
+              f"(wall) = {pairs / ms / 1e6:.2f} G pairs/s; tau {tau:.4f} m, flagged "
+              f"{r['n_flagged'].sum() / pairs:.2%}; {r['collision'].sum()} paths collide")
+    finally:
+        svm.svm_destroy_model(h)
