@@ -103,6 +103,10 @@ typedef struct svm_model svm_model;
 #define SVM_PATHS3        8u  /* motions 3p, 3p+1, 3p+2 are the segments of path
                                  p; one result per path (collision = OR), and a
                                  path stops at its first colliding segment      */
+#define SVM_PREDICT_ONLY 16u  /* run the network only: dhat_min (Eq. 6) per
+                                 motion, no exact check (collision = 0, d_min =
+                                 +inf); not with SVM_VERIFY_ALL or SVM_STRICT;
+                                 svm_check_motions / svm_check_batch only       */
 
 const char* svm_status_string(svm_status s);
 const char* svm_last_error(const svm_model* m);
@@ -175,6 +179,42 @@ svm_status svm_check_batch(svm_model* m, const double* q0, const double* q1,
                            const float* points_dev, const int64_t* scene_offsets,
                            int32_t n_scenes, float margin, int32_t steps, uint32_t flags,
                            svm_result* results_dev, void* stream);
+
+/* ------------------------------------------------------------ motion search
+ * Algorithm 1 (Sec. IV-B): find a collision-free motion among n_motions
+ * candidates with the network as a proxy.  d_hat(X, m) = min over the cloud of
+ * f(x, m) (Eq. 6) is computed for every motion in one network launch.  First
+ * loop: the motions with d_hat > margin, in the given order, are checked
+ * exactly (the geometric check of every point, free iff every distance >
+ * margin, Eq. 5); the first free one is returned.  Otherwise, second loop: the
+ * remaining motions sorted by decreasing d_hat (ties in the given order) are
+ * checked exactly until one is free.  With SVM_SEARCH_GCC0 the network is not
+ * used and every motion is checked exactly in the given order (GCC_0 of
+ * Sec. V-B).
+ *   wave    exact checks run `wave` candidates per launch (1 reproduces the
+ *           sequential algorithm; more trades extra checks for fewer round
+ *           trips); the result is the same for every wave.
+ * Synchronous on `stream` (it reads results back to decide); q0/q1 host,
+ * points device; out is a host struct.  Allocates its result buffers on the
+ * first call (cudaMalloc / cudaMallocHost), then reuses them. */
+#define SVM_SEARCH_GCC0 1u
+
+typedef struct {
+    int32_t motion;       /* index of the free motion found, -1 if none          */
+    int32_t loop;         /* 1 or 2: the loop that found it; 0 if none            */
+    float delta;          /* its exact distance d(X, m) (min over the cloud), m   */
+    float delta_hat;      /* its d_hat(X, m); +inf under SVM_SEARCH_GCC0          */
+    int32_t n_exact;      /* exact checks the sequential algorithm makes          */
+    int32_t n_exact_run;  /* exact checks run (n_exact rounded up to whole waves) */
+    int32_t n_nn;         /* motions evaluated by the network launch (n_motions)  */
+    int32_t n_nn_seq;     /* network evaluations the sequential first loop makes
+                             (up to the returned motion; all if it reaches the
+                             second loop)                                       */
+} svm_search_result;
+
+svm_status svm_search_free_motion(svm_model* m, const double* q0, const double* q1, int32_t n_motions,
+                                  const float* points_dev, int64_t n_points, float margin, int32_t steps,
+                                  int32_t wave, uint32_t flags, svm_search_result* out, void* stream);
 
 /* ------------------------------------------------------------ prepared batches
  * A plan holds a fixed batch (motions, their scenes, margin, steps, flags)
@@ -268,13 +308,19 @@ int64_t svm_train_param_count(const svm_trainer* t);
 svm_status svm_train_set_weights(svm_trainer* t, const void* blob, size_t bytes);
 svm_status svm_train_get_weights(svm_trainer* t, void* blob, size_t capacity, size_t* needed);
 
+/* The box of the uniformly drawn training points for later svm_train_make_data
+ * calls (lo, hi: 3 doubles each, lo < hi): cover the volume where the
+ * checked points will lie. */
+svm_status svm_train_set_box(svm_trainer* t, const double* lo, const double* hi);
+
 /* Generate n_motions * samples_per_motion labelled samples on the GPU for
  * the host motions q0, q1 (n_motions x 6): for motion m and local index j the
  * SplitMix64 stream (seed, m) gives draws u_0..u_6 at counters 8j..8j+6;
  * with u_0 < 0.7 the point is near capsule floor(u_2 * 7) at sample
  * floor(u_1 * (steps + 1)): a + u_3 e + (r + off) d with d the unit vector of
  * (z = 2 u_4 - 1, phi = 2 pi u_5) and off = -0.1 + 0.2 u_6; otherwise it is
- * uniform in [-0.75,0.75]^2 x [0,1.5] from u_1..u_3.  The label is the exact
+ * uniform in the sampling box (default [-0.75,0.75]^2 x [0,1.5]; coordinate
+ * q is lo_q + (hi_q - lo_q) u_{1+q}).  The label is the exact
  * sampled swept-volume distance with `steps` steps.  Sample s = m *
  * samples_per_motion + j. */
 svm_status svm_train_make_data(svm_trainer* t, const double* q0, const double* q1, int32_t n_motions,

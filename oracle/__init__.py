@@ -1,4 +1,5 @@
-"""Python access to the FP64 CPU oracle (``svm_oracle.c``).
+"""Python access to the FP64 CPU oracle (``svm_oracle.c``), and Algorithm 1
+(the motion search of Sec. IV-B) written out in plain Python on top of it.
 
 TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
 CPU-baseline leg use this module to state what the GPU path must compute.
@@ -82,6 +83,8 @@ def lib():
         L.orc_quantize_e4m3.argtypes = [_F, C.c_long, _F]
         L.orc_quantize_e4m3.restype = C.c_float
         L.orc_training_points.argtypes = [_D, C.c_double, _D, _D, _D, C.c_int, C.c_uint64, C.c_int, C.c_int, _D]
+        L.orc_training_points_region.argtypes = [_D, C.c_double, _D, _D, _D, C.c_int, C.c_uint64, C.c_int,
+                                                 C.c_int, _D, _D, _D]
         L.orc_splitmix64_u01.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
         L.orc_splitmix64_u01.restype = C.c_double
     return _lib
@@ -310,10 +313,70 @@ def splitmix64_u01(seed, stream, i) -> float:
     return lib().orc_splitmix64_u01(int(seed), int(stream), int(i))
 
 
-def training_points(robot, q0, q1, N, seed, m, spm) -> np.ndarray:
-    """The data generator's points and labels for motion index m: (spm, 4)."""
+def training_points(robot, q0, q1, N, seed, m, spm, lo=None, hi=None) -> np.ndarray:
+    """The data generator's points and labels for motion index m: (spm, 4).
+    lo, hi: the box of the uniform points (default [-0.75,0.75]^2 x [0,1.5])."""
     R = RobotArrays(robot)
     out = np.zeros(spm * 4)
-    lib().orc_training_points(R.dh, R.tool_len, R.radius, _d(q0).reshape(6), _d(q1).reshape(6), int(N),
-                              int(seed), int(m), int(spm), out)
+    if lo is None and hi is None:
+        lib().orc_training_points(R.dh, R.tool_len, R.radius, _d(q0).reshape(6), _d(q1).reshape(6), int(N),
+                                  int(seed), int(m), int(spm), out)
+    else:
+        lib().orc_training_points_region(R.dh, R.tool_len, R.radius, _d(q0).reshape(6), _d(q1).reshape(6),
+                                         int(N), int(seed), int(m), int(spm), _d(lo).reshape(3),
+                                         _d(hi).reshape(3), out)
     return out.reshape(spm, 4)
+
+
+# ------------------------------------------------------------ Algorithm 1
+
+def motion_dhat(P, width, n_hidden, act, q0, q1, points, fmt=0, scales=None) -> np.ndarray:
+    """Eq. 6 per motion: d_hat(X, m) = min over the cloud of f(x, m); fmt 0
+    evaluates the network in FP64, 1/2 with the hidden-layer inputs rounded
+    as the BF16 / FP8 model stores them."""
+    if len(_xyz(points)) == 0:
+        return np.full(_d(q0).reshape(-1, 6).shape[0], np.inf)
+    if fmt == 0:
+        f = mlp_pairs(P, width, n_hidden, act, q0, q1, points)
+    else:
+        f = mlp_pairs_rounded(P, width, n_hidden, act, fmt, scales, q0, q1, points)
+    return f.min(axis=1)
+
+
+def search_first_free(dhat, delta, eps):
+    """Algorithm 1 (Sec. IV-B), sequentially, on given per-motion values:
+    dhat[m] the network's estimate d_hat(X, m), delta[m] the exact distance
+    d(X, m); a motion is free iff its distance > eps.
+      first loop:  for m in the given order, if dhat[m] > eps, check m exactly
+                   (count it); return m if delta[m] > eps;
+      second loop: the motions not checked, by decreasing dhat (ties in the
+                   given order), check each exactly; return the first free.
+    Returns dict(motion, loop, n_exact, n_nn_seq); motion -1 if none is free.
+    n_nn_seq counts the network evaluations of the first loop."""
+    dhat = np.asarray(dhat, dtype=np.float64)
+    delta = np.asarray(delta, dtype=np.float64)
+    M = len(dhat)
+    done = np.zeros(M, dtype=bool)
+    n_exact = 0
+    for m in range(M):                                  # first loop
+        if dhat[m] > eps:
+            n_exact += 1
+            done[m] = True
+            if delta[m] > eps:
+                return {"motion": m, "loop": 1, "n_exact": n_exact, "n_nn_seq": m + 1}
+    rest = [m for m in range(M) if not done[m]]
+    rest.sort(key=lambda m: -dhat[m])                   # stable: ties keep the given order
+    for m in rest:                                      # second loop
+        n_exact += 1
+        if delta[m] > eps:
+            return {"motion": m, "loop": 2, "n_exact": n_exact, "n_nn_seq": M}
+    return {"motion": -1, "loop": 0, "n_exact": n_exact, "n_nn_seq": M}
+
+
+def search_gcc0(delta, eps):
+    """GCC_0 of Sec. V-B: the exact check of each motion in the given order
+    until one is free.  Returns dict(motion, n_exact)."""
+    for m, d in enumerate(np.asarray(delta, dtype=np.float64)):
+        if d > eps:
+            return {"motion": m, "n_exact": m + 1}
+    return {"motion": -1, "n_exact": len(delta)}

@@ -619,11 +619,13 @@ double orc_splitmix64_u01(uint64_t seed, uint64_t stream, uint64_t i)
  * near capsule c = floor(7 u_2) of sample k = floor((N+1) u_1):
  * a + u_3 (b - a) + (r_c + off) d, with d = (sqrt(1 - z^2) cos phi,
  * sqrt(1 - z^2) sin phi, z), z = 2 u_4 - 1, phi = 2 pi u_5,
- * off = -0.1 + 0.2 u_6; otherwise uniform in [-0.75,0.75]^2 x [0,1.5] from
- * u_1..u_3.  Each point gets its exact sampled swept-volume distance.
+ * off = -0.1 + 0.2 u_6; otherwise uniform in the box [lo, hi] from u_1..u_3
+ * (lo + (hi - lo) u per axis).  Each point gets its exact sampled
+ * swept-volume distance.
  * out is (spm, 4): x, y, z, delta. */
-void orc_training_points(const double *dh, double tool_len, const double *radius, const double *q0,
-                         const double *q1, int N, uint64_t seed, int m, int spm, double *out)
+void orc_training_points_region(const double *dh, double tool_len, const double *radius, const double *q0,
+                                const double *q1, int N, uint64_t seed, int m, int spm, const double *lo,
+                                const double *hi, double *out)
 {
     double A[(N + 1) * NCAPS * 3], Bx[(N + 1) * NCAPS * 3];
     motion_capsules(dh, tool_len, q0, q1, N, A, Bx);
@@ -645,9 +647,7 @@ void orc_training_points(const double *dh, double tool_len, const double *radius
             const double d[3] = {rxy * cos(phi), rxy * sin(phi), z};
             for (int q = 0; q < 3; ++q) p[q] = a[q] + u[3] * (b[q] - a[q]) + (radius[cj] + off) * d[q];
         } else {
-            p[0] = -0.75 + 1.5 * u[1];
-            p[1] = -0.75 + 1.5 * u[2];
-            p[2] = 1.5 * u[3];
+            for (int q = 0; q < 3; ++q) p[q] = lo[q] + (hi[q] - lo[q]) * u[1 + q];
         }
         double best = INFINITY;
         for (int k = 0; k <= N; ++k) {
@@ -657,4 +657,12 @@ void orc_training_points(const double *dh, double tool_len, const double *radius
         for (int q = 0; q < 3; ++q) out[4 * j + q] = p[q];
         out[4 * j + 3] = best;
     }
+}
+
+/* The same with the uniform points in the default box [-0.75,0.75]^2 x [0,1.5]. */
+void orc_training_points(const double *dh, double tool_len, const double *radius, const double *q0,
+                         const double *q1, int N, uint64_t seed, int m, int spm, double *out)
+{
+    const double lo[3] = {-0.75, -0.75, 0.0}, hi[3] = {0.75, 0.75, 1.5};
+    orc_training_points_region(dh, tool_len, radius, q0, q1, N, seed, m, spm, lo, hi, out);
 }

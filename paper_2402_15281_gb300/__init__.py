@@ -22,7 +22,8 @@ LIB_PATH = os.path.join(_HERE, "_build", platform.machine(), "libsvm.so")
 SVM_OK, SVM_E_INVALID, SVM_E_CUDA, SVM_E_OOM, SVM_E_TIMEOUT, SVM_E_WEIGHTS, SVM_E_UNSUPPORTED = range(7)
 SVM_FP32, SVM_BF16, SVM_FP8_E4M3 = 0, 1, 2
 SVM_RELU, SVM_SILU = 0, 1
-SVM_STRICT, SVM_NO_EARLY_EXIT, SVM_VERIFY_ALL, SVM_PATHS3 = 1, 2, 4, 8
+SVM_STRICT, SVM_NO_EARLY_EXIT, SVM_VERIFY_ALL, SVM_PATHS3, SVM_PREDICT_ONLY = 1, 2, 4, 8, 16
+SVM_SEARCH_GCC0 = 1
 
 RESULT_DTYPE = np.dtype([("collision", "u1"), ("early_exit", "u1"), ("status", "<u2"),
                          ("d_min", "<f4"), ("dhat_min", "<f4"), ("n_flagged", "<u4"),
@@ -94,6 +95,8 @@ def lib():
         L.svm_train_set_weights.argtypes = [vp, C.c_char_p, sz]
         L.svm_train_get_weights.argtypes = [vp, vp, sz, C.POINTER(sz)]
         L.svm_train_make_data.argtypes = [vp, vp, vp, i32, i32, i32, C.c_uint64]
+        L.svm_train_set_box.argtypes = [vp, vp, vp]
+        L.svm_train_set_box.restype = C.c_int
         L.svm_train_set_samples.argtypes = [vp, vp, vp, i32, vp, vp, i64]
         L.svm_train_copy_samples.argtypes = [vp, vp, vp, i64]
         L.svm_train_gradient.argtypes = [vp, i64, vp, vp]
@@ -107,6 +110,9 @@ def lib():
                   "svm_train_adam", "svm_train_epoch", "svm_train_evaluate", "svm_train_state",
                   "svm_train_restore"):
             getattr(L, f).restype = C.c_int
+        L.svm_search_free_motion.argtypes = [vp, vp, vp, i32, vp, i64, f32, i32, i32, u32,
+                                             C.POINTER(svm_search_result), vp]
+        L.svm_search_free_motion.restype = C.c_int
         L.svm_profile_enable.argtypes = [vp, C.c_int]
         L.svm_profile_read.argtypes = [vp, vp, i32]
         for f in ("svm_profile_enable", "svm_profile_read", "svm_create_model", "svm_destroy_model", "svm_load_weights", "svm_export_weights",
@@ -250,6 +256,25 @@ def _torch():
     return torch
 
 
+class svm_search_result(C.Structure):
+    _fields_ = [("motion", C.c_int32), ("loop", C.c_int32), ("delta", C.c_float), ("delta_hat", C.c_float),
+                ("n_exact", C.c_int32), ("n_exact_run", C.c_int32), ("n_nn", C.c_int32),
+                ("n_nn_seq", C.c_int32)]
+
+
+def svm_search_free_motion(model, q0, q1, points_dev, margin, steps, wave=1, flags=0, stream=None):
+    """Algorithm 1: the first collision-free motion found with the network as a
+    proxy (flags = SVM_SEARCH_GCC0: exact checks in the given order).  Returns a
+    dict of the svm_search_result fields."""
+    q0, p0 = _host_f64(q0)
+    q1, p1 = _host_f64(q1)
+    out = svm_search_result()
+    _check("svm_search_free_motion", lib().svm_search_free_motion(
+        model, p0, p1, q0.shape[0], _dev(points_dev), points_dev.shape[0], float(margin), int(steps),
+        int(wave), int(flags), C.byref(out), _stream(stream)), model)
+    return {f: getattr(out, f) for f, _ in svm_search_result._fields_}
+
+
 def svm_check_batch(model, q0, q1, motion_scene, points_dev, scene_offsets, margin, steps, flags,
                     results_dev, stream=None):
     q0, p0 = _host_f64(q0)
@@ -391,6 +416,13 @@ def svm_train_make_data(t, q0, q1, samples_per_motion, steps, seed):
     q1, p1 = _host_f64(q1)
     _tcheck("svm_train_make_data", lib().svm_train_make_data(t, p0, p1, q0.shape[0], int(samples_per_motion),
                                                              int(steps), int(seed)), t)
+
+
+def svm_train_set_box(t, lo, hi):
+    lo = np.ascontiguousarray(lo, dtype=np.float64).reshape(3)
+    hi = np.ascontiguousarray(hi, dtype=np.float64).reshape(3)
+    _tcheck("svm_train_set_box", lib().svm_train_set_box(t, lo.ctypes.data_as(C.c_void_p),
+                                                         hi.ctypes.data_as(C.c_void_p)), t)
 
 
 def svm_train_set_samples(t, q0, q1, x4, motion):

@@ -7,6 +7,7 @@
 // host-to-device copy, and enqueues the kernels on the caller's stream:
 // prologue (FK + per-motion bias) -> fused network + gate + compaction ->
 // verifier (-> strict second pass) -> finalize.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -168,6 +169,8 @@ svm_status svm_destroy_model(svm_model* m)
         if (m->d_weights) cudaFree(m->d_weights);
         if (m->ws) cudaFree(m->ws);
         if (m->pinned) cudaFreeHost(m->pinned);
+        if (m->search_dev) cudaFree(m->search_dev);
+        if (m->search_host) cudaFreeHost(m->search_host);
         if (m->staging_done) cudaEventDestroy(m->staging_done);
         for (auto& e : m->ev)
             if (e) cudaEventDestroy(e);
@@ -397,8 +400,10 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
     if (!(margin >= 0) || !std::isfinite(margin)) return fail(m, SVM_E_INVALID, "margin must be finite and >= 0");
     if (steps < 1 || steps > kMaxSteps) return fail(m, SVM_E_INVALID, "steps out of range");
     if ((flags & SVM_PATHS3) && (M % 3) != 0) return fail(m, SVM_E_INVALID, "paths need n_motions % 3 == 0");
-    if (flags & ~(SVM_STRICT | SVM_NO_EARLY_EXIT | SVM_VERIFY_ALL | SVM_PATHS3))
+    if (flags & ~(SVM_STRICT | SVM_NO_EARLY_EXIT | SVM_VERIFY_ALL | SVM_PATHS3 | SVM_PREDICT_ONLY))
         return fail(m, SVM_E_INVALID, "unknown flag");
+    if ((flags & SVM_PREDICT_ONLY) && (flags & (SVM_VERIFY_ALL | SVM_STRICT)))
+        return fail(m, SVM_E_INVALID, "SVM_PREDICT_ONLY excludes SVM_VERIFY_ALL and SVM_STRICT");
     if (scene_off[0] != 0) return fail(m, SVM_E_INVALID, "scene_offsets[0] must be 0");
     for (int s = 0; s < n_scenes; ++s)
         if (scene_off[s + 1] < scene_off[s]) return fail(m, SVM_E_INVALID, "scene offsets decrease");
@@ -500,7 +505,7 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
     a.act = d.act;
     a.flags = flags;
     a.margin = margin;
-    a.gate = (mode == kEval) ? -INFINITY : margin + m->tau;
+    a.gate = (mode == kEval || (flags & SVM_PREDICT_ONLY)) ? -INFINITY : margin + m->tau;
     a.q0 = reinterpret_cast<const double*>(ws + pl.o_q0);
     a.q1 = reinterpret_cast<const double*>(ws + pl.o_q1);
     a.pbeg = reinterpret_cast<const long long*>(ws + pl.o_pbeg);
@@ -540,8 +545,10 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
             return SVM_OK;
         }
         if (prof) CK(cudaEventRecord(m->ev[2], stream));
-        launch_verify(a, 0, 0, stream, m->n_sms);
-        if (flags & SVM_STRICT) launch_verify(a, 1, 1, stream, m->n_sms);
+        if (!(flags & SVM_PREDICT_ONLY)) {
+            launch_verify(a, 0, 0, stream, m->n_sms);
+            if (flags & SVM_STRICT) launch_verify(a, 1, 1, stream, m->n_sms);
+        }
     } else {
         if (prof) CK(cudaEventRecord(m->ev[2], stream));
         launch_verify(a, 1, 0, stream, m->n_sms);
@@ -696,6 +703,125 @@ svm_status svm_label_pairs(svm_model* m, const double* q0, const double* q1, int
     const int64_t off[2] = {0, n_points};
     return run_call(m, kLabel, q0, q1, n_motions, nullptr, points_dev, off, 1, 0.0f, steps, 0u, nullptr,
                     delta_dev, static_cast<cudaStream_t>(stream));
+}
+
+
+svm_status svm_search_free_motion(svm_model* m, const double* q0, const double* q1, int32_t n_motions,
+                                  const float* points_dev, int64_t n_points, float margin, int32_t steps,
+                                  int32_t wave, uint32_t flags, svm_search_result* out, void* stream_)
+{
+    if (!m || !out) return SVM_E_INVALID;
+    if (n_motions < 0 || n_points < 0) return fail(m, SVM_E_INVALID, "negative count");
+    if (wave < 1) return fail(m, SVM_E_INVALID, "wave must be >= 1");
+    if (flags & ~SVM_SEARCH_GCC0) return fail(m, SVM_E_INVALID, "unknown search flag");
+    const bool use_nn = !(flags & SVM_SEARCH_GCC0);
+    if (use_nn && !m->has_weights) return fail(m, SVM_E_WEIGHTS, "no weights loaded");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    *out = svm_search_result{-1, 0, INFINITY, INFINITY, 0, 0, 0, 0};
+    const int M = n_motions;
+    if (M == 0) return SVM_OK;
+    DeviceGuard g(m->device);
+    // result records: one per motion for the prediction, one per motion of a wave
+    const size_t need = (size_t)std::max(M, wave);
+    if (need > m->search_cap) {
+        CK(cudaStreamSynchronize(stream));
+        if (m->search_dev) cudaFree(m->search_dev);
+        if (m->search_host) cudaFreeHost(m->search_host);
+        m->search_dev = nullptr;
+        m->search_host = nullptr;
+        m->search_cap = 0;
+        if (cudaMalloc(&m->search_dev, need * sizeof(svm_result)) != cudaSuccess ||
+            cudaMallocHost(&m->search_host, need * sizeof(svm_result)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(m, SVM_E_OOM, "search buffers");
+        }
+        m->search_cap = need;
+    }
+    svm_result* rd = static_cast<svm_result*>(m->search_dev);
+    svm_result* rh = static_cast<svm_result*>(m->search_host);
+    const int64_t off[2] = {0, n_points};
+    // d_hat(X, m) of every motion (Eq. 6): one network launch, no exact check
+    std::vector<float> dhat(M, INFINITY);
+    if (use_nn) {
+        const svm_status st = run_call(m, kCheck, q0, q1, M, nullptr, points_dev, off, 1, margin, steps,
+                                       SVM_PREDICT_ONLY, rd, nullptr, stream);
+        if (st != SVM_OK) return st;
+        CK(cudaMemcpyAsync(rh, rd, (size_t)M * sizeof(svm_result), cudaMemcpyDeviceToHost, stream));
+        CK(cudaStreamSynchronize(stream));
+        for (int i = 0; i < M; ++i) {
+            if (rh[i].status != 0) return fail(m, SVM_E_TIMEOUT, "a device wait expired");
+            dhat[i] = rh[i].dhat_min;
+        }
+        out->n_nn = M;
+    }
+    // exact checks (the geometric check of every point, early exit at the first
+    // collision) of the motions `list`, in order, `wave` at a time; returns the
+    // position in `list` of the first free motion, or -1
+    std::vector<double> wq0, wq1;
+    auto exact_in_order = [&](const std::vector<int>& list, int& pos, svm_status& st) {
+        pos = -1;
+        for (size_t b = 0; b < list.size(); b += (size_t)wave) {
+            const int nw = (int)std::min<size_t>((size_t)wave, list.size() - b);
+            wq0.resize((size_t)nw * 6);
+            wq1.resize((size_t)nw * 6);
+            for (int k = 0; k < nw; ++k) {
+                std::memcpy(&wq0[(size_t)k * 6], q0 + (size_t)list[b + k] * 6, 48);
+                std::memcpy(&wq1[(size_t)k * 6], q1 + (size_t)list[b + k] * 6, 48);
+            }
+            st = run_call(m, kCheck, wq0.data(), wq1.data(), nw, nullptr, points_dev, off, 1, margin, steps,
+                          SVM_VERIFY_ALL, rd, nullptr, stream);
+            if (st != SVM_OK) return;
+            if (cudaMemcpyAsync(rh, rd, (size_t)nw * sizeof(svm_result), cudaMemcpyDeviceToHost, stream) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(stream) != cudaSuccess) {
+                st = fail(m, SVM_E_CUDA, "search result copy");
+                return;
+            }
+            out->n_exact_run += nw;
+            for (int k = 0; k < nw; ++k) {
+                if (rh[k].status != 0) {
+                    st = fail(m, SVM_E_TIMEOUT, "a device wait expired");
+                    return;
+                }
+                if (!rh[k].collision) {
+                    pos = (int)b + k;
+                    out->delta = rh[k].d_min;
+                    return;
+                }
+            }
+        }
+    };
+    svm_status st = SVM_OK;
+    int pos = -1;
+    // first loop: the motions predicted free, in the given order
+    std::vector<int> first, rest;
+    for (int i = 0; i < M; ++i) (dhat[i] > margin ? first : rest).push_back(i);
+    exact_in_order(first, pos, st);
+    if (st != SVM_OK) return st;
+    if (pos >= 0) {
+        out->motion = first[pos];
+        out->loop = 1;
+        out->n_exact = pos + 1;
+        out->delta_hat = dhat[first[pos]];
+        // the sequential first loop evaluated the network up to the returned motion
+        out->n_nn_seq = use_nn ? out->motion + 1 : 0;
+        return SVM_OK;
+    }
+    out->n_exact = (int)first.size();
+    out->n_nn_seq = use_nn ? M : 0;
+    // second loop: the others by decreasing prediction (ties keep the given order)
+    std::stable_sort(rest.begin(), rest.end(), [&](int a, int b) { return dhat[a] > dhat[b]; });
+    exact_in_order(rest, pos, st);
+    if (st != SVM_OK) return st;
+    if (pos >= 0) {
+        out->motion = rest[pos];
+        out->loop = 2;
+        out->n_exact += pos + 1;
+        out->delta_hat = dhat[rest[pos]];
+    } else {
+        out->n_exact += (int)rest.size();
+    }
+    return SVM_OK;
 }
 
 }  // extern "C"

@@ -22,6 +22,9 @@ struct svm_model {
     std::vector<float> used;          // weights as used, blob order
     std::vector<float> ascales;       // FP8 activation scales
     std::vector<float> bh_host;       // hidden biases [L][W] (for the FP8 scaled copy)
+    void* search_dev = nullptr;       // motion search: device result records
+    void* search_host = nullptr;      // and their pinned host copy
+    size_t search_cap = 0;            // records each holds
     void* d_weights = nullptr;        // one allocation for all weight arrays
     svm::DevWeights dw{};
     svm::TcModel tc{};                     // tensor-core path state (BF16 / FP8)

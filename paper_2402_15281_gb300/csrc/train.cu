@@ -6,7 +6,8 @@
 // with a counter-based SplitMix64 stream (seed, motion, point) -- 70 % near
 // the robot's swept surface (a random sample k, capsule j, position along its
 // axis, unit direction, and radial offset r_j + U[-0.1, 0.1] m), 30 % uniform
-// in the workspace cube [-0.75,0.75]^2 x [0,1.5] -- labelled with the exact
+// in a box (default the workspace cube [-0.75,0.75]^2 x [0,1.5]; see
+// svm_train_set_box) -- labelled with the exact
 // sampled swept-volume distance (the verifier's arithmetic, no gate).
 // Samples are stored grouped by motion; a batch takes every n_batch-th sample
 // from a per-epoch random offset, so each batch mixes all motions.
@@ -52,9 +53,14 @@ __device__ __forceinline__ double sm_u01(unsigned long long base, unsigned long 
     return (double)(sm_fin(base + (i + 1ull) * 0x9E3779B97F4A7C15ull) >> 11) * 0x1.0p-53;
 }
 
+// The box of the uniformly drawn training points.
+struct SampleBox {
+    double lo[3], hi[3];
+};
+
 // One training point of motion m, local index j, and its exact label.
 __global__ void __launch_bounds__(256) sample_kernel(const Capsule* caps, int N, int spm, unsigned long long seed,
-                                                     float4* X, int* MID)
+                                                     SampleBox box, float4* X, int* MID)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     Capsule* cs = reinterpret_cast<Capsule*>(smem);
@@ -85,9 +91,9 @@ __global__ void __launch_bounds__(256) sample_kernel(const Capsule* caps, int N,
             p.y = q.a_r.y + t * q.e_inv.y + rad * rxy * sp;
             p.z = q.a_r.z + t * q.e_inv.z + rad * zc;
         } else {
-            p.x = (float)(-0.75 + 1.5 * sm_u01(base, c + 1));
-            p.y = (float)(-0.75 + 1.5 * sm_u01(base, c + 2));
-            p.z = (float)(1.5 * sm_u01(base, c + 3));
+            p.x = (float)(box.lo[0] + (box.hi[0] - box.lo[0]) * sm_u01(base, c + 1));
+            p.y = (float)(box.lo[1] + (box.hi[1] - box.lo[1]) * sm_u01(base, c + 2));
+            p.z = (float)(box.lo[2] + (box.hi[2] - box.lo[2]) * sm_u01(base, c + 3));
         }
         float mn[kCaps];
         scan_samples(cs, ns, p, mn);
@@ -400,6 +406,7 @@ struct svm_trainer {
     // data
     float4* X = nullptr; int* MID = nullptr; double* q0 = nullptr; double* q1 = nullptr;
     int n_motions = 0; long long n_samples = 0;
+    double box_lo[3] = {-0.75, -0.75, 0.0}, box_hi[3] = {0.75, 0.75, 1.5};   // uniform training points
     std::vector<void*> allocs;
     std::string last_error;
 };
@@ -690,13 +697,32 @@ svm_status svm_train_make_data(svm_trainer* t, const double* q0, const double* q
     const size_t smem = (size_t)(steps + 1) * kCaps * sizeof(Capsule);
     cudaFuncSetAttribute(sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (kMaxSteps + 1) * kCaps * (int)sizeof(Capsule));
-    sample_kernel<<<n_motions, 256, smem, 0>>>(caps, steps, samples_per_motion, (unsigned long long)seed, t->X, t->MID);
+    SampleBox box;
+    for (int q = 0; q < 3; ++q) {
+        box.lo[q] = t->box_lo[q];
+        box.hi[q] = t->box_hi[q];
+    }
+    sample_kernel<<<n_motions, 256, smem, 0>>>(caps, steps, samples_per_motion, (unsigned long long)seed, box, t->X,
+                                               t->MID);
     const cudaError_t e = cudaDeviceSynchronize();
     cudaFree(caps);
     cudaFree(stt);
     if (e != cudaSuccess) return tfail(t, SVM_E_CUDA, std::string("data generation: ") + cudaGetErrorString(e));
     t->n_motions = n_motions;
     t->n_samples = S;
+    return SVM_OK;
+}
+
+svm_status svm_train_set_box(svm_trainer* t, const double* lo, const double* hi)
+{
+    if (!t || !lo || !hi) return SVM_E_INVALID;
+    for (int q = 0; q < 3; ++q)
+        if (!std::isfinite(lo[q]) || !std::isfinite(hi[q]) || !(hi[q] > lo[q]))
+            return tfail(t, SVM_E_INVALID, "box needs finite lo < hi");
+    for (int q = 0; q < 3; ++q) {
+        t->box_lo[q] = lo[q];
+        t->box_hi[q] = hi[q];
+    }
     return SVM_OK;
 }
 

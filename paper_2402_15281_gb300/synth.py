@@ -74,7 +74,7 @@ class Rng:
 
 
 # Purpose codes of the streams (one stream per purpose and seed).
-S_ROBOT, S_MOTION, S_CLOUD, S_WEIGHTS, S_SCENE, S_PATH = 1, 2, 3, 4, 5, 6
+S_ROBOT, S_MOTION, S_CLOUD, S_WEIGHTS, S_SCENE, S_PATH, S_BOX, S_BOX_MOTION = 1, 2, 3, 4, 5, 6, 7, 8
 
 DOF = 6
 N_CAPS = 7
@@ -323,6 +323,70 @@ def bin_paths(robot: Robot, n: int, seed: int = 0):
     q[:, 3] = Q_ABOVE_BIN_DEG + r.uniform(n * DOF, -5.0, 5.0).reshape(n, DOF)
     q *= DEG
     return np.clip(q, robot.qmin, robot.qmax)
+
+
+# --------------------------------------------------------------------------
+# Box world (Sec. V-B)
+# --------------------------------------------------------------------------
+
+BOX_LO = np.array([-1.0, -1.0, 0.0])
+BOX_HI = np.array([1.0, 1.0, 1.5])
+
+
+def _quat_to_matrix(w, x, y, z):
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def box_world(seed: int, n_boxes: int = 50, density_per_cm2: float = 0.1):
+    """A box-world scene as in Sec. V-B: n_boxes boxes with a uniformly random
+    orientation (unit quaternion from three uniforms, Shoemake's method),
+    centres uniform in [-1, 1]^2 x [0, 1.5] m, side lengths uniform in
+    [1, 10] cm; the cloud samples the box surfaces at density_per_cm2 points
+    per cm^2 (round(area * density) points per box, on faces chosen in
+    proportion to their area, uniform on the face).
+    Returns (points (P, 4) float32, centres (n, 3), rotations (n, 3, 3),
+    sides (n, 3))."""
+    r = Rng(seed, S_BOX)
+    centres = BOX_LO + (BOX_HI - BOX_LO) * r.uniform(3 * n_boxes).reshape(n_boxes, 3)
+    u = r.uniform(3 * n_boxes).reshape(n_boxes, 3)
+    sides = r.uniform(3 * n_boxes, 0.01, 0.10).reshape(n_boxes, 3)
+    rots = np.empty((n_boxes, 3, 3))
+    pts = []
+    for b in range(n_boxes):
+        u1, u2, u3 = u[b]
+        x, y = np.sqrt(1 - u1) * np.sin(2 * np.pi * u2), np.sqrt(1 - u1) * np.cos(2 * np.pi * u2)
+        z, w = np.sqrt(u1) * np.sin(2 * np.pi * u3), np.sqrt(u1) * np.cos(2 * np.pi * u3)
+        rots[b] = _quat_to_matrix(w, x, y, z)
+        a, bb, c = sides[b]
+        face_area = np.array([bb * c, bb * c, a * c, a * c, a * bb, a * bb])
+        n = int(round(face_area.sum() * 1e4 * density_per_cm2))
+        if n == 0:
+            continue
+        cum = np.cumsum(face_area) / face_area.sum()
+        f = np.minimum(np.searchsorted(cum, r.uniform(n), side="right"), 5)
+        s = r.uniform(2 * n, -0.5, 0.5).reshape(n, 2)
+        local = np.empty((n, 3))
+        axis, sign = f // 2, np.where(f % 2 == 0, 0.5, -0.5)
+        half = np.array([a, bb, c])
+        for k in range(n):
+            other = [i for i in range(3) if i != axis[k]]
+            local[k, axis[k]] = sign[k] * half[axis[k]]
+            local[k, other[0]] = s[k, 0] * half[other[0]]
+            local[k, other[1]] = s[k, 1] * half[other[1]]
+        pts.append(local @ rots[b].T + centres[b])
+    xyz = np.concatenate(pts) if pts else np.zeros((0, 3))
+    return _as_points4(xyz), centres, rots, sides
+
+
+def box_world_motions(robot: Robot, n_goals: int, seed: int):
+    """One start configuration and n_goals goals, all uniform within the joint
+    limits (Sec. V-B): q0 (n_goals, 6) repeats the start, q1 the goals."""
+    r = Rng(seed, S_BOX_MOTION)
+    start = robot.qmin + (robot.qmax - robot.qmin) * r.uniform(DOF)
+    goals = robot.qmin + (robot.qmax - robot.qmin) * r.uniform(n_goals * DOF).reshape(n_goals, DOF)
+    return np.repeat(start[None], n_goals, axis=0), goals
 
 
 # --------------------------------------------------------------------------

@@ -26,11 +26,25 @@ def bin_training_motions(robot, n, seed):
     return q0[order], q1[order]
 
 
+def path_training_motions(robot, n, seed):
+    """Motions like the three-segment paths of Sec. V-C: the segments of
+    n // 6 paths (synth.bin_paths: into the bin, between the vias, out of the
+    bin) plus bin_training_motions for the rest, in a seeded random order."""
+    n_paths = n // 6
+    paths = S.bin_paths(robot, n_paths, seed=seed)
+    pa0, pa1 = paths[:, :3].reshape(-1, 6), paths[:, 1:].reshape(-1, 6)
+    qb0, qb1 = bin_training_motions(robot, n - len(pa0), seed)
+    q0, q1 = np.concatenate([pa0, qb0]), np.concatenate([pa1, qb1])
+    order = np.argsort(S.Rng(seed, 98).uniform(n))
+    return q0[order], q1[order]
+
+
 def train_model(svm, robot, q0, q1, width=256, n_hidden=4, act=0, samples_per_motion=4096, steps=128,
                 batch=65536, epochs=30, lr=1e-3, val_fraction=0.2, patience=10, data_seed=7, init_seed=2,
-                device=0, log=None):
-    """Train f on GPU-generated data for the motions (q0, q1).  Returns
-    (blob of the best-validation weights, history dict)."""
+                device=0, log=None, box=None):
+    """Train f on GPU-generated data for the motions (q0, q1); box = (lo, hi)
+    sets the box of the uniformly drawn points.  Returns (blob of the
+    best-validation weights, history dict)."""
     t0 = time.perf_counter()
     n = len(q0)
     n_val = max(1, int(round(n * val_fraction)))
@@ -39,6 +53,8 @@ def train_model(svm, robot, q0, q1, width=256, n_hidden=4, act=0, samples_per_mo
     hist = {"epoch_loss": [], "val_mae": [], "lr": []}
     try:
         svm.svm_train_set_weights(t, svm.make_blob(S.xavier_weights(width, n_hidden, seed=init_seed), act=act))
+        if box is not None:
+            svm.svm_train_set_box(t, box[0], box[1])
         svm.svm_train_make_data(t, q0, q1, samples_per_motion, steps, data_seed)
         tr_end = n_tr * samples_per_motion
         va_end = n * samples_per_motion

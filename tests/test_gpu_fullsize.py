@@ -98,16 +98,19 @@ def test_full_size_verdicts_and_outputs(setup, prec):
 def test_config4_paths_full_size(setup):
     """Three-segment paths at full size: 128 paths q_start -> q_inVia ->
     q_outVia -> q_end (Sec. V-C) against a 300 000-point bin cloud, BF16,
-    trained network, early exit on the first colliding segment.  The gate is
-    calibrated on the segments of 16 separate paths: the network was trained
-    on grasp motions into the bin, and the reversed and via segments of a path
-    come from another distribution, for which a gate calibrated on grasp
-    motions alone misses collisions.  Verdicts (default and SVM_STRICT) equal
+    network trained on path segments (training.path_training_motions), early
+    exit on the first colliding segment.  The gate is calibrated on the
+    segments of 16 separate paths: a network trained on grasp motions into the
+    bin alone, with a gate calibrated on such motions, misses collisions on
+    the reversed and via segments of a path.  Verdicts (default and SVM_STRICT) equal
     the exact check of every pair (OR over segments, free iff d > eps); two
     paths are checked against the FP64 oracle (Eq. 5) in full.  The call is
     timed."""
     import time
-    svm, training, robot, blob, hist, _, _, _, _, _, _ = setup
+    svm, training, robot, _, _, _, _, _, _, _, _ = setup
+    tq0, tq1 = training.path_training_motions(robot, 1536, seed=43)
+    blob, hist = training.train_model(svm, robot, tq0, tq1, samples_per_motion=4096, steps=N, batch=65536,
+                                      epochs=30, patience=10)
     paths = S.bin_paths(robot, 128, seed=4)
     q0 = np.ascontiguousarray(paths[:, :3].reshape(-1, 6))
     q1 = np.ascontiguousarray(paths[:, 1:].reshape(-1, 6))
@@ -146,6 +149,7 @@ def test_config4_paths_full_size(setup):
         pairs = 3 * 128 * len(pts)
         print(f"config 4: 128 paths x 3 segments x {len(pts)} points = {pairs / 1e6:.0f} M pairs in {ms:.1f} ms "
               f"(wall) = {pairs / ms / 1e6:.2f} G pairs/s; tau {tau:.4f} m, flagged "
-              f"{r['n_flagged'].sum() / pairs:.2%}; {r['collision'].sum()} paths collide")
+              f"{r['n_flagged'].sum() / pairs:.2%}; {r['collision'].sum()} paths collide; "
+              f"validation MAE {hist['best_val_mae']:.4f} m")
     finally:
         svm.svm_destroy_model(h)

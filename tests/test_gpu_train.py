@@ -34,17 +34,21 @@ def robot():
     return S.make_robot(1)
 
 
-def test_training_data_matches_oracle(svm, robot):
+@pytest.mark.parametrize("box", [None, (S.BOX_LO, S.BOX_HI)])
+def test_training_data_matches_oracle(svm, robot, box):
     q0, q1 = S.uniform_motions(robot, 4, seed=21, max_step_deg=40)
     t = svm.svm_train_create(robot, 256, 2, 0, 256)
     try:
+        if box is not None:
+            svm.svm_train_set_box(t, *box)
         svm.svm_train_make_data(t, q0, q1, 1000, 32, 11)
         x4, mid = svm.svm_train_copy_samples(t, 4000)
     finally:
         svm.svm_train_destroy(t)
     np.testing.assert_array_equal(mid, np.repeat(np.arange(4), 1000))
+    lo, hi = box if box is not None else (None, None)
     for m in range(4):
-        ref = oracle.training_points(robot, q0[m], q1[m], 32, 11, m, 1000)
+        ref = oracle.training_points(robot, q0[m], q1[m], 32, 11, m, 1000, lo, hi)
         got = x4[m * 1000:(m + 1) * 1000].astype(np.float64)
         assert np.abs(got[:, :3] - ref[:, :3]).max() <= 1e-5
         assert np.abs(got[:, 3] - ref[:, 3]).max() <= 2e-5

@@ -492,3 +492,22 @@ def test_splitmix64_oracle_matches_generator():
     u = r.uniform(50)
     for i in range(50):
         assert oracle.splitmix64_u01(17, 9, i) == u[i]
+
+
+def test_training_points_box():
+    """The uniform training draws fill the requested box: the default box gives
+    the default generator's points bit for bit; a wider box moves only the
+    uniform draws (the near-surface ones stay), and those fill the wider box."""
+    robot = S.make_robot(1)
+    q0, q1 = S.uniform_motions(robot, 1, seed=5, max_step_deg=30)
+    a = oracle.training_points(robot, q0[0], q1[0], 16, 3, 0, 4000)
+    b = oracle.training_points(robot, q0[0], q1[0], 16, 3, 0, 4000, [-0.75, -0.75, 0.0], [0.75, 0.75, 1.5])
+    np.testing.assert_array_equal(a, b)
+    c = oracle.training_points(robot, q0[0], q1[0], 16, 3, 0, 4000, S.BOX_LO, S.BOX_HI)
+    moved = np.any(a[:, :3] != c[:, :3], axis=1)
+    assert 0.25 < moved.mean() < 0.35                       # the 30 % uniform draws
+    # a uniform draw keeps its unit coordinates: x' = lo' + (x - lo) / (hi - lo) * (hi' - lo')
+    lo0, hi0 = np.array([-0.75, -0.75, 0.0]), np.array([0.75, 0.75, 1.5])
+    u = (a[moved, :3] - lo0) / (hi0 - lo0)
+    np.testing.assert_allclose(c[moved, :3], S.BOX_LO + u * (S.BOX_HI - S.BOX_LO), atol=1e-12)
+    assert np.all(c[moved, :3] >= S.BOX_LO) and np.all(c[moved, :3] <= S.BOX_HI)
