@@ -116,15 +116,17 @@ def test_search_matches_algorithm1(setup, prec):
 
 
 def test_box_world_experiment(setup):
-    """The box-world experiment of Sec. V-B (Table III's quantities): 100
-    scenes x 100 motions from one start, 5 mm margin, 200 steps, BF16; for each
-    scene and several orders of its motions, the time to the first free motion
-    of GCC_0 and of Algorithm 1 (wave 1), and their exact-check counts."""
+    """The box-world experiment of Sec. V-B (the quantities of its results
+    table): 100 scenes x 100 motions from one start, 5 mm margin, 200 steps,
+    BF16; for each scene and several orders of its motions, the time to the
+    first free motion of GCC_0 and of Algorithm 1 and their exact-check
+    counts, run sequentially (wave 1, the paper's algorithm) and with 8 or all
+    candidates checked per launch (same answers, more exact checks run)."""
     svm, robot, blob, hist = setup
     h = _model(svm, robot, blob, 1)
     n_scenes, n_perm = 100, 5
     rng = np.random.default_rng(0)
-    rows = {"gcc0": [], "nn": [], "gcc0_w8": [], "nn_w8": []}
+    rows = {"gcc0": [], "nn": [], "gcc0_w8": [], "nn_w8": [], "gcc0_w128": [], "nn_w128": []}
     free_frac, cls = [], []
     try:
         for scene in range(n_scenes):
@@ -134,7 +136,8 @@ def test_box_world_experiment(setup):
             for k in range(n_perm):
                 perm = rng.permutation(100)
                 for name, flags, wave in (("gcc0", svm.SVM_SEARCH_GCC0, 1), ("nn", 0, 1),
-                                          ("gcc0_w8", svm.SVM_SEARCH_GCC0, 8), ("nn_w8", 0, 8)):
+                                          ("gcc0_w8", svm.SVM_SEARCH_GCC0, 8), ("nn_w8", 0, 8),
+                                          ("gcc0_w128", svm.SVM_SEARCH_GCC0, 128), ("nn_w128", 0, 128)):
                     torch.cuda.synchronize()
                     t = time.perf_counter()
                     r = svm.svm_search_free_motion(h, q0[perm], q1[perm], pts_d, EPS, N, wave=wave, flags=flags)
@@ -151,8 +154,8 @@ def test_box_world_experiment(setup):
                             np.mean(~pred_coll & (coll == 1))))
         g, n = np.array(rows["gcc0"]), np.array(rows["nn"])
         assert np.array_equal(g[:, 3], n[:, 3])             # both find a free motion in the same scenes
-        for w1, w8 in (("gcc0", "gcc0_w8"), ("nn", "nn_w8")):  # waves change the work, not the answer
-            assert np.array_equal(np.array(rows[w1])[:, 1], np.array(rows[w8])[:, 1])
+        for w1, wk in (("gcc0", "gcc0_w8"), ("nn", "nn_w8"), ("gcc0", "gcc0_w128"), ("nn", "nn_w128")):
+            assert np.array_equal(np.array(rows[w1])[:, 1], np.array(rows[wk])[:, 1])   # same answer, other work
         print(f"box world, {n_scenes} scenes x {n_perm} orders (BF16 256x4, val MAE {hist['best_val_mae']:.4f} m); "
               f"free motions in the first 10 scenes: {np.mean(free_frac):.1%}; "
               f"scenes with a free motion: {g[:, 3].mean():.1%}")
@@ -162,9 +165,10 @@ def test_box_world_experiment(setup):
         has_free = g[:, 3] > 0
         for subset, sel in (("all scenes", np.ones_like(has_free)), ("scenes with a free motion", has_free)):
             print(f"  {subset}:")
-            for name, key in (("GCC_0", "gcc0"), ("GCC-NN", "nn"), ("GCC_0 w8", "gcc0_w8"), ("GCC-NN w8", "nn_w8")):
+            for name, key in (("GCC_0", "gcc0"), ("GCC-NN", "nn"), ("GCC_0 w8", "gcc0_w8"), ("GCC-NN w8", "nn_w8"),
+                              ("GCC_0 w128", "gcc0_w128"), ("GCC-NN w128", "nn_w128")):
                 a = np.array(rows[key])[sel]
-                print(f"    {name:9s} time {a[:, 0].mean():.3f} +- {a[:, 0].std():.3f} ms, exact checks "
+                print(f"    {name:11s} time {a[:, 0].mean():.3f} +- {a[:, 0].std():.3f} ms, exact checks "
                       f"{a[:, 1].mean():.2f} +- {a[:, 1].std():.2f} (run {a[:, 4].mean():.2f})" +
                       (f", NN checks (sequential) {a[:, 2].mean():.2f} +- {a[:, 2].std():.2f}" if "NN" in name else ""))
         assert n[:, 1].mean() <= g[:, 1].mean()
