@@ -58,19 +58,30 @@ typedef enum { SVM_RELU = 0, SVM_SILU = 1 } svm_act;
  * dh[j] = {d_j, a_j, alpha_j, theta_j}.  Its geometry is 7 capsules: capsule
  * j < 6 joins the origins of frames j and j+1, capsule 6 runs tool_len along
  * the z axis of frame 6; radius[j] is capsule j's radius.
- * Network: input [x, y, z, q0_1..q0_6, q1_1..q1_6] -> width (act) ->
- * n_hidden x (width -> width, act) -> 1.  The BF16 and FP8 tensor-core path
- * needs width 256 and 1 <= n_hidden <= 16; the FP32 path takes width 64, 128,
- * 256 or 512 and 0 <= n_hidden <= 16. */
+ * Network (arch SVM_ARCH_MLP): input [x, y, z, q0_1..q0_6, q1_1..q1_6] ->
+ * width (act) -> n_hidden x (width -> width, act) -> 1.  The BF16 and FP8
+ * tensor-core path needs width 256 and 1 <= n_hidden <= 16; the FP32 path
+ * takes width 64, 128, 256 or 512 and 0 <= n_hidden <= 16.
+ * Network (arch SVM_ARCH_BLOCKS, the block architecture of Sec. IV-A):
+ * an initial linear layer 15 -> width, n_hidden blocks (linear -> ReLU ->
+ * BatchNorm at inference, plus the block input; from the second block on the
+ * linear layer also reads the network input, the jump connection), and a
+ * final layer [h; input] -> 1.  FP32 path only, ReLU, width 64..512,
+ * 1 <= n_hidden <= 16; BatchNorm is folded into a per-channel scale and
+ * shift at load. */
 typedef struct {
     double dh[6][4];
     double radius[7];
     double tool_len;
     int32_t width;
-    int32_t n_hidden;
-    int32_t act;     /* svm_act       */
-    int32_t prec;    /* svm_precision */
+    int32_t n_hidden;   /* hidden layers (SVM_ARCH_MLP) or blocks (SVM_ARCH_BLOCKS) */
+    int32_t act;        /* svm_act       */
+    int32_t prec;       /* svm_precision */
+    int32_t arch;       /* SVM_ARCH_MLP (0) or SVM_ARCH_BLOCKS (1) */
 } svm_model_desc;
+
+#define SVM_ARCH_MLP    0
+#define SVM_ARCH_BLOCKS 1
 
 /* Per-motion (or per-path) result, 32 bytes, written to device memory. */
 typedef struct {
@@ -128,7 +139,15 @@ svm_status svm_destroy_model(svm_model* m);
  * hidden weights to E4M3 (nearest-even, saturating) with the per-layer scale
  * s = max|W| / 448 (float) and the other layers to BF16.  Biases stay FP32.
  * tau sets the gate offset (see svm_set_gate).  Returns SVM_E_WEIGHTS on a
- * malformed blob. */
+ * malformed blob.
+ * SVM_ARCH_BLOCKS models take version 2:
+ *   char magic[4] = "SVMW"; uint32 version = 2; uint32 n_blocks;
+ *   uint32 in_dim = 15; uint32 width; uint32 act = 0; float tau; float bn_eps;
+ *   initial layer: uint32 width, uint32 15, float W[width][15], float b[width];
+ *   block l = 1..n_blocks: uint32 width, uint32 in (width for l = 1, width + 15
+ *   after: [h; x, q0, q1]), float W[width][in], b[width], gamma[width],
+ *   beta[width], running_mean[width], running_var[width];
+ *   final layer: uint32 1, uint32 width + 15, float W[width + 15], float b. */
 svm_status svm_load_weights(svm_model* m, const void* blob, size_t bytes);
 
 /* Copy the weights as the model uses them (after rounding, dequantised to

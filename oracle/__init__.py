@@ -380,3 +380,39 @@ def search_gcc0(delta, eps):
         if d > eps:
             return {"motion": m, "n_exact": m + 1}
     return {"motion": -1, "n_exact": len(delta)}
+
+
+# ------------------------------------------------------------ block architecture
+
+def block_forward(params, inputs, bn_eps=1e-5) -> np.ndarray:
+    """The network of Sec. IV-A in FP64, BatchNorm at inference (running
+    statistics), written from its definition:
+      h_0 = W_0 u + b_0                      (initial linear layer, u = [x; q0; q1])
+      block l: v = h_{l-1} (l = 1) or [h_{l-1}; u] (l > 1, jump connection)
+               h_l = BN_l(ReLU(W_l v + b_l)) + h_{l-1}   (skip connection)
+               BN(y) = gamma (y - mean) / sqrt(var + eps) + beta
+      f = w_f [h_L; u] + b_f                 (final layer)
+    inputs: (n, 15).  Returns (n,)."""
+    u = np.asarray(inputs, dtype=np.float64).reshape(-1, 15)
+    W0, b0 = (np.asarray(a, dtype=np.float64) for a in params["init"])
+    h = u @ W0.T + b0
+    for l, blk in enumerate(params["blocks"]):
+        W, b, gamma, beta, mean, var = (np.asarray(a, dtype=np.float64) for a in blk)
+        v = h if l == 0 else np.concatenate([h, u], axis=1)
+        y = np.maximum(v @ W.T + b, 0.0)
+        h = gamma * (y - mean) / np.sqrt(var + bn_eps) + beta + h
+    Wf, bf = (np.asarray(a, dtype=np.float64) for a in params["final"])
+    return (np.concatenate([h, u], axis=1) @ Wf.T + bf)[:, 0]
+
+
+def block_pairs(params, q0, q1, points, bn_eps=1e-5) -> np.ndarray:
+    """block_forward for every (motion, point) pair: (M, n)."""
+    q0 = _d(q0).reshape(-1, 6)
+    q1 = _d(q1).reshape(-1, 6)
+    pts = _xyz(points)
+    M, n = q0.shape[0], pts.shape[0]
+    out = np.empty((M, n))
+    for m in range(M):
+        u = np.concatenate([pts, np.repeat(q0[m][None], n, 0), np.repeat(q1[m][None], n, 0)], axis=1)
+        out[m] = block_forward(params, u, bn_eps)
+    return out

@@ -34,7 +34,8 @@ assert RESULT_DTYPE.itemsize == 32
 
 class svm_model_desc(C.Structure):
     _fields_ = [("dh", (C.c_double * 4) * 6), ("radius", C.c_double * 7), ("tool_len", C.c_double),
-                ("width", C.c_int32), ("n_hidden", C.c_int32), ("act", C.c_int32), ("prec", C.c_int32)]
+                ("width", C.c_int32), ("n_hidden", C.c_int32), ("act", C.c_int32), ("prec", C.c_int32),
+                ("arch", C.c_int32)]
 
 
 class SvmError(RuntimeError):
@@ -152,7 +153,10 @@ def _dev(t):
 
 # ------------------------------------------------------------------ entry points
 
-def svm_create_model(robot, width=256, n_hidden=4, act=SVM_RELU, prec=SVM_FP32, device=0):
+SVM_ARCH_MLP, SVM_ARCH_BLOCKS = 0, 1
+
+
+def svm_create_model(robot, width=256, n_hidden=4, act=SVM_RELU, prec=SVM_FP32, device=0, arch=SVM_ARCH_MLP):
     d = svm_model_desc()
     for j in range(6):
         for c in range(4):
@@ -160,7 +164,7 @@ def svm_create_model(robot, width=256, n_hidden=4, act=SVM_RELU, prec=SVM_FP32, 
     for j in range(7):
         d.radius[j] = float(robot.radius[j])
     d.tool_len = float(robot.tool_len)
-    d.width, d.n_hidden, d.act, d.prec = int(width), int(n_hidden), int(act), int(prec)
+    d.width, d.n_hidden, d.act, d.prec, d.arch = int(width), int(n_hidden), int(act), int(prec), int(arch)
     h = C.c_void_p()
     _check("svm_create_model", lib().svm_create_model(C.byref(d), int(device), C.byref(h)))
     return h
@@ -180,6 +184,21 @@ def make_blob(layers, act=SVM_RELU, tau=float("inf")) -> bytes:
         out.append(struct.pack("<II", W.shape[0], W.shape[1]))
         out.append(W.tobytes())
         out.append(b.tobytes())
+    return b"".join(out)
+
+
+def make_block_blob(params, tau=float("inf"), bn_eps=1e-5) -> bytes:
+    """Serialise the block architecture (synth.block_weights layout) in the
+    version-2 blob format of svm_load_weights."""
+    W0, b0 = params["init"]
+    width = W0.shape[0]
+    f4 = lambda a: np.ascontiguousarray(a, dtype="<f4").tobytes()
+    out = [b"SVMW", struct.pack("<IIIIIff", 2, len(params["blocks"]), 15, width, SVM_RELU, tau, bn_eps)]
+    out += [struct.pack("<II", *W0.shape), f4(W0), f4(b0)]
+    for (W, b, gamma, beta, mean, var) in params["blocks"]:
+        out += [struct.pack("<II", *W.shape), f4(W), f4(b), f4(gamma), f4(beta), f4(mean), f4(var)]
+    Wf, bf = params["final"]
+    out += [struct.pack("<II", *Wf.shape), f4(Wf), f4(bf)]
     return b"".join(out)
 
 

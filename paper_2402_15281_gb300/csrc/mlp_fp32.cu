@@ -29,8 +29,12 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// W: network width.  KC: hidden-weight rows per pipeline stage.
-template <int W, int KC>
+// W: network width.  KC: hidden-weight rows per pipeline stage.  BLOCK: the
+// block architecture (initial layer without activation; per block
+// h = s * relu(W h + Wx x + c_{m,l}) + t + h, the jump input's q-part folded
+// into c_{m,l} by the prologue, BatchNorm folded into s and t; final layer
+// w_f . h + w_fx . x + c_{m,f}).
+template <int W, int KC, bool BLOCK>
 __global__ void __launch_bounds__(NT, 1) mlp_fp32_kernel(CallArgs A, DevWeights Wt)
 {
     constexpr int CPT = W / 16;          // columns per thread
@@ -40,6 +44,7 @@ __global__ void __launch_bounds__(NT, 1) mlp_fp32_kernel(CallArgs A, DevWeights 
     float* H = smem;                     // [BM][HS] activations, row-major
     float* WS = smem + BM * HS;          // [2][KC][W] transposed weight stages
     __shared__ float f_s[BM];
+    __shared__ float4 x_s[BM];           // the tile's points (block architecture)
 
     const int tid = threadIdx.x;
     const int ty = tid >> 4, tx = tid & 15;
@@ -47,7 +52,7 @@ __global__ void __launch_bounds__(NT, 1) mlp_fp32_kernel(CallArgs A, DevWeights 
     const int m = find_segment(A.tile_off, A.M, tile);
     const long long p0 = A.pbeg[m] + (long long)(tile - A.tile_off[m]) * BM;
     const long long pe = A.pend[m];
-    const float* cb = A.cbias + (long long)m * W;
+    const float* cb = A.cbias + (long long)m * A.cb_stride;
 
     // stage loader: flat chunk g = layer * (W/KC) + kc
     constexpr int CHUNKS_PER_LAYER = W / KC;
@@ -80,9 +85,13 @@ __global__ void __launch_bounds__(NT, 1) mlp_fp32_kernel(CallArgs A, DevWeights 
                 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     const float z = fmaf(w2, xr[r].z, fmaf(w1, xr[r].y, fmaf(w0, xr[r].x, bo)));
-                    H[(ty * 4 + r) * HS + o] = act_fn(z, A.act);
+                    H[(ty * 4 + r) * HS + o] = BLOCK ? z : act_fn(z, A.act);
                 }
             }
+        }
+        if (BLOCK && tx == 0) {
+            #pragma unroll
+            for (int r = 0; r < 4; ++r) x_s[ty * 4 + r] = xr[r];
         }
     }
     // calibration: the largest magnitude entering each hidden layer (valid rows only)
@@ -141,6 +150,34 @@ __global__ void __launch_bounds__(NT, 1) mlp_fp32_kernel(CallArgs A, DevWeights 
             __syncthreads();   // stage (g & 1) and H reads done
         }
 
+        if constexpr (BLOCK) {
+            // z = W h + Wx x + c_{m,l}; h <- s relu(z) + t + h (own elements, after the GEMM's reads)
+            const float* cl = cb + (long long)(l + 1) * W;
+            const float* wxl = Wt.blk_wx + (long long)l * W * 3;
+            const float* sl = Wt.blk_s + (long long)l * W;
+            const float* tl = Wt.blk_t + (long long)l * W;
+            const bool last = l + 1 == A.L;
+            #pragma unroll
+            for (int c = 0; c < CG; ++c)
+                #pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int o = tx * 4 + 64 * c + i;
+                    const float w0 = __ldg(wxl + o * 3 + 0), w1 = __ldg(wxl + o * 3 + 1), w2 = __ldg(wxl + o * 3 + 2);
+                    const float co = __ldg(cl + o), so = __ldg(sl + o), to = __ldg(tl + o);
+                    const float wo = last ? __ldg(Wt.wout + o) : 0.0f;
+                    #pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const float4 x = x_s[ty * 4 + r];
+                        const float z = fmaf(w2, x.z, fmaf(w1, x.y, fmaf(w0, x.x, acc[r][c * 4 + i] + co)));
+                        float* hp = H + (ty * 4 + r) * HS + o;
+                        const float h = fmaf(so, fmaxf(z, 0.0f), to) + *hp;
+                        if (last) fpart[r] = fmaf(wo, h, fpart[r]);
+                        else *hp = h;
+                    }
+                }
+            if (!last) __syncthreads();
+            continue;
+        }
         const float* bl = Wt.bh + (long long)l * W;
         if (l + 1 < A.L) {
             // epilogue: bias + activation back into the activation tile
@@ -198,7 +235,16 @@ __global__ void __launch_bounds__(NT, 1) mlp_fp32_kernel(CallArgs A, DevWeights 
         v += __shfl_xor_sync(0xffffffffu, v, 4);
         v += __shfl_xor_sync(0xffffffffu, v, 2);
         v += __shfl_xor_sync(0xffffffffu, v, 1);
-        if (tx == 0) f_s[ty * 4 + r] = v + Wt.bout;
+        if (tx == 0) {
+            if constexpr (BLOCK) {
+                const float4 x = x_s[ty * 4 + r];
+                const float* ow = Wt.out_wx;
+                f_s[ty * 4 + r] = v + fmaf(__ldg(ow + 2), x.z, fmaf(__ldg(ow + 1), x.y,
+                                                                    fmaf(__ldg(ow), x.x, cb[(long long)(A.L + 1) * W])));
+            } else {
+                f_s[ty * 4 + r] = v + Wt.bout;
+            }
+        }
     }
     __syncthreads();
 
@@ -226,18 +272,25 @@ __global__ void __launch_bounds__(NT, 1) mlp_fp32_kernel(CallArgs A, DevWeights 
     }
 }
 
-template <int W, int KC>
-void launch_w(const CallArgs& a, const DevWeights& w, int n_tiles, cudaStream_t s)
+template <int W, int KC, bool BLOCK>
+void launch_wb(const CallArgs& a, const DevWeights& w, int n_tiles, cudaStream_t s)
 {
     const size_t smem = (size_t)(BM * (W + HPAD) + 2 * KC * W) * sizeof(float);
     int dev = 0;
     cudaGetDevice(&dev);
     static bool configured[64] = {};
     if (dev >= 0 && dev < 64 && !configured[dev]) {
-        cudaFuncSetAttribute(mlp_fp32_kernel<W, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(mlp_fp32_kernel<W, KC, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured[dev] = true;
     }
-    mlp_fp32_kernel<W, KC><<<n_tiles, NT, smem, s>>>(a, w);
+    mlp_fp32_kernel<W, KC, BLOCK><<<n_tiles, NT, smem, s>>>(a, w);
+}
+
+template <int W, int KC>
+void launch_w(const CallArgs& a, const DevWeights& w, int n_tiles, cudaStream_t s)
+{
+    if (a.arch == 1) launch_wb<W, KC, true>(a, w, n_tiles, s);
+    else launch_wb<W, KC, false>(a, w, n_tiles, s);
 }
 
 }  // namespace

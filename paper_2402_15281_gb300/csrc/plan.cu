@@ -68,6 +68,8 @@ CallArgs plan_args(svm_plan* p, const float* points)
     a.W = m->desc.width;
     a.L = m->desc.n_hidden;
     a.act = m->desc.act;
+    a.arch = m->desc.arch;
+    a.cb_stride = cbias_stride(m->desc);
     a.flags = p->flags;
     a.margin = p->margin;
     a.gate = p->margin + m->tau;
@@ -178,7 +180,7 @@ svm_status svm_plan_create(svm_model* m, const double* q0, const double* q1, int
     p->o_poff = at; at = al256(at + (size_t)(M + 1) * 8);
     const size_t header = at;
     p->o_caps = at; at = al256(at + (size_t)M * (steps + 1) * kCaps * sizeof(Capsule));
-    p->o_cbias = at; at = al256(at + (size_t)M * m->desc.width * 4);
+    p->o_cbias = at; at = al256(at + (size_t)M * cbias_stride(m->desc) * 4);
     p->o_st = at; at = al256(at + (size_t)M * sizeof(MotionState));
     p->o_idx = at; at = al256(at + (size_t)std::max<long long>(1, p->P_total) * 4);
     p->o_chunk = at; at = al256(at + (size_t)(M + 1) * 4);

@@ -64,16 +64,30 @@ __global__ void __launch_bounds__(128) prologue_kernel(CallArgs A, RobotParams R
         }
     }
 
-    // (b) c_m = W1q [q0; q1] + b1, q cast to FP32 once
+    // (b) c_m = W1q [q0; q1] + b1, q cast to FP32 once.  Block architecture:
+    //     the same for the initial layer and for every block (its q-weights
+    //     and bias; block 1 has no jump input), then the final layer's scalar.
     if (A.cbias != nullptr) {
         float qf[12];
         for (int i = 0; i < kDof; ++i) { qf[i] = (float)q0[i]; qf[kDof + i] = (float)q1[i]; }
-        for (int o = threadIdx.x; o < A.W; o += blockDim.x) {
-            float s = Wt.b1[o];
-            const float* wr = Wt.w1q + o * 12;
-            #pragma unroll
-            for (int i = 0; i < 12; ++i) s = fmaf(wr[i], qf[i], s);
-            A.cbias[(long long)m * A.W + o] = s;
+        float* cm = A.cbias + (long long)m * A.cb_stride;
+        if (A.arch == 0) {
+            for (int o = threadIdx.x; o < A.W; o += blockDim.x) {
+                float s = Wt.b1[o];
+                const float* wr = Wt.w1q + o * 12;
+                #pragma unroll
+                for (int i = 0; i < 12; ++i) s = fmaf(wr[i], qf[i], s);
+                cm[o] = s;
+            }
+        } else {
+            const int n = (A.L + 1) * A.W;
+            for (int k = threadIdx.x; k <= n; k += blockDim.x) {
+                const float* wr = k < n ? Wt.blk_wq + (long long)k * 12 : Wt.out_wq;
+                float s = k < n ? Wt.blk_b[k] : Wt.bout;
+                #pragma unroll
+                for (int i = 0; i < 12; ++i) s = fmaf(wr[i], qf[i], s);
+                cm[k] = s;
+            }
         }
     }
 

@@ -97,6 +97,113 @@ svm_status upload_scaled_biases(svm_model* m)
     return SVM_OK;
 }
 
+// Version-2 blob of the block architecture: parse, fold BatchNorm into a
+// per-channel scale and shift, and upload the FP32 layouts the FP32 kernel
+// and the prologue read.
+svm_status load_block_weights(svm_model* m, const unsigned char* p, size_t bytes)
+{
+    const svm_model_desc& d = m->desc;
+    auto rd32 = [&](size_t off) { uint32_t v; std::memcpy(&v, p + off, 4); return v; };
+    if (bytes < 32) return fail(m, SVM_E_WEIGHTS, "truncated blob");
+    const uint32_t nb = rd32(8), in_dim = rd32(12), width = rd32(16), act = rd32(20);
+    float tau, bn_eps;
+    std::memcpy(&tau, p + 24, 4);
+    std::memcpy(&bn_eps, p + 28, 4);
+    if ((int)nb != d.n_hidden || in_dim != (uint32_t)kInDim || width != (uint32_t)d.width || act != SVM_RELU)
+        return fail(m, SVM_E_WEIGHTS, "blob does not match the model description");
+    if (!(bn_eps >= 0.0f) || !std::isfinite(bn_eps)) return fail(m, SVM_E_WEIGHTS, "bad BatchNorm epsilon");
+    const long long W = d.width, L = d.n_hidden, J = W + kInDim;
+    size_t off = 32;
+    std::vector<float> all;   // every float of the blob in order (the export)
+    auto take = [&](uint32_t want_o, uint32_t want_i, size_t n_extra, std::vector<float>& dst) -> bool {
+        if (off + 8 > bytes) return false;
+        if (rd32(off) != want_o || rd32(off + 4) != want_i) return false;
+        off += 8;
+        const size_t n = (size_t)want_o * want_i + n_extra;
+        if (off + n * 4 > bytes) return false;
+        dst.resize(n);
+        std::memcpy(dst.data(), p + off, n * 4);
+        off += n * 4;
+        all.insert(all.end(), dst.begin(), dst.end());
+        return true;
+    };
+    std::vector<float> init, fin;
+    std::vector<std::vector<float>> blk(L);
+    if (!take((uint32_t)W, (uint32_t)kInDim, W, init)) return fail(m, SVM_E_WEIGHTS, "initial layer shape or size");
+    for (long long l = 0; l < L; ++l)
+        if (!take((uint32_t)W, (uint32_t)(l == 0 ? W : J), 5 * W, blk[l]))
+            return fail(m, SVM_E_WEIGHTS, "block shape or size");
+    if (!take(1u, (uint32_t)J, 1, fin)) return fail(m, SVM_E_WEIGHTS, "final layer shape or size");
+    if (off != bytes) return fail(m, SVM_E_WEIGHTS, "trailing bytes in blob");
+    for (float v : all)
+        if (!std::isfinite(v)) return fail(m, SVM_E_WEIGHTS, "non-finite weight");
+
+    std::vector<float> w1x(W * 3), wT(L * W * W), wout(W), blk_wx(L * W * 3, 0.0f), blk_wq((L + 1) * W * 12),
+        blk_b((L + 1) * W), blk_s(L * W), blk_t(L * W), out_wx(3), out_wq(12);
+    for (long long o = 0; o < W; ++o) {
+        for (int c = 0; c < 3; ++c) w1x[o * 3 + c] = init[o * kInDim + c];
+        for (int c = 0; c < 12; ++c) blk_wq[o * 12 + c] = init[o * kInDim + 3 + c];
+        blk_b[o] = init[W * kInDim + o];
+    }
+    for (long long l = 0; l < L; ++l) {
+        const long long in = l == 0 ? W : J;
+        const float* Wl = blk[l].data();
+        const float* bl = Wl + W * in;
+        const float *gamma = bl + W, *beta = bl + 2 * W, *mean = bl + 3 * W, *var = bl + 4 * W;
+        for (long long o = 0; o < W; ++o) {
+            for (long long i = 0; i < W; ++i) wT[(l * W + i) * W + o] = Wl[o * in + i];
+            if (l > 0) {
+                for (int c = 0; c < 3; ++c) blk_wx[(l * W + o) * 3 + c] = Wl[o * in + W + c];
+                for (int c = 0; c < 12; ++c) blk_wq[((l + 1) * W + o) * 12 + c] = Wl[o * in + W + 3 + c];
+            } else {
+                for (int c = 0; c < 12; ++c) blk_wq[((l + 1) * W + o) * 12 + c] = 0.0f;
+            }
+            blk_b[(l + 1) * W + o] = bl[o];
+            const double sc = (double)gamma[o] / std::sqrt((double)var[o] + (double)bn_eps);
+            blk_s[l * W + o] = (float)sc;
+            blk_t[l * W + o] = (float)((double)beta[o] - (double)mean[o] * sc);
+        }
+    }
+    for (long long o = 0; o < W; ++o) wout[o] = fin[o];
+    for (int c = 0; c < 3; ++c) out_wx[c] = fin[W + c];
+    for (int c = 0; c < 12; ++c) out_wq[c] = fin[W + 3 + c];
+    const float bout = fin[J];
+
+    DeviceGuard g(m->device);
+    CK(cudaDeviceSynchronize());
+    size_t total = 0;
+    const std::vector<const std::vector<float>*> parts = {&w1x, &wT, &wout, &blk_wx, &blk_wq, &blk_b, &blk_s,
+                                                          &blk_t, &out_wx, &out_wq};
+    for (auto* v : parts) total += align256(std::max<size_t>(1, v->size()) * 4);
+    if (m->d_weights) { cudaFree(m->d_weights); m->d_weights = nullptr; }
+    if (cudaMalloc(&m->d_weights, total) != cudaSuccess) return fail(m, SVM_E_OOM, "weights allocation failed");
+    char* base = static_cast<char*>(m->d_weights);
+    size_t at = 0;
+    std::vector<const float*> dev;
+    for (auto* v : parts) {
+        if (!v->empty()) CK(cudaMemcpy(base + at, v->data(), v->size() * 4, cudaMemcpyHostToDevice));
+        dev.push_back(reinterpret_cast<const float*>(base + at));
+        at += align256(std::max<size_t>(1, v->size()) * 4);
+    }
+    DevWeights& dw = m->dw;
+    dw = DevWeights{};
+    dw.w1x = dev[0];
+    dw.wT = dev[1];
+    dw.wout = dev[2];
+    dw.blk_wx = dev[3];
+    dw.blk_wq = dev[4];
+    dw.blk_b = dev[5];
+    dw.blk_s = dev[6];
+    dw.blk_t = dev[7];
+    dw.out_wx = dev[8];
+    dw.out_wq = dev[9];
+    dw.bout = bout;
+    m->used = all;
+    m->tau = std::isfinite(tau) && tau >= 0 ? tau : INFINITY;
+    m->has_weights = true;
+    return SVM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -123,6 +230,9 @@ svm_status svm_create_model(const svm_model_desc* desc, int device, svm_model** 
     if (d.act != SVM_RELU && d.act != SVM_SILU) return SVM_E_INVALID;
     if (d.prec < SVM_FP32 || d.prec > SVM_FP8_E4M3) return SVM_E_INVALID;
     if (d.n_hidden < 0 || d.n_hidden > 16) return SVM_E_INVALID;
+    if (d.arch != SVM_ARCH_MLP && d.arch != SVM_ARCH_BLOCKS) return SVM_E_INVALID;
+    if (d.arch == SVM_ARCH_BLOCKS && (d.prec != SVM_FP32 || d.act != SVM_RELU || d.n_hidden < 1))
+        return SVM_E_UNSUPPORTED;
     if (d.prec == SVM_FP32) {
         if (!(d.width == 64 || d.width == 128 || d.width == 256 || d.width == 512)) return SVM_E_UNSUPPORTED;
     } else {
@@ -210,6 +320,10 @@ svm_status svm_load_weights(svm_model* m, const void* blob, size_t bytes)
     const unsigned char* p = static_cast<const unsigned char*>(blob);
     auto rd32 = [&](size_t off) { uint32_t v; std::memcpy(&v, p + off, 4); return v; };
     if (bytes < 28 || std::memcmp(p, "SVMW", 4) != 0) return fail(m, SVM_E_WEIGHTS, "bad magic");
+    if (d.arch == SVM_ARCH_BLOCKS) {
+        if (rd32(4) != 2) return fail(m, SVM_E_WEIGHTS, "block models take blob version 2");
+        return load_block_weights(m, p, bytes);
+    }
     if (rd32(4) != 1) return fail(m, SVM_E_WEIGHTS, "unsupported blob version");
     const uint32_t n_layers = rd32(8), in_dim = rd32(12), width = rd32(16), act = rd32(20);
     float tau;
@@ -442,7 +556,7 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
     pl.o_poff = at; at = align256(at + (size_t)(M + 1) * 8);
     pl.header_bytes = at;
     pl.o_caps = at; at = align256(at + (size_t)M * (steps + 1) * kCaps * sizeof(Capsule));
-    pl.o_cbias = at; at = align256(at + (size_t)M * d.width * 4);
+    pl.o_cbias = at; at = align256(at + (size_t)M * cbias_stride(d) * 4);
     pl.o_st = at; at = align256(at + (size_t)M * sizeof(MotionState));
     pl.o_idx = at; at = align256(at + (size_t)std::max<long long>(1, pl.P_total) * 4);
     pl.o_chunk = at; at = align256(at + (size_t)(M + 1) * 4);
@@ -503,6 +617,8 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
     a.W = d.width;
     a.L = d.n_hidden;
     a.act = d.act;
+    a.arch = d.arch;
+    a.cb_stride = cbias_stride(d);
     a.flags = flags;
     a.margin = margin;
     a.gate = (mode == kEval || (flags & SVM_PREDICT_ONLY)) ? -INFINITY : margin + m->tau;
@@ -916,7 +1032,7 @@ extern "C" svm_status svm_check_motions_noalloc(svm_model* m, const double* q0_d
     const size_t o_toff = at; at = align256(at + (size_t)(M + 1) * 4);
     const size_t o_poff = at; at = align256(at + (size_t)(M + 1) * 8);
     const size_t o_caps = at; at = align256(at + (size_t)M * (steps + 1) * kCaps * sizeof(Capsule));
-    const size_t o_cbias = at; at = align256(at + (size_t)M * d.width * 4);
+    const size_t o_cbias = at; at = align256(at + (size_t)M * cbias_stride(d) * 4);
     const size_t o_st = at; at = align256(at + (size_t)M * sizeof(MotionState));
     const size_t o_idx = at; at = align256(at + (size_t)std::max<long long>(1, (long long)M * n_points) * 4);
     const size_t o_chunk = at; at = align256(at + (size_t)(M + 1) * 4);
@@ -940,6 +1056,8 @@ extern "C" svm_status svm_check_motions_noalloc(svm_model* m, const double* q0_d
     a.W = d.width;
     a.L = d.n_hidden;
     a.act = d.act;
+    a.arch = d.arch;
+    a.cb_stride = cbias_stride(d);
     a.flags = flags;
     a.margin = margin;
     a.gate = margin + m->tau;

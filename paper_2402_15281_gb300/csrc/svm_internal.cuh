@@ -60,6 +60,8 @@ struct CallArgs {
     int W;              // network width
     int L;              // hidden layers
     int act;            // 0 relu, 1 silu
+    int arch;           // 0 plain MLP, 1 block architecture
+    int cb_stride;      // per-motion bias floats: W (arch 0), (L + 1) W + 1 (arch 1)
     uint32_t flags;
     float margin;
     float gate;         // margin + tau
@@ -101,6 +103,14 @@ struct DevWeights {
     const float* ascale;  // [L] per-layer activation scale (FP8), else 1
     const float* bhs;     // FP8: [L][W] hidden biases divided by the next layer's
                           // activation scale (b_l / ascale[l], l < L-1)
+    // block architecture (arch 1): L blocks
+    const float* blk_wx;  // [L][W][3]   jump weights of x, y, z (block 1: zero)
+    const float* blk_wq;  // [L+1][W][12] weights of q0, q1: initial layer, then blocks
+    const float* blk_b;   // [L+1][W]    biases: initial layer, then blocks
+    const float* blk_s;   // [L][W]      folded BatchNorm scale gamma / sqrt(var + eps)
+    const float* blk_t;   // [L][W]      folded BatchNorm shift beta - mean * scale
+    const float* out_wx;  // [3]         final-layer weights of x, y, z
+    const float* out_wq;  // [12]        final-layer weights of q0, q1
 };
 
 __device__ __forceinline__ float act_fn(float z, int act) {

@@ -39,3 +39,11 @@ struct svm_model {
     unsigned int* calib_amax = nullptr;   // set only on a calibration model
     std::string last_error;
 };
+
+// Per-motion bias floats of the prologue: c_m (plain MLP), or the initial
+// layer's and every block's c (W each) and the final layer's scalar (blocks).
+inline int cbias_stride(const svm_model_desc& d)
+{
+    return d.arch == SVM_ARCH_BLOCKS ? (d.n_hidden + 1) * d.width + 1 : d.width;
+}
+

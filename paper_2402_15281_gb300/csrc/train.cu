@@ -522,6 +522,7 @@ svm_status svm_train_create(const svm_model_desc* desc, int device, int32_t batc
     *out = nullptr;
     const svm_model_desc& d = *desc;
     if (!(d.width == 256 || d.width == 512) || d.n_hidden < 1 || d.n_hidden > 16) return SVM_E_UNSUPPORTED;
+    if (d.arch != SVM_ARCH_MLP) return SVM_E_UNSUPPORTED;
     if (d.act != SVM_RELU && d.act != SVM_SILU) return SVM_E_INVALID;
     if (batch < 256 || batch % 256 != 0) return SVM_E_INVALID;
     int n_dev = 0;

@@ -414,5 +414,34 @@ def xavier_weights(width: int = 256, n_hidden: int = 4, seed: int = 2):
     return out
 
 
+def block_weights(width: int = 512, n_blocks: int = 5, seed: int = 2, bn_scale: float = 1.0):
+    """Parameters of the block architecture of Sec. IV-A: an initial layer
+    15 -> width, n_blocks blocks (linear width (+15 for the jump input from
+    the second block on) -> width, ReLU, BatchNorm, skip), a final layer
+    width + 15 -> 1.  Glorot-uniform weights, small uniform biases and
+    BatchNorm statistics (gamma, beta, running mean and variance) drawn in
+    float64 and stored as float32.  Returns dict(init=(W, b), blocks=[(W, b,
+    gamma, beta, mean, var)], final=(W, b))."""
+    r = Rng(seed, S_WEIGHTS)
+
+    def glorot(o, i):
+        lim = math.sqrt(6.0 / (i + o))
+        return r.uniform(o * i, -lim, lim).reshape(o, i).astype(np.float32)
+
+    init = (glorot(width, IN_DIM), r.uniform(width, -0.05, 0.05).astype(np.float32))
+    blocks = []
+    for b in range(n_blocks):
+        fan_in = width if b == 0 else width + IN_DIM
+        W = glorot(width, fan_in)
+        bias = r.uniform(width, -0.05, 0.05).astype(np.float32)
+        gamma = (bn_scale * r.uniform(width, 0.5, 1.5)).astype(np.float32)
+        beta = r.uniform(width, -0.1, 0.1).astype(np.float32)
+        mean = r.uniform(width, 0.0, 0.3).astype(np.float32)
+        var = r.uniform(width, 0.2, 1.0).astype(np.float32)
+        blocks.append((W, bias, gamma, beta, mean, var))
+    final = (glorot(1, width + IN_DIM), r.uniform(1, -0.05, 0.05).astype(np.float32))
+    return {"init": init, "blocks": blocks, "final": final}
+
+
 # Activation codes shared with the C interface.
 ACT_RELU, ACT_SILU = 0, 1
