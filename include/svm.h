@@ -114,6 +114,8 @@ typedef struct svm_model svm_model;
 #define SVM_PATHS3        8u  /* motions 3p, 3p+1, 3p+2 are the segments of path
                                  p; one result per path (collision = OR), and a
                                  path stops at its first colliding segment      */
+#define SVM_PATHS2       32u  /* as SVM_PATHS3 with paths of two segments
+                                 (motions 2p, 2p+1); n_motions % 2 == 0        */
 #define SVM_PREDICT_ONLY 16u  /* run the network only: dhat_min (Eq. 6) per
                                  motion, no exact check (collision = 0, d_min =
                                  +inf); not with SVM_VERIFY_ALL or SVM_STRICT;
@@ -182,7 +184,8 @@ svm_status svm_calibrate_act_scales(svm_model* m, const double* q0, const double
  *   steps        N >= 1: the motion is sampled at q_k = ((N-k) q0 + k q1) / N,
  *                k = 0..N, and each sample is checked exactly.
  *   results_dev  device, n_motions svm_result records (n_motions / 3 with
- *                SVM_PATHS3, which needs n_motions % 3 == 0).
+ *                SVM_PATHS3, which needs n_motions % 3 == 0; n_motions / 2
+ *                with SVM_PATHS2).
  * The model's workspace grows on demand (cudaMalloc; SVM_E_OOM on failure). */
 svm_status svm_check_motions(svm_model* m, const double* q0, const double* q1,
                              int32_t n_motions, const float* points_dev, int64_t n_points,
@@ -213,10 +216,20 @@ svm_status svm_check_batch(svm_model* m, const double* q0, const double* q1,
  *   wave    exact checks run `wave` candidates per launch (1 reproduces the
  *           sequential algorithm; more trades extra checks for fewer round
  *           trips); the result is the same for every wave.
+ * With SVM_SEARCH_SORTED only the second loop runs: every candidate is
+ * checked in decreasing d_hat (the bin-picking use of Sec. V-C, where the
+ * network predicts no free motion).  With SVM_SEARCH_PATHS2 / _PATHS3 the
+ * candidates are paths of 2 / 3 consecutive segments (n_motions a multiple
+ * of that): a path's d_hat is the minimum over its segments and its exact
+ * check that of SVM_PATHS2 / SVM_PATHS3 (free iff every segment is free);
+ * `motion` then indexes paths.
  * Synchronous on `stream` (it reads results back to decide); q0/q1 host,
  * points device; out is a host struct.  Allocates its result buffers on the
  * first call (cudaMalloc / cudaMallocHost), then reuses them. */
-#define SVM_SEARCH_GCC0 1u
+#define SVM_SEARCH_GCC0   1u
+#define SVM_SEARCH_SORTED 2u
+#define SVM_SEARCH_PATHS2 4u
+#define SVM_SEARCH_PATHS3 8u
 
 typedef struct {
     int32_t motion;       /* index of the free motion found, -1 if none          */
@@ -225,10 +238,10 @@ typedef struct {
     float delta_hat;      /* its d_hat(X, m); +inf under SVM_SEARCH_GCC0          */
     int32_t n_exact;      /* exact checks the sequential algorithm makes          */
     int32_t n_exact_run;  /* exact checks run (n_exact rounded up to whole waves) */
-    int32_t n_nn;         /* motions evaluated by the network launch (n_motions)  */
-    int32_t n_nn_seq;     /* network evaluations the sequential first loop makes
-                             (up to the returned motion; all if it reaches the
-                             second loop)                                       */
+    int32_t n_nn;         /* segments evaluated by the network launch (n_motions) */
+    int32_t n_nn_seq;     /* network evaluations (segments) the sequential first
+                             loop makes: up to the returned candidate, all if
+                             the second loop runs                               */
 } svm_search_result;
 
 svm_status svm_search_free_motion(svm_model* m, const double* q0, const double* q1, int32_t n_motions,

@@ -373,6 +373,19 @@ def search_first_free(dhat, delta, eps):
     return {"motion": -1, "loop": 0, "n_exact": n_exact, "n_nn_seq": M}
 
 
+def search_sorted(dhat, delta, eps):
+    """The second loop of Algorithm 1 alone (its use in Sec. V-C): every
+    candidate checked exactly by decreasing dhat (ties in the given order)
+    until one is free.  Returns dict(motion, n_exact)."""
+    dhat = np.asarray(dhat, dtype=np.float64)
+    delta = np.asarray(delta, dtype=np.float64)
+    order = sorted(range(len(dhat)), key=lambda m: -dhat[m])
+    for n, m in enumerate(order):
+        if delta[m] > eps:
+            return {"motion": m, "n_exact": n + 1}
+    return {"motion": -1, "n_exact": len(dhat)}
+
+
 def search_gcc0(delta, eps):
     """GCC_0 of Sec. V-B: the exact check of each motion in the given order
     until one is free.  Returns dict(motion, n_exact)."""

@@ -22,8 +22,8 @@ LIB_PATH = os.path.join(_HERE, "_build", platform.machine(), "libsvm.so")
 SVM_OK, SVM_E_INVALID, SVM_E_CUDA, SVM_E_OOM, SVM_E_TIMEOUT, SVM_E_WEIGHTS, SVM_E_UNSUPPORTED = range(7)
 SVM_FP32, SVM_BF16, SVM_FP8_E4M3 = 0, 1, 2
 SVM_RELU, SVM_SILU = 0, 1
-SVM_STRICT, SVM_NO_EARLY_EXIT, SVM_VERIFY_ALL, SVM_PATHS3, SVM_PREDICT_ONLY = 1, 2, 4, 8, 16
-SVM_SEARCH_GCC0 = 1
+SVM_STRICT, SVM_NO_EARLY_EXIT, SVM_VERIFY_ALL, SVM_PATHS3, SVM_PREDICT_ONLY, SVM_PATHS2 = 1, 2, 4, 8, 16, 32
+SVM_SEARCH_GCC0, SVM_SEARCH_SORTED, SVM_SEARCH_PATHS2, SVM_SEARCH_PATHS3 = 1, 2, 4, 8
 
 RESULT_DTYPE = np.dtype([("collision", "u1"), ("early_exit", "u1"), ("status", "<u2"),
                          ("d_min", "<f4"), ("dhat_min", "<f4"), ("n_flagged", "<u4"),

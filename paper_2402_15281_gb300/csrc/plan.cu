@@ -87,7 +87,7 @@ CallArgs plan_args(svm_plan* p, const float* points)
     a.chunk_off = reinterpret_cast<int*>(ws + p->o_chunk);
     a.f_out = nullptr;
     a.f_stride = 0;
-    a.paths3 = (p->flags & SVM_PATHS3) ? 1 : 0;
+    a.path_len = path_len_of(p->flags);
     a.dev_err = reinterpret_cast<unsigned int*>(ws + p->o_err);
     a.amax = nullptr;
     return a;
@@ -135,9 +135,10 @@ svm_status svm_plan_create(svm_model* m, const double* q0, const double* q1, int
     if (!m->has_weights && !(flags & SVM_VERIFY_ALL)) return pfail(m, SVM_E_WEIGHTS, "no weights loaded");
     if (!(margin >= 0) || !std::isfinite(margin)) return pfail(m, SVM_E_INVALID, "margin must be finite and >= 0");
     if (steps < 1 || steps > kMaxSteps) return pfail(m, SVM_E_INVALID, "steps out of range");
-    if ((flags & SVM_PATHS3) && (M % 3) != 0) return pfail(m, SVM_E_INVALID, "paths need n_motions % 3 == 0");
-    if (flags & ~(SVM_STRICT | SVM_NO_EARLY_EXIT | SVM_VERIFY_ALL | SVM_PATHS3))
+    if (flags & ~(SVM_STRICT | SVM_NO_EARLY_EXIT | SVM_VERIFY_ALL | SVM_PATHS3 | SVM_PATHS2))
         return pfail(m, SVM_E_INVALID, "unknown flag");
+    if ((flags & SVM_PATHS3) && (flags & SVM_PATHS2)) return pfail(m, SVM_E_INVALID, "SVM_PATHS2 with SVM_PATHS3");
+    if (M % path_len_of(flags) != 0) return pfail(m, SVM_E_INVALID, "n_motions is not a multiple of the path length");
     if (scene_offsets[0] != 0) return pfail(m, SVM_E_INVALID, "scene_offsets[0] must be 0");
     for (int s = 0; s < n_scenes; ++s)
         if (scene_offsets[s + 1] < scene_offsets[s]) return pfail(m, SVM_E_INVALID, "scene offsets decrease");

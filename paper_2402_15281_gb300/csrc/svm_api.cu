@@ -513,9 +513,10 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
     if (mode != kCheck && M > 0 && !out_dev) return fail(m, SVM_E_INVALID, "null output");
     if (!(margin >= 0) || !std::isfinite(margin)) return fail(m, SVM_E_INVALID, "margin must be finite and >= 0");
     if (steps < 1 || steps > kMaxSteps) return fail(m, SVM_E_INVALID, "steps out of range");
-    if ((flags & SVM_PATHS3) && (M % 3) != 0) return fail(m, SVM_E_INVALID, "paths need n_motions % 3 == 0");
-    if (flags & ~(SVM_STRICT | SVM_NO_EARLY_EXIT | SVM_VERIFY_ALL | SVM_PATHS3 | SVM_PREDICT_ONLY))
+    if (flags & ~(SVM_STRICT | SVM_NO_EARLY_EXIT | SVM_VERIFY_ALL | SVM_PATHS3 | SVM_PATHS2 | SVM_PREDICT_ONLY))
         return fail(m, SVM_E_INVALID, "unknown flag");
+    if ((flags & SVM_PATHS3) && (flags & SVM_PATHS2)) return fail(m, SVM_E_INVALID, "SVM_PATHS2 with SVM_PATHS3");
+    if (M % path_len_of(flags) != 0) return fail(m, SVM_E_INVALID, "n_motions is not a multiple of the path length");
     if ((flags & SVM_PREDICT_ONLY) && (flags & (SVM_VERIFY_ALL | SVM_STRICT)))
         return fail(m, SVM_E_INVALID, "SVM_PREDICT_ONLY excludes SVM_VERIFY_ALL and SVM_STRICT");
     if (scene_off[0] != 0) return fail(m, SVM_E_INVALID, "scene_offsets[0] must be 0");
@@ -636,7 +637,7 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
     a.chunk_off = reinterpret_cast<int*>(ws + pl.o_chunk);
     a.f_out = (mode == kEval) ? out_dev : nullptr;
     a.f_stride = (n_scenes == 1) ? scene_off[1] : 0;
-    a.paths3 = (flags & SVM_PATHS3) ? 1 : 0;
+    a.path_len = path_len_of(flags);
     a.amax = m->calib_amax;
     void* tc_ws = ws + pl.o_chunk + align256((size_t)(M + 1) * 4);
     a.dev_err = static_cast<unsigned int*>(tc_ws);
@@ -829,12 +830,19 @@ svm_status svm_search_free_motion(svm_model* m, const double* q0, const double* 
     if (!m || !out) return SVM_E_INVALID;
     if (n_motions < 0 || n_points < 0) return fail(m, SVM_E_INVALID, "negative count");
     if (wave < 1) return fail(m, SVM_E_INVALID, "wave must be >= 1");
-    if (flags & ~SVM_SEARCH_GCC0) return fail(m, SVM_E_INVALID, "unknown search flag");
+    if (flags & ~(SVM_SEARCH_GCC0 | SVM_SEARCH_SORTED | SVM_SEARCH_PATHS2 | SVM_SEARCH_PATHS3))
+        return fail(m, SVM_E_INVALID, "unknown search flag");
+    if ((flags & SVM_SEARCH_PATHS2) && (flags & SVM_SEARCH_PATHS3))
+        return fail(m, SVM_E_INVALID, "SVM_SEARCH_PATHS2 with SVM_SEARCH_PATHS3");
     const bool use_nn = !(flags & SVM_SEARCH_GCC0);
     if (use_nn && !m->has_weights) return fail(m, SVM_E_WEIGHTS, "no weights loaded");
+    // candidates: single motions, or paths of 2 or 3 consecutive segments
+    const int plen = (flags & SVM_SEARCH_PATHS3) ? 3 : (flags & SVM_SEARCH_PATHS2) ? 2 : 1;
+    const uint32_t pflag = plen == 3 ? SVM_PATHS3 : plen == 2 ? SVM_PATHS2 : 0u;
+    if (n_motions % plen != 0) return fail(m, SVM_E_INVALID, "n_motions is not a multiple of the path length");
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     *out = svm_search_result{-1, 0, INFINITY, INFINITY, 0, 0, 0, 0};
-    const int M = n_motions;
+    const int M = n_motions / plen;           // candidates
     if (M == 0) return SVM_OK;
     DeviceGuard g(m->device);
     // result records: one per motion for the prediction, one per motion of a wave
@@ -859,16 +867,16 @@ svm_status svm_search_free_motion(svm_model* m, const double* q0, const double* 
     // d_hat(X, m) of every motion (Eq. 6): one network launch, no exact check
     std::vector<float> dhat(M, INFINITY);
     if (use_nn) {
-        const svm_status st = run_call(m, kCheck, q0, q1, M, nullptr, points_dev, off, 1, margin, steps,
-                                       SVM_PREDICT_ONLY, rd, nullptr, stream);
+        const svm_status st = run_call(m, kCheck, q0, q1, n_motions, nullptr, points_dev, off, 1, margin, steps,
+                                       SVM_PREDICT_ONLY | pflag, rd, nullptr, stream);
         if (st != SVM_OK) return st;
         CK(cudaMemcpyAsync(rh, rd, (size_t)M * sizeof(svm_result), cudaMemcpyDeviceToHost, stream));
         CK(cudaStreamSynchronize(stream));
         for (int i = 0; i < M; ++i) {
             if (rh[i].status != 0) return fail(m, SVM_E_TIMEOUT, "a device wait expired");
-            dhat[i] = rh[i].dhat_min;
+            dhat[i] = rh[i].dhat_min;      // a path's: the minimum over its segments
         }
-        out->n_nn = M;
+        out->n_nn = n_motions;
     }
     // exact checks (the geometric check of every point, early exit at the first
     // collision) of the motions `list`, in order, `wave` at a time; returns the
@@ -878,14 +886,14 @@ svm_status svm_search_free_motion(svm_model* m, const double* q0, const double* 
         pos = -1;
         for (size_t b = 0; b < list.size(); b += (size_t)wave) {
             const int nw = (int)std::min<size_t>((size_t)wave, list.size() - b);
-            wq0.resize((size_t)nw * 6);
-            wq1.resize((size_t)nw * 6);
+            wq0.resize((size_t)nw * plen * 6);
+            wq1.resize((size_t)nw * plen * 6);
             for (int k = 0; k < nw; ++k) {
-                std::memcpy(&wq0[(size_t)k * 6], q0 + (size_t)list[b + k] * 6, 48);
-                std::memcpy(&wq1[(size_t)k * 6], q1 + (size_t)list[b + k] * 6, 48);
+                std::memcpy(&wq0[(size_t)k * plen * 6], q0 + (size_t)list[b + k] * plen * 6, 48 * (size_t)plen);
+                std::memcpy(&wq1[(size_t)k * plen * 6], q1 + (size_t)list[b + k] * plen * 6, 48 * (size_t)plen);
             }
-            st = run_call(m, kCheck, wq0.data(), wq1.data(), nw, nullptr, points_dev, off, 1, margin, steps,
-                          SVM_VERIFY_ALL, rd, nullptr, stream);
+            st = run_call(m, kCheck, wq0.data(), wq1.data(), nw * plen, nullptr, points_dev, off, 1, margin, steps,
+                          SVM_VERIFY_ALL | pflag, rd, nullptr, stream);
             if (st != SVM_OK) return;
             if (cudaMemcpyAsync(rh, rd, (size_t)nw * sizeof(svm_result), cudaMemcpyDeviceToHost, stream) !=
                     cudaSuccess ||
@@ -909,9 +917,11 @@ svm_status svm_search_free_motion(svm_model* m, const double* q0, const double* 
     };
     svm_status st = SVM_OK;
     int pos = -1;
-    // first loop: the motions predicted free, in the given order
+    // first loop: the motions predicted free, in the given order (none when only
+    // the second loop runs)
+    const bool sorted_only = use_nn && (flags & SVM_SEARCH_SORTED);
     std::vector<int> first, rest;
-    for (int i = 0; i < M; ++i) (dhat[i] > margin ? first : rest).push_back(i);
+    for (int i = 0; i < M; ++i) (dhat[i] > margin && !sorted_only ? first : rest).push_back(i);
     exact_in_order(first, pos, st);
     if (st != SVM_OK) return st;
     if (pos >= 0) {
@@ -920,13 +930,14 @@ svm_status svm_search_free_motion(svm_model* m, const double* q0, const double* 
         out->n_exact = pos + 1;
         out->delta_hat = dhat[first[pos]];
         // the sequential first loop evaluated the network up to the returned motion
-        out->n_nn_seq = use_nn ? out->motion + 1 : 0;
+        out->n_nn_seq = use_nn ? (out->motion + 1) * plen : 0;
         return SVM_OK;
     }
     out->n_exact = (int)first.size();
-    out->n_nn_seq = use_nn ? M : 0;
-    // second loop: the others by decreasing prediction (ties keep the given order)
-    std::stable_sort(rest.begin(), rest.end(), [&](int a, int b) { return dhat[a] > dhat[b]; });
+    out->n_nn_seq = use_nn ? n_motions : 0;
+    // second loop: the others by decreasing prediction (ties keep the given order);
+    // GCC_0 keeps the given order
+    if (use_nn) std::stable_sort(rest.begin(), rest.end(), [&](int a, int b) { return dhat[a] > dhat[b]; });
     exact_in_order(rest, pos, st);
     if (st != SVM_OK) return st;
     if (pos >= 0) {
@@ -1016,9 +1027,10 @@ extern "C" svm_status svm_check_motions_noalloc(svm_model* m, const double* q0_d
     if (!m->has_weights && !(flags & SVM_VERIFY_ALL)) return fail(m, SVM_E_WEIGHTS, "no weights loaded");
     if (!(margin >= 0) || !std::isfinite(margin)) return fail(m, SVM_E_INVALID, "margin must be finite and >= 0");
     if (steps < 1 || steps > kMaxSteps) return fail(m, SVM_E_INVALID, "steps out of range");
-    if ((flags & SVM_PATHS3) && (M % 3) != 0) return fail(m, SVM_E_INVALID, "paths need n_motions % 3 == 0");
-    if (flags & ~(SVM_STRICT | SVM_NO_EARLY_EXIT | SVM_VERIFY_ALL | SVM_PATHS3))
+    if (flags & ~(SVM_STRICT | SVM_NO_EARLY_EXIT | SVM_VERIFY_ALL | SVM_PATHS3 | SVM_PATHS2))
         return fail(m, SVM_E_INVALID, "unknown flag");
+    if ((flags & SVM_PATHS3) && (flags & SVM_PATHS2)) return fail(m, SVM_E_INVALID, "SVM_PATHS2 with SVM_PATHS3");
+    if (M % path_len_of(flags) != 0) return fail(m, SVM_E_INVALID, "n_motions is not a multiple of the path length");
 
     const bool tc = d.prec != SVM_FP32;
     const int bm = tc ? tc_tile_rows() : mlp_fp32_tile_rows();
@@ -1075,7 +1087,7 @@ extern "C" svm_status svm_check_motions_noalloc(svm_model* m, const double* q0_d
     a.chunk_off = reinterpret_cast<int*>(ws + o_chunk);
     a.f_out = nullptr;
     a.f_stride = n_points;
-    a.paths3 = (flags & SVM_PATHS3) ? 1 : 0;
+    a.path_len = path_len_of(flags);
     a.dev_err = reinterpret_cast<unsigned int*>(ws + o_err);
 
     noalloc_setup_kernel<<<(M + 256) / 256, 256, 0, stream>>>(

@@ -79,7 +79,7 @@ struct CallArgs {
     int* chunk_off;
     float* f_out;       // optional per-pair network output (eval mode)
     long long f_stride; // row stride of f_out (points per motion row)
-    int paths3;         // motions form paths of 3 segments
+    int path_len;       // segments per path: 1 (single motions), 2 or 3
     unsigned int* dev_err;  // per-call error word: nonzero if a bounded wait expired
     unsigned int* amax;     // optional [L]: bit patterns of max |input of hidden layer l| (calibration)
 };

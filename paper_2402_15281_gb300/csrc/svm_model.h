@@ -47,3 +47,9 @@ inline int cbias_stride(const svm_model_desc& d)
     return d.arch == SVM_ARCH_BLOCKS ? (d.n_hidden + 1) * d.width + 1 : d.width;
 }
 
+// Segments per path of a check call's flags (1: every motion stands alone).
+inline int path_len_of(uint32_t flags)
+{
+    return (flags & SVM_PATHS3) ? 3 : (flags & SVM_PATHS2) ? 2 : 1;
+}
+

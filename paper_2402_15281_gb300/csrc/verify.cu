@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(VT) verify_kernel(CallArgs A, int strict_pass)
         if (threadIdx.x == 0) {
             const int m = find_segment(A.chunk_off, A.M, c);
             s_m = m;
-            const int path_head = A.paths3 ? (m / 3) * 3 : m;
+            const int path_head = (m / A.path_len) * A.path_len;
             int skip = 0;
             if (early && *(volatile int*)&A.st[path_head].collided) skip = 1;
             // second pass of strict mode: only motions still without a collision
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(VT) verify_kernel(CallArgs A, int strict_pass)
             if (fabsf(d - A.margin) < kAmbiguousBand) atomicAdd(&s_namb, 1u);
             atomicMin(&s_dkey, float_key(d));
             if (d <= A.margin) {
-                const int path_head = A.paths3 ? (m / 3) * 3 : m;
+                const int path_head = (m / A.path_len) * A.path_len;
                 if (atomicCAS(&A.st[m].collided, 0, 1) == 0) {
                     A.st[m].witness_point = (int)pidx[j];
                     A.st[m].witness_step = witness_sample(cs, n_samples, x[j], A.margin);
@@ -211,10 +211,10 @@ static_assert(sizeof(ResultRec) == 32, "result record is 32 bytes");
 
 __global__ void finalize_kernel(CallArgs A, ResultRec* out)
 {
-    const int n_out = A.paths3 ? A.M / 3 : A.M;
+    const int n_out = A.M / A.path_len;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_out) return;
-    const int seg = A.paths3 ? 3 : 1;
+    const int seg = A.path_len;
     ResultRec o;
     o.collision = 0;
     o.early_exit = 0;
@@ -310,7 +310,7 @@ void launch_label(const CallArgs& a, float* delta, long long stride, cudaStream_
 
 void launch_finalize(const CallArgs& a, void* results, cudaStream_t s)
 {
-    const int n_out = a.paths3 ? a.M / 3 : a.M;
+    const int n_out = a.M / a.path_len;
     if (n_out <= 0) return;
     finalize_kernel<<<(n_out + 127) / 128, 128, 0, s>>>(a, reinterpret_cast<ResultRec*>(results));
 }

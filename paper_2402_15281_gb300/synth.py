@@ -325,6 +325,28 @@ def bin_paths(robot: Robot, n: int, seed: int = 0):
     return np.clip(q, robot.qmin, robot.qmax)
 
 
+S_GRASP = 9
+
+
+def bin_grasp_paths(robot: Robot, n: int, seed: int = 0):
+    """The two-segment motions of Sec. V-C for n grasp candidates: into the
+    bin preStart -> preVia -> grasp, out of it grasp -> postVia -> postEnd.
+    preStart and postEnd are the above-bin pose plus U(+-5 deg) per joint
+    (drawn separately), the grasp is drawn from the grasp box, each via is
+    the grasp plus U(+-8 deg) per joint (close to the object).  Returns
+    (into (n, 3, 6), out (n, 3, 6)) waypoints."""
+    r = Rng(seed, S_GRASP)
+    above = lambda: Q_ABOVE_BIN_DEG + r.uniform(n * DOF, -5.0, 5.0).reshape(n, DOF)
+    start = above()
+    grasp = Q_GRASP_DEG + r.uniform(n * DOF, -1.0, 1.0).reshape(n, DOF) * Q_GRASP_SPREAD_DEG
+    pre_via = grasp + r.uniform(n * DOF, -8.0, 8.0).reshape(n, DOF)
+    post_via = grasp + r.uniform(n * DOF, -8.0, 8.0).reshape(n, DOF)
+    end = above()
+    into = np.stack([start, pre_via, grasp], axis=1) * DEG
+    out = np.stack([grasp, post_via, end], axis=1) * DEG
+    return np.clip(into, robot.qmin, robot.qmax), np.clip(out, robot.qmin, robot.qmax)
+
+
 # --------------------------------------------------------------------------
 # Box world (Sec. V-B)
 # --------------------------------------------------------------------------

@@ -39,6 +39,20 @@ def path_training_motions(robot, n, seed):
     return q0[order], q1[order]
 
 
+def grasp_training_motions(robot, n, seed):
+    """Segments of the two-segment grasp motions of Sec. V-C (into and out of
+    the bin, synth.bin_grasp_paths) for half of the n motions,
+    bin_training_motions for the rest, in a seeded random order."""
+    k = n // 8                         # k candidates give 4k segments
+    into, out = S.bin_grasp_paths(robot, k, seed=seed)
+    seg0 = np.concatenate([into[:, :2], out[:, :2]]).reshape(-1, 6)
+    seg1 = np.concatenate([into[:, 1:], out[:, 1:]]).reshape(-1, 6)
+    qb0, qb1 = bin_training_motions(robot, n - len(seg0), seed)
+    q0, q1 = np.concatenate([seg0, qb0]), np.concatenate([seg1, qb1])
+    order = np.argsort(S.Rng(seed, 97).uniform(n))
+    return q0[order], q1[order]
+
+
 def train_model(svm, robot, q0, q1, width=256, n_hidden=4, act=0, samples_per_motion=4096, steps=128,
                 batch=65536, epochs=30, lr=1e-3, val_fraction=0.2, patience=10, data_seed=7, init_seed=2,
                 device=0, log=None, box=None):

@@ -109,3 +109,29 @@ def test_inference_times_at_the_paper_shapes(svm):
     for name, n, ms in rows:
         print(f"block network {name} FP32, 1 motion x {n} points: {ms:.3f} ms")
     assert all(ms > 0 for _, _, ms in rows)
+
+
+def test_block_model_arguments(svm):
+    import struct
+    robot = S.make_robot(1)
+    P = S.block_weights(64, 2, seed=3)
+    blob = svm.make_block_blob(P)
+    # the block architecture runs on the FP32 path with ReLU only
+    for prec, act in ((svm.SVM_BF16, 0), (svm.SVM_FP32, 1)):
+        with pytest.raises(svm.SvmError):
+            svm.svm_create_model(robot, 64, 2, act, prec, 0, arch=svm.SVM_ARCH_BLOCKS)
+    h = svm.svm_create_model(robot, 64, 2, 0, svm.SVM_FP32, 0, arch=svm.SVM_ARCH_BLOCKS)
+    try:
+        bad = [svm.make_blob(S.xavier_weights(64, 2)),                      # version 1
+               blob[:-4],                                                   # truncated
+               blob + b"\0\0\0\0",                                          # trailing bytes
+               svm.make_block_blob(S.block_weights(64, 3, seed=3)),         # 3 blocks for a 2-block model
+               blob[:28] + struct.pack("<f", float("nan")) + blob[32:]]     # bad BatchNorm epsilon
+        for b in bad:
+            with pytest.raises(svm.SvmError):
+                svm.svm_load_weights(h, b)
+        svm.svm_load_weights(h, blob)
+        used = svm.svm_export_weights(h)
+        assert used.size == (len(blob) - 32) // 4 - 2 * (2 + 2)          # every float, no shape words
+    finally:
+        svm.svm_destroy_model(h)

@@ -174,3 +174,32 @@ def test_box_world_experiment(setup):
         assert n[:, 1].mean() <= g[:, 1].mean()
     finally:
         svm.svm_destroy_model(h)
+
+
+def test_search_edge_cases(setup):
+    svm, robot, blob, _ = setup
+    h = _model(svm, robot, blob, 1)
+    try:
+        pts, *_ = S.box_world(5)
+        pts_d = torch.from_numpy(pts).cuda()
+        q0, q1 = S.box_world_motions(robot, 10, seed=5)
+        empty = np.zeros((0, 6))
+        r = svm.svm_search_free_motion(h, empty, empty, pts_d, EPS, N)
+        assert (r["motion"], r["loop"], r["n_exact"], r["n_nn"]) == (-1, 0, 0, 0)
+        # no points: every motion is free (d = d_hat = +inf); the first one is returned by the first loop
+        none = torch.zeros((0, 4), dtype=torch.float32, device="cuda")
+        r = svm.svm_search_free_motion(h, q0, q1, none, EPS, N)
+        assert (r["motion"], r["loop"], r["n_exact"]) == (0, 1, 1) and r["delta"] == np.inf
+        # a wave larger than the candidate list changes the work, not the answer
+        a = svm.svm_search_free_motion(h, q0, q1, pts_d, EPS, N, wave=1)
+        b = svm.svm_search_free_motion(h, q0, q1, pts_d, EPS, N, wave=1000)
+        assert (a["motion"], a["loop"], a["n_exact"]) == (b["motion"], b["loop"], b["n_exact"])
+        for kw in ({"wave": 0}, {"flags": 16}, {"flags": svm.SVM_SEARCH_PATHS2 | svm.SVM_SEARCH_PATHS3},
+                   {"flags": svm.SVM_SEARCH_PATHS3}):         # 10 motions are not whole 3-segment paths
+            with pytest.raises(svm.SvmError):
+                svm.svm_search_free_motion(h, q0, q1, pts_d, EPS, N, **kw)
+        res = svm.new_results(10)
+        with pytest.raises(svm.SvmError):
+            svm.svm_check_motions(h, q0, q1, pts_d, EPS, N, svm.SVM_PREDICT_ONLY | svm.SVM_VERIFY_ALL, res)
+    finally:
+        svm.svm_destroy_model(h)

@@ -85,3 +85,22 @@ def test_box_world_motions_share_one_start():
     assert q0.shape == q1.shape == (100, 6)
     assert np.all(q0 == q0[0])
     assert np.all(q1 >= robot.qmin) and np.all(q1 <= robot.qmax)
+
+
+def test_sorted_search_hand_worked():
+    # by decreasing prediction: m2 (0.4, collides), m0 (0.1, free) -> m0 after 2 checks
+    assert oracle.search_sorted([0.1, -0.3, 0.4], [0.2, 0.5, -0.1], 0.0) == {"motion": 0, "n_exact": 2}
+    assert oracle.search_sorted([0.1, 0.1], [-1.0, -1.0], 0.0) == {"motion": -1, "n_exact": 2}
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_sorted_search_special_cases(seed):
+    rng = np.random.default_rng(seed)
+    delta = rng.uniform(-0.2, 0.1, 30)
+    g = oracle.search_gcc0(delta, 0.0)
+    # a constant prediction keeps the given order: GCC_0
+    assert oracle.search_sorted(np.zeros(30), delta, 0.0) == g
+    # a perfect predictor finds a free motion (the farthest one) with one check
+    r = oracle.search_sorted(delta, delta, 0.0)
+    if g["motion"] >= 0:
+        assert r == {"motion": int(np.argmax(delta)), "n_exact": 1}
