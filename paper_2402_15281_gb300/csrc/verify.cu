@@ -9,8 +9,10 @@
 // and takes 7 square roots at the end.
 //
 // Work: persistent CTAs walk a list of chunks (256 points of one motion).
-// The motion's capsule table is staged in shared memory and read as
-// broadcasts; points are read as float4.  A motion that has collided stops
+// The motion's capsule table is staged in shared memory as packed pairs of
+// capsules and read as broadcasts, and the distance tests run on FP32 pairs
+// (sub/mul/fma.rn.f32x2: two capsules per instruction, the same roundings as
+// the scalar expressions); points are read as float4.  A motion that has collided stops
 // its remaining chunks (early exit), as Algorithm 1 needs only the verdict.
 #include "svm_internal.cuh"
 
@@ -74,13 +76,59 @@ __device__ int witness_sample(const Capsule* cs, int n_samples, float3 x, float 
     return n_samples - 1;
 }
 
+// ---- packed FP32 pairs: two capsules per instruction
+__device__ __forceinline__ uint64_t pk(float lo, float hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(uint64_t v, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t p_sub(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t p_mul(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t p_fma(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// The capsule table of one motion in the form the verifier reads: for sample
+// k and capsule pair p (capsules 2p and 2p+1; pair 3 repeats capsule 6),
+// seven packed pairs (a_x, a_y, a_z, -e_x, -e_y, -e_z, -1/|e|^2).  With the
+// negated axis the test below computes exactly the scalar expressions
+//   t = sat((w . e) / |e|^2),  d = w - t e,  |d|^2   (w = x - a),
+// two capsules per instruction: w.(-e) = -(w.e) and fma(t, -e, w) =
+// fma(-t, e, w) bit for bit.  Same size as the Capsule table (224 B per sample).
+// (A field-major layout read with 16-byte loads was measured slower: it holds
+// the whole sample in registers.)
+constexpr int kPairs = 4;
+struct CapPair {
+    uint64_t ax, ay, az, nex, ney, nez, nei;
+};
+static_assert(sizeof(CapPair) * kPairs == sizeof(Capsule) * kCaps, "packed table size");
+
 // One chunk = VT * PPT points of one motion; thread t checks points
 // t, t + VT, ..., so each capsule read from shared memory serves PPT points.
 template <int RANGE, int PPT>
 __global__ void __launch_bounds__(VT) verify_kernel(CallArgs A, int strict_pass)
 {
     extern __shared__ __align__(16) unsigned char vsm[];
-    Capsule* cs = reinterpret_cast<Capsule*>(vsm);
+    CapPair* cp = reinterpret_cast<CapPair*>(vsm);
+    __shared__ float s_r[kCaps];
     __shared__ int s_m;
     __shared__ int s_skip;
     __shared__ unsigned s_nver, s_namb;
@@ -108,10 +156,22 @@ __global__ void __launch_bounds__(VT) verify_kernel(CallArgs A, int strict_pass)
         __syncthreads();
         const int m = s_m;
         if (s_skip) { __syncthreads(); continue; }
+        const Capsule* mcaps = A.caps + (long long)m * n_samples * kCaps;
         if (m != cur_m) {
-            const float4* src = reinterpret_cast<const float4*>(A.caps + (long long)m * n_samples * kCaps);
-            float4* dst = reinterpret_cast<float4*>(cs);
-            for (int i = threadIdx.x; i < n_samples * kCaps * 2; i += VT) dst[i] = __ldg(src + i);
+            for (int i = threadIdx.x; i < n_samples * kPairs; i += VT) {
+                const int k = i / kPairs, pr = i % kPairs;
+                const Capsule c0 = mcaps[k * kCaps + 2 * pr], c1 = mcaps[k * kCaps + min(2 * pr + 1, kCaps - 1)];
+                CapPair q;
+                q.ax = pk(c0.a_r.x, c1.a_r.x);
+                q.ay = pk(c0.a_r.y, c1.a_r.y);
+                q.az = pk(c0.a_r.z, c1.a_r.z);
+                q.nex = pk(-c0.e_inv.x, -c1.e_inv.x);
+                q.ney = pk(-c0.e_inv.y, -c1.e_inv.y);
+                q.nez = pk(-c0.e_inv.z, -c1.e_inv.z);
+                q.nei = pk(-c0.e_inv.w, -c1.e_inv.w);
+                cp[i] = q;
+            }
+            if (threadIdx.x < kCaps) s_r[threadIdx.x] = mcaps[threadIdx.x].a_r.w;
             cur_m = m;
             __syncthreads();
         }
@@ -132,22 +192,34 @@ __global__ void __launch_bounds__(VT) verify_kernel(CallArgs A, int strict_pass)
                 x[j] = make_float3(x4.x, x4.y, x4.z);
             }
         }
-        float mn[PPT][kCaps];
+        // per point and capsule: minimum squared axis distance over the samples
+        float mn[PPT][2 * kPairs];
+        uint64_t X[PPT], Y[PPT], Z[PPT];
 #pragma unroll
-        for (int j = 0; j < PPT; ++j)
+        for (int j = 0; j < PPT; ++j) {
+            X[j] = pk(x[j].x, x[j].x);
+            Y[j] = pk(x[j].y, x[j].y);
+            Z[j] = pk(x[j].z, x[j].z);
 #pragma unroll
-            for (int q = 0; q < kCaps; ++q) mn[j][q] = __int_as_float(0x7f800000);
+            for (int q = 0; q < 2 * kPairs; ++q) mn[j][q] = __int_as_float(0x7f800000);
+        }
         for (int k = 0; k < n_samples; ++k) {
 #pragma unroll
-            for (int q = 0; q < kCaps; ++q) {
-                const float4 ar = cs[k * kCaps + q].a_r;
-                const float4 ei = cs[k * kCaps + q].e_inv;
+            for (int pr = 0; pr < kPairs; ++pr) {
+                const CapPair q = cp[k * kPairs + pr];
+                float ni0, ni1;
+                upk(q.nei, ni0, ni1);
 #pragma unroll
                 for (int j = 0; j < PPT; ++j) {
-                    const float wx = x[j].x - ar.x, wy = x[j].y - ar.y, wz = x[j].z - ar.z;
-                    const float t = __saturatef(fmaf(wz, ei.z, fmaf(wy, ei.y, wx * ei.x)) * ei.w);
-                    const float dx = fmaf(-t, ei.x, wx), dy = fmaf(-t, ei.y, wy), dz = fmaf(-t, ei.z, wz);
-                    mn[j][q] = fminf(mn[j][q], fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+                    const uint64_t wx = p_sub(X[j], q.ax), wy = p_sub(Y[j], q.ay), wz = p_sub(Z[j], q.az);
+                    float nd0, nd1;       // -(w . e) for the two capsules
+                    upk(p_fma(wz, q.nez, p_fma(wy, q.ney, p_mul(wx, q.nex))), nd0, nd1);
+                    const uint64_t t = pk(__saturatef(nd0 * ni0), __saturatef(nd1 * ni1));
+                    const uint64_t dx = p_fma(t, q.nex, wx), dy = p_fma(t, q.ney, wy), dz = p_fma(t, q.nez, wz);
+                    float d0, d1;
+                    upk(p_fma(dz, dz, p_fma(dy, dy, p_mul(dx, dx))), d0, d1);
+                    mn[j][2 * pr] = fminf(mn[j][2 * pr], d0);
+                    mn[j][2 * pr + 1] = fminf(mn[j][2 * pr + 1], d1);
                 }
             }
         }
@@ -156,7 +228,7 @@ __global__ void __launch_bounds__(VT) verify_kernel(CallArgs A, int strict_pass)
             if (!valid[j]) continue;
             float d = __int_as_float(0x7f800000);
 #pragma unroll
-            for (int q = 0; q < kCaps; ++q) d = fminf(d, sqrtf(mn[j][q]) - cs[q].a_r.w);
+            for (int q = 0; q < kCaps; ++q) d = fminf(d, sqrtf(mn[j][q]) - s_r[q]);
             atomicAdd(&s_nver, 1u);
             if (fabsf(d - A.margin) < kAmbiguousBand) atomicAdd(&s_namb, 1u);
             atomicMin(&s_dkey, float_key(d));
@@ -164,7 +236,7 @@ __global__ void __launch_bounds__(VT) verify_kernel(CallArgs A, int strict_pass)
                 const int path_head = (m / A.path_len) * A.path_len;
                 if (atomicCAS(&A.st[m].collided, 0, 1) == 0) {
                     A.st[m].witness_point = (int)pidx[j];
-                    A.st[m].witness_step = witness_sample(cs, n_samples, x[j], A.margin);
+                    A.st[m].witness_step = witness_sample(mcaps, n_samples, x[j], A.margin);
                 }
                 if (path_head != m) atomicExch(&A.st[path_head].collided, 1);
             }
