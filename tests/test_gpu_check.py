@@ -57,7 +57,7 @@ def _dev(a):
 
 
 def _check(svm, model, q0, q1, pts, eps, N, flags):
-    n_out = len(q0) // 3 if flags & svm.SVM_PATHS3 else len(q0)
+    n_out = len(q0) // 3 if flags & svm.SVM_PATHS3 else len(q0) // 2 if flags & svm.SVM_PATHS2 else len(q0)
     res = svm.new_results(n_out)
     svm.svm_check_motions(model.h, q0, q1, _dev(pts), eps, N, flags, res)
     torch.cuda.synchronize()
@@ -248,23 +248,26 @@ def test_invalid_arguments_are_rejected(svm, robot):
         m.close()
 
 
-def test_paths_of_three_segments(svm, robot):
-    """Config 4 shape: paths q_start -> q_inVia -> q_outVia -> q_end, one
-    verdict per path (OR over its segments)."""
-    paths = S.bin_paths(robot, 8, seed=1)
-    q0 = paths[:, :3].reshape(-1, 6)
+@pytest.mark.parametrize("seg", [2, 3])
+def test_paths_of_segments(svm, robot, seg):
+    """Config 4 shape (three segments q_start -> q_inVia -> q_outVia -> q_end)
+    and the two-segment grasp motions of Sec. V-C: one verdict per path (OR
+    over its segments)."""
+    paths = S.bin_paths(robot, 8, seed=1)[:, :seg + 1]
+    q0 = paths[:, :seg].reshape(-1, 6)
     q1 = paths[:, 1:].reshape(-1, 6)
+    flag = svm.SVM_PATHS3 if seg == 3 else svm.SVM_PATHS2
     pts = S.bin_cloud(3000, seed=0)
     m = Model(svm, robot, _layers())
     eps, N = 0.03, 32
     try:
-        r = _check(svm, m, q0, q1, pts, eps, N, svm.SVM_PATHS3)
+        r = _check(svm, m, q0, q1, pts, eps, N, flag)
         dmin, coll = oracle.gcc_motion(robot, q0, q1, N, pts, eps)
-        want = coll.reshape(-1, 3).max(axis=1)
+        want = coll.reshape(-1, seg).max(axis=1)
         np.testing.assert_array_equal(r["collision"], want)
-        r2 = _check(svm, m, q0, q1, pts, eps, N, svm.SVM_PATHS3 | svm.SVM_NO_EARLY_EXIT)
+        r2 = _check(svm, m, q0, q1, pts, eps, N, flag | svm.SVM_NO_EARLY_EXIT)
         np.testing.assert_array_equal(r2["collision"], want)
-        assert np.abs(r2["d_min"] - dmin.reshape(-1, 3).min(axis=1)).max() <= DIST_TOL
+        assert np.abs(r2["d_min"] - dmin.reshape(-1, seg).min(axis=1)).max() <= DIST_TOL
     finally:
         m.close()
 

@@ -157,3 +157,20 @@ def test_training_lowers_heldout_error_and_resumes(svm, robot):
         svm.svm_destroy_model(h)
     finally:
         svm.svm_train_destroy(t)
+
+
+def test_training_throughput_config5_shape(svm, robot):
+    """Training at the shape of the paper-scale configuration: 15 -> 512 x 6
+    SiLU -> 1, batch 65 536, GPU-generated data (2 048 motions x 1 024 points),
+    three epochs.  The loss falls; samples/s and the GEMM work rate are
+    printed (forward 2 (15 W + L W^2 + W) FLOP per sample, backward twice
+    that)."""
+    from paper_2402_15281_gb300 import training
+    q0, q1 = S.uniform_motions(robot, 2048, seed=61)
+    blob, hist = training.train_model(svm, robot, q0, q1, width=512, n_hidden=6, act=1, samples_per_motion=1024,
+                                      steps=64, batch=65536, epochs=3, patience=3)
+    flop = 3 * 2 * (15 * 512 + 6 * 512 * 512 + 512)
+    print(f"512x6 SiLU: {hist['samples_per_s'] / 1e6:.1f} M samples/s = "
+          f"{hist['samples_per_s'] * flop / 1e12:.0f} TFLOP/s of training arithmetic; "
+          f"epoch losses {[round(v, 4) for v in hist['epoch_loss']]}")
+    assert hist["epoch_loss"][-1] < hist["epoch_loss"][0]
