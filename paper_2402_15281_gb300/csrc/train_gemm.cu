@@ -14,7 +14,8 @@
 //
 // Persistent kernel, one CTA per SM, 10 warps: warp 0 streams A and B tiles
 // (128 x 64 and 256 x 64 bfloat16, 128B swizzle) with TMA into a 4-stage
-// ring; warp 1 issues tcgen05.mma (M = 128, N = 256, K = 16) into one of two
+// ring; warp 1 issues tcgen05.mma (M = 128, N = 256, K = 16; warp-uniform
+// loop, one elected lane) into one of two
 // TMEM accumulators; warps 2-9 drain the other accumulator (two warps per TMEM
 // lane quarter, 128 columns each), so the epilogue of one tile overlaps the
 // MMAs of the next.  Transposed outputs are staged per warp in shared memory
@@ -191,35 +192,38 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
-            int stage = 0;
-            uint32_t phase = 0;
-            uint32_t acce_phase[2] = {0u, 0u};
-            bool ok = true;
-            for (int i = 0; i < n_mine && ok; ++i) {
-                const int b = i & 1;
-                if (!mbar_wait(acce_bar(b), acce_phase[b] ^ 1u, abort_flag, g.err)) { ok = false; break; }
-                acce_phase[b] ^= 1u;
+        // warp-uniform issue loop, one elected lane issues; descriptors advance
+        // by adding to the start-address field (32 B within a swizzle atom)
+        int stage = 0;
+        uint32_t phase = 0;
+        uint32_t acce_phase0 = 0u, acce_phase1 = 0u;
+        const uint64_t a_desc0 = sdesc(sbase), b_desc0 = sdesc(sbase + A_BYTES);
+        bool ok = true;
+        for (int i = 0; i < n_mine && ok; ++i) {
+            const int b = i & 1;
+            uint32_t& ap = b == 0 ? acce_phase0 : acce_phase1;
+            if (!mbar_wait_warp(acce_bar(b), ap ^ 1u, abort_flag, g.err)) { ok = false; break; }
+            ap ^= 1u;
+            tc_fence_after();
+            const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
+            for (int kk = 0; kk < k_slices; ++kk) {
+                if (!mbar_wait_warp(full_bar(stage), phase, abort_flag, g.err)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
-                for (int kk = 0; kk < k_slices; ++kk) {
-                    if (!mbar_wait(full_bar(stage), phase, abort_flag, g.err)) { ok = false; break; }
-                    tc_fence_after();
-                    const uint32_t a0 = sbase + stage * STAGE_BYTES;
-                    const uint32_t b0 = a0 + A_BYTES;
+                const uint64_t ad = a_desc0 + (uint64_t)(stage * (STAGE_BYTES >> 4));
+                const uint64_t bd = b_desc0 + (uint64_t)(stage * (STAGE_BYTES >> 4));
 #pragma unroll
-                    for (int k = 0; k < BK / 16; ++k)
-                        mma_f16(d_tmem, sdesc(a0 + k * 32), sdesc(b0 + k * 32), IDESC, (kk | k) != 0 ? 1u : 0u);
-                    mma_commit(empty_bar(stage));
-                    if (++stage == STAGES) { stage = 0; phase ^= 1u; }
-                }
-                if (ok) mma_commit(accf_bar(b));
+                for (int k = 0; k < BK / 16; ++k)
+                    mma_f16_warp(d_tmem, ad + 2 * k, bd + 2 * k, IDESC, (kk | k) != 0 ? 1u : 0u);
+                mma_commit_warp(empty_bar(stage));
+                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
             }
-            mma_commit(drain_bar);
-            const uint64_t t0 = globaltimer();
-            while (!mbar_try(drain_bar, 0u) && globaltimer() - t0 < kTimeoutNs) {
-            }
+            if (ok) mma_commit_warp(accf_bar(b));
         }
+        mma_commit_warp(drain_bar);
+        const uint64_t t0 = globaltimer();
+        while (!mbar_try(drain_bar, 0u) && globaltimer() - t0 < kTimeoutNs) {
+        }
+        __syncwarp();
     } else {
         const int ew = warp - 2;
         const int quarter = warp & 3;
