@@ -158,6 +158,16 @@ svm_status svm_load_weights(svm_model* m, const void* blob, size_t bytes);
  * to *needed (may be NULL). */
 svm_status svm_export_weights(const svm_model* m, float* out, size_t count, size_t* needed);
 
+/* Test hook for the failure path of the bounded device waits: the next
+ * n_calls check calls of this tensor-core model run with CTA 0 withholding
+ * its first layer-0 hand-over, so that its MMA warp's wait expires after
+ * 2 s; every role of that CTA leaves its loop, waits (bounded) for its own
+ * operations in flight and frees its TMEM, the other CTAs finish, and every
+ * record of the call carries status 1.  Later calls are unaffected.  The
+ * call itself returns SVM_OK (the failure is reported in the records).
+ * SVM_E_UNSUPPORTED for FP32 models (no device waits). */
+svm_status svm_test_expire_wait(svm_model* m, int32_t n_calls);
+
 /* Gate offset tau >= 0 (metres): a pair is checked exactly iff its network
  * prediction f <= margin + tau.  tau = +inf checks every pair. */
 svm_status svm_set_gate(svm_model* m, float tau);

@@ -114,6 +114,8 @@ def lib():
         L.svm_search_free_motion.argtypes = [vp, vp, vp, i32, vp, i64, f32, i32, i32, u32,
                                              C.POINTER(svm_search_result), vp]
         L.svm_search_free_motion.restype = C.c_int
+        L.svm_test_expire_wait.argtypes = [vp, i32]
+        L.svm_test_expire_wait.restype = C.c_int
         L.svm_profile_enable.argtypes = [vp, C.c_int]
         L.svm_profile_read.argtypes = [vp, vp, i32]
         for f in ("svm_profile_enable", "svm_profile_read", "svm_create_model", "svm_destroy_model", "svm_load_weights", "svm_export_weights",
@@ -228,6 +230,10 @@ def svm_export_weights(model) -> np.ndarray:
     _check("svm_export_weights", lib().svm_export_weights(model, out.ctypes.data_as(C.c_void_p),
                                                           out.shape[0], None), model)
     return out
+
+
+def svm_test_expire_wait(model, n_calls: int = 1):
+    _check("svm_test_expire_wait", lib().svm_test_expire_wait(model, int(n_calls)), model)
 
 
 def svm_set_gate(model, tau: float):

@@ -595,7 +595,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         bool valid = false;
         if (s < n_mine) {
             tile_info(s, m, p, valid);
-            stage_x(load_x(p, valid));
+            if (!(A.test_stall && blockIdx.x == 0 && s == 0)) stage_x(load_x(p, valid));
         }
         for (int i = s; i < n_mine && ok; i += 2) {
             // the slot's next tile: looked up, and its points loaded, during the

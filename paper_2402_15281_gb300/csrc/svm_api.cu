@@ -289,6 +289,14 @@ svm_status svm_destroy_model(svm_model* m)
     return SVM_OK;
 }
 
+svm_status svm_test_expire_wait(svm_model* m, int32_t n_calls)
+{
+    if (!m || n_calls < 0) return SVM_E_INVALID;
+    if (m->desc.prec == SVM_FP32) return fail(m, SVM_E_UNSUPPORTED, "the FP32 path has no device waits");
+    m->test_stalls = n_calls;
+    return SVM_OK;
+}
+
 svm_status svm_set_gate(svm_model* m, float tau)
 {
     if (!m) return SVM_E_INVALID;
@@ -639,6 +647,10 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
     a.f_stride = (n_scenes == 1) ? scene_off[1] : 0;
     a.path_len = path_len_of(flags);
     a.amax = m->calib_amax;
+    if (mode == kCheck && tc && m->test_stalls > 0 && !(flags & SVM_VERIFY_ALL)) {
+        a.test_stall = 1;
+        --m->test_stalls;
+    }
     void* tc_ws = ws + pl.o_chunk + align256((size_t)(M + 1) * 4);
     a.dev_err = static_cast<unsigned int*>(tc_ws);
     CK(cudaMemsetAsync(a.dev_err, 0, sizeof(unsigned int), stream));

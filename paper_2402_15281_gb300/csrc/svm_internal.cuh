@@ -82,6 +82,8 @@ struct CallArgs {
     int path_len;       // segments per path: 1 (single motions), 2 or 3
     unsigned int* dev_err;  // per-call error word: nonzero if a bounded wait expired
     unsigned int* amax;     // optional [L]: bit patterns of max |input of hidden layer l| (calibration)
+    int test_stall;         // test hook: CTA 0 withholds its first layer-0 hand-over, so that
+                            // the MMA warp's bounded wait expires (tensor-core path)
 };
 
 // Model weights on the device.  FP32 copies are always present; the layer-1

@@ -37,6 +37,7 @@ struct svm_model {
     bool prof_valid = false;
     cudaEvent_t ev[5] = {};
     unsigned int* calib_amax = nullptr;   // set only on a calibration model
+    int test_stalls = 0;                   // check calls left to run with the test stall
     std::string last_error;
 };
 

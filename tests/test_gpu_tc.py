@@ -163,3 +163,36 @@ def test_bf16_open_gate_equals_geometric_check(svm, robot):
         assert np.all(r["n_flagged"] == 20000)
     finally:
         svm.svm_destroy_model(h)
+
+
+def test_bounded_wait_expiry_is_reported_and_recoverable(svm, robot):
+    """The failure path of the bounded device waits, without a GPU fault: a
+    test hook withholds one layer-0 hand-over in CTA 0, its MMA warp's wait
+    expires after 2 s, every record of that call carries status 1, and the
+    next call on the same model and context gives the normal records."""
+    import time
+    pts = torch.from_numpy(S.bin_cloud(20000, seed=2)).cuda()
+    q0, q1 = S.bin_motions(robot, 8, seed=2)
+    h = svm.svm_create_model(robot, 256, 4, 0, svm.SVM_BF16, 0)
+    try:
+        svm.svm_load_weights(h, svm.make_blob(S.xavier_weights(256, 4, seed=2)))
+        res = svm.new_results(8)
+        svm.svm_check_motions(h, q0, q1, pts, 0.03, 32, svm.SVM_NO_EARLY_EXIT, res)
+        torch.cuda.synchronize()
+        want = svm.results_to_numpy(res)[:8].copy()
+        assert np.all(want["status"] == 0)
+        svm.svm_test_expire_wait(h, 1)
+        t = time.perf_counter()
+        svm.svm_check_motions(h, q0, q1, pts, 0.03, 32, svm.SVM_NO_EARLY_EXIT, res)
+        torch.cuda.synchronize()
+        waited = time.perf_counter() - t
+        bad = svm.results_to_numpy(res)[:8].copy()
+        assert np.all(bad["status"] == 1) and 1.5 < waited < 30
+        svm.svm_check_motions(h, q0, q1, pts, 0.03, 32, svm.SVM_NO_EARLY_EXIT, res)
+        torch.cuda.synchronize()
+        again = svm.results_to_numpy(res)[:8]
+        assert np.all(again["status"] == 0)
+        for k in ("collision", "d_min", "dhat_min", "n_flagged", "n_verified"):
+            np.testing.assert_array_equal(again[k], want[k], err_msg=k)
+    finally:
+        svm.svm_destroy_model(h)
