@@ -230,55 +230,9 @@ __device__ __forceinline__ uint32_t relu_e4m3x2(uint64_t v)
 //   FP8 hidden:  h = relu(acc * c + b)  with c = s_w s_a / s_next and b
 //                already divided by s_next          -> E4M3
 //   FP8 layer 0: h = relu((acc + b) * c), c = 1 / s_next
-template <int PREC, bool LAYER0>
-__device__ __forceinline__ void epilogue32_relu(uint32_t base, int r, int o0, const float (&v)[32],
-                                                const float* bias, float c)
-{
-    const uint64_t c2 = f2(c, c);
-    uint32_t out[16];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + o0 + 4 * q));
-        const uint64_t a0 = f2(v[4 * q + 0], v[4 * q + 1]), a1 = f2(v[4 * q + 2], v[4 * q + 3]);
-        const uint64_t b0 = f2(b4.x, b4.y), b1 = f2(b4.z, b4.w);
-        uint64_t z0, z1;
-        if constexpr (PREC == SVM_BF16) {
-            z0 = f2_add(a0, b0);
-            z1 = f2_add(a1, b1);
-            out[2 * q + 0] = relu_bf16x2(z0);
-            out[2 * q + 1] = relu_bf16x2(z1);
-        } else {
-            if constexpr (LAYER0) {
-                z0 = f2_mul(f2_add(a0, b0), c2);
-                z1 = f2_mul(f2_add(a1, b1), c2);
-            } else {
-                z0 = f2_fma(a0, c2, b0);
-                z1 = f2_fma(a1, c2, b1);
-            }
-            out[2 * q + 0] = relu_e4m3x2(z0);
-            out[2 * q + 1] = relu_e4m3x2(z1);
-        }
-    }
-    if constexpr (PREC == SVM_BF16) {
-        const int kb = o0 >> 6, c0 = (o0 & 63) >> 3;
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            st_shared_v4(act_chunk_addr(base, kb, r, c0 + k), out[4 * k + 0], out[4 * k + 1], out[4 * k + 2],
-                         out[4 * k + 3]);
-    } else {
-        // 16 E4M3 pairs (16 bits each) -> 8 words -> two 16-byte chunks
-        uint32_t w[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) w[k] = (out[2 * k] & 0xFFFFu) | (out[2 * k + 1] << 16);
-        const int kb = o0 >> 7, c0 = (o0 & 127) >> 4;
-        st_shared_v4(act_chunk_addr(base, kb, r, c0), w[0], w[1], w[2], w[3]);
-        st_shared_v4(act_chunk_addr(base, kb, r, c0 + 1), w[4], w[5], w[6], w[7]);
-    }
-}
-
-// The same with the 32 biases of the chunk held one per lane (lane i holds
-// the bias of column o0 + i) and broadcast by shuffles: no memory access on
-// the path from the accumulator to the stores.
+// The 32 biases of the chunk are held one per lane (lane i holds the bias of
+// column o0 + i) and broadcast by shuffles: no memory access on the path from
+// the accumulator to the stores.
 template <int PREC, bool LAYER0>
 __device__ __forceinline__ void epilogue32_relu_lane(uint32_t base, int r, int o0, const float (&v)[32], float bl,
                                                      float c)

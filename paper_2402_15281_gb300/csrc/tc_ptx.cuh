@@ -111,26 +111,6 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
 // One tcgen05.mma of kind::f16 (BF16/FP16 operands) or kind::f8f6f4 (FP8),
 // D in TMEM, A and B from shared-memory descriptors, idesc the instruction
 // descriptor; accumulate = 0 overwrites D.
-__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                        uint32_t accumulate)
-{
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_f8f6f4(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                           uint32_t accumulate)
-{
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
 // Warp-wide forms: all 32 lanes execute them with the same operands and one
 // lane, chosen by elect.sync, issues the instruction.  Keeping the issuing
 // loop warp-uniform lets its address arithmetic stay on the uniform datapath.
@@ -160,12 +140,6 @@ __device__ __forceinline__ void mma_commit_warp(uint32_t bar)
         "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
         " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}" ::"r"(bar)
         : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
