@@ -347,7 +347,7 @@ def run_gpu(args):
                 "verdicts_equal": bool(np.array_equal(r32["collision"], r["collision"]))}
         svm.svm_destroy_model(m32)
 
-    launches_per_step = 5 + (2 if flags & svm.SVM_STRICT else 0)
+    launches_per_step = 6 + (2 if flags & svm.SVM_STRICT else 0)
     line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAMES[args.prec], "data": "synthetic",
@@ -363,7 +363,8 @@ def run_gpu(args):
             "fp32_path": fp32, "speedup_vs_fp32_path": (value / fp32["value"]) if fp32 else None,
             "training": train_info,
             "flagged_fraction": float(r["n_flagged"].sum()) / pairs_step,
-            "verified_fraction": n_verified / pairs_step}
+            "verified_fraction": n_verified / pairs_step,
+            "margin_ties_fp64": int(r["n_ambiguous"].sum())}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt, cores = oracle_sample(robot, pts, q0, q1, layers, args.prec, EPS + tau, 2)
         line["cpu_baseline"] = {"value": v, "unit": "queries/s", "cores": cores, "kind": "oracle",

@@ -99,7 +99,10 @@ typedef struct {
     int32_t witness_point;  /* index of a colliding point, -1 if none           */
     int32_t witness_step;   /* a sample k in [0, steps] where it collides, -1 if
                                none; for paths: segment * (steps + 1) + k       */
-    uint32_t n_ambiguous;   /* checked points within 4e-6 m of the margin       */
+    uint32_t n_ambiguous;   /* checked points whose FP32 distance lies within
+                               4e-6 m of the margin; their verdict and distance
+                               are recomputed in FP64 (the first 16384 such
+                               pairs of a call; the FP32 decision beyond)      */
 } svm_result;
 
 typedef struct svm_model svm_model;

@@ -24,7 +24,7 @@ struct svm_plan {
     long long P_total = 0;
     void* ws = nullptr;
     size_t o_q0 = 0, o_q1 = 0, o_pbeg = 0, o_pend = 0, o_toff = 0, o_poff = 0;
-    size_t o_caps = 0, o_cbias = 0, o_st = 0, o_idx = 0, o_chunk = 0, o_err = 0, total = 0;
+    size_t o_caps = 0, o_fk64 = 0, o_cbias = 0, o_st = 0, o_idx = 0, o_chunk = 0, o_err = 0, o_tie = 0, total = 0;
     VerifyConfig vcfg{};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -69,6 +69,7 @@ CallArgs plan_args(svm_plan* p, const float* points)
     a.L = m->desc.n_hidden;
     a.act = m->desc.act;
     a.arch = m->desc.arch;
+    a.rp = m->rp;
     a.cb_stride = cbias_stride(m->desc);
     a.flags = p->flags;
     a.margin = p->margin;
@@ -81,6 +82,7 @@ CallArgs plan_args(svm_plan* p, const float* points)
     a.pair_off = reinterpret_cast<const long long*>(ws + p->o_poff);
     a.points = reinterpret_cast<const float4*>(points);
     a.caps = reinterpret_cast<Capsule*>(ws + p->o_caps);
+    a.fk64 = reinterpret_cast<double*>(ws + p->o_fk64);
     a.cbias = (p->flags & SVM_VERIFY_ALL) ? nullptr : reinterpret_cast<float*>(ws + p->o_cbias);
     a.st = reinterpret_cast<MotionState*>(ws + p->o_st);
     a.idx = reinterpret_cast<unsigned*>(ws + p->o_idx);
@@ -89,6 +91,8 @@ CallArgs plan_args(svm_plan* p, const float* points)
     a.f_stride = 0;
     a.path_len = path_len_of(p->flags);
     a.dev_err = reinterpret_cast<unsigned int*>(ws + p->o_err);
+    a.tie_count = reinterpret_cast<unsigned int*>(ws + p->o_tie);
+    a.tie_list = reinterpret_cast<TiePair*>(ws + p->o_tie + 256);
     a.amax = nullptr;
     return a;
 }
@@ -113,6 +117,7 @@ svm_status enqueue(svm_plan* p, const float* points, svm_result* results, cudaSt
     } else {
         launch_verify_cfg(a, 1, 0, s, m->n_sms, p->vcfg);
     }
+    launch_ties(a, s, m->n_sms);
     launch_finalize(a, results, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return pfail(m, SVM_E_CUDA, cudaGetErrorString(e));
@@ -181,11 +186,13 @@ svm_status svm_plan_create(svm_model* m, const double* q0, const double* q1, int
     p->o_poff = at; at = al256(at + (size_t)(M + 1) * 8);
     const size_t header = at;
     p->o_caps = at; at = al256(at + (size_t)M * (steps + 1) * kCaps * sizeof(Capsule));
+    p->o_fk64 = at; at = al256(at + (size_t)M * (steps + 1) * 24 * sizeof(double));
     p->o_cbias = at; at = al256(at + (size_t)M * cbias_stride(m->desc) * 4);
     p->o_st = at; at = al256(at + (size_t)M * sizeof(MotionState));
     p->o_idx = at; at = al256(at + (size_t)std::max<long long>(1, p->P_total) * 4);
     p->o_chunk = at; at = al256(at + (size_t)(M + 1) * 4);
     p->o_err = at; at = al256(at + 4);
+    p->o_tie = at; at = al256(at + 256 + tie_list_bytes());
     p->total = at;
     Guard g(m->device);
     if (cudaMalloc(&p->ws, p->total) != cudaSuccess) {

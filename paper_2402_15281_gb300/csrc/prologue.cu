@@ -4,12 +4,13 @@
 //     linear joint motion (Eq. 2 with s = k/N; the paper discretises motions
 //     by joint interpolation, Sec. IV-C), in FP64 -- the only FP64 arithmetic
 //     on the GPU -- and the 7 capsules of the robot at that sample, cast once
-//     to FP32 for the verifier.
+//     to FP32 for the verifier; the FP64 joint origins and tool axis are kept
+//     for the FP64 decision of pairs at the margin.
 // (b) The per-motion part of the first network layer.  The input of the
 //     network is [x, q0, q1] (Sec. IV-A), so W1 [x; q0; q1] + b1 splits into
 //     W1x x + c_m with c_m = W1q [q0; q1] + b1, computed here once per motion
 //     instead of once per pair.
-// (c) Reset of the per-motion counters and minima.
+// (c) Reset of the per-motion counters and minima, and of the call's tie list.
 #include "svm_internal.cuh"
 
 namespace svm {
@@ -49,6 +50,12 @@ __global__ void __launch_bounds__(128) prologue_kernel(CallArgs A, RobotParams R
             for (int i = 0; i < 3; ++i) { p[i] = pn[i]; o[j + 1][i] = pn[i]; }
         }
         Capsule* out = A.caps + ((long long)m * (N + 1) + k) * kCaps;
+        if (A.fk64 != nullptr) {
+            double* f = A.fk64 + ((long long)m * (N + 1) + k) * 24;
+            for (int j = 0; j <= kDof; ++j)
+                for (int i = 0; i < 3; ++i) f[j * 3 + i] = o[j][i];
+            for (int i = 0; i < 3; ++i) f[21 + i] = R.tool_len * Rm[i * 3 + 2];
+        }
         for (int j = 0; j < kCaps; ++j) {
             double a3[3], e3[3];
             for (int i = 0; i < 3; ++i) {
@@ -103,6 +110,7 @@ __global__ void __launch_bounds__(128) prologue_kernel(CallArgs A, RobotParams R
         z.witness_step = -1;
         z.n_ambiguous = 0;
         A.st[m] = z;
+        if (m == 0 && A.tie_count) *A.tie_count = 0;
     }
 }
 

@@ -259,7 +259,10 @@ svm_status svm_create_model(const svm_model_desc* desc, int device, svm_model** 
         m->rp.th0[j] = d.dh[j][3];
     }
     m->rp.tool_len = d.tool_len;
-    for (int j = 0; j < 7; ++j) m->rp.radius[j] = (float)d.radius[j];
+    for (int j = 0; j < 7; ++j) {
+        m->rp.radius[j] = (float)d.radius[j];
+        m->rp.radius64[j] = d.radius[j];
+    }
     if (cudaEventCreateWithFlags(&m->staging_done, cudaEventDisableTiming) != cudaSuccess) {
         delete m;
         return SVM_E_CUDA;
@@ -502,7 +505,7 @@ struct CallPlan {
     int bm;
     // offsets in the workspace
     size_t o_q0, o_q1, o_pbeg, o_pend, o_toff, o_poff, header_bytes;
-    size_t o_caps, o_cbias, o_st, o_idx, o_chunk, total;
+    size_t o_caps, o_fk64, o_cbias, o_st, o_idx, o_chunk, o_tie, total;
 };
 
 // Shared driver of the check, eval and label calls.
@@ -565,11 +568,13 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
     pl.o_poff = at; at = align256(at + (size_t)(M + 1) * 8);
     pl.header_bytes = at;
     pl.o_caps = at; at = align256(at + (size_t)M * (steps + 1) * kCaps * sizeof(Capsule));
+    pl.o_fk64 = at; at = align256(at + (size_t)M * (steps + 1) * 24 * sizeof(double));
     pl.o_cbias = at; at = align256(at + (size_t)M * cbias_stride(d) * 4);
     pl.o_st = at; at = align256(at + (size_t)M * sizeof(MotionState));
     pl.o_idx = at; at = align256(at + (size_t)std::max<long long>(1, pl.P_total) * 4);
     pl.o_chunk = at; at = align256(at + (size_t)(M + 1) * 4);
     at = align256(at + tc_workspace_bytes(M));
+    pl.o_tie = at; at = align256(at + 256 + tie_list_bytes());
     pl.total = at;
 
     DeviceGuard g(m->device);
@@ -627,6 +632,7 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
     a.L = d.n_hidden;
     a.act = d.act;
     a.arch = d.arch;
+    a.rp = m->rp;
     a.cb_stride = cbias_stride(d);
     a.flags = flags;
     a.margin = margin;
@@ -639,6 +645,7 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
     a.pair_off = reinterpret_cast<const long long*>(ws + pl.o_poff);
     a.points = reinterpret_cast<const float4*>(points_dev);
     a.caps = reinterpret_cast<Capsule*>(ws + pl.o_caps);
+    a.fk64 = reinterpret_cast<double*>(ws + pl.o_fk64);
     a.cbias = (mode == kLabel || (flags & SVM_VERIFY_ALL)) ? nullptr : reinterpret_cast<float*>(ws + pl.o_cbias);
     a.st = reinterpret_cast<MotionState*>(ws + pl.o_st);
     a.idx = reinterpret_cast<unsigned*>(ws + pl.o_idx);
@@ -653,6 +660,8 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
     }
     void* tc_ws = ws + pl.o_chunk + align256((size_t)(M + 1) * 4);
     a.dev_err = static_cast<unsigned int*>(tc_ws);
+    a.tie_count = reinterpret_cast<unsigned int*>(ws + pl.o_tie);
+    a.tie_list = reinterpret_cast<TiePair*>(ws + pl.o_tie + 256);
     CK(cudaMemsetAsync(a.dev_err, 0, sizeof(unsigned int), stream));
 
     launch_prologue_fk(a, m->rp, m->dw, stream);
@@ -677,10 +686,12 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
         if (!(flags & SVM_PREDICT_ONLY)) {
             launch_verify(a, 0, 0, stream, m->n_sms);
             if (flags & SVM_STRICT) launch_verify(a, 1, 1, stream, m->n_sms);
+            launch_ties(a, stream, m->n_sms);
         }
     } else {
         if (prof) CK(cudaEventRecord(m->ev[2], stream));
         launch_verify(a, 1, 0, stream, m->n_sms);
+        launch_ties(a, stream, m->n_sms);
     }
     if (prof) CK(cudaEventRecord(m->ev[3], stream));
     launch_finalize(a, results_dev, stream);
@@ -1056,16 +1067,18 @@ extern "C" svm_status svm_check_motions_noalloc(svm_model* m, const double* q0_d
     const size_t o_toff = at; at = align256(at + (size_t)(M + 1) * 4);
     const size_t o_poff = at; at = align256(at + (size_t)(M + 1) * 8);
     const size_t o_caps = at; at = align256(at + (size_t)M * (steps + 1) * kCaps * sizeof(Capsule));
+    const size_t o_fk64 = at; at = align256(at + (size_t)M * (steps + 1) * 24 * sizeof(double));
     const size_t o_cbias = at; at = align256(at + (size_t)M * cbias_stride(d) * 4);
     const size_t o_st = at; at = align256(at + (size_t)M * sizeof(MotionState));
     const size_t o_idx = at; at = align256(at + (size_t)std::max<long long>(1, (long long)M * n_points) * 4);
     const size_t o_chunk = at; at = align256(at + (size_t)(M + 1) * 4);
     const size_t o_err = at; at = align256(at + 4);
+    const size_t o_tie = at; at = align256(at + 256 + tie_list_bytes());
     if (at > kNoAllocScratchBytes)
         return fail(m, SVM_E_INVALID,
                     "svm_check_motions_noalloc: the call needs " + std::to_string(at) +
                         " bytes of scratch, more than its fixed 32 MiB; use fewer motions or points per call "
-                        "(about 4 bytes per motion-point pair plus ~29 KB per motion at 128 steps)");
+                        "(about 4 bytes per motion-point pair plus ~54 KB per motion at 128 steps)");
 
     DeviceGuard g(m->device);
     void* sp = nullptr;
@@ -1081,6 +1094,7 @@ extern "C" svm_status svm_check_motions_noalloc(svm_model* m, const double* q0_d
     a.L = d.n_hidden;
     a.act = d.act;
     a.arch = d.arch;
+    a.rp = m->rp;
     a.cb_stride = cbias_stride(d);
     a.flags = flags;
     a.margin = margin;
@@ -1093,6 +1107,7 @@ extern "C" svm_status svm_check_motions_noalloc(svm_model* m, const double* q0_d
     a.pair_off = reinterpret_cast<const long long*>(ws + o_poff);
     a.points = reinterpret_cast<const float4*>(points_dev);
     a.caps = reinterpret_cast<Capsule*>(ws + o_caps);
+    a.fk64 = reinterpret_cast<double*>(ws + o_fk64);
     a.cbias = (flags & SVM_VERIFY_ALL) ? nullptr : reinterpret_cast<float*>(ws + o_cbias);
     a.st = reinterpret_cast<MotionState*>(ws + o_st);
     a.idx = reinterpret_cast<unsigned*>(ws + o_idx);
@@ -1101,6 +1116,8 @@ extern "C" svm_status svm_check_motions_noalloc(svm_model* m, const double* q0_d
     a.f_stride = n_points;
     a.path_len = path_len_of(flags);
     a.dev_err = reinterpret_cast<unsigned int*>(ws + o_err);
+    a.tie_count = reinterpret_cast<unsigned int*>(ws + o_tie);
+    a.tie_list = reinterpret_cast<TiePair*>(ws + o_tie + 256);
 
     noalloc_setup_kernel<<<(M + 256) / 256, 256, 0, stream>>>(
         M, n_points, bm, reinterpret_cast<long long*>(ws + o_pbeg), reinterpret_cast<long long*>(ws + o_pend),
@@ -1119,6 +1136,7 @@ extern "C" svm_status svm_check_motions_noalloc(svm_model* m, const double* q0_d
     } else {
         launch_verify(a, 1, 0, stream, m->n_sms);
     }
+    launch_ties(a, stream, m->n_sms);
     launch_finalize(a, results_dev, stream);
     CK(cudaGetLastError());
     return SVM_OK;

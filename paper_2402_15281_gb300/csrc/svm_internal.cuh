@@ -22,6 +22,16 @@ constexpr int kCaps = 7;
 constexpr int kInDim = 15;
 constexpr int kMaxSteps = 900;        // capsule table of one motion fits in shared memory
 constexpr float kAmbiguousBand = 4e-6f;
+constexpr int kTieCap = 16384;        // pairs per call whose verdict is re-decided in FP64
+
+// A (motion, point) pair whose FP32 distance fell within kAmbiguousBand of the
+// margin; the verifier defers it to the FP64 tie kernel.
+struct TiePair {
+    int m;
+    int pad;
+    long long p;
+};
+inline size_t tie_list_bytes() { return (size_t)kTieCap * sizeof(TiePair); }
 
 // One capsule at one sample: a = start point, r = radius; e = b - a and
 // inv_ee = 1 / |e|^2 (0 for a zero-length axis, which makes it a sphere).
@@ -52,6 +62,15 @@ __device__ __forceinline__ float key_float(unsigned int k) {
     unsigned int u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
     return __uint_as_float(u);
 }
+
+// Robot geometry (FP64 kinematics; FP32 radii for the capsule tables, FP64
+// radii for the re-check of pairs at the margin).
+struct RobotParams {
+    double d[kDof], a[kDof], ca[kDof], sa[kDof], th0[kDof];
+    double tool_len;
+    float radius[kCaps];
+    double radius64[kCaps];
+};
 
 // Everything a kernel of one call needs, passed by value.
 struct CallArgs {
@@ -84,6 +103,10 @@ struct CallArgs {
     unsigned int* amax;     // optional [L]: bit patterns of max |input of hidden layer l| (calibration)
     int test_stall;         // test hook: CTA 0 withholds its first layer-0 hand-over, so that
                             // the MMA warp's bounded wait expires (tensor-core path)
+    RobotParams rp;         // robot (FP64 re-check of pairs at the margin)
+    double* fk64;           // [M][N+1][8][3]: joint origins o_0..o_6 and tool axis of every sample, FP64
+    unsigned int* tie_count;    // pairs appended to tie_list (reset by the prologue)
+    TiePair* tie_list;          // [kTieCap] pairs deferred to the FP64 tie kernel
 };
 
 // Model weights on the device.  FP32 copies are always present; the layer-1
@@ -168,6 +191,7 @@ struct VerifyConfig {
 void launch_verify(const CallArgs& a, int range_mode, int strict_pass, cudaStream_t s, int n_sms);
 void launch_verify_cfg(const CallArgs& a, int range_mode, int strict_pass, cudaStream_t s, int n_sms,
                        const VerifyConfig& cfg);
+void launch_ties(const CallArgs& a, cudaStream_t s, int n_sms);
 void launch_finalize(const CallArgs& a, void* results, cudaStream_t s);
 void launch_label(const CallArgs& a, float* delta, long long stride, cudaStream_t s);
 void launch_quantize_bf16(const float* in, uint16_t* out, long long n, cudaStream_t s);
@@ -178,11 +202,5 @@ void launch_transpose(const float* in, float* out, int rows, int cols, int batch
 }  // namespace svm
 
 namespace svm {
-// Robot geometry as kernel parameters (FP64 kinematics, FP32 radii).
-struct RobotParams {
-    double d[kDof], a[kDof], ca[kDof], sa[kDof], th0[kDof];
-    double tool_len;
-    float radius[kCaps];
-};
 void launch_prologue_fk(const CallArgs& a, const RobotParams& rp, const DevWeights& w, cudaStream_t s);
 }  // namespace svm

@@ -541,7 +541,10 @@ svm_status svm_train_create(const svm_model_desc* desc, int device, int32_t batc
         t->rp.ca[j] = std::cos(d.dh[j][2]); t->rp.sa[j] = std::sin(d.dh[j][2]); t->rp.th0[j] = d.dh[j][3];
     }
     t->rp.tool_len = d.tool_len;
-    for (int j = 0; j < 7; ++j) t->rp.radius[j] = (float)d.radius[j];
+    for (int j = 0; j < 7; ++j) {
+        t->rp.radius[j] = (float)d.radius[j];
+        t->rp.radius64[j] = d.radius[j];
+    }
     t->W = d.width; t->L = d.n_hidden; t->act = d.act; t->B = batch;
     const long long W = t->W, L = t->L, B = t->B;
     t->off_w1 = 0; t->off_b1 = W * 15; t->off_h = W * 16;

@@ -76,6 +76,36 @@ __device__ int witness_sample(const Capsule* cs, int n_samples, float3 x, float 
     return n_samples - 1;
 }
 
+// Distance of x to capsule j at sample k of motion m in FP64 (Eqs. 1, 3-5),
+// from the prologue's FP64 joint origins and tool axis:
+// t = clamp(((x - a) . e) / |e|^2, 0, 1) (0 for a degenerate axis), then
+// |x - (a + t e)| - r.
+__device__ double capsule_distance64(const CallArgs& A, int m, int k, int j, const double (&x)[3])
+{
+    const double* f = A.fk64 + ((long long)m * (A.N + 1) + k) * 24;
+    double a[3], e[3];
+    for (int i = 0; i < 3; ++i) {
+        a[i] = f[j * 3 + i];
+        e[i] = j < kDof ? f[(j + 1) * 3 + i] - a[i] : f[21 + i];
+    }
+    const double ee = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+    const double we = (x[0] - a[0]) * e[0] + (x[1] - a[1]) * e[1] + (x[2] - a[2]) * e[2];
+    double t = ee > 0.0 ? we / ee : 0.0;
+    t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+    const double dx = x[0] - (a[0] + t * e[0]), dy = x[1] - (a[1] + t * e[1]), dz = x[2] - (a[2] + t * e[2]);
+    return sqrt(dx * dx + dy * dy + dz * dz) - A.rp.radius64[j];
+}
+
+// The same distance in FP32 from the capsule table, with the verifier's
+// roundings (its minimum over all (k, j) is the verifier's distance).
+__device__ __forceinline__ float capsule_distance32(const Capsule& c, float3 x)
+{
+    const float wx = x.x - c.a_r.x, wy = x.y - c.a_r.y, wz = x.z - c.a_r.z;
+    const float t = __saturatef(fmaf(wz, c.e_inv.z, fmaf(wy, c.e_inv.y, wx * c.e_inv.x)) * c.e_inv.w);
+    const float dx = fmaf(-t, c.e_inv.x, wx), dy = fmaf(-t, c.e_inv.y, wy), dz = fmaf(-t, c.e_inv.z, wz);
+    return sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx))) - c.a_r.w;
+}
+
 // ---- packed FP32 pairs: two capsules per instruction
 __device__ __forceinline__ uint64_t pk(float lo, float hi)
 {
@@ -230,7 +260,16 @@ __global__ void __launch_bounds__(VT) verify_kernel(CallArgs A, int strict_pass)
 #pragma unroll
             for (int q = 0; q < kCaps; ++q) d = fminf(d, sqrtf(mn[j][q]) - s_r[q]);
             atomicAdd(&s_nver, 1u);
-            if (fabsf(d - A.margin) < kAmbiguousBand) atomicAdd(&s_namb, 1u);
+            // within the FP32 error band of the margin: the FP64 tie kernel decides
+            // (FP32 verdict only if the tie list is full)
+            if (fabsf(d - A.margin) < kAmbiguousBand) {
+                atomicAdd(&s_namb, 1u);
+                const unsigned slot = atomicAdd(A.tie_count, 1u);
+                if (slot < (unsigned)kTieCap) {
+                    A.tie_list[slot] = TiePair{m, 0, pidx[j]};
+                    continue;
+                }
+            }
             atomicMin(&s_dkey, float_key(d));
             if (d <= A.margin) {
                 const int path_head = (m / A.path_len) * A.path_len;
@@ -268,6 +307,64 @@ __global__ void __launch_bounds__(VT) label_kernel(CallArgs A, float* delta, lon
         float mn[kCaps];
         scan_samples(cs, n_samples, make_float3(x4.x, x4.y, x4.z), mn);
         delta[(long long)m * stride + local] = capsule_min(mn, cs);
+    }
+}
+
+// FP64 decision of the pairs the verifier deferred (FP32 distance within
+// kAmbiguousBand of the margin).  One warp per pair, consecutive pairs on
+// different CTAs (FP64 throughput is per SM).  The lanes first take the FP32
+// distance of every (sample, capsule) item and its minimum lo; FP64 is then
+// spent only on items within 4 kAmbiguousBand of lo.  With an FP32 error below
+// 2 kAmbiguousBand per item, an item above that cut can neither be the FP64
+// minimum nor lie within the margin (the pair's lo is within kAmbiguousBand of
+// it), so the result equals the FP64 check of all items.  Collision iff the
+// FP64 distance <= margin; the pair's distance enters d_min rounded to FP32
+// (rounding is monotone, so a collision never reports d_min above the margin);
+// the witness is the first colliding sample.
+__global__ void __launch_bounds__(256) tie_kernel(CallArgs A)
+{
+    const unsigned n = min(*A.tie_count, (unsigned)kTieCap);
+    const int lane = threadIdx.x & 31;
+    const unsigned n_warps = gridDim.x * (blockDim.x >> 5);
+    const int n_items = (A.N + 1) * kCaps;
+    for (unsigned i = blockIdx.x + gridDim.x * (threadIdx.x >> 5); i < n; i += n_warps) {
+        const TiePair tp = A.tie_list[i];
+        const float4 x4 = __ldg(A.points + tp.p);
+        const float3 xf = make_float3(x4.x, x4.y, x4.z);
+        const double x[3] = {(double)x4.x, (double)x4.y, (double)x4.z};
+        const Capsule* cs = A.caps + (long long)tp.m * n_items;
+        float lo = __int_as_float(0x7f800000);
+        for (int it = lane; it < n_items; it += 32) lo = fminf(lo, capsule_distance32(cs[it], xf));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        const float cut = lo + 4.0f * kAmbiguousBand;
+        const double margin = (double)A.margin;
+        double best = 1.0 / 0.0;
+        int first = 0x7fffffff;
+        for (int it = lane; it < n_items; it += 32) {
+            if (capsule_distance32(cs[it], xf) > cut) continue;
+            const int k = it / kCaps;
+            const double dk = capsule_distance64(A, tp.m, k, it - k * kCaps, x);
+            best = fmin(best, dk);
+            if (dk <= margin && k < first) first = k;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+            first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
+        }
+        if (lane == 0) {
+            MotionState& st = A.st[tp.m];
+            atomicMin(&st.dmin_key, float_key((float)best));
+            if (best <= margin) {
+                if (atomicCAS(&st.collided, 0, 1) == 0) {
+                    st.witness_point = (int)tp.p;
+                    st.witness_step = first;
+                }
+                const int path_head = (tp.m / A.path_len) * A.path_len;
+                if (path_head != tp.m) atomicExch(&A.st[path_head].collided, 1);
+            }
+        }
     }
 }
 
@@ -378,6 +475,11 @@ void launch_label(const CallArgs& a, float* delta, long long stride, cudaStream_
     const size_t smem = (size_t)(a.N + 1) * kCaps * sizeof(Capsule);
     const int gx = 64;
     label_kernel<<<dim3(gx, a.M), VT, smem, s>>>(a, delta, stride);
+}
+
+void launch_ties(const CallArgs& a, cudaStream_t s, int n_sms)
+{
+    if (a.M > 0 && a.tie_count) tie_kernel<<<n_sms, 256, 0, s>>>(a);
 }
 
 void launch_finalize(const CallArgs& a, void* results, cudaStream_t s)

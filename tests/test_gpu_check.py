@@ -297,3 +297,35 @@ def test_batch_over_scenes(svm, robot):
                 assert off[scene[i]] <= r["witness_point"][i] < off[scene[i] + 1] or r["witness_point"][i] == -1
     finally:
         m.close()
+
+
+@pytest.mark.parametrize("prec,gated", [(0, False), (0, True), (1, True)])
+def test_margin_ties_decided_in_fp64(svm, robot, prec, gated):
+    """Pairs whose FP32 distance lies within 4e-6 m of the margin are counted
+    and re-decided in FP64: with the margin set 1e-7 m above and below a point's
+    exact distance (FP32 spacing there is ~7e-9 m), the verdicts follow the FP64
+    distance (Eq. 5, free iff d > margin) and d_min is the FP64 value rounded to
+    FP32.  Gated: every pair is flagged (tau = inf) and reaches the verifier
+    through the network and compaction kernels."""
+    q0, q1 = S.uniform_motions(robot, 4, seed=77, max_step_deg=30)
+    pts = S.cube_cloud(4, seed=77)
+    N = 16
+    delta = oracle.swept_sdf_batch(robot, q0, q1, N, pts)          # (4, 4)
+    m = Model(svm, robot, _layers(), prec=prec)
+    flags = svm.SVM_NO_EARLY_EXIT | (0 if gated else svm.SVM_VERIFY_ALL)
+    try:
+        for k in range(4):
+            one = pts[k:k + 1]
+            d = delta[:, k]
+            for off in (1e-7, -1e-7):
+                eps = np.float32(np.abs(d).min() + off)             # near the closest motion's distance
+                r = _check(svm, m, q0, q1, one, float(eps), N, flags)
+                want = (d <= float(eps)).astype(np.uint8)
+                np.testing.assert_array_equal(r["collision"], want)
+                j = int(np.argmin(np.abs(d)))
+                assert r["n_ambiguous"][j] == 1
+                assert r["d_min"][j] == np.float32(d[j])
+                if want[j]:
+                    assert r["witness_point"][j] == 0 and 0 <= r["witness_step"][j] <= N
+    finally:
+        m.close()
