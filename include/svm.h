@@ -316,7 +316,9 @@ svm_status svm_label_pairs(svm_model* m, const double* q0, const double* q1, int
  *     checked); the other arguments and the results are as in
  *     svm_check_motions.
  *   - A call needs about 4 bytes per motion-point pair plus, per motion,
- *     (steps + 1) * 7 * 32 bytes and 1.3 KB; a call needing more than the
+ *     (steps + 1) * 416 bytes (the FP32 capsule table and the FP64 kinematics
+ *     kept for pairs at the margin) and about 1.3 KB, plus 256 KB for the
+ *     list of pairs at the margin; a call needing more than the
  *     32 MiB is rejected with SVM_E_INVALID and a message naming the sizes
  *     (e.g. 64 motions x 100 000 points fit, 64 x 200 000 do not).
  *   - The first call on a device looks up the scratch array's device address

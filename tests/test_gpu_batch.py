@@ -1,4 +1,4 @@
-"""Config 3: a batch of uneven scenes in one launch sequence.
+"""A batch of 32 uneven bin scenes in one launch sequence.
 
 32 bin scenes with log-uniform cloud sizes in [10k, 500k] points (5.4 M
 points for this seed), 16 motions per scene (512 motions, 86 M pairs), checked with

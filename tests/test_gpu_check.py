@@ -76,8 +76,9 @@ def test_weight_rounding_matches_oracle_bitwise(svm, robot, prec):
         m.close()
 
 
-def test_eval_pairs_fp32_config1(svm, robot):
-    """Config 1 shape: 8 motions x 4096 points, 15 -> 256 x 4 -> 1 ReLU."""
+def test_eval_pairs_fp32_8x4096(svm, robot):
+    """Small uniform workload: 8 motions x 4096 points in the 1.5 m cube,
+    15 -> 256 x 4 -> 1 ReLU."""
     q0, q1 = S.uniform_motions(robot, 8, seed=0)
     pts = S.cube_cloud(4096, seed=0)
     m = Model(svm, robot, _layers())
@@ -137,7 +138,7 @@ def _compare(r, ref, pts_f=None, gate=None, exact_dmin=True):
 
 @pytest.mark.parametrize("strict", [False, True])
 def test_check_balanced_gated(svm, robot, strict):
-    """Balanced variant of config 1 (short motions, both verdicts) with a gate
+    """8 short motions (|q1 - q0| <= 15 deg, both verdicts) x 4096 points with a gate
     in the middle of the prediction range, so some points are not flagged."""
     q0, q1 = S.uniform_motions(robot, 8, seed=15, max_step_deg=15)
     pts = S.cube_cloud(4096, seed=8)
@@ -250,7 +251,7 @@ def test_invalid_arguments_are_rejected(svm, robot):
 
 @pytest.mark.parametrize("seg", [2, 3])
 def test_paths_of_segments(svm, robot, seg):
-    """Config 4 shape (three segments q_start -> q_inVia -> q_outVia -> q_end)
+    """Three-segment paths q_start -> q_inVia -> q_outVia -> q_end
     and the two-segment grasp motions of Sec. V-C: one verdict per path (OR
     over its segments)."""
     paths = S.bin_paths(robot, 8, seed=1)[:, :seg + 1]

@@ -95,7 +95,7 @@ def test_full_size_verdicts_and_outputs(setup, prec):
         svm.svm_destroy_model(h)
 
 
-def test_config4_paths_full_size(setup):
+def test_three_segment_paths_full_size(setup):
     """Three-segment paths at full size: 128 paths q_start -> q_inVia ->
     q_outVia -> q_end (Sec. V-C) against a 300 000-point bin cloud, BF16,
     network trained on path segments (training.path_training_motions), early
@@ -147,7 +147,7 @@ def test_config4_paths_full_size(setup):
         np.testing.assert_array_equal(r["collision"][pick], coll.reshape(-1, 3).max(axis=1))
         assert np.abs(g["d_min"][pick] - dmin.reshape(-1, 3).min(axis=1)).max() <= 1e-5
         pairs = 3 * 128 * len(pts)
-        print(f"config 4: 128 paths x 3 segments x {len(pts)} points = {pairs / 1e6:.0f} M pairs in {ms:.1f} ms "
+        print(f"three-segment paths: 128 paths x 3 segments x {len(pts)} points = {pairs / 1e6:.0f} M pairs in {ms:.1f} ms "
               f"(wall) = {pairs / ms / 1e6:.2f} G pairs/s; tau {tau:.4f} m, flagged "
               f"{r['n_flagged'].sum() / pairs:.2%}; {r['collision'].sum()} paths collide; "
               f"validation MAE {hist['best_val_mae']:.4f} m")

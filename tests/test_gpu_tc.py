@@ -118,7 +118,8 @@ def test_eval_pairs_tc_silu_and_depth(svm, robot, prec):
 
 @pytest.mark.parametrize("prec", [1, 2])
 def test_check_tc_verdicts(svm, robot, prec):
-    """Balanced config-1 variant with a gate inside the prediction range."""
+    """8 short motions (both verdicts) x 4096 cube points, gate inside the
+    prediction range."""
     q0, q1 = S.uniform_motions(robot, 8, seed=15, max_step_deg=15)
     pts = S.cube_cloud(4096, seed=8)
     layers = _layers(bout=0.1)

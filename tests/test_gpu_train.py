@@ -159,8 +159,8 @@ def test_training_lowers_heldout_error_and_resumes(svm, robot):
         svm.svm_train_destroy(t)
 
 
-def test_training_throughput_config5_shape(svm, robot):
-    """Training at the shape of the paper-scale configuration: 15 -> 512 x 6
+def test_training_throughput_512x6_silu(svm, robot):
+    """Training at the large network shape: 15 -> 512 x 6
     SiLU -> 1, batch 65 536, GPU-generated data (2 048 motions x 1 024 points),
     three epochs.  The loss falls; samples/s and the GEMM work rate are
     printed (forward 2 (15 W + L W^2 + W) FLOP per sample, backward twice
