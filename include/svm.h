@@ -61,12 +61,12 @@ typedef enum { SVM_RELU = 0, SVM_SILU = 1 } svm_act;
  * Network (arch SVM_ARCH_MLP): input [x, y, z, q0_1..q0_6, q1_1..q1_6] ->
  * width (act) -> n_hidden x (width -> width, act) -> 1.  The BF16 and FP8
  * tensor-core path needs width 256 and 1 <= n_hidden <= 16; the FP32 path
- * takes width 64, 128, 256 or 512 and 0 <= n_hidden <= 16.
+ * takes width 64, 128, 256, 512 or 1024 and 0 <= n_hidden <= 16.
  * Network (arch SVM_ARCH_BLOCKS, the block architecture of Sec. IV-A):
  * an initial linear layer 15 -> width, n_hidden blocks (linear -> ReLU ->
  * BatchNorm at inference, plus the block input; from the second block on the
  * linear layer also reads the network input, the jump connection), and a
- * final layer [h; input] -> 1.  FP32 path only, ReLU, width 64..512,
+ * final layer [h; input] -> 1.  FP32 path only, ReLU, width 64..1024,
  * 1 <= n_hidden <= 16; BatchNorm is folded into a per-channel scale and
  * shift at load. */
 typedef struct {

@@ -1,7 +1,8 @@
 // mlp_fp32.cu -- the plain FP32 path of the network f(x, q0, q1) (Sec. IV-A)
 // on CUDA cores, fused with the gate and the compaction of flagged pairs.
 //
-// One CTA takes a tile of 64 pairs of one motion.  Layer 1 uses the split
+// One CTA takes a tile of 64 pairs of one motion (at width 1024 in two passes
+// of 32 pairs, so that the activations fit in shared memory).  Layer 1 uses the split
 // W1 [x; q0; q1] + b1 = W1x x + c_m (c_m from the prologue); the hidden
 // layers are register-blocked SIMT GEMMs over activations kept in shared
 // memory, with the transposed weights streamed through a double-buffered
@@ -40,9 +41,12 @@ __global__ void __launch_bounds__(NT, 1) mlp_fp32_kernel(CallArgs A, DevWeights 
     constexpr int CPT = W / 16;          // columns per thread
     constexpr int CG = CPT / 4;          // float4 column groups per thread
     constexpr int HS = W + HPAD;         // activation row stride
+    constexpr int BMP = W > 512 ? 32 : BM;   // pairs per pass
+    constexpr int RPT = BMP / 16;        // rows per thread
+    constexpr int NPASS = BM / BMP;
     extern __shared__ __align__(16) float smem[];
-    float* H = smem;                     // [BM][HS] activations, row-major
-    float* WS = smem + BM * HS;          // [2][KC][W] transposed weight stages
+    float* H = smem;                     // [BMP][HS] activations of the pass, row-major
+    float* WS = smem + BMP * HS;         // [2][KC][W] transposed weight stages
     __shared__ float f_s[BM];
     __shared__ float4 x_s[BM];           // the tile's points (block architecture)
 
@@ -65,187 +69,193 @@ __global__ void __launch_bounds__(NT, 1) mlp_fp32_kernel(CallArgs A, DevWeights 
         for (int i = tid; i < KC * W / 4; i += NT) cp_async16(dst + i * 4, src + i * 4);
         cp_async_commit();
     };
-    if (total_chunks > 0) load_chunk(0, 0);
+    for (int pass = 0; pass < NPASS; ++pass) {
+        const int r0 = pass * BMP;           // first tile row of this pass
+        if (pass > 0) __syncthreads();       // the previous pass is done with H and WS
+        if (total_chunks > 0) load_chunk(0, 0);
 
-    // ---- layer 1: h = act(W1x x + c_m)
-    {
-        float4 xr[4];
-        #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const long long p = p0 + ty * 4 + r;
-            xr[r] = p < pe ? __ldg(A.points + p) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        #pragma unroll
-        for (int c = 0; c < CG; ++c) {
+        // ---- layer 1: h = act(W1x x + c_m)
+        {
+            float4 xr[RPT];
             #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int o = tx * 4 + 64 * c + i;
-                const float w0 = __ldg(Wt.w1x + o * 3 + 0), w1 = __ldg(Wt.w1x + o * 3 + 1),
-                            w2 = __ldg(Wt.w1x + o * 3 + 2), bo = __ldg(cb + o);
-                #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const float z = fmaf(w2, xr[r].z, fmaf(w1, xr[r].y, fmaf(w0, xr[r].x, bo)));
-                    H[(ty * 4 + r) * HS + o] = BLOCK ? z : act_fn(z, A.act);
-                }
+            for (int r = 0; r < RPT; ++r) {
+                const long long p = p0 + r0 + ty * RPT + r;
+                xr[r] = p < pe ? __ldg(A.points + p) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-        }
-        if (BLOCK && tx == 0) {
             #pragma unroll
-            for (int r = 0; r < 4; ++r) x_s[ty * 4 + r] = xr[r];
-        }
-    }
-    // calibration: the largest magnitude entering each hidden layer (valid rows only)
-    auto record_amax = [&](int layer) {
-        float mx = 0.0f;
-        for (int r = 0; r < 4; ++r) {
-            if (p0 + ty * 4 + r >= pe) continue;
-            for (int c = 0; c < CG; ++c)
-                for (int i = 0; i < 4; ++i) mx = fmaxf(mx, fabsf(H[(ty * 4 + r) * HS + tx * 4 + 64 * c + i]));
-        }
-        #pragma unroll
-        for (int s = 16; s > 0; s >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, s));
-        if ((tid & 31) == 0) atomicMax(A.amax + layer, __float_as_uint(mx));
-    };
-    if (A.amax != nullptr && A.L > 0) { __syncthreads(); record_amax(0); }
-
-    float acc[4][CPT];
-    float fpart[4] = {0.f, 0.f, 0.f, 0.f};
-    int g = 0;
-    for (int l = 0; l < A.L; ++l) {
-        #pragma unroll
-        for (int r = 0; r < 4; ++r)
-            #pragma unroll
-            for (int j = 0; j < CPT; ++j) acc[r][j] = 0.f;
-
-        for (int kc = 0; kc < CHUNKS_PER_LAYER; ++kc, ++g) {
-            if (g + 1 < total_chunks) { load_chunk(g + 1, (g + 1) & 1); cp_async_wait<1>(); }
-            else cp_async_wait<0>();
-            __syncthreads();
-            const float* ws = WS + (g & 1) * KC * W;
-            #pragma unroll 2
-            for (int k4 = 0; k4 < KC; k4 += 4) {
-                float4 a4[4];
+            for (int c = 0; c < CG; ++c) {
                 #pragma unroll
-                for (int r = 0; r < 4; ++r)
-                    a4[r] = *reinterpret_cast<const float4*>(H + (ty * 4 + r) * HS + kc * KC + k4);
-                #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    float av[4];
+                for (int i = 0; i < 4; ++i) {
+                    const int o = tx * 4 + 64 * c + i;
+                    const float w0 = __ldg(Wt.w1x + o * 3 + 0), w1 = __ldg(Wt.w1x + o * 3 + 1),
+                                w2 = __ldg(Wt.w1x + o * 3 + 2), bo = __ldg(cb + o);
                     #pragma unroll
-                    for (int r = 0; r < 4; ++r)
-                        av[r] = kk == 0 ? a4[r].x : kk == 1 ? a4[r].y : kk == 2 ? a4[r].z : a4[r].w;
-                    #pragma unroll
-                    for (int c = 0; c < CG; ++c) {
-                        const float4 b = *reinterpret_cast<const float4*>(ws + (k4 + kk) * W + tx * 4 + 64 * c);
-                        #pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            acc[r][c * 4 + 0] = fmaf(av[r], b.x, acc[r][c * 4 + 0]);
-                            acc[r][c * 4 + 1] = fmaf(av[r], b.y, acc[r][c * 4 + 1]);
-                            acc[r][c * 4 + 2] = fmaf(av[r], b.z, acc[r][c * 4 + 2]);
-                            acc[r][c * 4 + 3] = fmaf(av[r], b.w, acc[r][c * 4 + 3]);
-                        }
+                    for (int r = 0; r < RPT; ++r) {
+                        const float z = fmaf(w2, xr[r].z, fmaf(w1, xr[r].y, fmaf(w0, xr[r].x, bo)));
+                        H[(ty * RPT + r) * HS + o] = BLOCK ? z : act_fn(z, A.act);
                     }
                 }
             }
-            __syncthreads();   // stage (g & 1) and H reads done
+            if (BLOCK && tx == 0) {
+                #pragma unroll
+                for (int r = 0; r < RPT; ++r) x_s[r0 + ty * RPT + r] = xr[r];
+            }
         }
+        // calibration: the largest magnitude entering each hidden layer (valid rows only)
+        auto record_amax = [&](int layer) {
+            float mx = 0.0f;
+            for (int r = 0; r < RPT; ++r) {
+                if (p0 + r0 + ty * RPT + r >= pe) continue;
+                for (int c = 0; c < CG; ++c)
+                    for (int i = 0; i < 4; ++i) mx = fmaxf(mx, fabsf(H[(ty * RPT + r) * HS + tx * 4 + 64 * c + i]));
+            }
+            #pragma unroll
+            for (int s = 16; s > 0; s >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, s));
+            if ((tid & 31) == 0) atomicMax(A.amax + layer, __float_as_uint(mx));
+        };
+        if (A.amax != nullptr && A.L > 0) { __syncthreads(); record_amax(0); }
 
-        if constexpr (BLOCK) {
-            // z = W h + Wx x + c_{m,l}; h <- s relu(z) + t + h (own elements, after the GEMM's reads)
-            const float* cl = cb + (long long)(l + 1) * W;
-            const float* wxl = Wt.blk_wx + (long long)l * W * 3;
-            const float* sl = Wt.blk_s + (long long)l * W;
-            const float* tl = Wt.blk_t + (long long)l * W;
-            const bool last = l + 1 == A.L;
+        float acc[RPT][CPT];
+        float fpart[RPT];
+        #pragma unroll
+        for (int r = 0; r < RPT; ++r) fpart[r] = 0.f;
+        int g = 0;
+        for (int l = 0; l < A.L; ++l) {
+            #pragma unroll
+            for (int r = 0; r < RPT; ++r)
+                #pragma unroll
+                for (int j = 0; j < CPT; ++j) acc[r][j] = 0.f;
+
+            for (int kc = 0; kc < CHUNKS_PER_LAYER; ++kc, ++g) {
+                if (g + 1 < total_chunks) { load_chunk(g + 1, (g + 1) & 1); cp_async_wait<1>(); }
+                else cp_async_wait<0>();
+                __syncthreads();
+                const float* ws = WS + (g & 1) * KC * W;
+                #pragma unroll 2
+                for (int k4 = 0; k4 < KC; k4 += 4) {
+                    float4 a4[RPT];
+                    #pragma unroll
+                    for (int r = 0; r < RPT; ++r)
+                        a4[r] = *reinterpret_cast<const float4*>(H + (ty * RPT + r) * HS + kc * KC + k4);
+                    #pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        float av[RPT];
+                        #pragma unroll
+                        for (int r = 0; r < RPT; ++r)
+                            av[r] = kk == 0 ? a4[r].x : kk == 1 ? a4[r].y : kk == 2 ? a4[r].z : a4[r].w;
+                        #pragma unroll
+                        for (int c = 0; c < CG; ++c) {
+                            const float4 b = *reinterpret_cast<const float4*>(ws + (k4 + kk) * W + tx * 4 + 64 * c);
+                            #pragma unroll
+                            for (int r = 0; r < RPT; ++r) {
+                                acc[r][c * 4 + 0] = fmaf(av[r], b.x, acc[r][c * 4 + 0]);
+                                acc[r][c * 4 + 1] = fmaf(av[r], b.y, acc[r][c * 4 + 1]);
+                                acc[r][c * 4 + 2] = fmaf(av[r], b.z, acc[r][c * 4 + 2]);
+                                acc[r][c * 4 + 3] = fmaf(av[r], b.w, acc[r][c * 4 + 3]);
+                            }
+                        }
+                    }
+                }
+                __syncthreads();   // stage (g & 1) and H reads done
+            }
+
+            if constexpr (BLOCK) {
+                // z = W h + Wx x + c_{m,l}; h <- s relu(z) + t + h (own elements, after the GEMM's reads)
+                const float* cl = cb + (long long)(l + 1) * W;
+                const float* wxl = Wt.blk_wx + (long long)l * W * 3;
+                const float* sl = Wt.blk_s + (long long)l * W;
+                const float* tl = Wt.blk_t + (long long)l * W;
+                const bool last = l + 1 == A.L;
+                #pragma unroll
+                for (int c = 0; c < CG; ++c)
+                    #pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int o = tx * 4 + 64 * c + i;
+                        const float w0 = __ldg(wxl + o * 3 + 0), w1 = __ldg(wxl + o * 3 + 1), w2 = __ldg(wxl + o * 3 + 2);
+                        const float co = __ldg(cl + o), so = __ldg(sl + o), to = __ldg(tl + o);
+                        const float wo = last ? __ldg(Wt.wout + o) : 0.0f;
+                        #pragma unroll
+                        for (int r = 0; r < RPT; ++r) {
+                            const float4 x = x_s[r0 + ty * RPT + r];
+                            const float z = fmaf(w2, x.z, fmaf(w1, x.y, fmaf(w0, x.x, acc[r][c * 4 + i] + co)));
+                            float* hp = H + (ty * RPT + r) * HS + o;
+                            const float h = fmaf(so, fmaxf(z, 0.0f), to) + *hp;
+                            if (last) fpart[r] = fmaf(wo, h, fpart[r]);
+                            else *hp = h;
+                        }
+                    }
+                if (!last) __syncthreads();
+                continue;
+            }
+            const float* bl = Wt.bh + (long long)l * W;
+            if (l + 1 < A.L) {
+                // epilogue: bias + activation back into the activation tile
+                #pragma unroll
+                for (int c = 0; c < CG; ++c) {
+                    const int o = tx * 4 + 64 * c;
+                    const float4 bb = __ldg(reinterpret_cast<const float4*>(bl + o));
+                    #pragma unroll
+                    for (int r = 0; r < RPT; ++r) {
+                        float4 h;
+                        h.x = act_fn(acc[r][c * 4 + 0] + bb.x, A.act);
+                        h.y = act_fn(acc[r][c * 4 + 1] + bb.y, A.act);
+                        h.z = act_fn(acc[r][c * 4 + 2] + bb.z, A.act);
+                        h.w = act_fn(acc[r][c * 4 + 3] + bb.w, A.act);
+                        *reinterpret_cast<float4*>(H + (ty * RPT + r) * HS + o) = h;
+                    }
+                }
+                __syncthreads();
+                if (A.amax != nullptr) record_amax(l + 1);
+            } else {
+                // last hidden layer: fold the output layer into the epilogue
+                #pragma unroll
+                for (int c = 0; c < CG; ++c) {
+                    const int o = tx * 4 + 64 * c;
+                    const float4 bb = __ldg(reinterpret_cast<const float4*>(bl + o));
+                    const float4 wo = __ldg(reinterpret_cast<const float4*>(Wt.wout + o));
+                    #pragma unroll
+                    for (int r = 0; r < RPT; ++r) {
+                        fpart[r] = fmaf(wo.x, act_fn(acc[r][c * 4 + 0] + bb.x, A.act), fpart[r]);
+                        fpart[r] = fmaf(wo.y, act_fn(acc[r][c * 4 + 1] + bb.y, A.act), fpart[r]);
+                        fpart[r] = fmaf(wo.z, act_fn(acc[r][c * 4 + 2] + bb.z, A.act), fpart[r]);
+                        fpart[r] = fmaf(wo.w, act_fn(acc[r][c * 4 + 3] + bb.w, A.act), fpart[r]);
+                    }
+                }
+            }
+        }
+        if (A.L == 0) {
+            // no hidden layer: output directly from the layer-1 activations
+            __syncthreads();
             #pragma unroll
             for (int c = 0; c < CG; ++c)
                 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int o = tx * 4 + 64 * c + i;
-                    const float w0 = __ldg(wxl + o * 3 + 0), w1 = __ldg(wxl + o * 3 + 1), w2 = __ldg(wxl + o * 3 + 2);
-                    const float co = __ldg(cl + o), so = __ldg(sl + o), to = __ldg(tl + o);
-                    const float wo = last ? __ldg(Wt.wout + o) : 0.0f;
                     #pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const float4 x = x_s[ty * 4 + r];
-                        const float z = fmaf(w2, x.z, fmaf(w1, x.y, fmaf(w0, x.x, acc[r][c * 4 + i] + co)));
-                        float* hp = H + (ty * 4 + r) * HS + o;
-                        const float h = fmaf(so, fmaxf(z, 0.0f), to) + *hp;
-                        if (last) fpart[r] = fmaf(wo, h, fpart[r]);
-                        else *hp = h;
-                    }
+                    for (int r = 0; r < RPT; ++r) fpart[r] = fmaf(__ldg(Wt.wout + o), H[(ty * RPT + r) * HS + o], fpart[r]);
                 }
-            if (!last) __syncthreads();
-            continue;
         }
-        const float* bl = Wt.bh + (long long)l * W;
-        if (l + 1 < A.L) {
-            // epilogue: bias + activation back into the activation tile
-            #pragma unroll
-            for (int c = 0; c < CG; ++c) {
-                const int o = tx * 4 + 64 * c;
-                const float4 bb = __ldg(reinterpret_cast<const float4*>(bl + o));
-                #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    float4 h;
-                    h.x = act_fn(acc[r][c * 4 + 0] + bb.x, A.act);
-                    h.y = act_fn(acc[r][c * 4 + 1] + bb.y, A.act);
-                    h.z = act_fn(acc[r][c * 4 + 2] + bb.z, A.act);
-                    h.w = act_fn(acc[r][c * 4 + 3] + bb.w, A.act);
-                    *reinterpret_cast<float4*>(H + (ty * 4 + r) * HS + o) = h;
-                }
-            }
-            __syncthreads();
-            if (A.amax != nullptr) record_amax(l + 1);
-        } else {
-            // last hidden layer: fold the output layer into the epilogue
-            #pragma unroll
-            for (int c = 0; c < CG; ++c) {
-                const int o = tx * 4 + 64 * c;
-                const float4 bb = __ldg(reinterpret_cast<const float4*>(bl + o));
-                const float4 wo = __ldg(reinterpret_cast<const float4*>(Wt.wout + o));
-                #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    fpart[r] = fmaf(wo.x, act_fn(acc[r][c * 4 + 0] + bb.x, A.act), fpart[r]);
-                    fpart[r] = fmaf(wo.y, act_fn(acc[r][c * 4 + 1] + bb.y, A.act), fpart[r]);
-                    fpart[r] = fmaf(wo.z, act_fn(acc[r][c * 4 + 2] + bb.z, A.act), fpart[r]);
-                    fpart[r] = fmaf(wo.w, act_fn(acc[r][c * 4 + 3] + bb.w, A.act), fpart[r]);
-                }
-            }
-        }
-    }
-    if (A.L == 0) {
-        // no hidden layer: output directly from the layer-1 activations
-        __syncthreads();
-        #pragma unroll
-        for (int c = 0; c < CG; ++c)
-            #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int o = tx * 4 + 64 * c + i;
-                #pragma unroll
-                for (int r = 0; r < 4; ++r) fpart[r] = fmaf(__ldg(Wt.wout + o), H[(ty * 4 + r) * HS + o], fpart[r]);
-            }
-    }
 
-    // reduce the output dot over the 16 column groups (one half-warp)
-    #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        float v = fpart[r];
-        v += __shfl_xor_sync(0xffffffffu, v, 8);
-        v += __shfl_xor_sync(0xffffffffu, v, 4);
-        v += __shfl_xor_sync(0xffffffffu, v, 2);
-        v += __shfl_xor_sync(0xffffffffu, v, 1);
-        if (tx == 0) {
-            if constexpr (BLOCK) {
-                const float4 x = x_s[ty * 4 + r];
-                const float* ow = Wt.out_wx;
-                f_s[ty * 4 + r] = v + fmaf(__ldg(ow + 2), x.z, fmaf(__ldg(ow + 1), x.y,
-                                                                    fmaf(__ldg(ow), x.x, cb[(long long)(A.L + 1) * W])));
-            } else {
-                f_s[ty * 4 + r] = v + Wt.bout;
+        // reduce the output dot over the 16 column groups (one half-warp)
+        #pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            float v = fpart[r];
+            v += __shfl_xor_sync(0xffffffffu, v, 8);
+            v += __shfl_xor_sync(0xffffffffu, v, 4);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            if (tx == 0) {
+                if constexpr (BLOCK) {
+                    const float4 x = x_s[r0 + ty * RPT + r];
+                    const float* ow = Wt.out_wx;
+                    f_s[r0 + ty * RPT + r] = v + fmaf(__ldg(ow + 2), x.z, fmaf(__ldg(ow + 1), x.y,
+                                                                        fmaf(__ldg(ow), x.x, cb[(long long)(A.L + 1) * W])));
+                } else {
+                    f_s[r0 + ty * RPT + r] = v + Wt.bout;
+                }
             }
         }
-    }
+    }   // passes
     __syncthreads();
 
     // gate + compaction + running minimum (warps 0 and 1: one pair each)
@@ -275,7 +285,8 @@ __global__ void __launch_bounds__(NT, 1) mlp_fp32_kernel(CallArgs A, DevWeights 
 template <int W, int KC, bool BLOCK>
 void launch_wb(const CallArgs& a, const DevWeights& w, int n_tiles, cudaStream_t s)
 {
-    const size_t smem = (size_t)(BM * (W + HPAD) + 2 * KC * W) * sizeof(float);
+    constexpr int BMP = W > 512 ? 32 : BM;
+    const size_t smem = (size_t)(BMP * (W + HPAD) + 2 * KC * W) * sizeof(float);
     int dev = 0;
     cudaGetDevice(&dev);
     static bool configured[64] = {};
@@ -306,6 +317,7 @@ void launch_mlp_fp32(const CallArgs& a, const DevWeights& w, int n_tiles, int bm
         case 128: launch_w<128, 32>(a, w, n_tiles, s); break;
         case 256: launch_w<256, 32>(a, w, n_tiles, s); break;
         case 512: launch_w<512, 16>(a, w, n_tiles, s); break;
+        case 1024: launch_w<1024, 8>(a, w, n_tiles, s); break;
         default: break;
     }
 }

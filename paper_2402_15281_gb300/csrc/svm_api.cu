@@ -234,7 +234,8 @@ svm_status svm_create_model(const svm_model_desc* desc, int device, svm_model** 
     if (d.arch == SVM_ARCH_BLOCKS && (d.prec != SVM_FP32 || d.act != SVM_RELU || d.n_hidden < 1))
         return SVM_E_UNSUPPORTED;
     if (d.prec == SVM_FP32) {
-        if (!(d.width == 64 || d.width == 128 || d.width == 256 || d.width == 512)) return SVM_E_UNSUPPORTED;
+        if (!(d.width == 64 || d.width == 128 || d.width == 256 || d.width == 512 || d.width == 1024))
+            return SVM_E_UNSUPPORTED;
     } else {
         if (d.width != 256 || d.n_hidden < 1) return SVM_E_UNSUPPORTED;
     }

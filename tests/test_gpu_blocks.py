@@ -3,7 +3,8 @@
 against the oracle's unfolded FP64 definition, a gated check against the
 oracle's flags and exact distances, and the inference times at the shapes
 of the paper's inference-time table (one motion x 1 000 / 3 000 / 20 000
-points)."""
+points; 5x512, 11x512 and 11x1024).  At width 1024 the FP32 kernel runs each
+64-pair tile in two passes of 32 pairs, so the parity cases include it."""
 import numpy as np
 import pytest
 
@@ -28,7 +29,7 @@ def _model(svm, robot, P, tau=float("inf")):
     return h
 
 
-@pytest.mark.parametrize("width,nb", [(64, 1), (256, 2), (512, 5), (512, 11)])
+@pytest.mark.parametrize("width,nb", [(64, 1), (256, 2), (512, 5), (512, 11), (1024, 2), (1024, 11)])
 def test_block_network_matches_oracle(svm, width, nb):
     robot = S.make_robot(1)
     P = S.block_weights(width, nb, seed=width + nb)
@@ -49,12 +50,13 @@ def test_block_network_matches_oracle(svm, width, nb):
     assert err <= 2e-5 * scale * np.sqrt(nb)
 
 
-def test_block_network_gated_check(svm):
+@pytest.mark.parametrize("width,nb", [(256, 3), (1024, 2)])
+def test_block_network_gated_check(svm, width, nb):
     """Flags and verdicts of a gated check equal the oracle's: flagged iff
     f <= margin + tau (no f within 1e-3 of the gate), collision iff a flagged
     point's exact distance is <= margin."""
     robot = S.make_robot(1)
-    P = S.block_weights(256, 3, seed=9)
+    P = S.block_weights(width, nb, seed=9)
     q0, q1 = S.uniform_motions(robot, 6, seed=9, max_step_deg=25)
     pts = S.cube_cloud(2000, seed=9)
     f = oracle.block_pairs(P, q0, q1, pts)
@@ -87,7 +89,7 @@ def test_inference_times_at_the_paper_shapes(svm):
     robot = S.make_robot(1)
     q0, q1 = S.uniform_motions(robot, 1, seed=0)
     rows = []
-    for nb, width in ((5, 512), (11, 512)):
+    for nb, width in ((5, 512), (11, 512), (11, 1024)):
         P = S.block_weights(width, nb, seed=1)
         h = _model(svm, robot, P)
         try:

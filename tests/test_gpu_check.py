@@ -93,7 +93,7 @@ def test_eval_pairs_fp32_8x4096(svm, robot):
         m.close()
 
 
-@pytest.mark.parametrize("width,n_hidden,act", [(64, 1, 0), (128, 2, 1), (512, 2, 1), (256, 0, 0)])
+@pytest.mark.parametrize("width,n_hidden,act", [(64, 1, 0), (128, 2, 1), (512, 2, 1), (1024, 2, 1), (256, 0, 0)])
 def test_eval_pairs_fp32_shapes(svm, robot, width, n_hidden, act):
     q0, q1 = S.uniform_motions(robot, 3, seed=1)
     pts = S.cube_cloud(1000, seed=1)         # ragged: 1000 = 15 * 64 + 40
