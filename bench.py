@@ -348,7 +348,8 @@ def run_gpu(args):
                 "verdicts_equal": bool(np.array_equal(r32["collision"], r["collision"]))}
         svm.svm_destroy_model(m32)
 
-    launches_per_step = 6 + (2 if flags & svm.SVM_STRICT else 0)
+    # prologue, network, probe (early exit on), plan + verify, ties, finalize; strict adds plan + verify
+    launches_per_step = 6 + (0 if flags & svm.SVM_NO_EARLY_EXIT else 1) + (2 if flags & svm.SVM_STRICT else 0)
     line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAMES[args.prec], "data": "synthetic",

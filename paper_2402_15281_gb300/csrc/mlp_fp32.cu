@@ -279,6 +279,11 @@ __global__ void __launch_bounds__(NT, 1) mlp_fp32_kernel(CallArgs A, DevWeights 
         #pragma unroll
         for (int s = 16; s > 0; s >>= 1) fm = fminf(fm, __shfl_xor_sync(0xffffffffu, fm, s));
         if (lane == 0 && fm < __int_as_float(0x7f800000)) atomicMin(&A.st[m].dhat_key, float_key(fm));
+        if (fm <= A.gate) {            // the warp's smallest prediction is flagged: a probe candidate
+            const unsigned who = __ballot_sync(0xffffffffu, valid && f == fm);
+            const unsigned pi = __shfl_sync(0xffffffffu, (unsigned)p, __ffs(who) - 1);
+            if (lane == 0) atomicMin(&A.st[m].probe_key, ((unsigned long long)float_key(fm) << 32) | pi);
+        }
     }
 }
 

@@ -537,6 +537,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
             for (int sh = 16; sh > 0; sh >>= 1) fm = fminf(fm, __shfl_xor_sync(0xffffffffu, fm, sh));
             if (lane == 0 && fm < __int_as_float(0x7f800000)) atomicMin(&A.st[pm].dhat_key, float_key(fm));
+            if (fm <= A.gate) {        // the warp's smallest prediction is flagged: a probe candidate
+                const unsigned who = __ballot_sync(0xffffffffu, pvalid && pf == fm);
+                const unsigned pi = __shfl_sync(0xffffffffu, (unsigned)pp, __ffs(who) - 1);
+                if (lane == 0) atomicMin(&A.st[pm].probe_key, ((unsigned long long)float_key(fm) << 32) | pi);
+            }
         };
         auto gate_store = [&]() {
             pstore = false;

@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(128) prologue_kernel(CallArgs A, RobotParams R
         z.witness_point = -1;
         z.witness_step = -1;
         z.n_ambiguous = 0;
+        z.probe_key = ~0ull;
         A.st[m] = z;
         if (m == 0 && A.tie_count) *A.tie_count = 0;
     }

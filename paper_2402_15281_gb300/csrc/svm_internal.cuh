@@ -50,6 +50,8 @@ struct MotionState {
     int witness_point;
     int witness_step;
     unsigned int n_ambiguous;
+    unsigned long long probe_key;   // (float_key(f) << 32) | point index of the motion's
+                                    // smallest flagged prediction; ~0 if none
 };
 
 // Order-preserving float <-> uint32 map: unsigned comparison of keys equals

@@ -368,6 +368,50 @@ __global__ void __launch_bounds__(256) tie_kernel(CallArgs A)
     }
 }
 
+// Early exit first: before the flagged lists are checked, each motion's
+// point of smallest prediction (recorded by the network kernel's gate) is
+// checked alone, one warp per motion.  A collision found there (outside the
+// margin's FP32 band, which is left to the main pass and the tie kernel)
+// marks the motion -- and its path -- as colliding, so the main pass skips
+// every chunk of it; otherwise the point is checked again in the main pass,
+// which counts it.  The order follows Algorithm 1's use of the prediction to
+// choose what to check first, inside one motion.
+__global__ void __launch_bounds__(256) probe_kernel(CallArgs A)
+{
+    const int lane = threadIdx.x & 31;
+    const int m = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (m >= A.M) return;
+    const unsigned long long key = A.st[m].probe_key;
+    const int path_head = (m / A.path_len) * A.path_len;
+    if (key == ~0ull || *(volatile int*)&A.st[path_head].collided) return;
+    const unsigned p = (unsigned)(key & 0xffffffffull);
+    const float4 x4 = __ldg(A.points + p);
+    const float3 xf = make_float3(x4.x, x4.y, x4.z);
+    const int n_items = (A.N + 1) * kCaps;
+    const Capsule* cs = A.caps + (long long)m * n_items;
+    float d = __int_as_float(0x7f800000);
+    int first = 0x7fffffff;
+    for (int it = lane; it < n_items; it += 32) {
+        const float di = capsule_distance32(cs[it], xf);
+        d = fminf(d, di);
+        if (di <= A.margin && it / kCaps < first) first = it / kCaps;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        d = fminf(d, __shfl_xor_sync(0xffffffffu, d, o));
+        first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
+    }
+    if (lane != 0 || !(d <= A.margin) || fabsf(d - A.margin) < kAmbiguousBand) return;
+    MotionState& st = A.st[m];
+    atomicAdd(&st.n_verified, 1u);
+    atomicMin(&st.dmin_key, float_key(d));
+    if (atomicCAS(&st.collided, 0, 1) == 0) {
+        st.witness_point = (int)p;
+        st.witness_step = first;
+    }
+    if (path_head != m) atomicExch(&A.st[path_head].collided, 1);
+}
+
 struct ResultRec {
     uint8_t collision, early_exit;
     uint16_t status;
@@ -443,6 +487,7 @@ void launch_verify_cfg(const CallArgs& a, int range_mode, int strict_pass, cudaS
     if (a.M <= 0) return;
     configure_smem();
     const int ppt = (cfg.points_per_thread == 1 || cfg.points_per_thread == 4) ? cfg.points_per_thread : 2;
+    if (!range_mode && !strict_pass && !(a.flags & 2u)) probe_kernel<<<(a.M + 7) / 8, 256, 0, s>>>(a);
     plan_kernel<<<1, 1024, 0, s>>>(a, range_mode, VT * ppt);
     const size_t smem = (size_t)(a.N + 1) * kCaps * sizeof(Capsule);
     // enough resident CTAs to fill the GPU: shared memory bounds CTAs per SM

@@ -133,7 +133,8 @@ def _compare(r, ref, pts_f=None, gate=None, exact_dmin=True):
     if pts_f is not None:
         near = (np.abs(pts_f - gate) < 1e-4).sum(axis=1)
         assert np.all(np.abs(r["n_flagged"].astype(np.int64) - ref["n_flagged"]) <= near)
-    assert np.all(r["dhat_min"][np.isfinite(ref["dhat_min"])] - ref["dhat_min"][np.isfinite(ref["dhat_min"])] <= F32_TOL)
+    fin = np.isfinite(ref["dhat_min"])
+    assert np.all(np.abs(r["dhat_min"][fin] - ref["dhat_min"][fin]) <= F32_TOL)
 
 
 @pytest.mark.parametrize("strict", [False, True])
@@ -224,6 +225,32 @@ def test_check_edge_cases(svm, robot):
         r = _check(svm, m, q0, q1, pts, 0.0, 16, 0)
         f = oracle.mlp_pairs(m.used, 256, 4, 0, q0, q1, pts)
         assert np.all(r["n_flagged"] == (f <= 0.0).sum(axis=1))
+    finally:
+        m.close()
+
+
+def test_max_steps_and_static_motions(svm, robot):
+    """The largest sample count a call takes (900 steps: a 201 KB capsule
+    table in shared memory) against the oracle; 901 steps are rejected.  A
+    motion with q0 = q1 sweeps nothing: its sampled distance is the static
+    robot's distance at every step count (the oracle pins this bitwise), so
+    its check at 1 and at 900 steps gives the same verdict and d_min."""
+    m = Model(svm, robot, _layers())
+    try:
+        q0, q1 = S.uniform_motions(robot, 3, seed=24, max_step_deg=40)
+        q1[2] = q0[2]                                  # a static motion
+        pts = S.cube_cloud(60, seed=24)                # motion 1 collides, 0 and 2 are free
+        r = _check(svm, m, q0, q1, pts, 0.05, 900, svm.SVM_NO_EARLY_EXIT)
+        ref = oracle.check_motions(m.used, 256, 4, 0, robot, q0, q1, 900, pts, 0.05, np.inf)
+        _compare(r, ref)
+        np.testing.assert_array_equal(r["collision"], [0, 1, 0])
+        assert np.all(r["n_verified"] == 60)
+        r1 = _check(svm, m, q0[2:], q1[2:], pts, 0.05, 1, svm.SVM_NO_EARLY_EXIT)
+        assert r1["collision"][0] == r["collision"][2]
+        assert abs(float(r1["d_min"][0]) - float(r["d_min"][2])) <= DIST_TOL
+        with pytest.raises(svm.SvmError) as e:
+            _check(svm, m, q0, q1, pts, 0.05, 901, 0)
+        assert e.value.status == svm.SVM_E_INVALID
     finally:
         m.close()
 
