@@ -2,7 +2,10 @@
 // on CUDA cores, fused with the gate and the compaction of flagged pairs.
 //
 // One CTA takes a tile of 64 pairs of one motion (at width 1024 in two passes
-// of 32 pairs, so that the activations fit in shared memory).  Layer 1 uses the split
+// of 32 pairs, so that the activations fit in shared memory), or of 16 pairs
+// when all 16-pair tiles of the call fit in one wave on the SMs (a call of few
+// pairs: the time is then the network's depth on one SM, and smaller tiles
+// spread it over more SMs).  Layer 1 uses the split
 // W1 [x; q0; q1] + b1 = W1x x + c_m (c_m from the prologue); the hidden
 // layers are register-blocked SIMT GEMMs over activations kept in shared
 // memory, with the transposed weights streamed through a double-buffered
@@ -18,7 +21,8 @@ namespace svm {
 
 namespace {
 
-constexpr int BM = 64;        // pairs per tile
+constexpr int BM_LARGE = 64;  // pairs per tile
+constexpr int BM_SMALL = 16;  // pairs per tile of small calls
 constexpr int NT = 256;       // threads: 16 row groups x 16 column groups
 constexpr int HPAD = 4;       // row padding of the activation tile (floats)
 
@@ -35,13 +39,13 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // h = s * relu(W h + Wx x + c_{m,l}) + t + h, the jump input's q-part folded
 // into c_{m,l} by the prologue, BatchNorm folded into s and t; final layer
 // w_f . h + w_fx . x + c_{m,f}).
-template <int W, int KC, bool BLOCK>
+template <int W, int KC, bool BLOCK, int BM>
 __global__ void __launch_bounds__(NT, 1) mlp_fp32_kernel(CallArgs A, DevWeights Wt)
 {
     constexpr int CPT = W / 16;          // columns per thread
     constexpr int CG = CPT / 4;          // float4 column groups per thread
     constexpr int HS = W + HPAD;         // activation row stride
-    constexpr int BMP = W > 512 ? 32 : BM;   // pairs per pass
+    constexpr int BMP = (W > 512 && BM > 32) ? 32 : BM;   // pairs per pass
     constexpr int RPT = BMP / 16;        // rows per thread
     constexpr int NPASS = BM / BMP;
     extern __shared__ __align__(16) float smem[];
@@ -258,11 +262,11 @@ __global__ void __launch_bounds__(NT, 1) mlp_fp32_kernel(CallArgs A, DevWeights 
     }   // passes
     __syncthreads();
 
-    // gate + compaction + running minimum (warps 0 and 1: one pair each)
-    if (tid < BM) {
+    // gate + compaction + running minimum (whole warps, one pair per lane)
+    if (tid < (BM + 31) / 32 * 32) {
         const long long p = p0 + tid;
-        const bool valid = p < pe;
-        const float f = f_s[tid];
+        const bool valid = tid < BM && p < pe;
+        const float f = tid < BM ? f_s[tid] : __int_as_float(0x7f800000);
         if (A.f_out != nullptr && valid)
             A.f_out[(long long)m * A.f_stride + (p - A.pbeg[m])] = f;
         const bool flag = valid && f <= A.gate;
@@ -287,42 +291,56 @@ __global__ void __launch_bounds__(NT, 1) mlp_fp32_kernel(CallArgs A, DevWeights 
     }
 }
 
-template <int W, int KC, bool BLOCK>
+template <int W, int KC, bool BLOCK, int BM>
 void launch_wb(const CallArgs& a, const DevWeights& w, int n_tiles, cudaStream_t s)
 {
-    constexpr int BMP = W > 512 ? 32 : BM;
+    constexpr int BMP = (W > 512 && BM > 32) ? 32 : BM;
     const size_t smem = (size_t)(BMP * (W + HPAD) + 2 * KC * W) * sizeof(float);
     int dev = 0;
     cudaGetDevice(&dev);
     static bool configured[64] = {};
     if (dev >= 0 && dev < 64 && !configured[dev]) {
-        cudaFuncSetAttribute(mlp_fp32_kernel<W, KC, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(mlp_fp32_kernel<W, KC, BLOCK, BM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
         configured[dev] = true;
     }
-    mlp_fp32_kernel<W, KC, BLOCK><<<n_tiles, NT, smem, s>>>(a, w);
+    mlp_fp32_kernel<W, KC, BLOCK, BM><<<n_tiles, NT, smem, s>>>(a, w);
 }
 
 template <int W, int KC>
-void launch_w(const CallArgs& a, const DevWeights& w, int n_tiles, cudaStream_t s)
+void launch_w(const CallArgs& a, const DevWeights& w, int n_tiles, int bm, cudaStream_t s)
 {
-    if (a.arch == 1) launch_wb<W, KC, true>(a, w, n_tiles, s);
-    else launch_wb<W, KC, false>(a, w, n_tiles, s);
+    if (bm == BM_SMALL) {
+        if (a.arch == 1) launch_wb<W, KC, true, BM_SMALL>(a, w, n_tiles, s);
+        else launch_wb<W, KC, false, BM_SMALL>(a, w, n_tiles, s);
+    } else {
+        if (a.arch == 1) launch_wb<W, KC, true, BM_LARGE>(a, w, n_tiles, s);
+        else launch_wb<W, KC, false, BM_LARGE>(a, w, n_tiles, s);
+    }
 }
 
 }  // namespace
 
-int mlp_fp32_tile_rows() { return BM; }
+// A 16-pair tile takes 0.5-0.65 of a 64-pair tile's time (measured), so 16-pair
+// tiles win only when they all run in one wave.
+int mlp_fp32_tile_rows(long long tiles_small, int n_sms)
+{
+    return tiles_small <= (long long)n_sms ? BM_SMALL : BM_LARGE;
+}
+
+int mlp_fp32_small_tile_rows() { return BM_SMALL; }
+
+int mlp_fp32_tile_rows() { return BM_LARGE; }
 
 void launch_mlp_fp32(const CallArgs& a, const DevWeights& w, int n_tiles, int bm, cudaStream_t s)
 {
-    (void)bm;
     if (n_tiles <= 0) return;
     switch (a.W) {
-        case 64: launch_w<64, 32>(a, w, n_tiles, s); break;
-        case 128: launch_w<128, 32>(a, w, n_tiles, s); break;
-        case 256: launch_w<256, 32>(a, w, n_tiles, s); break;
-        case 512: launch_w<512, 16>(a, w, n_tiles, s); break;
-        case 1024: launch_w<1024, 8>(a, w, n_tiles, s); break;
+        case 64: launch_w<64, 32>(a, w, n_tiles, bm, s); break;
+        case 128: launch_w<128, 32>(a, w, n_tiles, bm, s); break;
+        case 256: launch_w<256, 32>(a, w, n_tiles, bm, s); break;
+        case 512: launch_w<512, 16>(a, w, n_tiles, bm, s); break;
+        case 1024: launch_w<1024, 8>(a, w, n_tiles, bm, s); break;
         default: break;
     }
 }

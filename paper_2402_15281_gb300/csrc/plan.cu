@@ -161,6 +161,15 @@ svm_status svm_plan_create(svm_model* m, const double* q0, const double* q1, int
     p->flags = flags;
     p->margin = margin;
     p->bm = m->desc.prec != SVM_FP32 ? tc_tile_rows() : mlp_fp32_tile_rows();
+    if (m->desc.prec == SVM_FP32) {
+        const long long sb = mlp_fp32_small_tile_rows();
+        long long small = 0;
+        for (int i = 0; i < M; ++i) {
+            const long long n = scene_offsets[motion_scene[i] + 1] - scene_offsets[motion_scene[i]];
+            small += (n + sb - 1) / sb;
+        }
+        p->bm = mlp_fp32_tile_rows(small, m->n_sms);
+    }
     std::vector<long long> pbeg(M), pend(M), poff(M + 1);
     std::vector<int> toff(M + 1);
     toff[0] = 0;

@@ -552,14 +552,22 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
     pl.M = M;
     pl.N = steps;
     pl.bm = tc ? tc_tile_rows() : mlp_fp32_tile_rows();
-    pl.P_total = 0;
-    pl.n_tiles = 0;
-    for (int i = 0; i < M; ++i) {
-        const int s = motion_scene ? motion_scene[i] : 0;
-        const long long n = scene_off[s + 1] - scene_off[s];
-        pl.P_total += n;
-        pl.n_tiles += (int)((n + pl.bm - 1) / pl.bm);
+    auto count_tiles = [&]() {
+        pl.P_total = 0;
+        pl.n_tiles = 0;
+        for (int i = 0; i < M; ++i) {
+            const int s = motion_scene ? motion_scene[i] : 0;
+            const long long n = scene_off[s + 1] - scene_off[s];
+            pl.P_total += n;
+            pl.n_tiles += (int)((n + pl.bm - 1) / pl.bm);
+        }
+    };
+    if (!tc) {
+        pl.bm = mlp_fp32_small_tile_rows();
+        count_tiles();
+        pl.bm = mlp_fp32_tile_rows(pl.n_tiles, m->n_sms);
     }
+    count_tiles();
     size_t at = 0;
     pl.o_q0 = at; at = align256(at + (size_t)M * 6 * 8);
     pl.o_q1 = at; at = align256(at + (size_t)M * 6 * 8);
@@ -1057,7 +1065,11 @@ extern "C" svm_status svm_check_motions_noalloc(svm_model* m, const double* q0_d
     if (M % path_len_of(flags) != 0) return fail(m, SVM_E_INVALID, "n_motions is not a multiple of the path length");
 
     const bool tc = d.prec != SVM_FP32;
-    const int bm = tc ? tc_tile_rows() : mlp_fp32_tile_rows();
+    int bm = tc ? tc_tile_rows() : mlp_fp32_tile_rows();
+    if (!tc) {
+        const long long sb = mlp_fp32_small_tile_rows();
+        bm = mlp_fp32_tile_rows((long long)M * ((n_points + sb - 1) / sb), m->n_sms);
+    }
     const long long tiles_per = (n_points + bm - 1) / bm;
     if ((long long)M * tiles_per > 0x7fffffffLL || n_points > (int64_t)0xffffffffLL)
         return fail(m, SVM_E_INVALID, "too many tiles");

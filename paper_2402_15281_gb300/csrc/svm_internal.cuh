@@ -183,7 +183,11 @@ __device__ __forceinline__ float capsule_min(const float (&mn)[kCaps], const Cap
 // ---------------------------------------------------------------- launches
 void launch_prologue(const CallArgs& a, const DevWeights& w, cudaStream_t s);
 void launch_mlp_fp32(const CallArgs& a, const DevWeights& w, int n_tiles, int bm, cudaStream_t s);
-int  mlp_fp32_tile_rows();
+int  mlp_fp32_tile_rows();                                  // pairs per tile (64)
+// Pairs per tile of the FP32 path for a call that has `tiles_small` tiles of
+// 16 pairs: 16 when those fit in one wave on n_sms SMs, else 64.
+int  mlp_fp32_tile_rows(long long tiles_small, int n_sms);
+int  mlp_fp32_small_tile_rows();                            // 16
 // Verifier launch shape: points each thread checks per chunk (1, 2 or 4) and
 // resident CTAs per SM (0 = as many as shared memory allows, at most 8).
 struct VerifyConfig {
