@@ -153,6 +153,27 @@ def _dev(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _points(t):
+    """A point cloud: contiguous (P, 4) float32 CUDA tensor."""
+    if t.dtype != _torch().float32 or t.dim() != 2 or t.shape[1] != 4:
+        raise ValueError("points must be a (P, 4) float32 CUDA tensor")
+    return _dev(t)
+
+
+def _out(t, nbytes, what):
+    """An output buffer the call writes `nbytes` into (checked before the
+    launch: a short buffer would be overrun on the device)."""
+    have = t.numel() * t.element_size()
+    if have < nbytes:
+        raise ValueError(f"{what} holds {have} bytes; the call writes {nbytes}")
+    return _dev(t)
+
+
+def _n_records(n_motions, flags):
+    """Result records a check call writes: one per motion, or per path."""
+    return n_motions // 3 if flags & SVM_PATHS3 else n_motions // 2 if flags & SVM_PATHS2 else n_motions
+
+
 # ------------------------------------------------------------------ entry points
 
 SVM_ARCH_MLP, SVM_ARCH_BLOCKS = 0, 1
@@ -261,8 +282,9 @@ def svm_check_motions(model, q0, q1, points_dev, margin, steps, flags, results_d
     q0, p0 = _host_f64(q0)
     q1, p1 = _host_f64(q1)
     _check("svm_check_motions", lib().svm_check_motions(
-        model, p0, p1, q0.shape[0], _dev(points_dev), points_dev.shape[0], float(margin), int(steps),
-        int(flags), _dev(results_dev), _stream(stream)), model)
+        model, p0, p1, q0.shape[0], _points(points_dev), points_dev.shape[0], float(margin), int(steps),
+        int(flags), _out(results_dev, 32 * _n_records(q0.shape[0], int(flags)), "results"), _stream(stream)),
+        model)
 
 
 def svm_check_motions_noalloc(model, q0_dev, q1_dev, points_dev, margin, steps, flags, results_dev, stream=None):
@@ -272,8 +294,9 @@ def svm_check_motions_noalloc(model, q0_dev, q1_dev, points_dev, margin, steps, 
     if q0_dev.shape != q1_dev.shape or q0_dev.shape[-1] != 6:
         raise ValueError("q0_dev and q1_dev must both be (M, 6)")
     _check("svm_check_motions_noalloc", lib().svm_check_motions_noalloc(
-        model, _dev(q0_dev), _dev(q1_dev), q0_dev.shape[0], _dev(points_dev), points_dev.shape[0],
-        float(margin), int(steps), int(flags), _dev(results_dev), _stream(stream)), model)
+        model, _dev(q0_dev), _dev(q1_dev), q0_dev.shape[0], _points(points_dev), points_dev.shape[0],
+        float(margin), int(steps), int(flags), _out(results_dev, 32 * _n_records(q0_dev.shape[0], int(flags)),
+                                                    "results"), _stream(stream)), model)
 
 
 def _torch():
@@ -295,7 +318,7 @@ def svm_search_free_motion(model, q0, q1, points_dev, margin, steps, wave=1, fla
     q1, p1 = _host_f64(q1)
     out = svm_search_result()
     _check("svm_search_free_motion", lib().svm_search_free_motion(
-        model, p0, p1, q0.shape[0], _dev(points_dev), points_dev.shape[0], float(margin), int(steps),
+        model, p0, p1, q0.shape[0], _points(points_dev), points_dev.shape[0], float(margin), int(steps),
         int(wave), int(flags), C.byref(out), _stream(stream)), model)
     return {f: getattr(out, f) for f, _ in svm_search_result._fields_}
 
@@ -307,9 +330,9 @@ def svm_check_batch(model, q0, q1, motion_scene, points_dev, scene_offsets, marg
     ms = np.ascontiguousarray(motion_scene, dtype=np.int32)
     so = np.ascontiguousarray(scene_offsets, dtype=np.int64)
     _check("svm_check_batch", lib().svm_check_batch(
-        model, p0, p1, q0.shape[0], ms.ctypes.data_as(C.c_void_p), _dev(points_dev),
+        model, p0, p1, q0.shape[0], ms.ctypes.data_as(C.c_void_p), _points(points_dev),
         so.ctypes.data_as(C.c_void_p), so.shape[0] - 1, float(margin), int(steps), int(flags),
-        _dev(results_dev), _stream(stream)), model)
+        _out(results_dev, 32 * _n_records(q0.shape[0], int(flags)), "results"), _stream(stream)), model)
 
 
 class Plan:
@@ -321,17 +344,21 @@ class Plan:
         ms = np.ascontiguousarray(motion_scene, dtype=np.int32)
         so = np.ascontiguousarray(scene_offsets, dtype=np.int64)
         self.model = model
+        self.n_records = _n_records(q0.shape[0], int(flags))
         self.h = C.c_void_p()
         _check("svm_plan_create", lib().svm_plan_create(
             model, p0, p1, q0.shape[0], ms.ctypes.data_as(C.c_void_p), so.ctypes.data_as(C.c_void_p),
             so.shape[0] - 1, float(margin), int(steps), int(flags), C.byref(self.h)), model)
 
+    def _bufs(self, points_dev, results_dev):
+        return _points(points_dev), _out(results_dev, 32 * self.n_records, "results")
+
     def launch(self, points_dev, results_dev, stream=None):
-        _check("svm_plan_launch", lib().svm_plan_launch(self.h, _dev(points_dev), _dev(results_dev),
+        _check("svm_plan_launch", lib().svm_plan_launch(self.h, *self._bufs(points_dev, results_dev),
                                                         _stream(stream)), self.model)
 
     def graph_launch(self, points_dev, results_dev, stream):
-        _check("svm_plan_graph_launch", lib().svm_plan_graph_launch(self.h, _dev(points_dev), _dev(results_dev),
+        _check("svm_plan_graph_launch", lib().svm_plan_graph_launch(self.h, *self._bufs(points_dev, results_dev),
                                                                     _stream(stream)), self.model)
 
     def set_verify_shape(self, points_per_thread, ctas_per_sm):
@@ -340,7 +367,7 @@ class Plan:
 
     def autotune(self, points_dev, results_dev, stream=None) -> str:
         buf = C.create_string_buffer(4096)
-        _check("svm_plan_autotune", lib().svm_plan_autotune(self.h, _dev(points_dev), _dev(results_dev),
+        _check("svm_plan_autotune", lib().svm_plan_autotune(self.h, *self._bufs(points_dev, results_dev),
                                                             _stream(stream), buf, 4096), self.model)
         return buf.value.decode()
 
@@ -353,16 +380,17 @@ class Plan:
 def svm_eval_pairs(model, q0, q1, points_dev, f_dev, stream=None):
     q0, p0 = _host_f64(q0)
     q1, p1 = _host_f64(q1)
-    _check("svm_eval_pairs", lib().svm_eval_pairs(model, p0, p1, q0.shape[0], _dev(points_dev),
-                                                  points_dev.shape[0], _dev(f_dev), _stream(stream)), model)
+    _check("svm_eval_pairs", lib().svm_eval_pairs(
+        model, p0, p1, q0.shape[0], _points(points_dev), points_dev.shape[0],
+        _out(f_dev, 4 * q0.shape[0] * points_dev.shape[0], "f"), _stream(stream)), model)
 
 
 def svm_label_pairs(model, q0, q1, points_dev, steps, delta_dev, stream=None):
     q0, p0 = _host_f64(q0)
     q1, p1 = _host_f64(q1)
-    _check("svm_label_pairs", lib().svm_label_pairs(model, p0, p1, q0.shape[0], _dev(points_dev),
-                                                    points_dev.shape[0], int(steps), _dev(delta_dev),
-                                                    _stream(stream)), model)
+    _check("svm_label_pairs", lib().svm_label_pairs(
+        model, p0, p1, q0.shape[0], _points(points_dev), points_dev.shape[0], int(steps),
+        _out(delta_dev, 4 * q0.shape[0] * points_dev.shape[0], "delta"), _stream(stream)), model)
 
 
 def svm_profile_enable(model, on=True):

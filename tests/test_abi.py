@@ -63,3 +63,21 @@ def test_blob_layout():
     o, i = struct.unpack("<II", blob[28:36])
     assert (o, i) == (16, 15)
     np.testing.assert_array_equal(np.frombuffer(blob[36:36 + 4 * 240], "<f4").reshape(16, 15), layers[0][0])
+
+
+def test_binding_checks_buffers_before_the_call():
+    """The binding refuses, before any library call, point buffers that are
+    not (P, 4) float32 and output buffers shorter than what the call writes
+    (one 32-byte record per motion or per path; M x P floats of f)."""
+    import torch
+    import paper_2402_15281_gb300 as svm
+    with pytest.raises(ValueError, match="float32"):
+        svm._points(torch.zeros((10, 4), dtype=torch.float64))
+    with pytest.raises(ValueError, match="float32"):
+        svm._points(torch.zeros((10, 3), dtype=torch.float32))
+    with pytest.raises(ValueError, match="CUDA"):               # right shape, but host memory
+        svm._points(torch.zeros((10, 4), dtype=torch.float32))
+    with pytest.raises(ValueError, match="writes 256"):
+        svm._out(torch.zeros((7, 32), dtype=torch.uint8), 32 * 8, "results")
+    assert svm._n_records(9, svm.SVM_PATHS3) == 3 and svm._n_records(8, svm.SVM_PATHS2) == 4
+    assert svm._n_records(5, svm.SVM_STRICT | svm.SVM_NO_EARLY_EXIT) == 5
