@@ -28,6 +28,14 @@
  *     aligned.  Joint angles are radians, 6 per configuration, row-major.
  *   - A model is not thread safe: calls on one model must not overlap in
  *     host threads; calls on one model are serialised in stream order.
+ *   - Profiling: the check, evaluation, labelling, search, plan-launch and
+ *     training-epoch calls each push an NVTX range named after the call; a
+ *     check call also names its phases (prologue, network, verify, finalize),
+ *     so that `ncu --nvtx` can select kernels by call and phase.
+ *   - The environment variable SVM_WORKSPACE_LIMIT (decimal bytes), when set,
+ *     caps the device workspace a model allocates for its check, evaluation
+ *     and labelling calls: a call that needs more returns SVM_E_OOM before it
+ *     allocates anything (this is how the out-of-memory path is tested).
  */
 #ifndef SVM_H
 #define SVM_H

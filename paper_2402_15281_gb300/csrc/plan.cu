@@ -241,6 +241,7 @@ svm_status svm_plan_destroy(svm_plan* p)
 
 svm_status svm_plan_launch(svm_plan* p, const float* points_dev, svm_result* results_dev, void* stream)
 {
+    const Range call_range("svm_plan_launch");
     if (!p || !results_dev) return SVM_E_INVALID;
     if (p->P_total > 0 && (!points_dev || reinterpret_cast<uintptr_t>(points_dev) % 16))
         return pfail(p->m, SVM_E_INVALID, "points missing or not 16-byte aligned");
@@ -250,6 +251,7 @@ svm_status svm_plan_launch(svm_plan* p, const float* points_dev, svm_result* res
 
 svm_status svm_plan_graph_launch(svm_plan* p, const float* points_dev, svm_result* results_dev, void* stream)
 {
+    const Range call_range("svm_plan_graph_launch");
     if (!p || !results_dev) return SVM_E_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread)

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -39,6 +40,17 @@ svm_status fail(svm_model* m, svm_status s, const std::string& msg)
         if (e_ != cudaSuccess)                                                           \
             return fail(m, SVM_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
+
+// SVM_WORKSPACE_LIMIT (decimal bytes), when set, caps the device workspace a
+// model may allocate for its calls; 0 when unset or malformed.
+size_t workspace_limit()
+{
+    const char* s = std::getenv("SVM_WORKSPACE_LIMIT");
+    if (!s || !*s) return 0;
+    char* end = nullptr;
+    const unsigned long long v = std::strtoull(s, &end, 10);
+    return (end && *end == 0) ? (size_t)v : 0;
+}
 
 struct DeviceGuard {
     int prev = -1;
@@ -515,6 +527,7 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
                     int32_t n_scenes, float margin, int32_t steps, uint32_t flags, void* results_dev,
                     float* out_dev, cudaStream_t stream)
 {
+    const Range call_range(mode == kCheck ? "svm_check" : mode == kEval ? "svm_eval_pairs" : "svm_label_pairs");
     const svm_model_desc& d = m->desc;
     if (M < 0) return fail(m, SVM_E_INVALID, "n_motions < 0");
     if (M > 0 && (!q0 || !q1)) return fail(m, SVM_E_INVALID, "null q0/q1");
@@ -589,11 +602,17 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
     DeviceGuard g(m->device);
     // grow the workspace and staging buffer (not inside a stream capture)
     if (pl.total > m->ws_bytes) {
+        const size_t limit = workspace_limit();
+        if (limit && pl.total > limit)
+            return fail(m, SVM_E_OOM, "the call needs " + std::to_string(pl.total) +
+                                          " bytes of workspace, more than SVM_WORKSPACE_LIMIT = " +
+                                          std::to_string(limit));
         CK(cudaDeviceSynchronize());
         if (m->ws) cudaFree(m->ws);
         m->ws = nullptr;
         m->ws_bytes = 0;
-        const size_t want = pl.total + pl.total / 4;
+        size_t want = pl.total + pl.total / 4;
+        if (limit && want > limit) want = limit;
         if (cudaMalloc(&m->ws, want) != cudaSuccess) {
             cudaGetLastError();
             return fail(m, SVM_E_OOM, "workspace allocation failed");
@@ -673,19 +692,26 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
     a.tie_list = reinterpret_cast<TiePair*>(ws + pl.o_tie + 256);
     CK(cudaMemsetAsync(a.dev_err, 0, sizeof(unsigned int), stream));
 
-    launch_prologue_fk(a, m->rp, m->dw, stream);
+    {
+        const Range r("prologue");
+        launch_prologue_fk(a, m->rp, m->dw, stream);
+    }
     if (prof) CK(cudaEventRecord(m->ev[1], stream));
     if (mode == kLabel) {
+        const Range r("label");
         launch_label(a, out_dev, a.f_stride, stream);
         CK(cudaGetLastError());
         return SVM_OK;
     }
     if (!(flags & SVM_VERIFY_ALL)) {
-        if (tc) {
-            const int st = tc_launch(m->tc, a, m->dw, pl.n_tiles, tc_ws, m->n_sms, stream);
-            if (st != 0) return fail(m, SVM_E_CUDA, "tensor-core launch failed");
-        } else {
-            launch_mlp_fp32(a, m->dw, pl.n_tiles, pl.bm, stream);
+        {
+            const Range r("network");
+            if (tc) {
+                const int st = tc_launch(m->tc, a, m->dw, pl.n_tiles, tc_ws, m->n_sms, stream);
+                if (st != 0) return fail(m, SVM_E_CUDA, "tensor-core launch failed");
+            } else {
+                launch_mlp_fp32(a, m->dw, pl.n_tiles, pl.bm, stream);
+            }
         }
         if (mode == kEval) {
             CK(cudaGetLastError());
@@ -693,17 +719,22 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
         }
         if (prof) CK(cudaEventRecord(m->ev[2], stream));
         if (!(flags & SVM_PREDICT_ONLY)) {
+            const Range r("verify");
             launch_verify(a, 0, 0, stream, m->n_sms);
             if (flags & SVM_STRICT) launch_verify(a, 1, 1, stream, m->n_sms);
             launch_ties(a, stream, m->n_sms);
         }
     } else {
         if (prof) CK(cudaEventRecord(m->ev[2], stream));
+        const Range r("verify");
         launch_verify(a, 1, 0, stream, m->n_sms);
         launch_ties(a, stream, m->n_sms);
     }
     if (prof) CK(cudaEventRecord(m->ev[3], stream));
-    launch_finalize(a, results_dev, stream);
+    {
+        const Range r("finalize");
+        launch_finalize(a, results_dev, stream);
+    }
     if (prof) {
         CK(cudaEventRecord(m->ev[4], stream));
         m->prof_valid = true;
@@ -859,6 +890,7 @@ svm_status svm_search_free_motion(svm_model* m, const double* q0, const double* 
                                   const float* points_dev, int64_t n_points, float margin, int32_t steps,
                                   int32_t wave, uint32_t flags, svm_search_result* out, void* stream_)
 {
+    const Range call_range("svm_search_free_motion");
     if (!m || !out) return SVM_E_INVALID;
     if (n_motions < 0 || n_points < 0) return fail(m, SVM_E_INVALID, "negative count");
     if (wave < 1) return fail(m, SVM_E_INVALID, "wave must be >= 1");

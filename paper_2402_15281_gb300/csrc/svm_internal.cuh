@@ -14,8 +14,18 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace svm {
+
+// A named NVTX range on the host timeline for the life of a scope: profilers
+// (ncu --nvtx) attribute the kernels launched inside it to the call or phase.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 constexpr int kDof = 6;
 constexpr int kCaps = 7;

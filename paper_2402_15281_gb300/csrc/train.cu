@@ -831,6 +831,7 @@ svm_status svm_train_adam(svm_trainer* t, float lr)
 svm_status svm_train_epoch(svm_trainer* t, int64_t sample_begin, int64_t sample_end, float lr, uint64_t shuffle_seed,
                            float* mean_loss)
 {
+    const Range call_range("svm_train_epoch");
     if (!t || !(lr > 0)) return SVM_E_INVALID;
     const long long S = sample_end - sample_begin;
     if (sample_begin < 0 || sample_end > t->n_samples || S < t->B) return tfail(t, SVM_E_INVALID, "bad sample range");

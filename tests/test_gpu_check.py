@@ -255,6 +255,26 @@ def test_max_steps_and_static_motions(svm, robot):
         m.close()
 
 
+def test_workspace_limit_reports_out_of_memory(svm, robot, monkeypatch):
+    """The out-of-memory path without exhausting the GPU: with
+    SVM_WORKSPACE_LIMIT below what a call needs, the call returns
+    SVM_E_OOM before it allocates, and the model stays usable -- the same call
+    without the limit gives the oracle's verdicts."""
+    m = Model(svm, robot, _layers())
+    try:
+        q0, q1 = S.uniform_motions(robot, 3, seed=4, max_step_deg=10)
+        pts = S.cube_cloud(500, seed=4)
+        monkeypatch.setenv("SVM_WORKSPACE_LIMIT", "65536")
+        with pytest.raises(svm.SvmError) as e:
+            _check(svm, m, q0, q1, pts, 0.05, 16, svm.SVM_NO_EARLY_EXIT)
+        assert e.value.status == svm.SVM_E_OOM and "SVM_WORKSPACE_LIMIT" in str(e.value)
+        monkeypatch.delenv("SVM_WORKSPACE_LIMIT")
+        r = _check(svm, m, q0, q1, pts, 0.05, 16, svm.SVM_NO_EARLY_EXIT)
+        _compare(r, oracle.check_motions(m.used, 256, 4, 0, robot, q0, q1, 16, pts, 0.05, np.inf))
+    finally:
+        m.close()
+
+
 def test_invalid_arguments_are_rejected(svm, robot):
     m = Model(svm, robot, _layers())
     try:
