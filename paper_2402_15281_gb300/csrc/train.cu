@@ -316,14 +316,7 @@ __global__ void __launch_bounds__(256) colsum_kernel(const __nv_bfloat16* GT, lo
 {
     const int n = blockIdx.x;
     float s = 0.0f;
-    // 16-byte loads of 8 values (B is a multiple of 256, rows are 16-byte aligned)
-    const uint4* row = reinterpret_cast<const uint4*>(GT + (long long)n * B);
-    for (long long b = threadIdx.x; b < B / 8; b += blockDim.x) {
-        const uint4 w = row[b];
-        const uint32_t u[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) s += __uint_as_float(u[k] << 16) + __uint_as_float(u[k] & 0xFFFF0000u);
-    }
+    for (long long b = threadIdx.x; b < B; b += blockDim.x) s += __bfloat162float(GT[(long long)n * B + b]);
     __shared__ float red[8];
 #pragma unroll
     for (int sh = 16; sh > 0; sh >>= 1) s += __shfl_xor_sync(0xffffffffu, s, sh);
@@ -333,30 +326,6 @@ __global__ void __launch_bounds__(256) colsum_kernel(const __nv_bfloat16* GT, lo
         float t = 0.0f;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
         db[n] += t;
-    }
-}
-
-// dst[j] += sum_{p < P} part[p * n + j] for few columns and many partials:
-// a block of 32 x 32 threads takes 32 columns; thread (x, y) sums the rows
-// p = y, y + 32, ... of column x in that order, and the 32 row sums of a
-// column are then added in the order y = 0..31 -- a fixed order, so the
-// result does not depend on scheduling.
-__global__ void __launch_bounds__(1024) reduce_rows_kernel(const float* part, int P, long long n, float* dst)
-{
-    __shared__ float acc[32][33];
-    const int x = threadIdx.x & 31, y = threadIdx.x >> 5;
-    const long long j = (long long)blockIdx.x * 32 + x;
-    float s = 0.0f;
-    if (j < n) {
-#pragma unroll 8
-        for (int p = y; p < P; p += 32) s += part[(long long)p * n + j];
-    }
-    acc[y][x] = s;
-    __syncthreads();
-    if (y == 0 && j < n) {
-        float t = 0.0f;
-        for (int r = 0; r < 32; ++r) t += acc[r][x];
-        dst[j] += t;
     }
 }
 
@@ -517,9 +486,9 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
     }
     if (t->act == 0) head_kernel<0><<<B / 32, 128, 0, s>>>(a, t->H[L], t->Z[L], t->G[L], t->GT[L], grad ? 0 : 1);
     else head_kernel<1><<<B / 32, 128, 0, s>>>(a, t->H[L], t->Z[L], t->G[L], t->GT[L], grad ? 0 : 1);
-    reduce_rows_kernel<<<1, 1024, 0, s>>>(t->loss, B / 32, 1, t->loss_sum);
+    reduce_kernel<<<1, 1, 0, s>>>(t->loss, B / 32, 1, t->loss_sum);
     if (!grad) return SVM_OK;
-    reduce_rows_kernel<<<(W + 1 + 31) / 32, 1024, 0, s>>>(t->part, B / 32, W + 1, t->Gr + t->off_out);
+    reduce_kernel<<<grid_for(W + 1), 256, 0, s>>>(t->part, B / 32, W + 1, t->Gr + t->off_out);
     for (int l = L; l >= 1; --l) {
         const long long woff = t->off_h + (long long)(l - 1) * ((long long)W * W + W);
         GemmArgs g{};
@@ -536,7 +505,7 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
         launch_train_gemm(kEpiDgrad, t->act, t->mapG[l].b, t->mapWT[l - 1].b, d, t->n_sms, s);
     }
     layer1_bwd_kernel<<<B / 256, 256, 0, s>>>(a, t->G[0]);
-    reduce_rows_kernel<<<(W * 16 + 31) / 32, 1024, 0, s>>>(t->part, B / 256, (long long)W * 16, t->Gr + t->off_w1);
+    reduce_kernel<<<grid_for((long long)W * 16), 256, 0, s>>>(t->part, B / 256, (long long)W * 16, t->Gr + t->off_w1);
     return SVM_OK;
 }
 
