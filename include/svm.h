@@ -281,7 +281,13 @@ typedef struct svm_plan svm_plan;
 svm_status svm_plan_create(svm_model* m, const double* q0, const double* q1, int32_t n_motions,
                            const int32_t* motion_scene, const int64_t* scene_offsets, int32_t n_scenes,
                            float margin, int32_t steps, uint32_t flags, svm_plan** out);
+/* Waits for the device, then frees the plan's workspace and graph. */
 svm_status svm_plan_destroy(svm_plan* p);
+/* One check of the plan's batch on `stream`: points_dev holds the scenes'
+ * clouds concatenated as described by scene_offsets at creation (float4,
+ * 16-byte aligned, device); results_dev receives one record per motion (or
+ * per path), device, caller-owned.  SVM_E_INVALID for null or misaligned
+ * buffers; enqueue errors as SVM_E_CUDA. */
 svm_status svm_plan_launch(svm_plan* p, const float* points_dev, svm_result* results_dev, void* stream);
 /* Replay the plan as a CUDA graph on `stream` (a created stream, not the
  * default one).  The first call, and any call with other points or results
@@ -354,13 +360,19 @@ typedef struct svm_trainer svm_trainer;
  * 256 (>= 256).  Parameters start at zero: load initial weights with
  * svm_train_set_weights.  Needs a GPU of compute capability 10.3. */
 svm_status svm_train_create(const svm_model_desc* desc, int device, int32_t batch, svm_trainer** out);
+/* Waits for the device, then frees everything the trainer owns. */
 svm_status svm_train_destroy(svm_trainer* t);
+/* Text of the last failing call on the trainer. */
 const char* svm_train_last_error(const svm_trainer* t);
+/* Number of parameters in blob order (weights and biases of every layer). */
 int64_t svm_train_param_count(const svm_trainer* t);
 
 /* Weights in the blob format of svm_load_weights (tau ignored).  Setting
  * weights resets the Adam moments and the step count. */
 svm_status svm_train_set_weights(svm_trainer* t, const void* blob, size_t bytes);
+/* The current FP32 master weights as a blob (tau = +inf): *needed receives
+ * its size; with blob = NULL only the size is returned; SVM_E_INVALID if
+ * capacity is smaller than that.  Synchronous. */
 svm_status svm_train_get_weights(svm_trainer* t, void* blob, size_t capacity, size_t* needed);
 
 /* The box of the uniformly drawn training points for later svm_train_make_data
@@ -383,6 +395,9 @@ svm_status svm_train_make_data(svm_trainer* t, const double* q0, const double* q
 /* Explicit samples: x4 (n x 4 floats: x, y, z, delta) and motion indices. */
 svm_status svm_train_set_samples(svm_trainer* t, const double* q0, const double* q1, int32_t n_motions,
                                  const float* x4, const int32_t* motion, int64_t n);
+/* Copy the first n samples to the host (either output may be NULL):
+ * x4_out n x 4 floats (x, y, z, delta), motion_out n motion indices;
+ * SVM_E_INVALID if n exceeds the samples held.  Synchronous. */
 svm_status svm_train_copy_samples(svm_trainer* t, float* x4_out, int32_t* motion_out, int64_t n);
 
 /* Loss and gradient (blob order, param_count floats, host) of the batch of
@@ -399,6 +414,9 @@ svm_status svm_train_epoch(svm_trainer* t, int64_t sample_begin, int64_t sample_
 svm_status svm_train_evaluate(svm_trainer* t, int64_t sample_begin, int64_t sample_end, float* mae);
 /* Checkpoint: parameters, Adam moments (param_count floats each) and step. */
 svm_status svm_train_state(svm_trainer* t, float* params, float* m1, float* m2, int64_t* step, int64_t n);
+/* The inverse of svm_train_state (n must equal svm_train_param_count); a
+ * restored trainer continues bit for bit as the one the state was taken
+ * from. */
 svm_status svm_train_restore(svm_trainer* t, const float* params, const float* m1, const float* m2, int64_t step,
                              int64_t n);
 
