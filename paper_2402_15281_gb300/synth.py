@@ -412,6 +412,61 @@ def box_world_motions(robot: Robot, n_goals: int, seed: int):
 
 
 # --------------------------------------------------------------------------
+# Named workloads: the bin-picking shapes of Sec. V-C, drawn the same way by
+# the tests, the benchmark and the script that stores the oracle's verdicts.
+# --------------------------------------------------------------------------
+
+def bin_picking_workload(seed: int = 0, n_motions: int = 64, n_points: int = 200_000):
+    """n_motions grasp motions (bin_motions) against one n_points bin cloud
+    (bin_cloud) of the same seed, arm of seed 1.  Returns (robot, points (P, 4)
+    float32, q0, q1)."""
+    robot = make_robot(1)
+    pts = bin_cloud(n_points, seed=seed)
+    q0, q1 = bin_motions(robot, n_motions, seed=seed)
+    return robot, pts, q0, q1
+
+
+def uneven_batch_workload(n_scenes: int = 32, per_scene: int = 16, lo: int = 10_000, hi: int = 500_000):
+    """n_scenes bin scenes whose cloud sizes are log-uniform in [lo, hi]
+    (scene s: bin_cloud of seed 200 + s), per_scene grasp motions each
+    (bin_motions of seed 300 + s), motions grouped by scene.  Returns (robot,
+    sizes (S,), clouds (list of (P_s, 4)), q0, q1, motion_scene (M,) int32)."""
+    robot = make_robot(1)
+    sizes = np.round(np.exp(Rng(3, 77).uniform(n_scenes, np.log(lo), np.log(hi)))).astype(np.int64)
+    clouds = [bin_cloud(int(n), seed=200 + s) for s, n in enumerate(sizes)]
+    q0s, q1s = [], []
+    for s in range(n_scenes):
+        a, b = bin_motions(robot, per_scene, seed=300 + s)
+        q0s.append(a)
+        q1s.append(b)
+    scene = np.repeat(np.arange(n_scenes, dtype=np.int32), per_scene)
+    return robot, sizes, clouds, np.concatenate(q0s), np.concatenate(q1s), scene
+
+
+def three_segment_path_workload(n_paths: int = 128, n_points: int = 300_000, seed: int = 4):
+    """n_paths three-segment paths (bin_paths) against one bin cloud of
+    n_points; segment 3p + s runs from configuration s to s + 1 of path p.
+    Returns (robot, points, q0 (3 n_paths, 6), q1 (3 n_paths, 6))."""
+    robot = make_robot(1)
+    paths = bin_paths(robot, n_paths, seed=seed)
+    q0 = np.ascontiguousarray(paths[:, :3].reshape(-1, DOF))
+    q1 = np.ascontiguousarray(paths[:, 1:].reshape(-1, DOF))
+    return robot, bin_cloud(n_points, seed=seed), q0, q1
+
+
+def inputs_digest(*arrays) -> str:
+    """SHA-256 of the arrays' bytes (dtype, shape and values), to tell whether
+    two machines drew the same inputs."""
+    import hashlib
+    h = hashlib.sha256()
+    for a in arrays:
+        a = np.ascontiguousarray(a)
+        h.update(f"{a.dtype.str}{a.shape}".encode())
+        h.update(a.tobytes())
+    return h.hexdigest()
+
+
+# --------------------------------------------------------------------------
 # Network parameters
 # --------------------------------------------------------------------------
 

@@ -511,3 +511,47 @@ def test_training_points_box():
     u = (a[moved, :3] - lo0) / (hi0 - lo0)
     np.testing.assert_allclose(c[moved, :3], S.BOX_LO + u * (S.BOX_HI - S.BOX_LO), atol=1e-12)
     assert np.all(c[moved, :3] >= S.BOX_LO) and np.all(c[moved, :3] <= S.BOX_HI)
+
+
+def test_training_points_near_surface_branch():
+    """The near-surface draws of the training sampler (Sec. IV-C data recipe
+    on capsules), pinned by geometry rather than by its own formula: with the
+    draws u_0..u_6 recomputed from the (separately pinned) SplitMix64 stream,
+    every draw with u_0 < 0.7 lies at distance exactly |r_c + off| from the
+    point a + u_3 (b - a) of the axis of capsule c = floor(7 u_2) at sample
+    k = floor((N + 1) u_1) (axes from the pinned FK), off = -0.1 + 0.2 u_6;
+    its label is at most that distance minus r_c (the capsule it was drawn
+    near bounds the minimum) and equals the pinned swept-volume distance; the
+    offset directions are uniform on the sphere (mean 0, second moment I / 3);
+    about 70 % of the draws take this branch."""
+    robot = S.make_robot(1)
+    q0, q1 = S.uniform_motions(robot, 1, seed=9, max_step_deg=40)
+    q0, q1 = q0[0], q1[0]
+    N, seed, m, spm = 24, 11, 3, 3000
+    pts = oracle.training_points(robot, q0, q1, N, seed, m, spm)
+    dirs, near = [], 0
+    for j in range(spm):
+        u = [oracle.splitmix64_u01(seed, m, 8 * j + i) for i in range(7)]
+        if u[0] >= 0.7:
+            continue
+        near += 1
+        k = min(int(u[1] * (N + 1)), N)
+        c = min(int(u[2] * 7), 6)
+        qk = ((N - k) * q0 + k * q1) / N
+        A, B = oracle.capsules(robot, qk)
+        foot = A[c] + u[3] * (B[c] - A[c])
+        off = -0.1 + 0.2 * u[6]
+        rc = robot.radius[c]
+        v = pts[j, :3] - foot
+        dist = np.linalg.norm(v)
+        assert abs(dist - abs(rc + off)) <= 1e-12, (j, dist, rc + off)
+        assert pts[j, 3] <= abs(rc + off) - rc + 1e-12
+        assert pts[j, 3] == oracle.swept_sdf(robot, q0, q1, N, pts[j, :3])
+        if abs(rc + off) > 1e-3:
+            dirs.append(v / (rc + off))
+    d = np.array(dirs)
+    n = len(d)
+    assert abs(near / spm - 0.7) <= 4 * np.sqrt(0.21 / spm)
+    np.testing.assert_allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-9)
+    assert np.abs(d.mean(axis=0)).max() <= 4 / np.sqrt(3 * n)
+    assert np.abs(d.T @ d / n - np.eye(3) / 3).max() <= 0.05
