@@ -48,16 +48,51 @@ DTYPE_NAMES = {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}
 METRIC = "verified motion-point queries/s"
 FLOP_PER_PAIR = 2 * (3 * WIDTH + HIDDEN * WIDTH * WIDTH + WIDTH)   # 526 336
 FLOP_PER_CAPSULE_TEST = 20
-# DRAM bytes (read + write) of one launch of the tensor-core network kernel on this workload, from
-# one-pass ncu captures of a full-size launch; to be reset to None whenever that kernel changes.
-TC_TRAFFIC_BYTES = {"bf16": 3.86e6, "fp8": 3.62e6}
+# DRAM bytes (read + write) per launch of the tensor-core network kernel on this workload come from the
+# committed one-pass ncu summary, valid only for the kernel source it was captured on.
+TC_SOURCES = ("mlp_tc.cu", "mlp_tc.cuh", "tc_ptx.cuh")
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "mlp_tc_dram_bin64.md")
+# The FP64 oracle's verdicts for this workload, stored by tests/golden/oracle_verdicts.py.
+ORACLE_RECORD = os.path.join(ROOT, "tests", "golden", "oracle_verdicts.json")
 
 
 def workload(seed=0):
-    robot = S.make_robot(1)
-    pts = S.bin_cloud(N_POINTS, seed=seed)
-    q0, q1 = S.bin_motions(robot, N_MOTIONS, seed=seed)
-    return robot, pts, q0, q1
+    return S.bin_picking_workload(seed, N_MOTIONS, N_POINTS)
+
+
+def tc_traffic(prec):
+    """DRAM bytes per launch of the tensor-core network kernel (ncu, full-size launch) from the
+    committed summary, or None when the kernel's source has changed since the capture."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in TC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2402_15281_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    digest, traffic = None, {}
+    try:
+        for line in open(TRAFFIC_PROFILE):
+            line = line.strip()
+            if line.startswith("kernel-source-sha256-16:"):
+                digest = line.split(":", 1)[1].strip()
+            elif line.startswith("traffic-bytes-per-launch:"):
+                traffic = dict(kv.split("=") for kv in line.split(":", 1)[1].split())
+    except OSError:
+        return None
+    if digest != h.hexdigest()[:16] or prec not in traffic:
+        return None
+    return float(traffic[prec])
+
+
+def oracle_record(pts, q0, q1):
+    """(collision, d_min) of the FP64 oracle for these inputs from the stored record, or None if
+    this machine drew other inputs."""
+    try:
+        rec = json.load(open(ORACLE_RECORD))["bin_picking"]
+    except (OSError, KeyError, ValueError):
+        return None
+    if rec["inputs_sha256"] != S.inputs_digest(pts, q0, q1):
+        return None
+    return np.array(rec["collision"], dtype=np.uint8), np.array(rec["d_min"])
 
 
 def weights():
@@ -199,6 +234,30 @@ def job_throughput(pairs_per_rank_step, steps, total_ms_max, world):
 
 # --------------------------------------------------------------------- GPU arm
 
+def network_roofline(prec, pairs, mlp_ms, peaks):
+    """Roofline of the network kernel: algorithmic FLOP (FLOP_PER_PAIR per pair) over its
+    CUDA-event time against the measured burst peak (the kernel runs a few ms at a time at the
+    maximum clock), with the sustained peak beside it."""
+    achieved = pairs * FLOP_PER_PAIR / (mlp_ms * 1e-3) / 1e12
+    if prec == "fp32":
+        pk = 152 * 128 * 2 * 2070.0 * 1e6 / 1e12      # FP32 TFLOP/s at the maximum SM clock
+        return {"kernel": "mlp_fp32", "bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz", "frac": achieved / pk, "traffic": None}
+    scale = 2.0 if prec == "fp8" else 1.0
+    burst, sust = peaks.get("bf16_tflops"), peaks.get("bf16_tflops_sustained")
+    src = "measured burst bf16 (MEASURED_PEAKS.json)"
+    if burst is None:
+        burst, src = 1900.0, "fallback burst bf16"
+    if sust is None:
+        sust = 1700.0
+    if scale > 1:
+        src += " x2 for fp8 (nominal fp8/bf16 ratio)"
+    return {"kernel": f"mlp_tc_{prec}", "bound": "tensor", "achieved": achieved, "peak": burst * scale,
+            "unit": "TFLOP/s", "peak_source": src, "frac": achieved / (burst * scale),
+            "peak_sustained": sust * scale, "frac_of_sustained": achieved / (sust * scale),
+            "traffic": tc_traffic(prec)}
+
+
 def run_gpu(args):
     import torch
     import paper_2402_15281_gb300 as svm
@@ -227,6 +286,8 @@ def run_gpu(args):
     layers = svm.parse_blob(blob)
     pts_d = torch.from_numpy(pts).to(dev)
     cq0, cq1 = S.bin_motions(robot, 16, seed=1000)
+    pairs_step = N_MOTIONS * N_POINTS
+    ref = oracle_record(pts, q0, q1) if rank == 0 else None
 
     def make_model(p):
         h = svm.svm_create_model(robot, WIDTH, HIDDEN, svm.SVM_RELU, p, local)
@@ -235,45 +296,54 @@ def run_gpu(args):
             # per-layer activation scales from the calibration motions (2x headroom)
             svm.svm_calibrate_act_scales(h, cq0, cq1, pts_d, 2.0)
         t = training.calibrate_tau(svm, h, robot, pts_d, EPS, STEPS, cq0, cq1)
-        svm.svm_set_gate(h, t)
         return h, t
 
-    model, tau = make_model(prec)
-    svm.svm_profile_enable(model, True)
     res = svm.new_results(N_MOTIONS, dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     flags = 0
 
-    def step():
-        svm.svm_check_motions(model, q0, q1, pts_d, EPS, STEPS, flags, res, stream)
-
-    for _ in range(args.warmup):
-        step()
-        flush.fill_(1.0)
-    torch.cuda.synchronize()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    phases = np.zeros(4)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for k in range(args.steps):
-            flush.fill_(float(k))
-            starts[k].record(stream)
-            step()
-            ends[k].record(stream)
-            phases += svm.svm_profile_read(model)
+    def timed(h, steps, warmup, clocks=None):
+        """K steps of one check call each, CUDA events on the launching stream, an L2 flush
+        between steps outside the events; returns per-step ms, mean phase ms, the records."""
+        svm.svm_profile_enable(h, True)
+        for _ in range(warmup):
+            svm.svm_check_motions(h, q0, q1, pts_d, EPS, STEPS, flags, res, stream)
+            flush.fill_(1.0)
         torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        phases = np.zeros(4)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local) if clocks is not None else None
+        if sampler:
+            sampler.__enter__()
+        try:
+            for k in range(steps):
+                flush.fill_(float(k))
+                starts[k].record(stream)
+                svm.svm_check_motions(h, q0, q1, pts_d, EPS, STEPS, flags, res, stream)
+                ends[k].record(stream)
+                phases += svm.svm_profile_read(h)
+            torch.cuda.synchronize()
+        finally:
+            if sampler:
+                sampler.__exit__(None, None, None)
+                clocks.update(sampler.summary())
+        if world > 1:
+            torch.distributed.barrier()
+        ms = np.array([a.elapsed_time(b) for a, b in zip(starts, ends)])
+        return ms, phases / steps, svm.results_to_numpy(res)[:N_MOTIONS].copy()
+
+    def mismatches(r):
+        return None if ref is None else int(np.sum(r["collision"] != ref[0]))
+
+    model, tau = make_model(prec)
+    clocks = {}
+    ms, phases, r = timed(model, args.steps, args.warmup, clocks)
     total_ms = max_over_ranks(float(ms.sum()), dev)
-    clocks = clk.summary()
-    phases /= args.steps
-    r = svm.results_to_numpy(res)[:N_MOTIONS]
-    pairs_step = N_MOTIONS * N_POINTS
     value = job_throughput(pairs_step, args.steps, total_ms, world)
 
     # end to end through the C ABI with host buffers: H2D cloud, check, D2H results
@@ -295,57 +365,47 @@ def run_gpu(args):
     e2e_value = job_throughput(pairs_step, args.steps, e2e_total, world)
 
     # roofline of the dominant kernel
-    import json as _json
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
-        peaks = _json.load(open(pk_path))
+        peaks = json.load(open(pk_path))
     n_verified = int(r["n_verified"].sum())
     mlp_ms, ver_ms = phases[1], phases[2]
-    sm_max = 2070.0
-    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # FP32 TFLOP/s at the maximum SM clock
     if mlp_ms >= ver_ms:
-        flop = pairs_step * FLOP_PER_PAIR
-        achieved = flop / (mlp_ms * 1e-3) / 1e12
-        if args.prec == "fp32":
-            roof = {"kernel": "mlp_fp32", "bound": "alu", "achieved": achieved, "peak": alu_peak,
-                    "unit": "TFLOP/s", "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
-        else:
-            scale = 2.0 if args.prec == "fp8" else 1.0
-            pk = peaks.get("bf16_tflops_sustained")
-            src = "measured sustained bf16 (MEASURED_PEAKS.json)" + (" x2 for fp8" if scale > 1 else "")
-            if pk is None:
-                pk, src = 1700.0, "fallback sustained bf16"
-            roof = {"kernel": f"mlp_tc_{args.prec}", "bound": "tensor", "achieved": achieved, "peak": pk * scale,
-                    "unit": "TFLOP/s", "peak_source": src}
+        roof = network_roofline(args.prec, pairs_step, mlp_ms, peaks)
     else:
-        flop = n_verified * (STEPS + 1) * 7 * FLOP_PER_CAPSULE_TEST
-        achieved = flop / (ver_ms * 1e-3) / 1e12
+        alu_peak = 152 * 128 * 2 * 2070.0 * 1e6 / 1e12
+        achieved = n_verified * (STEPS + 1) * 7 * FLOP_PER_CAPSULE_TEST / (ver_ms * 1e-3) / 1e12
         roof = {"kernel": "verify", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = TC_TRAFFIC_BYTES.get(args.prec) if roof["kernel"].startswith("mlp_tc") else None
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz", "frac": achieved / alu_peak,
+                "traffic": None}
+
+    # the same step in FP8 E4M3 (per-layer scales, own calibrated gate), timed the same way
+    fp8 = None
+    if args.prec == "bf16" and not args.no_fp8_path:
+        m8, tau8 = make_model(svm.SVM_FP8_E4M3)
+        ms8, ph8, r8 = timed(m8, args.steps, args.warmup)
+        fp8 = {"value": job_throughput(pairs_step, args.steps, max_over_ranks(float(ms8.sum()), dev), world),
+               "ms_per_step": float(ms8.mean()),
+               "phases_ms": {"prologue": float(ph8[0]), "network": float(ph8[1]), "verify": float(ph8[2]),
+                             "finalize": float(ph8[3])},
+               "tau_m": tau8, "flagged_fraction": float(r8["n_flagged"].sum()) / pairs_step,
+               "verified_fraction": float(r8["n_verified"].sum()) / pairs_step,
+               "collisions": int(r8["collision"].sum()),
+               "verdicts_equal": bool(np.array_equal(r8["collision"], r["collision"])),
+               "oracle_mismatches": mismatches(r8),
+               "roofline": network_roofline("fp8", pairs_step, ph8[1], peaks)}
+        svm.svm_destroy_model(m8)
 
     # the plain FP32 path on the same workload and weights (SIMT network, same verifier)
     fp32 = None
     if args.prec != "fp32" and not args.no_fp32_path:
         m32, tau32 = make_model(svm.SVM_FP32)
-        for _ in range(2):
-            svm.svm_check_motions(m32, q0, q1, pts_d, EPS, STEPS, flags, res, stream)
-        flush.fill_(0.0)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        k32 = 3
-        e0.record(stream)
-        for _ in range(k32):
-            svm.svm_check_motions(m32, q0, q1, pts_d, EPS, STEPS, flags, res, stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms32 = e0.elapsed_time(e1) / k32
-        r32 = svm.results_to_numpy(res)[:N_MOTIONS]
-        fp32 = {"value": pairs_step / (ms32 / 1e3), "ms_per_step": ms32, "tau_m": tau32,
-                "collisions": int(r32["collision"].sum()),
-                "verdicts_equal": bool(np.array_equal(r32["collision"], r["collision"]))}
+        ms32, _, r32 = timed(m32, 3, 2)
+        fp32 = {"value": pairs_step / (float(ms32.mean()) / 1e3), "ms_per_step": float(ms32.mean()),
+                "tau_m": tau32, "collisions": int(r32["collision"].sum()),
+                "verdicts_equal": bool(np.array_equal(r32["collision"], r["collision"])),
+                "oracle_mismatches": mismatches(r32)}
         svm.svm_destroy_model(m32)
 
     # prologue, network, probe (early exit on), plan + verify, ties, finalize; strict adds plan + verify
@@ -362,11 +422,17 @@ def run_gpu(args):
             "phases_ms": {"prologue": float(phases[0]), "network": float(phases[1]),
                           "verify": float(phases[2]), "finalize": float(phases[3])},
             "tau_m": tau, "collisions": int(r["collision"].sum()),
+            "oracle_mismatches": mismatches(r),
+            "oracle_record": ("stored FP64 oracle verdicts of all 64 motions (tests/golden/oracle_verdicts.json), "
+                              "compared outside the timed region") if ref is not None else
+                             "not compared: this rank's inputs differ from the stored record",
+            "fp8_path": fp8,
             "fp32_path": fp32, "speedup_vs_fp32_path": (value / fp32["value"]) if fp32 else None,
             "training": train_info,
             "flagged_fraction": float(r["n_flagged"].sum()) / pairs_step,
             "verified_fraction": n_verified / pairs_step,
-            "margin_ties_fp64": int(r["n_ambiguous"].sum())}
+            "margin_ties_fp64": int(r["n_ambiguous"].sum()),
+            "inexact_records": int(np.sum(r["status"] == 2))}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt, cores = oracle_sample(robot, pts, q0, q1, layers, args.prec, EPS + tau, 2)
         line["cpu_baseline"] = {"value": v, "unit": "queries/s", "cores": cores, "kind": "oracle",
@@ -399,7 +465,7 @@ def profile_call(args):
         cq0, cq1 = S.bin_motions(robot, 16, seed=1000)
         if args.prec == "fp8":
             svm.svm_calibrate_act_scales(h, cq0, cq1, pts_d, 2.0)
-        svm.svm_set_gate(h, training.calibrate_tau(svm, h, robot, pts_d, EPS, STEPS, cq0, cq1))
+        training.calibrate_tau(svm, h, robot, pts_d, EPS, STEPS, cq0, cq1)
     else:
         svm.svm_load_weights(h, svm.make_blob(weights()))
         if args.prec == "fp8":
@@ -421,6 +487,7 @@ def main():
     ap.add_argument("--prec", choices=list(PREC_NAMES), default="bf16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-path", action="store_true")
+    ap.add_argument("--no-fp8-path", action="store_true")
     ap.add_argument("--weights", choices=["trained", "random"], default="trained")
     ap.add_argument("--profile-call", type=int, default=0, metavar="M",
                     help="for profilers: one svm_check_motions call on the first M bench motions (weights "

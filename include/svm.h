@@ -96,7 +96,13 @@ typedef struct {
     uint8_t collision;      /* 1 iff some checked point has distance <= margin */
     uint8_t early_exit;     /* 1 if checking stopped at the first collision     */
     uint16_t status;        /* 0 = valid; 1 = a bounded device wait expired during
-                               the call and this record is not valid           */
+                               the call and this record is not valid; 2 = valid
+                               except that a checked pair of this motion (or
+                               path) whose FP32 distance lay within 4e-6 m of
+                               the margin found the call's list of such pairs
+                               full (16 384) and was decided in FP32, so its
+                               verdict and d_min may differ from the FP64
+                               decision                                        */
     float d_min;            /* minimum exact distance over the checked points;
                                +inf if none was checked; on early exit the first
                                value found <= margin                            */
@@ -110,7 +116,8 @@ typedef struct {
     uint32_t n_ambiguous;   /* checked points whose FP32 distance lies within
                                4e-6 m of the margin; their verdict and distance
                                are recomputed in FP64 (the first 16384 such
-                               pairs of a call; the FP32 decision beyond)      */
+                               pairs of a call; beyond that the FP32 decision
+                               stands and the record carries status 2)        */
 } svm_result;
 
 typedef struct svm_model svm_model;
@@ -179,6 +186,12 @@ svm_status svm_export_weights(const svm_model* m, float* out, size_t count, size
  * SVM_E_UNSUPPORTED for FP32 models (no device waits). */
 svm_status svm_test_expire_wait(svm_model* m, int32_t n_calls);
 
+/* Test hook for the tie-list overflow path: later calls of this model keep
+ * at most `cap` pairs at the margin (1..16384) for the FP64 decision, so that
+ * a small case overflows the list; 0 restores the full list.  Records of
+ * motions with a pair beyond the cap carry status 2. */
+svm_status svm_test_set_tie_cap(svm_model* m, int32_t cap);
+
 /* Gate offset tau >= 0 (metres): a pair is checked exactly iff its network
  * prediction f <= margin + tau.  tau = +inf checks every pair. */
 svm_status svm_set_gate(svm_model* m, float tau);
@@ -197,6 +210,30 @@ svm_status svm_set_act_scales(svm_model* m, const float* scales, int32_t n);
 svm_status svm_calibrate_act_scales(svm_model* m, const double* q0, const double* q1, int32_t n_motions,
                                     const float* points_dev, int64_t n_points, float headroom,
                                     float* scales_out);
+
+/* Gate calibration: the margin widened by the measured error of the network
+ * (Sec. IV-B gates the exact check with the network's prediction; here the
+ * gate is g = margin + tau).  Over every (motion, point) pair given (host
+ * q0/q1, n_motions x 6; device points), with f the network output in the
+ * model's own precision and delta the exact sampled distance at `steps`
+ * steps (the values svm_eval_pairs and svm_label_pairs would write):
+ *   over = max (f - delta) over the pairs with delta <= margin + band
+ *          (the pairs that can collide; margin + band rounded to float),
+ *   tau  = max(0, safety * over), or 0 when no pair is that close.
+ * Sets the model's gate to tau (svm_set_gate) and writes tau, over (-inf if
+ * no pair qualifies) and the number of qualifying pairs to the host outputs
+ * (each may be NULL).  The calibration motions should be separate from the
+ * motions to be checked and drawn like them; the gate is an empirical bound,
+ * not a guarantee (SVM_STRICT confirms free verdicts regardless).
+ *   band >= 0, safety >= 1, margin >= 0, steps as in svm_check_motions;
+ *   n_motions * n_points < 2^32.
+ * The network outputs are formed in chunks of motions in a temporary buffer
+ * of at most 2^26 floats (cudaMalloc, freed before return); delta is never
+ * stored.  Synchronous on `stream`.  SVM_E_WEIGHTS without weights. */
+svm_status svm_calibrate_gate(svm_model* m, const double* q0, const double* q1, int32_t n_motions,
+                              const float* points_dev, int64_t n_points, float margin, int32_t steps, float band,
+                              float safety, float* tau_out, float* overestimate_out, int64_t* n_near_out,
+                              void* stream);
 
 /* Check n_motions linear motions q0[m] -> q1[m] against one point cloud.
  *   q0, q1       host, n_motions x 6 doubles, finite.
@@ -296,10 +333,17 @@ svm_status svm_plan_graph_launch(svm_plan* p, const float* points_dev, svm_resul
 /* Verifier launch shape: points per thread (1, 2 or 4: one shared-memory read
  * of a capsule serves that many points) and CTAs per SM (0 = all that fit). */
 svm_status svm_plan_set_verify_shape(svm_plan* p, int32_t points_per_thread, int32_t ctas_per_sm);
-/* Time every launch shape on the plan's data (3 launches each, CUDA events,
- * synchronous), keep the fastest, and write a JSON report of all timings and
- * the choice to `report` (may be NULL).  The report can be stored and the
- * choice re-applied later with svm_plan_set_verify_shape. */
+/* Persistent grid of the tensor-core network kernel: ctas CTAs (1..number of
+ * SMs; 0 = one per SM, the default).  No effect on FP32 models. */
+svm_status svm_plan_set_network_grid(svm_plan* p, int32_t ctas);
+/* Time the launch shapes on the plan's data (one warm-up and 3 timed
+ * launches each, CUDA events, synchronous) and keep the fastest: first the
+ * network kernel's grid (tensor-core models: all SMs, 15/16, 7/8, 3/4 and
+ * 1/2 of them), then, at that grid, the verifier's 9 shapes.  Writes a JSON
+ * report {"network_candidates": [...], "candidates": [...], "best": {...}}
+ * of all timings and the choice to `report` (may be NULL); the choice can be
+ * re-applied later with svm_plan_set_network_grid and
+ * svm_plan_set_verify_shape. */
 svm_status svm_plan_autotune(svm_plan* p, const float* points_dev, svm_result* results_dev, void* stream,
                              char* report, size_t capacity);
 
@@ -317,18 +361,19 @@ svm_status svm_label_pairs(svm_model* m, const double* q0, const double* q1, int
                            float* delta_dev, void* stream);
 
 /* Allocation-free variant of svm_check_motions, for callers that cannot
- * allocate device memory while they check motions: a real-time loop whose
- * memory is fixed at start-up, a process whose allocator belongs to another
- * framework, or code between the begin and end of a stream capture, where
- * cudaMalloc is not allowed.  The paper has no counterpart; this is an
- * interface of this library only.
+ * allocate device memory while they check motions: a real-time control loop
+ * whose memory is fixed at start-up (an allocation there can stall, or fail
+ * when the device is full), or a process whose device memory is owned by
+ * another framework's allocator, which may already hold all of it.  The paper
+ * has no counterpart; this is an interface of this library only.
  *   - Allocates nothing: no cudaMalloc, cudaFree, pinned host memory or
  *     allocating library call.  Its scratch is one fixed 32 MiB array in
  *     device memory that the library declares at file scope; every GPU that
  *     loads the library holds it until the process exits.
- *   - q0_dev, q1_dev are DEVICE arrays (n_motions x 6 doubles, finite; not
- *     checked); the other arguments and the results are as in
- *     svm_check_motions.
+ *   - q0_dev, q1_dev are DEVICE (or managed) arrays, n_motions x 6 doubles,
+ *     8-byte aligned, on the model's device (checked: SVM_E_INVALID
+ *     otherwise); their values must be finite (not checked).  The other
+ *     arguments and the results are as in svm_check_motions.
  *   - A call needs about 4 bytes per motion-point pair plus, per motion,
  *     (steps + 1) * 416 bytes (the FP32 capsule table and the FP64 kinematics
  *     kept for pairs at the margin) and about 1.3 KB, plus 256 KB for the
@@ -336,7 +381,10 @@ svm_status svm_label_pairs(svm_model* m, const double* q0, const double* q1, int
  *     32 MiB is rejected with SVM_E_INVALID and a message naming the sizes
  *     (e.g. 64 motions x 100 000 points fit, 64 x 200 000 do not).
  *   - The first call on a device looks up the scratch array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress) and keeps it for the life of the process; make
+ *     that first call before any stream capture.  A cudaDeviceReset (or any
+ *     other teardown of the device's primary context) invalidates the kept
+ *     address: do not call this entry point on that device afterwards.
  *   - Every call, from every model on that device, shares the one array and
  *     finds the previous call's contents in it; the call re-initialises what
  *     it needs.  Calls whose kernels overlap on the GPU (different streams

@@ -69,6 +69,7 @@ def lib():
         L.svm_load_weights.argtypes = [vp, C.c_char_p, sz]
         L.svm_export_weights.argtypes = [vp, vp, sz, C.POINTER(sz)]
         L.svm_set_gate.argtypes = [vp, f32]
+        L.svm_test_set_tie_cap.argtypes = [vp, i32]
         L.svm_set_act_scales.argtypes = [vp, vp, i32]
         L.svm_check_motions.argtypes = [vp, vp, vp, i32, vp, i64, f32, i32, u32, vp, vp]
         L.svm_check_batch.argtypes = [vp, vp, vp, i32, vp, vp, vp, i32, f32, i32, u32, vp, vp]
@@ -79,12 +80,15 @@ def lib():
         L.svm_plan_launch.argtypes = [vp, vp, vp, vp]
         L.svm_plan_graph_launch.argtypes = [vp, vp, vp, vp]
         L.svm_plan_set_verify_shape.argtypes = [vp, i32, i32]
+        L.svm_plan_set_network_grid.argtypes = [vp, i32]
         L.svm_plan_autotune.argtypes = [vp, vp, vp, vp, C.c_char_p, sz]
         for f in ("svm_plan_create", "svm_plan_destroy", "svm_plan_launch", "svm_plan_graph_launch",
                   "svm_plan_set_verify_shape", "svm_plan_autotune"):
             getattr(L, f).restype = C.c_int
         L.svm_calibrate_act_scales.argtypes = [vp, vp, vp, i32, vp, i64, f32, vp]
         L.svm_calibrate_act_scales.restype = C.c_int
+        L.svm_calibrate_gate.argtypes = [vp, vp, vp, i32, vp, i64, f32, i32, f32, f32, vp, vp, vp, vp]
+        L.svm_calibrate_gate.restype = C.c_int
         L.svm_check_motions_noalloc.argtypes = [vp, vp, vp, i32, vp, i64, f32, i32, u32, vp, vp]
         L.svm_check_motions_noalloc.restype = C.c_int
         L.svm_train_create.argtypes = [C.POINTER(svm_model_desc), C.c_int, i32, C.POINTER(vp)]
@@ -257,6 +261,10 @@ def svm_test_expire_wait(model, n_calls: int = 1):
     _check("svm_test_expire_wait", lib().svm_test_expire_wait(model, int(n_calls)), model)
 
 
+def svm_test_set_tie_cap(model, cap: int):
+    _check("svm_test_set_tie_cap", lib().svm_test_set_tie_cap(model, int(cap)), model)
+
+
 def svm_set_gate(model, tau: float):
     _check("svm_set_gate", lib().svm_set_gate(model, float(tau)), model)
 
@@ -275,6 +283,18 @@ def svm_calibrate_act_scales(model, q0, q1, points_dev, headroom=2.0) -> np.ndar
         model, p0, p1, q0.shape[0], _dev(points_dev), points_dev.shape[0], float(headroom),
         out.ctypes.data_as(C.c_void_p)), model)
     return out
+
+
+def svm_calibrate_gate(model, q0, q1, points_dev, margin, steps, band=0.05, safety=1.25, stream=None):
+    """Set the gate from calibration motions (host (M, 6)) against a device
+    cloud; returns (tau, largest overestimate, number of near pairs)."""
+    q0, p0 = _host_f64(q0)
+    q1, p1 = _host_f64(q1)
+    tau, over, n_near = C.c_float(0.0), C.c_float(0.0), C.c_int64(0)
+    _check("svm_calibrate_gate", lib().svm_calibrate_gate(
+        model, p0, p1, q0.shape[0], _points(points_dev), points_dev.shape[0], float(margin), int(steps),
+        float(band), float(safety), C.byref(tau), C.byref(over), C.byref(n_near), _stream(stream)), model)
+    return float(tau.value), float(over.value), int(n_near.value)
 
 
 def svm_check_motions(model, q0, q1, points_dev, margin, steps, flags, results_dev, stream=None):
@@ -364,6 +384,9 @@ class Plan:
     def set_verify_shape(self, points_per_thread, ctas_per_sm):
         _check("svm_plan_set_verify_shape", lib().svm_plan_set_verify_shape(self.h, int(points_per_thread),
                                                                             int(ctas_per_sm)), self.model)
+
+    def set_network_grid(self, ctas):
+        _check("svm_plan_set_network_grid", lib().svm_plan_set_network_grid(self.h, int(ctas)), self.model)
 
     def autotune(self, points_dev, results_dev, stream=None) -> str:
         buf = C.create_string_buffer(4096)

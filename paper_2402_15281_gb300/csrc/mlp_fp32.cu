@@ -15,6 +15,7 @@
 // flags and one atomicAdd per warp reserves their slots in the motion's index
 // list, and the motion's minimum prediction d^(X, m) of Eq. 6 is kept with
 // an atomic minimum.
+#include <mutex>
 #include "svm_internal.cuh"
 
 namespace svm {
@@ -298,12 +299,12 @@ void launch_wb(const CallArgs& a, const DevWeights& w, int n_tiles, cudaStream_t
     const size_t smem = (size_t)(BMP * (W + HPAD) + 2 * KC * W) * sizeof(float);
     int dev = 0;
     cudaGetDevice(&dev);
-    static bool configured[64] = {};
-    if (dev >= 0 && dev < 64 && !configured[dev]) {
-        cudaFuncSetAttribute(mlp_fp32_kernel<W, KC, BLOCK, BM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        configured[dev] = true;
-    }
+    static std::once_flag configured[64];      // once per device, safe across host threads
+    if (dev >= 0 && dev < 64)
+        std::call_once(configured[dev], [smem] {
+            cudaFuncSetAttribute(mlp_fp32_kernel<W, KC, BLOCK, BM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        });
     mlp_fp32_kernel<W, KC, BLOCK, BM><<<n_tiles, NT, smem, s>>>(a, w);
 }
 

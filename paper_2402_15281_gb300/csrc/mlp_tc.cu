@@ -36,6 +36,7 @@
 // sets the call's error word and an abort flag, every role leaves its loop,
 // the MMA issuer and the producer wait (bounded) for their own operations in
 // flight, and the TMEM is freed before the CTA exits.
+#include <mutex>
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -751,11 +752,12 @@ void launch_t(const TcModel& t, const CallArgs& a, const DevWeights& w, int n_ti
 {
     int dev = 0;
     cudaGetDevice(&dev);
-    static bool done[64] = {};
-    if (dev >= 0 && dev < 64 && !done[dev]) {
-        cudaFuncSetAttribute(mlp_tc_kernel<PREC, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<PREC>::DYN);
-        done[dev] = true;
-    }
+    static std::once_flag done[64];            // once per device, safe across host threads
+    if (dev >= 0 && dev < 64)
+        std::call_once(done[dev], [] {
+            cudaFuncSetAttribute(mlp_tc_kernel<PREC, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 Smem<PREC>::DYN);
+        });
     const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(t.wmap);
     const CUtensorMap* map1 = reinterpret_cast<const CUtensorMap*>(t.w1map);
     mlp_tc_kernel<PREC, ACT><<<grid, NUM_THREADS, Smem<PREC>::DYN, s>>>(*map, *map1, a, w, n_tiles);

@@ -2,9 +2,10 @@
 // motions over one or more scenes are validated and uploaded once, with the
 // plan's own workspace; a launch then only enqueues the kernels of a check
 // call (no host synchronisation, no allocation), so it can be captured in a
-// CUDA graph and replayed.  An autotuner times the verifier's launch shapes
-// (points per thread, CTAs per SM) on the plan's own data and keeps the
-// fastest.
+// CUDA graph and replayed.  An autotuner times the launch shapes on the
+// plan's own data and keeps the fastest: the persistent grid of the
+// tensor-core network kernel (CTAs, one per SM at most), then the verifier's
+// points per thread and CTAs per SM.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -26,6 +27,7 @@ struct svm_plan {
     size_t o_q0 = 0, o_q1 = 0, o_pbeg = 0, o_pend = 0, o_toff = 0, o_poff = 0;
     size_t o_caps = 0, o_fk64 = 0, o_cbias = 0, o_st = 0, o_idx = 0, o_chunk = 0, o_err = 0, o_tie = 0, total = 0;
     VerifyConfig vcfg{};
+    int net_grid = 0;                 // CTAs of the tensor-core network kernel (0 = one per SM)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     const void* g_points = nullptr;
@@ -107,7 +109,8 @@ svm_status enqueue(svm_plan* p, const float* points, svm_result* results, cudaSt
     launch_prologue_fk(a, m->rp, m->dw, s);
     if (!(p->flags & SVM_VERIFY_ALL)) {
         if (m->desc.prec != SVM_FP32) {
-            if (tc_launch(m->tc, a, m->dw, p->n_tiles, nullptr, m->n_sms, s) != 0)
+            const int grid = p->net_grid > 0 && p->net_grid < m->n_sms ? p->net_grid : m->n_sms;
+            if (tc_launch(m->tc, a, m->dw, p->n_tiles, nullptr, grid, s) != 0)
                 return pfail(m, SVM_E_CUDA, "tensor-core launch failed");
         } else {
             launch_mlp_fp32(a, m->dw, p->n_tiles, p->bm, s);
@@ -297,6 +300,17 @@ svm_status svm_plan_set_verify_shape(svm_plan* p, int32_t points_per_thread, int
     return SVM_OK;
 }
 
+svm_status svm_plan_set_network_grid(svm_plan* p, int32_t ctas)
+{
+    if (!p) return SVM_E_INVALID;
+    if (ctas < 0 || ctas > p->m->n_sms) return pfail(p->m, SVM_E_INVALID, "ctas must be 0..number of SMs");
+    p->net_grid = ctas;
+    Guard g(p->m->device);
+    cudaDeviceSynchronize();
+    drop_graph(p);
+    return SVM_OK;
+}
+
 svm_status svm_plan_autotune(svm_plan* p, const float* points_dev, svm_result* results_dev, void* stream,
                              char* report, size_t capacity)
 {
@@ -306,28 +320,53 @@ svm_status svm_plan_autotune(svm_plan* p, const float* points_dev, svm_result* r
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return pfail(p->m, SVM_E_CUDA, "event creation failed");
+    svm_status st = SVM_OK;
+    // mean time of 3 launches after one warm-up launch, CUDA events on the plan's stream
+    auto time_launch = [&](float& ms) {
+        st = enqueue(p, points_dev, results_dev, s);
+        if (st != SVM_OK) return false;
+        cudaEventRecord(e0, s);
+        const int reps = 3;
+        for (int r = 0; r < reps && st == SVM_OK; ++r) st = enqueue(p, points_dev, results_dev, s);
+        cudaEventRecord(e1, s);
+        if (st != SVM_OK) return false;
+        if (cudaEventSynchronize(e1) != cudaSuccess) { st = pfail(p->m, SVM_E_CUDA, "autotune timing failed"); return false; }
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        return true;
+    };
+    std::string rep = "{\"network_candidates\": [";
+    char buf[192];
+    // 1. the network kernel's persistent grid (tensor-core models run the network)
+    const bool net = p->m->desc.prec != SVM_FP32 && !(p->flags & SVM_VERIFY_ALL);
+    const int n_sms = p->m->n_sms;
+    int best_grid = p->net_grid;
+    if (net) {
+        const int grids[5] = {n_sms, n_sms - n_sms / 16, n_sms - n_sms / 8, (3 * n_sms) / 4, n_sms / 2};
+        float best = INFINITY;
+        for (int i = 0; i < 5 && st == SVM_OK; ++i) {
+            p->net_grid = grids[i];
+            float ms = 0.0f;
+            if (!time_launch(ms)) break;
+            std::snprintf(buf, sizeof buf, "%s{\"grid\": %d, \"ms\": %.4f}", i ? ", " : "", grids[i], ms);
+            rep += buf;
+            if (ms < best) { best = ms; best_grid = grids[i]; }
+        }
+    }
+    p->net_grid = best_grid;
+    // 2. the verifier's shape at that grid
     const int ppts[3] = {1, 2, 4};
     const int ctas[3] = {0, 4, 2};
     float best = INFINITY;
     VerifyConfig best_cfg = p->vcfg;
-    std::string rep = "{\"candidates\": [";
+    rep += "], \"candidates\": [";
     bool first = true;
-    svm_status st = SVM_OK;
     for (int a = 0; a < 3 && st == SVM_OK; ++a)
         for (int b = 0; b < 3 && st == SVM_OK; ++b) {
             p->vcfg.points_per_thread = ppts[a];
             p->vcfg.ctas_per_sm = ctas[b];
-            st = enqueue(p, points_dev, results_dev, s);          // warm-up
-            if (st != SVM_OK) break;
-            cudaEventRecord(e0, s);
-            const int reps = 3;
-            for (int r = 0; r < reps && st == SVM_OK; ++r) st = enqueue(p, points_dev, results_dev, s);
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) { st = pfail(p->m, SVM_E_CUDA, "autotune timing failed"); break; }
             float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            ms /= reps;
-            char buf[128];
+            if (!time_launch(ms)) break;
             std::snprintf(buf, sizeof buf, "%s{\"points_per_thread\": %d, \"ctas_per_sm\": %d, \"ms\": %.4f}",
                           first ? "" : ", ", ppts[a], ctas[b], ms);
             rep += buf;
@@ -339,9 +378,10 @@ svm_status svm_plan_autotune(svm_plan* p, const float* points_dev, svm_result* r
     p->vcfg = best_cfg;
     drop_graph(p);
     if (st != SVM_OK) return st;
-    char buf[160];
-    std::snprintf(buf, sizeof buf, "], \"best\": {\"points_per_thread\": %d, \"ctas_per_sm\": %d, \"ms\": %.4f}}",
-                  best_cfg.points_per_thread, best_cfg.ctas_per_sm, best);
+    std::snprintf(buf, sizeof buf,
+                  "], \"best\": {\"network_grid\": %d, \"points_per_thread\": %d, \"ctas_per_sm\": %d, "
+                  "\"ms\": %.4f}}",
+                  p->net_grid > 0 ? p->net_grid : n_sms, best_cfg.points_per_thread, best_cfg.ctas_per_sm, best);
     rep += buf;
     if (report && capacity > 0) {
         const size_t n = std::min(capacity - 1, rep.size());

@@ -110,6 +110,8 @@ __global__ void __launch_bounds__(128) prologue_kernel(CallArgs A, RobotParams R
         z.witness_step = -1;
         z.n_ambiguous = 0;
         z.probe_key = ~0ull;
+        z.inexact = 0;
+        z.pad = 0;
         A.st[m] = z;
         if (m == 0 && A.tie_count) *A.tie_count = 0;
     }

@@ -313,6 +313,13 @@ svm_status svm_test_expire_wait(svm_model* m, int32_t n_calls)
     return SVM_OK;
 }
 
+svm_status svm_test_set_tie_cap(svm_model* m, int32_t cap)
+{
+    if (!m || cap < 0 || cap > kTieCap) return SVM_E_INVALID;
+    m->tie_cap = cap;
+    return SVM_OK;
+}
+
 svm_status svm_set_gate(svm_model* m, float tau)
 {
     if (!m) return SVM_E_INVALID;
@@ -509,7 +516,7 @@ svm_status svm_export_weights(const svm_model* mc, float* out, size_t count, siz
 
 namespace {
 
-enum Mode { kCheck = 0, kEval = 1, kLabel = 2 };
+enum Mode { kCheck = 0, kEval = 1, kLabel = 2, kGate = 3 };
 
 struct CallPlan {
     int M, N;
@@ -527,12 +534,13 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
                     int32_t n_scenes, float margin, int32_t steps, uint32_t flags, void* results_dev,
                     float* out_dev, cudaStream_t stream)
 {
-    const Range call_range(mode == kCheck ? "svm_check" : mode == kEval ? "svm_eval_pairs" : "svm_label_pairs");
+    const Range call_range(mode == kCheck ? "svm_check" : mode == kEval ? "svm_eval_pairs"
+                           : mode == kLabel ? "svm_label_pairs" : "svm_calibrate_gate");
     const svm_model_desc& d = m->desc;
     if (M < 0) return fail(m, SVM_E_INVALID, "n_motions < 0");
     if (M > 0 && (!q0 || !q1)) return fail(m, SVM_E_INVALID, "null q0/q1");
     if (n_scenes < 1 || !scene_off) return fail(m, SVM_E_INVALID, "no scene");
-    if (mode != kLabel && !m->has_weights && !(flags & SVM_VERIFY_ALL))
+    if (mode != kLabel && mode != kGate && !m->has_weights && !(flags & SVM_VERIFY_ALL))
         return fail(m, SVM_E_WEIGHTS, "no weights loaded");
     if (mode == kCheck && M > 0 && !results_dev) return fail(m, SVM_E_INVALID, "null results");
     if (mode != kCheck && M > 0 && !out_dev) return fail(m, SVM_E_INVALID, "null output");
@@ -674,7 +682,8 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
     a.points = reinterpret_cast<const float4*>(points_dev);
     a.caps = reinterpret_cast<Capsule*>(ws + pl.o_caps);
     a.fk64 = reinterpret_cast<double*>(ws + pl.o_fk64);
-    a.cbias = (mode == kLabel || (flags & SVM_VERIFY_ALL)) ? nullptr : reinterpret_cast<float*>(ws + pl.o_cbias);
+    a.cbias = (mode == kLabel || mode == kGate || (flags & SVM_VERIFY_ALL)) ? nullptr
+                                                                           : reinterpret_cast<float*>(ws + pl.o_cbias);
     a.st = reinterpret_cast<MotionState*>(ws + pl.o_st);
     a.idx = reinterpret_cast<unsigned*>(ws + pl.o_idx);
     a.chunk_off = reinterpret_cast<int*>(ws + pl.o_chunk);
@@ -690,6 +699,7 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
     a.dev_err = static_cast<unsigned int*>(tc_ws);
     a.tie_count = reinterpret_cast<unsigned int*>(ws + pl.o_tie);
     a.tie_list = reinterpret_cast<TiePair*>(ws + pl.o_tie + 256);
+    a.tie_cap = m->tie_cap;
     CK(cudaMemsetAsync(a.dev_err, 0, sizeof(unsigned int), stream));
 
     {
@@ -700,6 +710,12 @@ svm_status run_call(svm_model* m, Mode mode, const double* q0, const double* q1,
     if (mode == kLabel) {
         const Range r("label");
         launch_label(a, out_dev, a.f_stride, stream);
+        CK(cudaGetLastError());
+        return SVM_OK;
+    }
+    if (mode == kGate) {
+        const Range r("overestimate");
+        launch_gate_overestimate(a, out_dev, a.f_stride, m->gate_cut, m->gate_out, stream);
         CK(cudaGetLastError());
         return SVM_OK;
     }
@@ -854,6 +870,65 @@ svm_status svm_calibrate_act_scales(svm_model* m, const double* q0, const double
     return svm_set_act_scales(m, sc.data(), d.n_hidden);
 }
 
+svm_status svm_calibrate_gate(svm_model* m, const double* q0, const double* q1, int32_t n_motions,
+                              const float* points_dev, int64_t n_points, float margin, int32_t steps, float band,
+                              float safety, float* tau_out, float* overestimate_out, int64_t* n_near_out,
+                              void* stream_v)
+{
+    if (!m) return SVM_E_INVALID;
+    if (!m->has_weights) return fail(m, SVM_E_WEIGHTS, "no weights loaded");
+    if (n_motions < 1 || n_points < 1) return fail(m, SVM_E_INVALID, "empty calibration set");
+    if ((long long)n_motions * n_points > 0xffffffffLL) return fail(m, SVM_E_INVALID, "calibration set too large");
+    if (!(band >= 0) || !std::isfinite(band)) return fail(m, SVM_E_INVALID, "band must be finite and >= 0");
+    if (!(safety >= 1) || !std::isfinite(safety)) return fail(m, SVM_E_INVALID, "safety must be finite and >= 1");
+    if (!(margin >= 0) || !std::isfinite(margin)) return fail(m, SVM_E_INVALID, "margin must be finite and >= 0");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    DeviceGuard g(m->device);
+    // motions in chunks whose network outputs fit in a bounded buffer (at most 2^26 floats)
+    const long long cap = 1LL << 26;
+    const int chunk = (int)std::max<long long>(1, std::min<long long>(n_motions, cap / n_points));
+    float* fbuf = nullptr;
+    unsigned int* outd = nullptr;
+    if (cudaMalloc(&fbuf, sizeof(float) * (size_t)chunk * n_points) != cudaSuccess ||
+        cudaMalloc(&outd, 2 * sizeof(unsigned int)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(fbuf);
+        return fail(m, SVM_E_OOM, "calibration buffer");
+    }
+    svm_status st = SVM_OK;
+    cudaError_t e = cudaMemsetAsync(outd, 0, 2 * sizeof(unsigned int), stream);
+    m->gate_out = outd;
+    m->gate_cut = (float)((double)margin + (double)band);
+    const int64_t off[2] = {0, n_points};
+    for (int c0 = 0; c0 < n_motions && st == SVM_OK && e == cudaSuccess; c0 += chunk) {
+        const int cm = std::min(chunk, n_motions - c0);
+        st = run_call(m, kEval, q0 + 6LL * c0, q1 + 6LL * c0, cm, nullptr, points_dev, off, 1, 0.0f, 1, 0u,
+                      nullptr, fbuf, stream);
+        if (st == SVM_OK)
+            st = run_call(m, kGate, q0 + 6LL * c0, q1 + 6LL * c0, cm, nullptr, points_dev, off, 1, 0.0f, steps,
+                          0u, nullptr, fbuf, stream);
+    }
+    m->gate_out = nullptr;
+    unsigned int h[2] = {0u, 0u};
+    if (st == SVM_OK && e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (st == SVM_OK && e == cudaSuccess) e = cudaMemcpy(h, outd, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(fbuf);
+    cudaFree(outd);
+    if (st != SVM_OK) return st;
+    if (e != cudaSuccess) return fail(m, SVM_E_CUDA, cudaGetErrorString(e));
+    float over = -INFINITY;
+    if (h[1] > 0) {
+        const unsigned int k = h[0];
+        const unsigned int u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+        std::memcpy(&over, &u, 4);
+    }
+    const float tau = h[1] > 0 ? (float)std::max(0.0, (double)safety * (double)over) : 0.0f;
+    if (tau_out) *tau_out = tau;
+    if (overestimate_out) *overestimate_out = over;
+    if (n_near_out) *n_near_out = (int64_t)h[1];
+    return svm_set_gate(m, tau);
+}
+
 svm_status svm_profile_enable(svm_model* m, int on)
 {
     if (!m) return SVM_E_INVALID;
@@ -937,7 +1012,7 @@ svm_status svm_search_free_motion(svm_model* m, const double* q0, const double* 
         CK(cudaMemcpyAsync(rh, rd, (size_t)M * sizeof(svm_result), cudaMemcpyDeviceToHost, stream));
         CK(cudaStreamSynchronize(stream));
         for (int i = 0; i < M; ++i) {
-            if (rh[i].status != 0) return fail(m, SVM_E_TIMEOUT, "a device wait expired");
+            if (rh[i].status == 1) return fail(m, SVM_E_TIMEOUT, "a device wait expired");
             dhat[i] = rh[i].dhat_min;      // a path's: the minimum over its segments
         }
         out->n_nn = n_motions;
@@ -967,7 +1042,7 @@ svm_status svm_search_free_motion(svm_model* m, const double* q0, const double* 
             }
             out->n_exact_run += nw;
             for (int k = 0; k < nw; ++k) {
-                if (rh[k].status != 0) {
+                if (rh[k].status == 1) {
                     st = fail(m, SVM_E_TIMEOUT, "a device wait expired");
                     return;
                 }
@@ -1088,6 +1163,24 @@ extern "C" svm_status svm_check_motions_noalloc(svm_model* m, const double* q0_d
     if (!q0_dev || !q1_dev || !results_dev) return fail(m, SVM_E_INVALID, "null q0/q1/results");
     if (n_points > 0 && !points_dev) return fail(m, SVM_E_INVALID, "null points");
     if (reinterpret_cast<uintptr_t>(points_dev) % 16) return fail(m, SVM_E_INVALID, "points not 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(q0_dev) % 8 || reinterpret_cast<uintptr_t>(q1_dev) % 8)
+        return fail(m, SVM_E_INVALID, "q0/q1 not 8-byte aligned");
+    {
+        // q0/q1 are read by the prologue kernel: they must be memory the device can address
+        // (device or managed memory), not pageable host memory
+        const void* ptrs[2] = {q0_dev, q1_dev};
+        for (const void* p : ptrs) {
+            cudaPointerAttributes at{};
+            if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(m, SVM_E_INVALID, "q0/q1 is not a CUDA pointer");
+            }
+            if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+                return fail(m, SVM_E_INVALID, "q0/q1 must be device or managed memory");
+            if (at.type == cudaMemoryTypeDevice && at.device != m->device)
+                return fail(m, SVM_E_INVALID, "q0/q1 live on another device than the model");
+        }
+    }
     if (!m->has_weights && !(flags & SVM_VERIFY_ALL)) return fail(m, SVM_E_WEIGHTS, "no weights loaded");
     if (!(margin >= 0) || !std::isfinite(margin)) return fail(m, SVM_E_INVALID, "margin must be finite and >= 0");
     if (steps < 1 || steps > kMaxSteps) return fail(m, SVM_E_INVALID, "steps out of range");

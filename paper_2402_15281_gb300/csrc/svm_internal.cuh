@@ -62,6 +62,9 @@ struct MotionState {
     unsigned int n_ambiguous;
     unsigned long long probe_key;   // (float_key(f) << 32) | point index of the motion's
                                     // smallest flagged prediction; ~0 if none
+    unsigned int inexact;           // 1 if a pair of this motion at the margin found the tie
+                                    // list full and was decided in FP32
+    unsigned int pad;
 };
 
 // Order-preserving float <-> uint32 map: unsigned comparison of keys equals
@@ -119,7 +122,13 @@ struct CallArgs {
     double* fk64;           // [M][N+1][8][3]: joint origins o_0..o_6 and tool axis of every sample, FP64
     unsigned int* tie_count;    // pairs appended to tie_list (reset by the prologue)
     TiePair* tie_list;          // [kTieCap] pairs deferred to the FP64 tie kernel
+    int tie_cap;                // list entries used, 1..kTieCap (0 = kTieCap); lowered by a test hook
 };
+
+// Entries of the tie list a call may use.
+__device__ __forceinline__ unsigned tie_capacity(const CallArgs& A) {
+    return (A.tie_cap > 0 && A.tie_cap < kTieCap) ? (unsigned)A.tie_cap : (unsigned)kTieCap;
+}
 
 // Model weights on the device.  FP32 copies are always present; the layer-1
 // and output weights hold the values of the model precision (BF16-rounded in
@@ -210,6 +219,10 @@ void launch_verify_cfg(const CallArgs& a, int range_mode, int strict_pass, cudaS
 void launch_ties(const CallArgs& a, cudaStream_t s, int n_sms);
 void launch_finalize(const CallArgs& a, void* results, cudaStream_t s);
 void launch_label(const CallArgs& a, float* delta, long long stride, cudaStream_t s);
+// out[0] = ordered key of max (f - delta) over pairs with delta <= near_cut (atomicMax; 0 if
+// none), out[1] += their count; out must be zeroed by the caller before the first launch.
+void launch_gate_overestimate(const CallArgs& a, const float* f, long long stride, float near_cut,
+                              unsigned int* out, cudaStream_t s);
 void launch_quantize_bf16(const float* in, uint16_t* out, long long n, cudaStream_t s);
 void launch_round_bf16(float* inout, long long n, cudaStream_t s);
 void launch_quantize_e4m3(const float* in, uint8_t* out, float* deq, long long n, float scale, cudaStream_t s);

@@ -37,7 +37,10 @@ struct svm_model {
     bool prof_valid = false;
     cudaEvent_t ev[5] = {};
     unsigned int* calib_amax = nullptr;   // set only on a calibration model
+    unsigned int* gate_out = nullptr;     // during svm_calibrate_gate: [2] max key and count
+    float gate_cut = 0.0f;                // during svm_calibrate_gate: margin + band
     int test_stalls = 0;                   // check calls left to run with the test stall
+    int tie_cap = 0;                       // tie-list entries per call (0 = all); a test hook
     std::string last_error;
 };
 

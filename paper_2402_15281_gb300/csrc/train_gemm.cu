@@ -21,6 +21,7 @@
 // MMAs of the next.  Transposed outputs are staged per warp in shared memory
 // (a padded 32 x 32 tile) and written as 64-byte row segments.
 // All mbarrier waits are bounded (see tc_ptx.cuh).
+#include <mutex>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -302,11 +303,11 @@ void launch_t(const CUtensorMap& a, const CUtensorMap& b, const GemmArgs& g, int
 {
     int dev = 0;
     cudaGetDevice(&dev);
-    static bool done[64] = {};
-    if (dev >= 0 && dev < 64 && !done[dev]) {
-        cudaFuncSetAttribute(train_gemm_kernel<EPI, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_DYN);
-        done[dev] = true;
-    }
+    static std::once_flag done[64];            // once per device, safe across host threads
+    if (dev >= 0 && dev < 64)
+        std::call_once(done[dev], [] {
+            cudaFuncSetAttribute(train_gemm_kernel<EPI, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_DYN);
+        });
     train_gemm_kernel<EPI, ACT><<<grid, THREADS, SMEM_DYN, s>>>(a, b, g);
 }
 

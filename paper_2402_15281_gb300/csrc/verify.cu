@@ -14,6 +14,7 @@
 // (sub/mul/fma.rn.f32x2: two capsules per instruction, the same roundings as
 // the scalar expressions); points are read as float4.  A motion that has collided stops
 // its remaining chunks (early exit), as Algorithm 1 needs only the verdict.
+#include <mutex>
 #include "svm_internal.cuh"
 
 namespace svm {
@@ -261,14 +262,15 @@ __global__ void __launch_bounds__(VT) verify_kernel(CallArgs A, int strict_pass)
             for (int q = 0; q < kCaps; ++q) d = fminf(d, sqrtf(mn[j][q]) - s_r[q]);
             atomicAdd(&s_nver, 1u);
             // within the FP32 error band of the margin: the FP64 tie kernel decides
-            // (FP32 verdict only if the tie list is full)
+            // (if the tie list is full, the FP32 verdict stands and the record says so)
             if (fabsf(d - A.margin) < kAmbiguousBand) {
                 atomicAdd(&s_namb, 1u);
                 const unsigned slot = atomicAdd(A.tie_count, 1u);
-                if (slot < (unsigned)kTieCap) {
+                if (slot < tie_capacity(A)) {
                     A.tie_list[slot] = TiePair{m, 0, pidx[j]};
                     continue;
                 }
+                atomicExch(&A.st[m].inexact, 1u);
             }
             atomicMin(&s_dkey, float_key(d));
             if (d <= A.margin) {
@@ -310,6 +312,48 @@ __global__ void __launch_bounds__(VT) label_kernel(CallArgs A, float* delta, lon
     }
 }
 
+// Gate calibration (the margin widened by the measured error of the network):
+// the largest overestimate f - delta over the pairs that can collide, delta <=
+// near_cut, where f is the network output of the pair (row stride `stride`)
+// and delta its exact distance, computed with the label kernel's arithmetic
+// (bit for bit the value svm_label_pairs writes; it is never stored).  out[0]
+// takes the ordered key of the maximum by atomicMax (0 if no pair qualifies),
+// out[1] counts the qualifying pairs; a maximum does not depend on the order
+// of the updates, so the result is deterministic.
+__global__ void __launch_bounds__(VT) gate_overestimate_kernel(CallArgs A, const float* f, long long stride,
+                                                             float near_cut, unsigned int* out)
+{
+    extern __shared__ __align__(16) unsigned char vsm[];
+    Capsule* cs = reinterpret_cast<Capsule*>(vsm);
+    const int m = blockIdx.y;
+    const int n_samples = A.N + 1;
+    const float4* src = reinterpret_cast<const float4*>(A.caps + (long long)m * n_samples * kCaps);
+    float4* dst = reinterpret_cast<float4*>(cs);
+    for (int i = threadIdx.x; i < n_samples * kCaps * 2; i += VT) dst[i] = __ldg(src + i);
+    __syncthreads();
+    const long long n = A.pend[m] - A.pbeg[m];
+    unsigned int best = 0u, cnt = 0u;
+    for (long long local = (long long)blockIdx.x * VT + threadIdx.x; local < n; local += (long long)gridDim.x * VT) {
+        const float4 x4 = __ldg(A.points + A.pbeg[m] + local);
+        float mn[kCaps];
+        scan_samples(cs, n_samples, make_float3(x4.x, x4.y, x4.z), mn);
+        const float delta = capsule_min(mn, cs);
+        if (delta <= near_cut) {
+            best = max(best, float_key(__ldg(f + (long long)m * stride + local) - delta));
+            ++cnt;
+        }
+    }
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if ((threadIdx.x & 31) == 0 && cnt) {
+        atomicMax(out, best);
+        atomicAdd(out + 1, cnt);
+    }
+}
+
 // FP64 decision of the pairs the verifier deferred (FP32 distance within
 // kAmbiguousBand of the margin).  One warp per pair, consecutive pairs on
 // different CTAs (FP64 throughput is per SM).  The lanes first take the FP32
@@ -323,7 +367,7 @@ __global__ void __launch_bounds__(VT) label_kernel(CallArgs A, float* delta, lon
 // the witness is the first colliding sample.
 __global__ void __launch_bounds__(256) tie_kernel(CallArgs A)
 {
-    const unsigned n = min(*A.tie_count, (unsigned)kTieCap);
+    const unsigned n = min(*A.tie_count, tie_capacity(A));
     const int lane = threadIdx.x & 31;
     const unsigned n_warps = gridDim.x * (blockDim.x >> 5);
     const int n_items = (A.N + 1) * kCaps;
@@ -438,8 +482,10 @@ __global__ void finalize_kernel(CallArgs A, ResultRec* out)
     o.witness_point = -1;
     o.witness_step = -1;
     o.n_ambiguous = 0;
+    bool inexact = false;
     for (int s = 0; s < seg; ++s) {
         const MotionState st = A.st[r * seg + s];
+        inexact = inexact || st.inexact != 0u;
         dk = min(dk, st.dmin_key);
         hk = min(hk, st.dhat_key);
         o.n_flagged += st.n_flagged;
@@ -455,6 +501,7 @@ __global__ void finalize_kernel(CallArgs A, ResultRec* out)
     o.early_exit = (early && o.collision) ? 1 : 0;
     o.d_min = key_float(dk);
     o.dhat_min = key_float(hk);
+    if (o.status == 0 && inexact) o.status = 2;
     out[r] = o;
 }
 
@@ -463,12 +510,12 @@ __global__ void finalize_kernel(CallArgs A, ResultRec* out)
 namespace {
 // The capsule table of one motion can exceed the default 48 KB of dynamic
 // shared memory; raise the limit once per device for the kernels that stage it.
-void configure_smem()
+// The kernels' shared-memory limits, set once per device; call_once makes the
+// first calls from several host threads on one device safe.
+std::once_flag g_smem_once[64];
+
+void configure_smem_now()
 {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    static bool configured[64] = {};
-    if (dev < 0 || dev >= 64 || configured[dev]) return;
     const int mx = (kMaxSteps + 1) * kCaps * (int)sizeof(Capsule);
     cudaFuncSetAttribute(verify_kernel<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(verify_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -477,7 +524,15 @@ void configure_smem()
     cudaFuncSetAttribute(verify_kernel<0, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(verify_kernel<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(label_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    configured[dev] = true;
+    cudaFuncSetAttribute(gate_overestimate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+}
+
+void configure_smem()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return;
+    std::call_once(g_smem_once[dev], configure_smem_now);
 }
 }  // namespace
 
@@ -520,6 +575,16 @@ void launch_label(const CallArgs& a, float* delta, long long stride, cudaStream_
     const size_t smem = (size_t)(a.N + 1) * kCaps * sizeof(Capsule);
     const int gx = 64;
     label_kernel<<<dim3(gx, a.M), VT, smem, s>>>(a, delta, stride);
+}
+
+void launch_gate_overestimate(const CallArgs& a, const float* f, long long stride, float near_cut,
+                              unsigned int* out, cudaStream_t s)
+{
+    if (a.M <= 0) return;
+    configure_smem();
+    const size_t smem = (size_t)(a.N + 1) * kCaps * sizeof(Capsule);
+    const int gx = 64;
+    gate_overestimate_kernel<<<dim3(gx, a.M), VT, smem, s>>>(a, f, stride, near_cut, out);
 }
 
 void launch_ties(const CallArgs& a, cudaStream_t s, int n_sms)

@@ -3,8 +3,8 @@
 Only orchestration lives here: the epoch loop, the learning-rate schedule of
 Sec. V (Adam at lr 1e-3, reduced by 10x after `patience` epochs without a
 better validation error, best-validation weights kept) and the split of the
-motions into training and validation sets (60/25/15 by motion in the paper;
-here train/validation only).  Data generation, labels, forward, backward and
+motions into training, validation and (optionally) test sets (60/25/15 by
+motion in the paper).  Data generation, labels, forward, backward and
 Adam run in the library's kernels.
 """
 from __future__ import annotations
@@ -55,14 +55,18 @@ def grasp_training_motions(robot, n, seed):
 
 def train_model(svm, robot, q0, q1, width=256, n_hidden=4, act=0, samples_per_motion=4096, steps=128,
                 batch=65536, epochs=30, lr=1e-3, val_fraction=0.2, patience=10, data_seed=7, init_seed=2,
-                device=0, log=None, box=None):
+                device=0, log=None, box=None, test_fraction=0.0):
     """Train f on GPU-generated data for the motions (q0, q1); box = (lo, hi)
-    sets the box of the uniformly drawn points.  Returns (blob of the
-    best-validation weights, history dict)."""
+    sets the box of the uniformly drawn points.  The motions split in order
+    into training, validation (val_fraction) and test (test_fraction) sets;
+    data is generated for all of them.  Returns (blob of the best-validation
+    weights, history dict); with a test set the history holds its mean
+    absolute error under the best weights ("test_mae") and its sample range."""
     t0 = time.perf_counter()
     n = len(q0)
+    n_te = int(round(n * test_fraction))
     n_val = max(1, int(round(n * val_fraction)))
-    n_tr = n - n_val
+    n_tr = n - n_val - n_te
     t = svm.svm_train_create(robot, width, n_hidden, act, batch, device)
     hist = {"epoch_loss": [], "val_mae": [], "lr": []}
     try:
@@ -71,7 +75,7 @@ def train_model(svm, robot, q0, q1, width=256, n_hidden=4, act=0, samples_per_mo
             svm.svm_train_set_box(t, box[0], box[1])
         svm.svm_train_make_data(t, q0, q1, samples_per_motion, steps, data_seed)
         tr_end = n_tr * samples_per_motion
-        va_end = n * samples_per_motion
+        va_end = (n_tr + n_val) * samples_per_motion
         best, best_blob, stale = np.inf, None, 0
         t_train = 0.0
         for e in range(epochs):
@@ -93,6 +97,11 @@ def train_model(svm, robot, q0, q1, width=256, n_hidden=4, act=0, samples_per_mo
                     stale = 0
         hist["best_val_mae"] = float(best)
         hist["train_samples"] = int(tr_end)
+        hist["total_samples"] = int(n * samples_per_motion)
+        if n_te > 0:
+            svm.svm_train_set_weights(t, best_blob)
+            hist["test_mae"] = float(svm.svm_train_evaluate(t, va_end, n * samples_per_motion))
+            hist["test_motions"] = (n_tr + n_val, n)
         hist["samples_per_s"] = float(epochs * (tr_end // batch) * batch / max(t_train, 1e-9))
         hist["seconds"] = time.perf_counter() - t0
         return best_blob, hist
@@ -101,17 +110,10 @@ def train_model(svm, robot, q0, q1, width=256, n_hidden=4, act=0, samples_per_mo
 
 
 def calibrate_tau(svm, model, robot, pts_d, margin, steps, q0, q1, band=0.05, safety=1.25):
-    """Gate offset tau = safety * max(f - delta) over calibration pairs whose
-    exact distance is within margin + band (pairs that can collide), never
-    below 0.  f comes from the model's own kernels in its precision, delta
-    from the exact label kernel."""
-    import torch
-    f = torch.empty((len(q0), pts_d.shape[0]), device=pts_d.device)
-    d = torch.empty_like(f)
-    svm.svm_eval_pairs(model, q0, q1, pts_d, f)
-    svm.svm_label_pairs(model, q0, q1, pts_d, steps, d)
-    near = d <= margin + band
-    if not bool(near.any()):
-        return 0.0
-    over = torch.where(near, f - d, torch.full_like(f, -float("inf"))).max().item()
-    return max(0.0, safety * over)
+    """Set the model's gate from calibration motions and return its offset:
+    tau = safety * max(f - delta) over the calibration pairs whose exact
+    distance is within margin + band (pairs that can collide), never below 0.
+    The whole computation (network in the model's precision, exact labels,
+    the maximum) runs in the library's svm_calibrate_gate."""
+    tau, _, _ = svm.svm_calibrate_gate(model, q0, q1, pts_d, margin, steps, band, safety)
+    return tau

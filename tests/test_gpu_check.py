@@ -377,3 +377,54 @@ def test_margin_ties_decided_in_fp64(svm, robot, prec, gated):
                     assert r["witness_point"][j] == 0 and 0 <= r["witness_step"][j] <= N
     finally:
         m.close()
+
+
+def test_tie_list_overflow_is_reported(svm, robot):
+    """Pairs at the margin beyond the tie list's capacity keep their FP32
+    decision, and the record says so: with the list cut to 4 entries by the
+    test hook, a motion with many points whose exact distance lies a few
+    1e-7 m above the margin (all within the 4e-6 m band, FP64: free) carries
+    status 2, and the motion without such points status 0; with the full list
+    every such pair is decided in FP64, the verdicts equal the oracle's (Eq. 5)
+    and every status is 0."""
+    q0, _ = S.uniform_motions(robot, 2, seed=31)
+    N = 4
+    A, B = oracle.capsules(robot, q0[0])
+    j = 1                                              # the upper arm, 0.47 m long
+    a, e, r = A[j], B[j] - A[j], robot.radius[j]
+    u = e / np.linalg.norm(e)
+    n1 = np.cross(u, [0.0, 0.0, 1.0] if abs(u[2]) < 0.9 else [1.0, 0.0, 0.0])
+    n1 /= np.linalg.norm(n1)
+    n2 = np.cross(u, n1)
+    g = S.Rng(5, 1)
+    t, th = g.uniform(4000, 0.2, 0.8), g.uniform(4000, 0.0, 2 * np.pi)
+    D = 0.05
+    cand = a + t[:, None] * e + (r + D) * (np.cos(th)[:, None] * n1 + np.sin(th)[:, None] * n2)
+    pts = np.zeros((len(cand), 4), np.float32)
+    pts[:, :3] = cand
+    d0 = oracle.swept_sdf_batch(robot, q0[:1], q0[:1], N, pts)[0]
+    keep = np.abs(d0 - D) < 1e-6                        # capsule j is the nearest part of the robot
+    pts = np.ascontiguousarray(pts[keep][:300])
+    assert len(pts) >= 50
+    q0s, q1s = q0.copy(), q0.copy()                   # two static motions; the second poses elsewhere
+    delta = oracle.swept_sdf_batch(robot, q0s, q1s, N, pts)
+    eps = float(np.float32(delta[0].min() - 2e-7))
+    assert np.all(delta[0] - eps < 3e-6)                 # every point of motion 0 is at the margin
+    want = (delta.min(axis=1) <= eps).astype(np.uint8)
+    m = Model(svm, robot, _layers(), prec=0)
+    flags = svm.SVM_VERIFY_ALL | svm.SVM_NO_EARLY_EXIT
+    try:
+        r = _check(svm, m, q0s, q1s, pts, eps, N, flags)
+        np.testing.assert_array_equal(r["collision"], want)
+        assert want[0] == 0 and r["n_ambiguous"][0] == len(pts)
+        np.testing.assert_array_equal(r["status"], [0, 0])
+        svm.svm_test_set_tie_cap(m.h, 4)
+        r = _check(svm, m, q0s, q1s, pts, eps, N, flags)
+        assert r["n_ambiguous"][0] == len(pts) and r["status"][0] == 2
+        assert r["status"][1] == 0 and r["n_ambiguous"][1] == 0 and r["collision"][1] == want[1]
+        svm.svm_test_set_tie_cap(m.h, 0)
+        r = _check(svm, m, q0s, q1s, pts, eps, N, flags)
+        np.testing.assert_array_equal(r["status"], [0, 0])
+        np.testing.assert_array_equal(r["collision"], want)
+    finally:
+        m.close()

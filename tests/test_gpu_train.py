@@ -174,3 +174,68 @@ def test_training_throughput_512x6_silu(svm, robot):
           f"{hist['samples_per_s'] * flop / 1e12:.0f} TFLOP/s of training arithmetic; "
           f"epoch losses {[round(v, 4) for v in hist['epoch_loss']]}")
     assert hist["epoch_loss"][-1] < hist["epoch_loss"][0]
+
+
+def test_training_50m_samples_512x6_silu_heldout_vs_oracle(svm, robot):
+    """Training at its full stated size (Sec. IV-C data, Sec. V recipe):
+    50.0 M samples (11 112 uniform motions x 4 500, 70 % near the swept
+    surface, 30 % uniform, exact labels at 128 steps) generated on the GPU,
+    network 15 -> 512 x 6 SiLU -> 1, batch 65 536, Adam, split 60/25/15 by
+    motion, best-validation weights.  Held-out error against the FP64 oracle:
+    on 200 test motions the oracle's own sampler (the same SplitMix64 draws)
+    gives 100 points each with FP64 labels; the trained network evaluated by
+    the library (FP32 path) and by the oracle (FP64, same weights) agree to
+    1e-4 m, and their mean absolute error against the FP64 labels is printed
+    with the samples/s and the training arithmetic's fraction of the BF16
+    peak."""
+    import json
+    import os
+    from paper_2402_15281_gb300 import training
+    n_mot, spm, N = 11112, 4500, 128
+    assert n_mot * spm >= 50_000_000
+    q0, q1 = S.uniform_motions(robot, n_mot, seed=61)
+    blob, hist = training.train_model(svm, robot, q0, q1, width=512, n_hidden=6, act=1, samples_per_motion=spm,
+                                      steps=N, batch=65536, epochs=4, patience=2, val_fraction=0.25,
+                                      test_fraction=0.15, data_seed=7)
+    t0, t1 = hist["test_motions"]
+    test = np.arange(t0, t1)[:: (t1 - t0) // 200][:200]
+    pts, lab = [], []
+    for m in test:
+        s = oracle.training_points(robot, q0[m], q1[m], N, 7, int(m), 100)
+        pts.append(s[:, :3])
+        lab.append(s[:, 3])
+    h = svm.svm_create_model(robot, 512, 6, 1, svm.SVM_FP32, 0)
+    try:
+        svm.svm_load_weights(h, blob)
+        cloud = np.zeros((200 * 100, 4), np.float32)
+        cloud[:, :3] = np.concatenate(pts)
+        f = torch.empty((200, 200 * 100), device="cuda")
+        svm.svm_eval_pairs(h, q0[test], q1[test], torch.from_numpy(cloud).cuda(), f)
+        torch.cuda.synchronize()
+        f = f.cpu().numpy()
+        f_lib = np.concatenate([f[i, 100 * i:100 * (i + 1)] for i in range(200)]).astype(np.float64)
+    finally:
+        svm.svm_destroy_model(h)
+    P = oracle.quantized_params(svm.parse_blob(blob), 0)
+    X = np.concatenate([cloud[:, :3].astype(np.float64), np.repeat(q0[test], 100, axis=0),
+                        np.repeat(q1[test], 100, axis=0)], axis=1)
+    f64 = oracle.mlp_forward(P, 512, 6, 1, X)
+    delta = np.concatenate(lab)
+    mae_lib, mae_64 = np.abs(f_lib - delta).mean(), np.abs(f64 - delta).mean()
+    flop = 3 * 2 * (15 * 512 + 6 * 512 * 512 + 512)
+    peaks = {}
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        peaks = json.load(open(path))
+    sust = peaks.get("bf16_tflops_sustained", 1700.0)
+    rate = hist["samples_per_s"] * flop / 1e12
+    print(f"50 M samples 512x6 SiLU: {hist['total_samples'] / 1e6:.1f} M samples, {hist['samples_per_s'] / 1e6:.1f} M "
+          f"samples/s = {rate:.0f} TFLOP/s of training arithmetic = {rate / sust:.1%} of the sustained BF16 peak; "
+          f"epoch losses {[round(v, 4) for v in hist['epoch_loss']]}; validation MAE {hist['best_val_mae']:.4f} m; "
+          f"test MAE (GPU labels) {hist['test_mae']:.4f} m; held-out MAE vs FP64 oracle labels {mae_lib:.4f} m "
+          f"(FP64 network {mae_64:.4f} m); {hist['seconds']:.1f} s in all")
+    assert hist["total_samples"] >= 50_000_000
+    assert hist["epoch_loss"][-1] < hist["epoch_loss"][0]
+    assert np.abs(f_lib - f64).max() <= 1e-4
+    assert abs(mae_lib - hist["test_mae"]) <= 0.25 * hist["test_mae"] + 1e-3
+    assert mae_lib < 0.1

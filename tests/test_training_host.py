@@ -85,27 +85,18 @@ def test_trainer_is_destroyed_when_a_call_fails():
     assert fake.calls[-1] == ("destroy",)
 
 
-def test_calibrate_tau_is_the_widened_overestimate():
-    """tau = 1.25 x max(f - delta) over the calibration pairs whose exact
-    distance is within margin + 0.05 m, and 0 when the network never
-    overestimates there (the gate of Algorithm 1 widened by the measured
-    error); pairs far from the robot do not count."""
-    import torch
-
-    f_vals = torch.tensor([[0.10, 0.02, 0.50], [0.03, 0.30, 0.00]])
-    d_vals = torch.tensor([[0.07, 0.01, 0.20], [0.05, 0.09, 0.02]])   # (0, 2) and (1, 1) are farther than 0.08
+def test_calibrate_tau_calls_the_library():
+    """The host driver holds no gate arithmetic: calibrate_tau passes the
+    calibration set, margin, steps, band (0.05 m) and safety factor (1.25) to
+    the library's svm_calibrate_gate and returns the tau it computed (the GPU
+    test test_gpu_gate.py checks that value)."""
+    calls = []
 
     class Fake:
-        def svm_eval_pairs(self, model, q0, q1, pts, f):
-            f.copy_(f_vals)
+        def svm_calibrate_gate(self, model, q0, q1, pts, margin, steps, band, safety):
+            calls.append((model, q0, q1, pts, margin, steps, band, safety))
+            return 0.0421, 0.0337, 17
 
-        def svm_label_pairs(self, model, q0, q1, pts, steps, d):
-            d.copy_(d_vals)
-
-    pts = torch.zeros((3, 4))
     q = np.zeros((2, 6))
-    tau = training.calibrate_tau(Fake(), None, None, pts, 0.03, 8, q, q)
-    # near pairs: f - d = 0.03, 0.01, -0.02, -0.02 -> 1.25 x 0.03
-    assert abs(tau - 1.25 * 0.03) < 1e-6
-    f_vals.copy_(d_vals - 0.01)                                         # never overestimates
-    assert training.calibrate_tau(Fake(), None, None, pts, 0.03, 8, q, q) == 0.0
+    assert training.calibrate_tau(Fake(), "h", None, "pts", 0.03, 8, q, q) == 0.0421
+    assert calls == [("h", q, q, "pts", 0.03, 8, 0.05, 1.25)]
