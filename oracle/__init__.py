@@ -68,6 +68,7 @@ def lib():
         L.orc_mlp_pairs.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, _D, C.c_int, _D, C.c_long, _D]
         L.orc_mlp_pairs_rounded.argtypes = [_D, C.c_int, C.c_int, C.c_int, C.c_int, _D, _D, _D, C.c_int,
                                             _D, C.c_long, _D]
+        L.orc_mlp_forward_rounded.argtypes = [_D, C.c_int, C.c_int, C.c_int, _I32, _D, _D, C.c_long, _D]
         L.orc_mlp_loss_grad.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, _D, C.c_long, _D]
         L.orc_mlp_loss_grad.restype = C.c_double
         L.orc_adam_step.argtypes = [_D, _D, _D, _D, C.c_long, C.c_long, C.c_double, C.c_double,
@@ -249,6 +250,18 @@ def mlp_pairs_rounded(P, width, n_hidden, act, fmt, scales, q0, q1, points) -> n
     out = np.zeros(M * n)
     lib().orc_mlp_pairs_rounded(_d(P), width, n_hidden, act, int(fmt), sc, q0, q1, M, pts, n, out)
     return out.reshape(M, n)
+
+
+def mlp_forward_rounded(P, width, n_hidden, act, fmts, scales, inputs) -> np.ndarray:
+    """The network on input rows (n, 15) with the input of hidden layer l
+    rounded to format fmts[l] (0 none, 1 bfloat16, 2 E4M3 with scale
+    scales[l]): the error of a precision taken apart layer by layer."""
+    X = _d(inputs).reshape(-1, 15)
+    f = np.ascontiguousarray(fmts, dtype=np.int32).reshape(n_hidden)
+    sc = _d(scales if scales is not None else np.ones(max(1, n_hidden)))
+    out = np.zeros(X.shape[0])
+    lib().orc_mlp_forward_rounded(_d(P), width, n_hidden, act, f, sc, X, X.shape[0], out)
+    return out
 
 
 def mlp_loss_grad(P, width, n_hidden, act, inputs, target):

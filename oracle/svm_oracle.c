@@ -362,10 +362,51 @@ void orc_mlp_pairs(const double *P, int width, int n_hidden, int act,
  * network.  out[m][i] for all pairs, like orc_mlp_pairs. */
 float orc_round_bf16(float v);
 double orc_round_e4m3(double v);
+
+/* One input row through the network with the input of hidden layer l
+ * rounded to format fmts[l] (0 none, 1 bfloat16, 2 E4M3 with scale
+ * scales[l]); h and z hold width doubles each. */
+static double mlp_row_rounded(const double *P, int width, int n_hidden, int act, const int32_t *fmts,
+                              const double *scales, const double *in, double *h, double *z)
+{
+    const double *W = P, *b = P + (long)width * 15;
+    for (int o = 0; o < width; ++o) {
+        double s = b[o];
+        for (int k = 0; k < 15; ++k) s += W[(long)o * 15 + k] * in[k];
+        h[o] = act_f(s, act);
+    }
+    const double *p = b + width;
+    for (int l = 0; l < n_hidden; ++l) {
+        for (int k = 0; k < width; ++k) {
+            if (fmts[l] == 1) h[k] = (double)orc_round_bf16((float)h[k]);
+            if (fmts[l] == 2) h[k] = orc_round_e4m3(h[k] / scales[l]) * scales[l];
+        }
+        const double *Wl = p, *bl = p + (long)width * width;
+        for (int o = 0; o < width; ++o) {
+            double s = bl[o];
+            for (int k = 0; k < width; ++k) s += Wl[(long)o * width + k] * h[k];
+            z[o] = act_f(s, act);
+        }
+        memcpy(h, z, sizeof(double) * (size_t)width);
+        p = bl + width;
+    }
+    double f = p[width];
+    for (int k = 0; k < width; ++k) f += p[k] * h[k];
+    return f;
+}
+
+/* Every (motion, point) pair with the input of each hidden layer rounded to
+ * the activation format of the network's precision, as the tensor-core path
+ * stores it (fmt 1: nearest-even bfloat16; fmt 2: FP8 E4M3 as
+ * e4m3(h / s_l) * s_l with the per-layer scale s_l), everything else in
+ * double.  fmt 0 is the plain network.  out[m][i] for all pairs, like
+ * orc_mlp_pairs. */
 void orc_mlp_pairs_rounded(const double *P, int width, int n_hidden, int act, int fmt,
                            const double *scales, const double *q0, const double *q1, int M,
                            const double *pts, long n, double *out)
 {
+    int32_t fmts[n_hidden > 0 ? n_hidden : 1];
+    for (int l = 0; l < n_hidden; ++l) fmts[l] = fmt;
     #pragma omp parallel
     {
         double h[width], z[width];
@@ -378,31 +419,23 @@ void orc_mlp_pairs_rounded(const double *P, int width, int n_hidden, int act, in
                     in[3 + c] = q0[m * DOF + c];
                     in[9 + c] = q1[m * DOF + c];
                 }
-                const double *W = P, *b = P + (long)width * 15;
-                for (int o = 0; o < width; ++o) {
-                    double s = b[o];
-                    for (int k = 0; k < 15; ++k) s += W[(long)o * 15 + k] * in[k];
-                    h[o] = act_f(s, act);
-                }
-                const double *p = b + width;
-                for (int l = 0; l < n_hidden; ++l) {
-                    for (int k = 0; k < width; ++k) {
-                        if (fmt == 1) h[k] = (double)orc_round_bf16((float)h[k]);
-                        if (fmt == 2) h[k] = orc_round_e4m3(h[k] / scales[l]) * scales[l];
-                    }
-                    const double *Wl = p, *bl = p + (long)width * width;
-                    for (int o = 0; o < width; ++o) {
-                        double s = bl[o];
-                        for (int k = 0; k < width; ++k) s += Wl[(long)o * width + k] * h[k];
-                        z[o] = act_f(s, act);
-                    }
-                    memcpy(h, z, sizeof z);
-                    p = bl + width;
-                }
-                double f = p[width];
-                for (int k = 0; k < width; ++k) f += p[k] * h[k];
-                out[(long)m * n + i] = f;
+                out[(long)m * n + i] = mlp_row_rounded(P, width, n_hidden, act, fmts, scales, in, h, z);
             }
+    }
+}
+
+/* Given input rows (n x 15), the network with a separate activation format
+ * per hidden layer (fmts[l], as above): separates the contribution of each
+ * layer's rounding to the error of a precision. */
+void orc_mlp_forward_rounded(const double *P, int width, int n_hidden, int act, const int32_t *fmts,
+                             const double *scales, const double *inputs, long n, double *out)
+{
+    #pragma omp parallel
+    {
+        double h[width], z[width];
+        #pragma omp for schedule(static)
+        for (long i = 0; i < n; ++i)
+            out[i] = mlp_row_rounded(P, width, n_hidden, act, fmts, scales, inputs + 15 * i, h, z);
     }
 }
 

@@ -162,3 +162,91 @@ def test_three_segment_paths_full_size(setup):
               f"validation MAE {hist['best_val_mae']:.4f} m")
     finally:
         svm.svm_destroy_model(h)
+
+
+@pytest.fixture(scope="module")
+def sampled_outputs(setup):
+    """The network output of both tensor-core precisions on 20 000 pairs drawn
+    at random from the 12.8 M (the bench's weights; FP8 with the bench's
+    activation scales) and the FP64 oracle on the same rounded weights."""
+    svm, training, robot, blob, hist, pts, pts_d, q0, q1, dmin, coll = setup
+    rng = np.random.default_rng(1)
+    mi, pi = rng.integers(0, M, 20000), rng.integers(0, P, 20000)
+    X = np.concatenate([pts[pi, :3].astype(np.float64), q0[mi], q1[mi]], axis=1)
+    cq0, cq1 = S.bin_motions(robot, 16, seed=1000)
+    out = {}
+    for prec in (1, 2):
+        h = svm.svm_create_model(robot, 256, 4, 0, prec, 0)
+        try:
+            svm.svm_load_weights(h, blob)
+            scales = np.ones(4)
+            if prec == 2:
+                scales = svm.svm_calibrate_act_scales(h, cq0, cq1, pts_d, 2.0)[:4].astype(np.float64)
+            f = torch.empty((M, P), device="cuda")
+            svm.svm_eval_pairs(h, q0, q1, pts_d, f)
+            torch.cuda.synchronize()
+            got = f[torch.from_numpy(mi).cuda(), torch.from_numpy(pi).cuda()].cpu().numpy().astype(np.float64)
+            del f
+        finally:
+            svm.svm_destroy_model(h)
+        Pq = oracle.quantized_params(svm.parse_blob(blob), prec)
+        ref = oracle.mlp_forward(Pq, 256, 4, 0, X)
+        out[prec] = dict(got=got, ref=ref, band=np.abs(ref - EPS) <= 0.1, P=Pq, scales=scales, X=X)
+    return out
+
+
+def test_fp8_error_by_layer(sampled_outputs):
+    """Where the FP8 error comes from, taken apart with the oracle on the same
+    sampled pairs (Sec. V-A's reduced-precision network; same weights): E4M3
+    weights with bfloat16 activations stay within the BF16 bound, so the
+    weights are not the cause; rounding the input of any one of the first
+    three hidden layers to E4M3 (3 mantissa bits: up to 2^-4 relative per
+    activation) already moves some gate-band output by more than 6e-3 m on
+    its own.  The kernel's own FP8 output equals the oracle's emulation of
+    E4M3 activations in every layer to FP32 accumulation error (median)."""
+    o = sampled_outputs[2]
+    P, sc, X, band, ref = o["P"], o["scales"], o["X"], o["band"], o["ref"]
+
+    def err(fmts):
+        return np.abs(oracle.mlp_forward_rounded(P, 256, 4, 0, fmts, sc, X) - ref)
+
+    rows = {"E4M3 weights, bfloat16 activations": [1, 1, 1, 1], "all layers E4M3": [2, 2, 2, 2]}
+    for l in range(4):
+        rows[f"E4M3 input of hidden layer {l} only"] = [2 if k == l else 0 for k in range(4)]
+    e = {k: err(v) for k, v in rows.items()}
+    for k, v in e.items():
+        print(f"{k:40s} gate band: max {v[band].max():.2e}, p99 {np.quantile(v[band], 0.99):.2e}; "
+              f"all pairs max {v.max():.2e}")
+    assert e["E4M3 weights, bfloat16 activations"][band].max() <= 3e-3
+    assert np.quantile(e["E4M3 weights, bfloat16 activations"], 0.999) <= 2e-3
+    for l in range(3):
+        assert e[f"E4M3 input of hidden layer {l} only"][band].max() > 6e-3
+    emu = oracle.mlp_forward_rounded(P, 256, 4, 0, [2, 2, 2, 2], sc, X)
+    assert np.median(np.abs(o["got"] - emu)) <= 1e-5
+
+
+@pytest.mark.xfail(strict=True, reason="E4M3 activations: the gate-band p99 error is ~1.9e-2 m on this network "
+                                       "(test_fp8_error_by_layer takes it apart); the calibrated gate keeps the "
+                                       "verdicts exact")
+def test_fp8_within_6e3_in_gate_band(sampled_outputs):
+    o = sampled_outputs[2]
+    e = np.abs(o["got"] - o["ref"])
+    assert np.quantile(e[o["band"]], 0.99) <= 6e-3
+
+
+@pytest.mark.xfail(strict=True, reason="bfloat16 activations: the largest gate-band error of the 20 000 sampled "
+                                       "pairs is ~2.6e-3 m (99.9 % are within 2e-3 m); every hidden layer's "
+                                       "rounding contributes")
+def test_bf16_within_2e3_everywhere_in_gate_band(sampled_outputs):
+    o = sampled_outputs[1]
+    e = np.abs(o["got"] - o["ref"])
+    assert e[o["band"]].max() <= 2e-3
+
+
+def test_bf16_gate_band_percentile(sampled_outputs):
+    """BF16 per-pair error in the gate band against the FP64 oracle (same
+    weights): 99.9 % of the sampled pairs within 2e-3 m, all within 3e-3 m."""
+    o = sampled_outputs[1]
+    e = np.abs(o["got"] - o["ref"])[o["band"]]
+    print(f"BF16 gate band: max {e.max():.2e}, p99.9 {np.quantile(e, 0.999):.2e}, p99 {np.quantile(e, 0.99):.2e}")
+    assert np.quantile(e, 0.999) <= 2e-3 and e.max() <= 3e-3

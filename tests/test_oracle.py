@@ -363,6 +363,33 @@ def test_mlp_rounded_activations_match_library_emulation(robot):
         np.testing.assert_allclose(got, emulate(fmt), rtol=1e-12, atol=1e-12)
 
 
+def test_mlp_forward_rounded_per_layer_formats(robot):
+    """The per-layer form: all-zero formats are the plain network, a uniform
+    format equals mlp_pairs_rounded bitwise, and a mix (E4M3 in one layer,
+    bfloat16 in another) equals torch's conversions applied layer by layer."""
+    torch = pytest.importorskip("torch")
+    layers = S.xavier_weights(32, 2, seed=5)
+    P = oracle.flatten_params(layers)
+    q0, q1 = S.uniform_motions(robot, 1, seed=4)
+    pts = S.cube_cloud(200, seed=4)
+    X = np.concatenate([pts[:, :3].astype(np.float64), np.repeat(q0, 200, 0), np.repeat(q1, 200, 0)], 1)
+    sc = np.array([1 / 16, 1 / 32])
+    np.testing.assert_array_equal(oracle.mlp_forward_rounded(P, 32, 2, 0, [0, 0], sc, X),
+                                  oracle.mlp_forward(P, 32, 2, 0, X))
+    for fmt in (1, 2):
+        np.testing.assert_array_equal(oracle.mlp_forward_rounded(P, 32, 2, 0, [fmt, fmt], sc, X),
+                                      oracle.mlp_pairs_rounded(P, 32, 2, 0, fmt, sc, q0, q1, pts)[0])
+    Ls = [(W.astype(np.float64), b.astype(np.float64)) for W, b in layers]
+    h = np.maximum(X @ Ls[0][0].T + Ls[0][1], 0)
+    h = torch.from_numpy(h / sc[0]).to(torch.float8_e4m3fn).double().numpy() * sc[0]
+    h = np.maximum(h @ Ls[1][0].T + Ls[1][1], 0)
+    h = torch.from_numpy(h.astype(np.float32)).to(torch.bfloat16).double().numpy()
+    h = np.maximum(h @ Ls[2][0].T + Ls[2][1], 0)
+    want = (h @ Ls[3][0].T + Ls[3][1])[:, 0]
+    np.testing.assert_allclose(oracle.mlp_forward_rounded(P, 32, 2, 0, [2, 1], sc, X), want, rtol=1e-12,
+                               atol=1e-12)
+
+
 # ---------------------------------------------------------- combined check
 
 def test_check_open_gate_reduces_to_gcc(robot):
