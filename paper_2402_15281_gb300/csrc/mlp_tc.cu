@@ -298,6 +298,43 @@ __device__ __forceinline__ void epilogue32_relu_e4m3_sm(uint32_t base, int r, in
     st_shared_v4(act_chunk_addr(base, kb, r, c0 + 1), w[4], w[5], w[6], w[7]);
 }
 
+// BF16 ReLU epilogue of 32 columns (o0..o0+31) of a warp's 32 rows, read in
+// the accumulator-fragment shape of tmem_ld_frag32: thread t owns columns
+// 8 g + 2 (t % 4), +1 of each 8-column group g, so it needs two biases per
+// group (two shuffles from bl, lane i holding the bias of column o0 + i)
+// where the row-per-lane shape needs all 32; h = relu(acc + b) rounded to
+// bfloat16 pairs, stored as the next layer's A operand (128B swizzle,
+// K-major) by four stmatrix.x4, one per (16-row block, 8-row half): lane l
+// addresses row l % 8 of the matrix of group l / 8.
+__device__ __forceinline__ void epilogue32_bf16_frag(uint32_t base, int quarter, int lane, int o0,
+                                                     const float (&v)[32], float bl)
+{
+    const int c2 = 2 * (lane & 3);
+    uint32_t pk[16];                                   // [16-row block][8-row half][group]
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const uint64_t b = f2(__shfl_sync(0xffffffffu, bl, 8 * g + c2), __shfl_sync(0xffffffffu, bl, 8 * g + c2 + 1));
+#pragma unroll
+        for (int rb = 0; rb < 2; ++rb)
+#pragma unroll
+            for (int rh = 0; rh < 2; ++rh) {
+                const int i = 16 * rb + 4 * g + 2 * rh;
+                pk[8 * rb + 4 * rh + g] = relu_bf16x2(f2_add(f2(v[i], v[i + 1]), b));
+            }
+    }
+    const int i = lane & 7, g = lane >> 3;   // row within the matrix (= row & 7), group of the matrix
+    const uint32_t cpart =
+        base + (uint32_t)((o0 >> 6) * KBLOCK_BYTES) + ((uint32_t)((((o0 & 63) >> 3) + g) ^ i) << 4);
+#pragma unroll
+    for (int rb = 0; rb < 2; ++rb)
+#pragma unroll
+        for (int rh = 0; rh < 2; ++rh) {
+            const int r = quarter * 32 + 16 * rb + 8 * rh + i;
+            stmatrix_x4(cpart + (uint32_t)(r * 128), pk[8 * rb + 4 * rh + 0], pk[8 * rb + 4 * rh + 1],
+                        pk[8 * rb + 4 * rh + 2], pk[8 * rb + 4 * rh + 3]);
+        }
+}
+
 // ------------------------------------------------------------------ kernel
 
 template <int PREC, int ACT>
@@ -478,6 +515,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         __syncwarp();
     } else {
         // ------------------------------------------------ epilogue warps
+        // BF16 ReLU reads the accumulator in the fragment shape (two biases per thread and
+        // 8-column group, stmatrix stores); FP8 and SiLU keep the row-per-lane shape
+        constexpr bool kFrag = PREC == SVM_BF16 && ACT == SVM_RELU;
         const int ew = warp - 2;
         const int s = ew / EPI_PER_SLOT;           // tile slot
         const int half = (ew % EPI_PER_SLOT) / 4;  // column half [half*128, half*128+128)
@@ -610,6 +650,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll 1
                     for (int o0 = 0; o0 < HALF_COLS; o0 += 32) {
                         float v[32];
+                        if constexpr (kFrag) {
+                            tmem_ld_frag32(t_row + (uint32_t)o0, v);
+                            epilogue32_bf16_frag(abase, quarter, lane, col0 + o0, v, bl0);
+                            bl0 = bl1;
+                            bl1 = bl2;
+                            bl2 = bl3;
+                            continue;
+                        }
                         tmem_ld32(t_row + (uint32_t)o0, v);
                         if constexpr (ACT == SVM_RELU) {
                             if (PREC == SVM_FP8_E4M3 && l == 0)
@@ -637,8 +685,55 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     float f = 0.0f;
                     uint64_t f2acc = f2(0.0f, 0.0f);
                     const uint64_t s2 = f2(scale, scale);
+                    if constexpr (kFrag) {
+                        // fragment shape: partial dot products of the thread's four rows, summed over the
+                        // four threads of a row, then handed to the row-per-lane layout of the gate
+                        const int c2 = 2 * (lane & 3);
+                        uint64_t acc4[4] = {f2acc, f2acc, f2acc, f2acc};
 #pragma unroll 1
-                    for (int o0 = 0; o0 < HALF_COLS; o0 += 32) {
+                        for (int o0 = 0; o0 < HALF_COLS; o0 += 32) {
+                            float v[32];
+                            tmem_ld_frag32(t_row + (uint32_t)o0, v);
+#pragma unroll
+                            for (int g = 0; g < 4; ++g) {
+                                const uint64_t b = f2(__shfl_sync(0xffffffffu, bl0, 8 * g + c2),
+                                                      __shfl_sync(0xffffffffu, bl0, 8 * g + c2 + 1));
+                                const uint64_t w = f2(__shfl_sync(0xffffffffu, wl0, 8 * g + c2),
+                                                      __shfl_sync(0xffffffffu, wl0, 8 * g + c2 + 1));
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) {
+                                    const int i = 16 * (k >> 1) + 4 * g + 2 * (k & 1);
+                                    float zl, zh;
+                                    asm("mov.b64 {%0, %1}, %2;" : "=f"(zl), "=f"(zh) : "l"(f2_add(f2(v[i], v[i + 1]), b)));
+                                    acc4[k] = f2_fma(w, f2(fmaxf(zl, 0.0f), fmaxf(zh, 0.0f)), acc4[k]);
+                                }
+                            }
+                            bl0 = bl1;
+                            bl1 = bl2;
+                            bl2 = bl3;
+                            wl0 = wl1;
+                            wl1 = wl2;
+                            wl2 = wl3;
+                        }
+                        float sk[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            float lo, hi;
+                            asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(acc4[k]));
+                            sk[k] = lo + hi;
+                            sk[k] += __shfl_xor_sync(0xffffffffu, sk[k], 1);
+                            sk[k] += __shfl_xor_sync(0xffffffffu, sk[k], 2);
+                        }
+                        // row 16 rb + 8 rh + t / 4 of the warp is in sk[2 rb + rh] of threads 4 (t / 4) ..;
+                        // lane L takes row L: k = L / 8 from thread 4 (L % 8)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const float x = __shfl_sync(0xffffffffu, sk[k], 4 * (lane & 7));
+                            if ((lane >> 3) == k) f = x;
+                        }
+                    }
+#pragma unroll 1
+                    for (int o0 = 0; o0 < (kFrag ? 0 : HALF_COLS); o0 += 32) {
                         float v[32];
                         tmem_ld32(t_row + (uint32_t)o0, v);
                         if (sm_bias) {
