@@ -715,6 +715,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                             wl1 = wl2;
                             wl2 = wl3;
                         }
+                        // every TMEM read of this tile is done: hand the slot and the next tile's layer-0
+                        // operand over now, before the reductions and the gate
+                        tc_fence_before();
+                        if (has_next) stage_x(nx);
                         float sk[4];
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
@@ -782,18 +786,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                             }
                         }
                     }
+                    if constexpr (!kFrag) {
+                        // every TMEM read of this tile is done: hand the slot and the next tile's
+                        // layer-0 operand over before the reductions and the gate
+                        tc_fence_before();
+                        if (has_next) stage_x(nx);
+                    }
                     {
                         float lo, hi;
                         asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(f2acc));
                         f += lo + hi;
                     }
-                    tc_fence_before();
                     // the two column halves of a row meet in shared memory
                     if (half == 1) red_s[r] = f;
                     named_sync(1 + s, 32 * EPI_PER_SLOT);
                     if (half == 0) f += red_s[r] + Wt.bout;
-                    // the TMEM slot and the layer-0 operand are free: hand them to the next tile
-                    if (has_next) stage_x(nx);
                     // FP8: the gate of this tile waits until the next tile's layer-0
                     // epilogue is done (its atomics would delay that epilogue; FP8's
                     // short MMA blocks leave no slack for them).  Measured slower
