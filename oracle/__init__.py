@@ -442,3 +442,55 @@ def block_pairs(params, q0, q1, points, bn_eps=1e-5) -> np.ndarray:
         u = np.concatenate([pts, np.repeat(q0[m][None], n, 0), np.repeat(q1[m][None], n, 0)], axis=1)
         out[m] = block_forward(params, u, bn_eps)
     return out
+
+
+def quantized_block_params(params, prec):
+    """The block architecture's parameters as a model of precision `prec`
+    uses them: 1 = BF16 rounds every weight matrix (initial layer, blocks,
+    final layer) to nearest-even bfloat16 with the oracle's quantiser; biases
+    and BatchNorm statistics are not rounded.  0 leaves everything as is."""
+    if prec == 0:
+        return params
+    init = (round_bf16(params["init"][0]), np.asarray(params["init"][1], dtype=np.float32))
+    blocks = [(round_bf16(W),) + tuple(np.asarray(a, dtype=np.float32) for a in rest)
+              for W, *rest in params["blocks"]]
+    final = (round_bf16(params["final"][0]), np.asarray(params["final"][1], dtype=np.float32))
+    return {"init": init, "blocks": blocks, "final": final}
+
+
+def block_forward_rounded(params, inputs, bn_eps=1e-5, fmt=1) -> np.ndarray:
+    """block_forward with the activations stored in a 16-bit format between
+    layers (fmt 1: nearest-even bfloat16; fmt 0: not rounded, block_forward
+    itself): h_0 and every h_l that a later block reads -- as its input and
+    as its skip term -- are rounded; the last block's output enters the final
+    layer unrounded.  Everything else in double.  inputs: (n, 15)."""
+    u = np.asarray(inputs, dtype=np.float64).reshape(-1, 15)
+
+    def rnd(h):
+        return round_bf16(h).astype(np.float64) if fmt == 1 else h
+
+    W0, b0 = (np.asarray(a, dtype=np.float64) for a in params["init"])
+    h = rnd(u @ W0.T + b0)
+    nb = len(params["blocks"])
+    for l, blk in enumerate(params["blocks"]):
+        W, b, gamma, beta, mean, var = (np.asarray(a, dtype=np.float64) for a in blk)
+        v = h if l == 0 else np.concatenate([h, u], axis=1)
+        y = np.maximum(v @ W.T + b, 0.0)
+        h = gamma * (y - mean) / np.sqrt(var + bn_eps) + beta + h
+        if l + 1 < nb:
+            h = rnd(h)
+    Wf, bf = (np.asarray(a, dtype=np.float64) for a in params["final"])
+    return (np.concatenate([h, u], axis=1) @ Wf.T + bf)[:, 0]
+
+
+def block_pairs_rounded(params, q0, q1, points, bn_eps=1e-5, fmt=1) -> np.ndarray:
+    """block_forward_rounded for every (motion, point) pair: (M, n)."""
+    q0 = _d(q0).reshape(-1, 6)
+    q1 = _d(q1).reshape(-1, 6)
+    pts = _xyz(points)
+    M, n = q0.shape[0], pts.shape[0]
+    out = np.empty((M, n))
+    for m in range(M):
+        u = np.concatenate([pts, np.repeat(q0[m][None], n, 0), np.repeat(q1[m][None], n, 0)], axis=1)
+        out[m] = block_forward_rounded(params, u, bn_eps, fmt)
+    return out

@@ -887,6 +887,7 @@ int tc_prepare(TcModel& t, const svm_model_desc& d, const DevWeights& w)
     t.ready = false;
     t.prec = d.prec;
     t.act = d.act;
+    t.arch = SVM_ARCH_MLP;
     EncodeFn enc = get_encode();
     if (!enc || d.width != WN || !w.wq || !w.w1pad) return -1;
     const int elem = d.prec == SVM_BF16 ? 2 : 1;
@@ -909,6 +910,7 @@ int tc_launch(TcModel& t, const CallArgs& a, const DevWeights& w, int n_tiles, v
     if (!t.ready) return -1;
     if (n_tiles <= 0) return 0;
     const int grid = n_tiles < n_sms ? n_tiles : n_sms;
+    if (t.arch == SVM_ARCH_BLOCKS) return tc_block_launch(t, a, w, n_tiles, grid, s);
     if (t.prec == SVM_BF16) {
         if (t.act == SVM_RELU) launch_t<SVM_BF16, SVM_RELU>(t, a, w, n_tiles, grid, s);
         else launch_t<SVM_BF16, SVM_SILU>(t, a, w, n_tiles, grid, s);

@@ -10,6 +10,7 @@ struct TcModel {
     bool ready = false;
     int prec = 0;                       // SVM_BF16 or SVM_FP8_E4M3
     int act = 0;                        // SVM_RELU or SVM_SILU
+    int arch = 0;                       // SVM_ARCH_MLP or SVM_ARCH_BLOCKS
     alignas(64) unsigned char wmap[128];  // CUtensorMap of the hidden weights
     alignas(64) unsigned char w1map[128]; // CUtensorMap of the padded layer-1 x-weights
 };
@@ -20,5 +21,9 @@ int tc_prepare(TcModel& t, const svm_model_desc& d, const DevWeights& w);
 void tc_release(TcModel& t);
 int tc_launch(TcModel& t, const CallArgs& a, const DevWeights& w, int n_tiles, void* ws, int n_sms,
               cudaStream_t s);
+// The block architecture (width 512, BF16, ReLU) on the tensor cores: wh is the
+// blocks' h-weights, [n_hidden * 512][512] bfloat16 (outputs x inputs) on the device.
+int tc_block_prepare(TcModel& t, const svm_model_desc& d, const void* wh);
+int tc_block_launch(const TcModel& t, const CallArgs& a, const DevWeights& w, int n_tiles, int grid, cudaStream_t s);
 
 }  // namespace svm

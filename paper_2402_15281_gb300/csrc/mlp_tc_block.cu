@@ -1,0 +1,530 @@
+// mlp_tc_block.cu -- the block architecture of Sec. IV-A (Fig. 2) on the
+// 5th-generation tensor cores: BF16 operands, FP32 accumulation in tensor
+// memory, width 512, fused with the gate and the compaction of flagged pairs.
+//
+// Network (u = [x; q0; q1]):
+//   h_0 = W_0 u + b_0                                   initial linear layer
+//   block l = 1..L:  z_l = W_l v_l + b_l,  v_1 = h_0,  v_l = [h_{l-1}; u]
+//                    (the jump connection from the second block on)
+//                    h_l = BN_l(relu(z_l)) + h_{l-1}    (skip connection)
+//   f = w_f [h_L; u] + b_f                              final layer
+// BatchNorm at inference is folded into a per-channel scale s_l and shift t_l
+// at load.  Every layer's q-part and bias is a per-motion constant c_{l,m}
+// (the prologue), every x-part (K = 3) runs on the CUDA cores in the epilogue,
+// and the h-parts are 128 x 512 x 512 tcgen05 GEMMs (two N = 256 halves).
+//
+// Persistent kernel, one CTA per SM, 18 warps:
+//   warp 0       TMA producer: weight slices of 64 K x 256 output rows (32 KB,
+//                128B swizzle, K-major B operand) into a 3-stage ring;
+//   warp 1       allocates the 512 TMEM columns and issues tcgen05.mma (one
+//                elected lane, warp-uniform loop): per block two N = 256 halves
+//                x 8 K-slices of 4 MMAs (K = 16);
+//   warps 2-17   epilogue: warp w reads TMEM lane quarter w % 4 and owns 128
+//                output columns, 128 * ((w - 2) / 4) onwards.
+// One 128-pair tile is in flight per CTA: its 512-wide FP32 accumulator fills
+// the TMEM, and the layer's input -- a 128 x 512 bfloat16 tile in shared
+// memory (K-major, 128B swizzle), which is also its skip term -- is updated in
+// place by the epilogue, so the MMAs of a block and its epilogue alternate.
+// The epilogue reads the accumulator in the 16x256b fragment shape (thread t:
+// two adjacent columns of two rows per 8-column group), reads the skip term
+// with ldmatrix and writes the new activation with stmatrix.  The final layer
+// sums per-thread partial dot products over the four threads of a row, the
+// four column quarters of a row meet in shared memory, and the gate, ballot
+// compaction and per-motion minima follow as in mlp_tc.cu.
+//
+// Every mbarrier wait is bounded (2 s); on expiry the waiter sets the call's
+// error word and the CTA's abort flag, every role leaves its loop, and the
+// TMEM is freed before the CTA exits (the records then carry status 1).
+#include <mutex>
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "mlp_tc.cuh"
+#include "tc_ptx.cuh"
+
+namespace svm {
+
+namespace {
+
+using namespace ptx;
+
+constexpr int TM = 128;                      // pairs per tile = MMA M
+constexpr int WB = 512;                      // network width
+constexpr int NH = 256;                      // MMA N: one half of the width
+constexpr int BK = 64;                       // K elements per weight slice (128 bytes)
+constexpr int KSL = WB / BK;                 // 8 slices per half and block
+constexpr int STAGES = 3;
+constexpr int STAGE_BYTES = NH * 128;        // 32 KB
+constexpr int KBLOCK_BYTES = TM * 128;       // one 128-byte K-block of the activation tile
+constexpr int ACT_BYTES = TM * WB * 2;       // 128 KB
+constexpr int NUM_EPI_WARPS = 16;
+constexpr int NUM_THREADS = (2 + NUM_EPI_WARPS) * 32;
+constexpr int OFF_W = ACT_BYTES;
+constexpr int OFF_RED = OFF_W + STAGES * STAGE_BYTES;       // [3][TM] floats: column quarters 1-3
+constexpr int OFF_BAR = OFF_RED + 3 * TM * 4;
+constexpr int N_BARS = 2 * STAGES + 3;
+constexpr int OFF_MISC = OFF_BAR + 8 * N_BARS;
+constexpr int SMEM_DYN = OFF_MISC + 16 + 1024;              // slack for 1024-byte alignment
+static_assert(SMEM_DYN <= 232448, "shared memory budget");
+// kind::f16: D f32, A and B bf16, both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NH >> 3) << 17) |
+                           ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ uint64_t f2(float lo, float hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_split(uint64_t v, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_relu(uint64_t v)
+{
+    float lo, hi;
+    f2_split(v, lo, hi);
+    return f2(fmaxf(lo, 0.0f), fmaxf(hi, 0.0f));
+}
+// both halves rounded to bfloat16, low half first
+__device__ __forceinline__ uint32_t bf16x2(uint64_t v)
+{
+    uint32_t d;
+    asm("{\n .reg .f32 lo, hi;\n mov.b64 {lo, hi}, %1;\n cvt.rn.bf16x2.f32 %0, hi, lo;\n}" : "=r"(d) : "l"(v));
+    return d;
+}
+__device__ __forceinline__ uint64_t bf16x2_to_f2(uint32_t w)
+{
+    return f2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u));
+}
+__device__ __forceinline__ float2 ldg2(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
+
+__device__ __forceinline__ float4 ld_stream_f4(const float4* p)
+{
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+// Shared-memory address of row `row`, 16-byte chunk of column c8 * 8, of the
+// activation tile (K-major, 128B swizzle: the layout the MMA descriptor reads).
+__device__ __forceinline__ uint32_t act_addr(uint32_t base, int row, int c8)
+{
+    return base + (uint32_t)((c8 >> 3) * KBLOCK_BYTES + row * 128 + (((c8 & 7) ^ (row & 7)) << 4));
+}
+
+// Linear x-part of 2 columns for the thread's 4 fragment rows: w = the 6
+// weights (x, y, z of column c, then of c + 1), added to z[k].
+__device__ __forceinline__ void add_xpart(const float* w, const float4 (&x4)[4], uint64_t (&z)[4])
+{
+    const float2 w0 = ldg2(w), w1 = ldg2(w + 2), w2 = ldg2(w + 4);
+    const uint64_t wx = f2(w0.x, w1.y), wy = f2(w0.y, w2.x), wz = f2(w1.x, w2.y);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        z[k] = f2_fma(wz, f2(x4[k].z, x4[k].z), f2_fma(wy, f2(x4[k].y, x4[k].y), f2_fma(wx, f2(x4[k].x, x4[k].x), z[k])));
+}
+
+template <bool HAS_WX, bool LAST>
+__device__ __forceinline__ void block_chunk(uint32_t abase, uint32_t t_addr, int q, int lane, int c0, const float* cl,
+                                            const float* s, const float* t, const float* wx, const float* wf,
+                                            const float4 (&x4)[4], uint64_t (&acc4)[4])
+{
+    float v[32];
+    tmem_ld_frag32(t_addr, v);
+    const int c2 = 2 * (lane & 3), i8 = lane & 7, j = lane >> 3;
+    uint32_t pk[16];                                  // [row block k][group g]
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const int c = c0 + 8 * g + c2;                // even: columns c and c + 1
+        // the skip term: the block's input at the same rows and columns
+        uint32_t hp[4];
+        ldmatrix_x4(act_addr(abase, q * 32 + 16 * (j >> 1) + 8 * (j & 1) + i8, (c0 + 8 * g) >> 3), hp[0], hp[1],
+                    hp[2], hp[3]);
+        const float2 b = ldg2(cl + c), sc = ldg2(s + c), sh = ldg2(t + c);
+        uint64_t z[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int vi = 16 * (k >> 1) + 4 * g + 2 * (k & 1);
+            z[k] = f2_add(f2(v[vi], v[vi + 1]), f2(b.x, b.y));
+        }
+        if constexpr (HAS_WX) add_xpart(wx + 3 * c, x4, z);
+        const uint64_t s2 = f2(sc.x, sc.y), t2 = f2(sh.x, sh.y);
+        uint64_t w2 = 0;
+        if constexpr (LAST) {
+            const float2 w = ldg2(wf + c);
+            w2 = f2(w.x, w.y);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint64_t h = f2_add(f2_fma(f2_relu(z[k]), s2, t2), bf16x2_to_f2(hp[k]));
+            if constexpr (LAST) acc4[k] = f2_fma(w2, h, acc4[k]);
+            else pk[4 * k + g] = bf16x2(h);
+        }
+    }
+    if constexpr (!LAST) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            stmatrix_x4(act_addr(abase, q * 32 + 16 * (k >> 1) + 8 * (k & 1) + i8, (c0 >> 3) + j), pk[4 * k + 0],
+                        pk[4 * k + 1], pk[4 * k + 2], pk[4 * k + 3]);
+    }
+}
+
+// h_0 = W_0x x + c_0 (no activation) for the warp's 32 rows and 128 columns
+// from col0, rounded to bfloat16, as the first block's input.
+__device__ __forceinline__ void initial_layer(uint32_t abase, int q, int lane, int col0, const float* w0x,
+                                              const float* c0m, const float4 (&x4)[4])
+{
+    const int c2 = 2 * (lane & 3), i8 = lane & 7, j = lane >> 3;
+#pragma unroll 1
+    for (int o0 = col0; o0 < col0 + 128; o0 += 32) {
+        uint32_t pk[16];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const int c = o0 + 8 * g + c2;
+            const float2 b = ldg2(c0m + c);
+            uint64_t z[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) z[k] = f2(b.x, b.y);
+            add_xpart(w0x + 3 * c, x4, z);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) pk[4 * k + g] = bf16x2(z[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            stmatrix_x4(act_addr(abase, q * 32 + 16 * (k >> 1) + 8 * (k & 1) + i8, (o0 >> 3) + j), pk[4 * k + 0],
+                        pk[4 * k + 1], pk[4 * k + 2], pk[4 * k + 3]);
+    }
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    mlp_tc_block_kernel(const __grid_constant__ CUtensorMap wmap, CallArgs A, DevWeights Wt, int n_tiles)
+{
+    extern __shared__ __align__(1024) unsigned char dsm_raw[];
+    unsigned char* dsm =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
+    const uint32_t sbase = smem_u32(dsm);
+    const uint32_t abase = sbase;
+    const uint32_t w_base = sbase + OFF_W;
+    const uint32_t bar0 = sbase + OFF_BAR;
+    float* red = reinterpret_cast<float*>(dsm + OFF_RED);
+    auto full_bar = [&](int s) { return bar0 + 8 * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8 * (STAGES + s); };
+    const uint32_t accf_bar = bar0 + 8 * (2 * STAGES);
+    const uint32_t epid_bar = bar0 + 8 * (2 * STAGES + 1);
+    const uint32_t drain_bar = bar0 + 8 * (2 * STAGES + 2);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(dsm + OFF_MISC);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(dsm + OFF_MISC + 4);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_mine =
+        n_tiles > (int)blockIdx.x ? (n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    const int L = A.L;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        mbar_init(accf_bar, 1);
+        mbar_init(epid_bar, NUM_EPI_WARPS);
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&wmap)) : "memory");
+            int stage = 0;
+            uint32_t phase = 0, armed = 0, armed_par = 0;
+            bool ok = true;
+            for (int i = 0; i < n_mine && ok; ++i)
+                for (int l = 1; l <= L && ok; ++l)
+                    for (int h = 0; h < 2 && ok; ++h)
+                        for (int kk = 0; kk < KSL; ++kk) {
+                            if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, A.dev_err)) { ok = false; break; }
+                            mbar_arrive_tx(full_bar(stage), STAGE_BYTES);
+                            tma_load_2d(w_base + stage * STAGE_BYTES, &wmap, kk * BK, (l - 1) * WB + h * NH,
+                                        full_bar(stage));
+                            armed |= 1u << stage;
+                            armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+                            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                        }
+            // wait (bounded) for every copy this thread started
+            for (int s = 0; s < STAGES; ++s)
+                if (armed & (1u << s)) {
+                    const uint32_t par = (armed_par >> s) & 1u;
+                    const uint64_t t0 = globaltimer();
+                    while (!mbar_try(full_bar(s), par) && globaltimer() - t0 < kTimeoutNs) {
+                    }
+                }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        const uint64_t a_desc0 = sdesc(abase), b_desc0 = sdesc(w_base);
+        int stage = 0;
+        uint32_t phase = 0, ep = 0;
+        bool ok = true;
+        for (int i = 0; i < n_mine && ok; ++i)
+            for (int l = 1; l <= L && ok; ++l) {
+                if (!mbar_wait_warp(epid_bar, ep, abort_flag, A.dev_err)) { ok = false; break; }
+                ep ^= 1u;
+                tc_fence_after();
+                for (int h = 0; h < 2 && ok; ++h) {
+                    const uint32_t d_tmem = tmem_base + (uint32_t)(h * NH);
+                    for (int kk = 0; kk < KSL; ++kk) {
+                        if (!mbar_wait_warp(full_bar(stage), phase, abort_flag, A.dev_err)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint64_t ad = a_desc0 + (uint64_t)(kk * (KBLOCK_BYTES >> 4));
+                        const uint64_t bd = b_desc0 + (uint64_t)(stage * (STAGE_BYTES >> 4));
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            mma_f16_warp(d_tmem, ad + 2 * k, bd + 2 * k, IDESC, (kk | k) != 0 ? 1u : 0u);
+                        mma_commit_warp(empty_bar(stage));
+                        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                    }
+                }
+                if (ok) mma_commit_warp(accf_bar);
+            }
+        // every MMA issued by this warp has completed before TMEM is freed
+        mma_commit_warp(drain_bar);
+        const uint64_t t0 = globaltimer();
+        while (!mbar_try(drain_bar, 0u) && globaltimer() - t0 < kTimeoutNs) {
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------ epilogue warps
+        const int q = warp & 3;                      // TMEM lane quarter: rows 32 q ..
+        const int cq = (warp - 2) >> 2;              // column quarter: columns 128 cq ..
+        const int col0 = cq * 128;
+        const int r = q * 32 + lane;                 // this lane's row (gate, reduction)
+        const uint32_t t_row = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)col0;
+        const int cbs = A.cb_stride;
+        uint32_t acc_phase = 0;
+        bool ok = true;
+        // tile i of this CTA: motion, first point, end of the motion's range
+        auto tile_of = [&](int i, int& m, long long& p0, long long& pe) {
+            const int t = (int)blockIdx.x + i * (int)gridDim.x;
+            m = find_segment(A.tile_off, A.M, t);
+            p0 = A.pbeg[m] + (long long)(t - A.tile_off[m]) * TM;
+            pe = A.pend[m];
+        };
+        // points of the thread's four fragment rows: row 16 (k >> 1) + 8 (k & 1) + lane / 4 of the quarter
+        auto load_x4 = [&](long long p0, long long pe, float4 (&x4)[4]) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const long long p = p0 + q * 32 + 16 * (k >> 1) + 8 * (k & 1) + (lane >> 2);
+                x4[k] = p < pe ? ld_stream_f4(A.points + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        };
+        auto stage_h0 = [&](int m, const float4 (&x4)[4]) {
+            initial_layer(abase, q, lane, col0, Wt.w1x, A.cbias + (long long)m * cbs, x4);
+            fence_async_smem();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(epid_bar);
+        };
+        int m = 0;
+        long long p0 = 0, pe = 0;
+        float4 x4[4];
+        if (n_mine > 0) {
+            tile_of(0, m, p0, pe);
+            load_x4(p0, pe, x4);
+            if (!(A.test_stall && blockIdx.x == 0)) stage_h0(m, x4);
+        }
+        for (int i = 0; i < n_mine && ok; ++i) {
+            const bool has_next = i + 1 < n_mine;
+            const float* cm = A.cbias + (long long)m * cbs;
+            for (int l = 1; l <= L && ok; ++l) {
+                const float* cl = cm + (long long)l * WB;
+                const float* s = Wt.blk_s + (long long)(l - 1) * WB;
+                const float* t = Wt.blk_t + (long long)(l - 1) * WB;
+                const float* wx = Wt.blk_wx + (long long)(l - 1) * WB * 3;
+                int nm = 0;
+                long long np0 = 0, npe = 0;
+                float4 xn[4];
+                if (l == L && has_next) {
+                    tile_of(i + 1, nm, np0, npe);
+                    load_x4(np0, npe, xn);
+                }
+                if (!mbar_wait(accf_bar, acc_phase, abort_flag, A.dev_err)) { ok = false; break; }
+                acc_phase ^= 1u;
+                tc_fence_after();
+                uint64_t acc4[4] = {0ull, 0ull, 0ull, 0ull};
+                if (l < L) {
+#pragma unroll 1
+                    for (int o = 0; o < 4; ++o) {
+                        if (l == 1)
+                            block_chunk<false, false>(abase, t_row + (uint32_t)(32 * o), q, lane, col0 + 32 * o, cl, s,
+                                                      t, wx, Wt.wout, x4, acc4);
+                        else
+                            block_chunk<true, false>(abase, t_row + (uint32_t)(32 * o), q, lane, col0 + 32 * o, cl, s,
+                                                     t, wx, Wt.wout, x4, acc4);
+                    }
+                    fence_async_smem();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(epid_bar);
+                    continue;
+                }
+                // ---- last block and the final layer
+#pragma unroll 1
+                for (int o = 0; o < 4; ++o) {
+                    if (l == 1)
+                        block_chunk<false, true>(abase, t_row + (uint32_t)(32 * o), q, lane, col0 + 32 * o, cl, s, t,
+                                                 wx, Wt.wout, x4, acc4);
+                    else
+                        block_chunk<true, true>(abase, t_row + (uint32_t)(32 * o), q, lane, col0 + 32 * o, cl, s, t,
+                                                wx, Wt.wout, x4, acc4);
+                }
+                // every read of this tile's TMEM and activation tile is done: the next tile's h_0
+                if (has_next) stage_h0(nm, xn);
+                float sk[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float lo, hi;
+                    f2_split(acc4[k], lo, hi);
+                    sk[k] = lo + hi;
+                    sk[k] += __shfl_xor_sync(0xffffffffu, sk[k], 1);
+                    sk[k] += __shfl_xor_sync(0xffffffffu, sk[k], 2);
+                }
+                // row 16 (k >> 1) + 8 (k & 1) + t / 4 of the quarter is in sk[k] of thread 4 (t / 4) ..:
+                // lane L takes row L, k = L / 8, from thread 4 (L % 8)
+                float f = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float v = __shfl_sync(0xffffffffu, sk[k], 4 * (lane & 7));
+                    if ((lane >> 3) == k) f = v;
+                }
+                // the four column quarters of a row meet in shared memory
+                if (cq > 0) red[(cq - 1) * TM + r] = f;
+                named_sync(1 + q, 128);
+                if (cq == 0) {
+                    const long long p = p0 + r;
+                    const bool valid = p < pe;
+                    const float4 xr = valid ? ld_stream_f4(A.points + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    f += red[r] + red[TM + r] + red[2 * TM + r];
+                    f = fmaf(__ldg(Wt.out_wx + 2), xr.z, fmaf(__ldg(Wt.out_wx + 1), xr.y, fmaf(__ldg(Wt.out_wx), xr.x, f)));
+                    f += __ldg(cm + (long long)(L + 1) * WB);
+                    // gate, compaction, per-motion minima (as in mlp_tc.cu)
+                    if (A.f_out != nullptr && valid) A.f_out[(long long)m * A.f_stride + (p - A.pbeg[m])] = f;
+                    const bool flag = valid && f <= A.gate;
+                    const unsigned mask = __ballot_sync(0xffffffffu, flag);
+                    unsigned base = 0;
+                    if (lane == 0 && mask) base = atomicAdd(&A.st[m].n_flagged, (unsigned)__popc(mask));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (flag) A.idx[A.pair_off[m] + base + __popc(mask & ((1u << lane) - 1u))] = (unsigned)p;
+                    float fm = valid ? f : __int_as_float(0x7f800000);
+#pragma unroll
+                    for (int sh = 16; sh > 0; sh >>= 1) fm = fminf(fm, __shfl_xor_sync(0xffffffffu, fm, sh));
+                    if (lane == 0 && fm < __int_as_float(0x7f800000)) atomicMin(&A.st[m].dhat_key, float_key(fm));
+                    if (fm <= A.gate) {
+                        const unsigned who = __ballot_sync(0xffffffffu, valid && f == fm);
+                        const unsigned pi = __shfl_sync(0xffffffffu, (unsigned)p, __ffs(who) - 1);
+                        if (lane == 0) atomicMin(&A.st[m].probe_key, ((unsigned long long)float_key(fm) << 32) | pi);
+                    }
+                }
+                // the reduction buffer is read before any warp of the quarter can write the next tile's sums
+                named_sync(5 + q, 128);
+                if (has_next) {
+                    m = nm;
+                    p0 = np0;
+                    pe = npe;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) x4[k] = xn[k];
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512) : "memory");
+    }
+}
+
+using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
+
+EncodeFn encode_fn()
+{
+    static EncodeFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) ==
+                cudaSuccess &&
+            qr == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+int tc_block_prepare(TcModel& t, const svm_model_desc& d, const void* wh)
+{
+    t.ready = false;
+    t.prec = d.prec;
+    t.act = d.act;
+    t.arch = SVM_ARCH_BLOCKS;
+    EncodeFn enc = encode_fn();
+    if (!enc || d.width != WB || d.prec != SVM_BF16 || d.act != SVM_RELU || !wh) return -1;
+    // the blocks' h-weights, [L * 512 rows (outputs)][512 (inputs, K)] bfloat16
+    const cuuint64_t dims[2] = {(cuuint64_t)WB, (cuuint64_t)WB * d.n_hidden};
+    const cuuint64_t strides[1] = {(cuuint64_t)WB * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)NH};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(reinterpret_cast<CUtensorMap*>(t.wmap), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(wh), dims,
+            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return -2;
+    t.ready = true;
+    return 0;
+}
+
+int tc_block_launch(const TcModel& t, const CallArgs& a, const DevWeights& w, int n_tiles, int grid, cudaStream_t s)
+{
+    if (!t.ready || t.arch != SVM_ARCH_BLOCKS) return -1;
+    if (n_tiles <= 0) return 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    static std::once_flag done[64];            // once per device, safe across host threads
+    if (dev >= 0 && dev < 64)
+        std::call_once(done[dev], [] {
+            cudaFuncSetAttribute(mlp_tc_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_DYN);
+        });
+    if (grid > n_tiles) grid = n_tiles;
+    mlp_tc_block_kernel<<<grid, NUM_THREADS, SMEM_DYN, s>>>(*reinterpret_cast<const CUtensorMap*>(t.wmap), a, w,
+                                                             n_tiles);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+}  // namespace svm

@@ -149,6 +149,28 @@ svm_status load_block_weights(svm_model* m, const unsigned char* p, size_t bytes
     if (off != bytes) return fail(m, SVM_E_WEIGHTS, "trailing bytes in blob");
     for (float v : all)
         if (!std::isfinite(v)) return fail(m, SVM_E_WEIGHTS, "non-finite weight");
+    const bool bf16 = d.prec == SVM_BF16;
+    if (bf16) {
+        // BF16 model: every weight matrix rounded to nearest-even bfloat16 (biases and BatchNorm
+        // statistics stay FP32); the export then holds the rounded values
+        auto rnd = [](float v) {
+            uint32_t u;
+            std::memcpy(&u, &v, 4);
+            u += 0x7FFFu + ((u >> 16) & 1u);
+            u &= 0xFFFF0000u;
+            float r;
+            std::memcpy(&r, &u, 4);
+            return r;
+        };
+        for (long long i = 0; i < W * kInDim; ++i) init[i] = rnd(init[i]);
+        for (long long l = 0; l < L; ++l)
+            for (long long i = 0; i < W * (l == 0 ? W : J); ++i) blk[l][i] = rnd(blk[l][i]);
+        for (long long i = 0; i < J; ++i) fin[i] = rnd(fin[i]);
+        all.clear();
+        all.insert(all.end(), init.begin(), init.end());
+        for (long long l = 0; l < L; ++l) all.insert(all.end(), blk[l].begin(), blk[l].end());
+        all.insert(all.end(), fin.begin(), fin.end());
+    }
 
     std::vector<float> w1x(W * 3), wT(L * W * W), wout(W), blk_wx(L * W * 3, 0.0f), blk_wq((L + 1) * W * 12),
         blk_b((L + 1) * W), blk_s(L * W), blk_t(L * W), out_wx(3), out_wq(12);
@@ -180,6 +202,20 @@ svm_status load_block_weights(svm_model* m, const unsigned char* p, size_t bytes
     for (int c = 0; c < 3; ++c) out_wx[c] = fin[W + c];
     for (int c = 0; c < 12; ++c) out_wq[c] = fin[W + 3 + c];
     const float bout = fin[J];
+    // BF16: the blocks' h-weights for the tensor cores, [L][W outputs][W inputs] bfloat16 (K-major B operand)
+    std::vector<uint16_t> wh;
+    if (bf16) {
+        wh.resize((size_t)L * W * W);
+        for (long long l = 0; l < L; ++l) {
+            const long long in = l == 0 ? W : J;
+            for (long long o = 0; o < W; ++o)
+                for (long long i = 0; i < W; ++i) {
+                    uint32_t u;
+                    std::memcpy(&u, &blk[l][o * in + i], 4);
+                    wh[((size_t)l * W + o) * W + i] = (uint16_t)(u >> 16);
+                }
+        }
+    }
 
     DeviceGuard g(m->device);
     CK(cudaDeviceSynchronize());
@@ -187,6 +223,8 @@ svm_status load_block_weights(svm_model* m, const unsigned char* p, size_t bytes
     const std::vector<const std::vector<float>*> parts = {&w1x, &wT, &wout, &blk_wx, &blk_wq, &blk_b, &blk_s,
                                                           &blk_t, &out_wx, &out_wq};
     for (auto* v : parts) total += align256(std::max<size_t>(1, v->size()) * 4);
+    const size_t wh_at = total;
+    total += align256(wh.size() * 2);
     if (m->d_weights) { cudaFree(m->d_weights); m->d_weights = nullptr; }
     if (cudaMalloc(&m->d_weights, total) != cudaSuccess) return fail(m, SVM_E_OOM, "weights allocation failed");
     char* base = static_cast<char*>(m->d_weights);
@@ -210,6 +248,11 @@ svm_status load_block_weights(svm_model* m, const unsigned char* p, size_t bytes
     dw.out_wx = dev[8];
     dw.out_wq = dev[9];
     dw.bout = bout;
+    if (bf16) {
+        CK(cudaMemcpy(base + wh_at, wh.data(), wh.size() * 2, cudaMemcpyHostToDevice));
+        dw.wq = base + wh_at;
+        if (tc_block_prepare(m->tc, d, dw.wq) != 0) return fail(m, SVM_E_UNSUPPORTED, "tensor-core block setup failed");
+    }
     m->used = all;
     m->tau = std::isfinite(tau) && tau >= 0 ? tau : INFINITY;
     m->has_weights = true;
@@ -243,9 +286,13 @@ svm_status svm_create_model(const svm_model_desc* desc, int device, svm_model** 
     if (d.prec < SVM_FP32 || d.prec > SVM_FP8_E4M3) return SVM_E_INVALID;
     if (d.n_hidden < 0 || d.n_hidden > 16) return SVM_E_INVALID;
     if (d.arch != SVM_ARCH_MLP && d.arch != SVM_ARCH_BLOCKS) return SVM_E_INVALID;
-    if (d.arch == SVM_ARCH_BLOCKS && (d.prec != SVM_FP32 || d.act != SVM_RELU || d.n_hidden < 1))
+    if (d.arch == SVM_ARCH_BLOCKS && (d.act != SVM_RELU || d.n_hidden < 1)) return SVM_E_UNSUPPORTED;
+    // the block architecture runs in FP32 (SIMT) or, at width 512, in BF16 on the tensor cores
+    if (d.arch == SVM_ARCH_BLOCKS && d.prec != SVM_FP32 && !(d.prec == SVM_BF16 && d.width == 512))
         return SVM_E_UNSUPPORTED;
-    if (d.prec == SVM_FP32) {
+    if (d.arch == SVM_ARCH_BLOCKS && d.prec == SVM_BF16) {
+        // checked above
+    } else if (d.prec == SVM_FP32) {
         if (!(d.width == 64 || d.width == 128 || d.width == 256 || d.width == 512 || d.width == 1024))
             return SVM_E_UNSUPPORTED;
     } else {

@@ -95,7 +95,7 @@ struct CallArgs {
     int L;              // hidden layers
     int act;            // 0 relu, 1 silu
     int arch;           // 0 plain MLP, 1 block architecture
-    int cb_stride;      // per-motion bias floats: W (arch 0), (L + 1) W + 1 (arch 1)
+    int cb_stride;      // per-motion bias floats: W (arch 0), (L + 1) W + 1 rounded up to a multiple of 4 (arch 1)
     uint32_t flags;
     float margin;
     float gate;         // margin + tau

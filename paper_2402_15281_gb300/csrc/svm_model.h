@@ -48,7 +48,9 @@ struct svm_model {
 // layer's and every block's c (W each) and the final layer's scalar (blocks).
 inline int cbias_stride(const svm_model_desc& d)
 {
-    return d.arch == SVM_ARCH_BLOCKS ? (d.n_hidden + 1) * d.width + 1 : d.width;
+    // blocks: padded to a multiple of 4 floats, so every motion's row starts 16-byte aligned (the
+    // tensor-core block kernel reads two adjacent columns' biases as one 8-byte load)
+    return d.arch == SVM_ARCH_BLOCKS ? ((d.n_hidden + 1) * d.width + 1 + 3) / 4 * 4 : d.width;
 }
 
 // Segments per path of a check call's flags (1: every motion stands alone).

@@ -200,6 +200,18 @@ __device__ __forceinline__ void tmem_ld_frag32(uint32_t taddr, float (&v)[32])
 // (register j: matrix j, thread t holds row t/4, columns 2 (t % 4), +1) to
 // shared memory; lane l gives the address of row l % 8 of matrix l / 8
 // (16 contiguous bytes).
+// The inverse of stmatrix_x4: four 8x8 matrices of 16-bit values from shared
+// memory into the accumulator-fragment layout (register j: matrix j, thread t
+// row t/4, columns 2 (t % 4), +1); lane l gives the address of row l % 8 of
+// matrix l / 8.
+__device__ __forceinline__ void ldmatrix_x4(uint32_t addr, uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
+                 : "r"(addr)
+                 : "memory");
+}
+
 __device__ __forceinline__ void stmatrix_x4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
 {
     asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b),

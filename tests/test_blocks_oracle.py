@@ -1,6 +1,7 @@
 """The block architecture of Sec. IV-A in the oracle, pinned on hand-worked
 and closed-form cases."""
 import numpy as np
+import pytest
 
 import oracle
 from paper_2402_15281_gb300 import synth as S
@@ -77,3 +78,34 @@ def test_block_blob_round_trip():
     n += 8 + 64 * 64 * 4 + 5 * 64 * 4 + 8 + 64 * 79 * 4 + 5 * 64 * 4
     n += 8 + 79 * 4 + 4
     assert len(blob) == 32 + n
+
+
+def test_block_forward_rounded():
+    """The 16-bit emulation of the block architecture: with fmt 0 it is
+    block_forward bitwise; with fmt 1 it equals torch's bfloat16 conversions
+    applied to h_0 and to every block output a later block reads (a library
+    routine), and the BF16 weight rounding equals torch's conversion."""
+    torch = pytest.importorskip("torch")
+    P = S.block_weights(64, 3, seed=11)
+    rng = np.random.default_rng(3)
+    X = rng.uniform(-1, 1, (50, 15))
+    np.testing.assert_array_equal(oracle.block_forward_rounded(P, X, fmt=0), oracle.block_forward(P, X))
+    Q = oracle.quantized_block_params(P, 1)
+    for (Wq, *_), (W, *_) in zip(Q["blocks"], P["blocks"]):
+        np.testing.assert_array_equal(Wq, torch.from_numpy(np.asarray(W, np.float32)).to(torch.bfloat16).float().numpy())
+
+    def bf(h):
+        return torch.from_numpy(h.astype(np.float32)).to(torch.bfloat16).double().numpy()
+
+    W0, b0 = (np.asarray(a, np.float64) for a in Q["init"])
+    h = bf(X @ W0.T + b0)
+    for l, (W, b, g, be, mu, var) in enumerate(Q["blocks"]):
+        W, b, g, be, mu, var = (np.asarray(a, np.float64) for a in (W, b, g, be, mu, var))
+        v = h if l == 0 else np.concatenate([h, X], axis=1)
+        y = np.maximum(v @ W.T + b, 0.0)
+        h = g * (y - mu) / np.sqrt(var + 1e-5) + be + h
+        if l < 2:
+            h = bf(h)
+    Wf, bfin = (np.asarray(a, np.float64) for a in Q["final"])
+    want = (np.concatenate([h, X], axis=1) @ Wf.T + bfin)[:, 0]
+    np.testing.assert_allclose(oracle.block_forward_rounded(Q, X, fmt=1), want, rtol=1e-12, atol=1e-12)
