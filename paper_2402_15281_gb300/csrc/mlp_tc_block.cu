@@ -24,7 +24,12 @@
 // One 128-pair tile is in flight per CTA: its 512-wide FP32 accumulator fills
 // the TMEM, and the layer's input -- a 128 x 512 bfloat16 tile in shared
 // memory (K-major, 128B swizzle), which is also its skip term -- is updated in
-// place by the epilogue, so the MMAs of a block and its epilogue alternate.
+// place by the epilogue.  The epilogue works in two column halves: a block
+// issues [output half 0 x input half 0], [half 0 x input half 1], [half 1 x
+// input half 0], then commits -- output half 0 is final and input half 0 has
+// been read by both halves, so the epilogue of columns 0-255 runs while the
+// last quarter [half 1 x input half 1] computes; the next block's first
+// quarter needs only that half of its input.
 // The epilogue reads the accumulator in the 16x256b fragment shape (thread t:
 // two adjacent columns of two rows per 8-column group), reads the skip term
 // with ldmatrix and writes the new activation with stmatrix.  The final layer
@@ -63,7 +68,7 @@ constexpr int NUM_THREADS = (2 + NUM_EPI_WARPS) * 32;
 constexpr int OFF_W = ACT_BYTES;
 constexpr int OFF_RED = OFF_W + STAGES * STAGE_BYTES;       // [3][TM] floats: column quarters 1-3
 constexpr int OFF_BAR = OFF_RED + 3 * TM * 4;
-constexpr int N_BARS = 2 * STAGES + 3;
+constexpr int N_BARS = 2 * STAGES + 5;
 constexpr int OFF_MISC = OFF_BAR + 8 * N_BARS;
 constexpr int SMEM_DYN = OFF_MISC + 16 + 1024;              // slack for 1024-byte alignment
 static_assert(SMEM_DYN <= 232448, "shared memory budget");
@@ -130,7 +135,7 @@ __device__ __forceinline__ uint32_t act_addr(uint32_t base, int row, int c8)
 
 // Linear x-part of 2 columns for the thread's 4 fragment rows: w = the 6
 // weights (x, y, z of column c, then of c + 1), added to z[k].
-__device__ __forceinline__ void add_xpart(const float* w, const float4 (&x4)[4], uint64_t (&z)[4])
+__device__ __forceinline__ void add_xpart(const float* w, const float3 (&x4)[4], uint64_t (&z)[4])
 {
     const float2 w0 = ldg2(w), w1 = ldg2(w + 2), w2 = ldg2(w + 4);
     const uint64_t wx = f2(w0.x, w1.y), wy = f2(w0.y, w2.x), wz = f2(w1.x, w2.y);
@@ -142,7 +147,7 @@ __device__ __forceinline__ void add_xpart(const float* w, const float4 (&x4)[4],
 template <bool HAS_WX, bool LAST>
 __device__ __forceinline__ void block_chunk(uint32_t abase, uint32_t t_addr, int q, int lane, int c0, const float* cl,
                                             const float* s, const float* t, const float* wx, const float* wf,
-                                            const float4 (&x4)[4], uint64_t (&acc4)[4])
+                                            const float3 (&x4)[4], uint64_t (&acc4)[4])
 {
     float v[32];
     tmem_ld_frag32(t_addr, v);
@@ -187,7 +192,7 @@ __device__ __forceinline__ void block_chunk(uint32_t abase, uint32_t t_addr, int
 // h_0 = W_0x x + c_0 (no activation) for the warp's 32 rows and 128 columns
 // from col0, rounded to bfloat16, as the first block's input.
 __device__ __forceinline__ void initial_layer(uint32_t abase, int q, int lane, int col0, const float* w0x,
-                                              const float* c0m, const float4 (&x4)[4])
+                                              const float* c0m, const float3 (&x4)[4])
 {
     const int c2 = 2 * (lane & 3), i8 = lane & 7, j = lane >> 3;
 #pragma unroll 1
@@ -224,9 +229,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     float* red = reinterpret_cast<float*>(dsm + OFF_RED);
     auto full_bar = [&](int s) { return bar0 + 8 * s; };
     auto empty_bar = [&](int s) { return bar0 + 8 * (STAGES + s); };
-    const uint32_t accf_bar = bar0 + 8 * (2 * STAGES);
-    const uint32_t epid_bar = bar0 + 8 * (2 * STAGES + 1);
-    const uint32_t drain_bar = bar0 + 8 * (2 * STAGES + 2);
+    // acc_bar(0): the first output half is final and the first input half consumed by both halves;
+    // acc_bar(1): the whole block.  epi_bar(e): column half e of the next input written (8 warps)
+    auto acc_bar = [&](int e) { return bar0 + 8 * (2 * STAGES + e); };
+    auto epi_bar = [&](int e) { return bar0 + 8 * (2 * STAGES + 2 + e); };
+    const uint32_t drain_bar = bar0 + 8 * (2 * STAGES + 4);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(dsm + OFF_MISC);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(dsm + OFF_MISC + 4);
 
@@ -240,8 +247,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             mbar_init(full_bar(s), 1);
             mbar_init(empty_bar(s), 1);
         }
-        mbar_init(accf_bar, 1);
-        mbar_init(epid_bar, NUM_EPI_WARPS);
+        for (int e = 0; e < 2; ++e) {
+            mbar_init(acc_bar(e), 1);
+            mbar_init(epi_bar(e), NUM_EPI_WARPS / 2);
+        }
         mbar_init(drain_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -287,30 +296,43 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
+        // Per block: [N-half 0, K 0-3] (needs input half 0), [N-half 0, K 4-7] (needs input half 1),
+        // [N-half 1, K 0-3], commit acc_bar(0), [N-half 1, K 4-7], commit acc_bar(1).  The epilogue
+        // of output half 0 then overlaps the last quarter of the block's MMAs, and the next block's
+        // first quarter waits only for it.
         const uint64_t a_desc0 = sdesc(abase), b_desc0 = sdesc(w_base);
         int stage = 0;
-        uint32_t phase = 0, ep = 0;
+        uint32_t phase = 0, ep0 = 0, ep1 = 0;
         bool ok = true;
+        auto quarter_block = [&](int h, int k0) {
+            const uint32_t d_tmem = tmem_base + (uint32_t)(h * NH);
+            for (int kk = k0; kk < k0 + KSL / 2; ++kk) {
+                if (!mbar_wait_warp(full_bar(stage), phase, abort_flag, A.dev_err)) { ok = false; return; }
+                tc_fence_after();
+                const uint64_t ad = a_desc0 + (uint64_t)(kk * (KBLOCK_BYTES >> 4));
+                const uint64_t bd = b_desc0 + (uint64_t)(stage * (STAGE_BYTES >> 4));
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    mma_f16_warp(d_tmem, ad + 2 * k, bd + 2 * k, IDESC, (kk | k) != 0 ? 1u : 0u);
+                mma_commit_warp(empty_bar(stage));
+                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+            }
+        };
         for (int i = 0; i < n_mine && ok; ++i)
             for (int l = 1; l <= L && ok; ++l) {
-                if (!mbar_wait_warp(epid_bar, ep, abort_flag, A.dev_err)) { ok = false; break; }
-                ep ^= 1u;
+                if (!mbar_wait_warp(epi_bar(0), ep0, abort_flag, A.dev_err)) { ok = false; break; }
+                ep0 ^= 1u;
                 tc_fence_after();
-                for (int h = 0; h < 2 && ok; ++h) {
-                    const uint32_t d_tmem = tmem_base + (uint32_t)(h * NH);
-                    for (int kk = 0; kk < KSL; ++kk) {
-                        if (!mbar_wait_warp(full_bar(stage), phase, abort_flag, A.dev_err)) { ok = false; break; }
-                        tc_fence_after();
-                        const uint64_t ad = a_desc0 + (uint64_t)(kk * (KBLOCK_BYTES >> 4));
-                        const uint64_t bd = b_desc0 + (uint64_t)(stage * (STAGE_BYTES >> 4));
-#pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            mma_f16_warp(d_tmem, ad + 2 * k, bd + 2 * k, IDESC, (kk | k) != 0 ? 1u : 0u);
-                        mma_commit_warp(empty_bar(stage));
-                        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
-                    }
-                }
-                if (ok) mma_commit_warp(accf_bar);
+                quarter_block(0, 0);
+                if (!ok) break;
+                if (!mbar_wait_warp(epi_bar(1), ep1, abort_flag, A.dev_err)) { ok = false; break; }
+                ep1 ^= 1u;
+                tc_fence_after();
+                quarter_block(0, KSL / 2);
+                if (ok) quarter_block(1, 0);
+                if (ok) mma_commit_warp(acc_bar(0));
+                if (ok) quarter_block(1, KSL / 2);
+                if (ok) mma_commit_warp(acc_bar(1));
             }
         // every MMA issued by this warp has completed before TMEM is freed
         mma_commit_warp(drain_bar);
@@ -323,6 +345,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int q = warp & 3;                      // TMEM lane quarter: rows 32 q ..
         const int cq = (warp - 2) >> 2;              // column quarter: columns 128 cq ..
         const int col0 = cq * 128;
+        const int eh = cq >> 1;                      // column half: 0 for columns 0-255, 1 for 256-511
         const int r = q * 32 + lane;                 // this lane's row (gate, reduction)
         const uint32_t t_row = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)col0;
         const int cbs = A.cb_stride;
@@ -336,23 +359,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             pe = A.pend[m];
         };
         // points of the thread's four fragment rows: row 16 (k >> 1) + 8 (k & 1) + lane / 4 of the quarter
-        auto load_x4 = [&](long long p0, long long pe, float4 (&x4)[4]) {
+        auto load_x4 = [&](long long p0, long long pe, float3 (&x4)[4]) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const long long p = p0 + q * 32 + 16 * (k >> 1) + 8 * (k & 1) + (lane >> 2);
-                x4[k] = p < pe ? ld_stream_f4(A.points + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 v = p < pe ? ld_stream_f4(A.points + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+                x4[k] = make_float3(v.x, v.y, v.z);
             }
         };
-        auto stage_h0 = [&](int m, const float4 (&x4)[4]) {
+        auto stage_h0 = [&](int m, const float3 (&x4)[4]) {
             initial_layer(abase, q, lane, col0, Wt.w1x, A.cbias + (long long)m * cbs, x4);
             fence_async_smem();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(epid_bar);
+            if (lane == 0) mbar_arrive(epi_bar(eh));
         };
         int m = 0;
         long long p0 = 0, pe = 0;
-        float4 x4[4];
+        float3 x4[4];
         if (n_mine > 0) {
             tile_of(0, m, p0, pe);
             load_x4(p0, pe, x4);
@@ -368,12 +392,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const float* wx = Wt.blk_wx + (long long)(l - 1) * WB * 3;
                 int nm = 0;
                 long long np0 = 0, npe = 0;
-                float4 xn[4];
+                float3 xn[4];
                 if (l == L && has_next) {
                     tile_of(i + 1, nm, np0, npe);
                     load_x4(np0, npe, xn);
                 }
-                if (!mbar_wait(accf_bar, acc_phase, abort_flag, A.dev_err)) { ok = false; break; }
+                if (!mbar_wait(acc_bar(eh), acc_phase, abort_flag, A.dev_err)) { ok = false; break; }
                 acc_phase ^= 1u;
                 tc_fence_after();
                 uint64_t acc4[4] = {0ull, 0ull, 0ull, 0ull};
@@ -390,7 +414,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     fence_async_smem();
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(epid_bar);
+                    if (lane == 0) mbar_arrive(epi_bar(eh));
                     continue;
                 }
                 // ---- last block and the final layer

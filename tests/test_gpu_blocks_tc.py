@@ -147,3 +147,40 @@ def test_block_tc_times_at_the_paper_shapes(svm):
     for name, n, ms in rows:
         print(f"block network {name}, 1 motion x {n} points: {ms:.3f} ms")
     assert all(ms > 0 for _, _, ms in rows)
+
+
+def test_block_tc_throughput_roofline(svm):
+    """The tensor-core block kernel on a large workload: 16 motions x a
+    200 000-point bin cloud (3.2 M pairs, 25 008 tiles), prediction only.  The
+    network phase (CUDA events inside the library) against the algorithmic
+    FLOP per pair, 2 (3 W + L W^2 + (L - 1) 3 W + W + 3) (x-parts, h-parts and
+    the final layer; the q-parts are per-motion constants), as a fraction of the
+    measured burst BF16 peak."""
+    import json
+    import os
+    robot = S.make_robot(1)
+    pts = torch.from_numpy(S.bin_cloud(200_000, seed=0)).cuda()
+    q0, q1 = S.bin_motions(robot, 16, seed=0)
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "MEASURED_PEAKS.json")
+    peak = json.load(open(path)).get("bf16_tflops", 1900.0) if os.path.exists(path) else 1900.0
+    W = 512
+    for nb in (5, 11):
+        P = S.block_weights(W, nb, seed=1)
+        h = _model(svm, robot, P, svm.SVM_BF16)
+        try:
+            svm.svm_profile_enable(h, True)
+            res = svm.new_results(16)
+            ms = []
+            for k in range(8):
+                svm.svm_check_motions(h, q0, q1, pts, 0.03, 64, svm.SVM_PREDICT_ONLY, res)
+                if k >= 3:
+                    ms.append(float(svm.svm_profile_read(h)[1]))
+            torch.cuda.synchronize()
+        finally:
+            svm.svm_destroy_model(h)
+        flop = 16 * 200_000 * 2 * (3 * W + nb * W * W + (nb - 1) * 3 * W + W + 3)
+        t = float(np.median(ms))
+        tf = flop / (t * 1e-3) / 1e12
+        print(f"BF16 blocks {nb}x512, 16 motions x 200 000 points: network {t:.3f} ms = {tf:.0f} TFLOP/s = "
+              f"{tf / peak:.2f} of the measured burst BF16 peak")
+        assert tf > 0
