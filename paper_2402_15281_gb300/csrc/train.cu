@@ -15,7 +15,8 @@
 // Step (loss: mean |f - delta|, the error the paper reports as MAE):
 //   layer 1 (15 -> W) in FP32 on CUDA cores, hidden layers as BF16 tcgen05
 //   GEMMs (train_gemm.cu), output layer, loss and its gradient on CUDA cores;
-//   backward: per hidden layer a split-K weight-gradient GEMM and an input-
+//   backward: per hidden layer a split-K weight-gradient GEMM (reading G and
+//   H as stored, [batch][features], as MN-major operands) and an input-
 //   gradient GEMM, bias gradients by column sums, layer-1 gradient on CUDA
 //   cores; then Adam (lr, betas (0.9, 0.999), eps 1e-8, as in Sec. V) on FP32
 //   master weights, which also refreshes the BF16 copies W and W^T.
@@ -194,7 +195,7 @@ __device__ __forceinline__ void load_bf16_row32(const __nv_bfloat16* src, float 
 }
 
 // Layer 1 forward: 32 samples per block (lane = sample), warps split the
-// feature chunks.  Writes Z0, H0 (row-major) and H0^T.
+// feature chunks.  Writes Z0, H0 (row-major) and, if H0T is given, H0^T.
 template <int ACT>
 __global__ void __launch_bounds__(128) layer1_fwd_kernel(StepArgs a, __nv_bfloat16* Z0, __nv_bfloat16* H0,
                                                          __nv_bfloat16* H0T)
@@ -222,13 +223,13 @@ __global__ void __launch_bounds__(128) layer1_fwd_kernel(StepArgs a, __nv_bfloat
         }
         store_bf16_row32(Z0 + (long long)r * a.W + c * 32, z);
         store_bf16_row32(H0 + (long long)r * a.W + c * 32, h);
-        store_bf16_transposed32(tp, lane, h, H0T + (long long)(c * 32) * a.B + blockIdx.x * 32, a.B);
+        if (H0T) store_bf16_transposed32(tp, lane, h, H0T + (long long)(c * 32) * a.B + blockIdx.x * 32, a.B);
     }
 }
 
 // Output layer, loss and its gradient: f = w_out . h_L + b_out, e = f - delta;
 // block b writes its sum of |e| to loss[b]; with eval == 0 also df = sign(e)/B,
-// G_L = df * w_out * act'(z_L) (as G_L and G_L^T), and the block's partial
+// G_L = df * w_out * act'(z_L) (as G_L and, if GLT is given, G_L^T), and the block's partial
 // gradients of w_out and b_out to part[b][0..W].  Sums over blocks follow in
 // a fixed order (reduce_kernel), so the step is deterministic.
 template <int ACT>
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(128) head_kernel(StepArgs a, const __nv_bfloat
             if (lane == i) pb[c * 32 + i] = dw;
         }
         store_bf16_row32(GL + (long long)r * a.W + c * 32, gv);
-        store_bf16_transposed32(tp, lane, gv, GLT + (long long)(c * 32) * a.B + blockIdx.x * 32, a.B);
+        if (GLT) store_bf16_transposed32(tp, lane, gv, GLT + (long long)(c * 32) * a.B + blockIdx.x * 32, a.B);
     }
 }
 
@@ -311,21 +312,35 @@ __global__ void __launch_bounds__(256) layer1_bwd_kernel(StepArgs a, const __nv_
     }
 }
 
-// db[n] = sum_b GT[n][b]
-__global__ void __launch_bounds__(256) colsum_kernel(const __nv_bfloat16* GT, long long B, float* db)
+// Bias gradients: db[n] += sum over the batch of G[b][n] (G row-major [B][W]).
+// A block takes 8 adjacent columns (16 bytes of every row); each column is
+// summed in a fixed order -- thread t over rows t, t + 256, ..., then a warp
+// butterfly, then the 8 warp sums in order -- so a step is deterministic.
+__global__ void __launch_bounds__(256) colsum_rows_kernel(const __nv_bfloat16* G, long long B, int W, float* db)
 {
-    const int n = blockIdx.x;
-    float s = 0.0f;
-    for (long long b = threadIdx.x; b < B; b += blockDim.x) s += __bfloat162float(GT[(long long)n * B + b]);
-    __shared__ float red[8];
+    const int n0 = blockIdx.x * 8;
+    float s[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    for (long long b = threadIdx.x; b < B; b += blockDim.x) {
+        const uint4 w = *reinterpret_cast<const uint4*>(G + b * W + n0);
+        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-    for (int sh = 16; sh > 0; sh >>= 1) s += __shfl_xor_sync(0xffffffffu, s, sh);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        for (int i = 0; i < 4; ++i) {
+            s[2 * i] += __uint_as_float(ws[i] << 16);
+            s[2 * i + 1] += __uint_as_float(ws[i] & 0xFFFF0000u);
+        }
+    }
+    __shared__ float red[8][8];                      // [column][warp]
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) s[j] += __shfl_xor_sync(0xffffffffu, s[j], sh);
+        if ((threadIdx.x & 31) == 0) red[j][threadIdx.x >> 5] = s[j];
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 8) {
         float t = 0.0f;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-        db[n] += t;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[threadIdx.x][i];
+        db[n0 + threadIdx.x] += t;
     }
 }
 
@@ -401,8 +416,10 @@ struct svm_trainer {
     long long part_n = 0;
     unsigned int* err = nullptr;
     __nv_bfloat16* wb = nullptr; __nv_bfloat16* wbt = nullptr;
-    std::vector<__nv_bfloat16*> H, Z, HT, G, GT;     // per layer 0..L
-    std::vector<Map> mapH, mapHT, mapG, mapGT, mapW, mapWT;
+    std::vector<__nv_bfloat16*> H, Z, G;             // per layer 0..L, [B][W]
+    // A operands of the forward and input-gradient GEMMs (K-major, 128-row boxes) and the MN-major
+    // operands of the weight-gradient GEMM (64 x 64 boxes)
+    std::vector<Map> mapH, mapG, mapHmn, mapGmn, mapW, mapWT;
     // data
     float4* X = nullptr; int* MID = nullptr; double* q0 = nullptr; double* q1 = nullptr;
     int n_motions = 0; long long n_samples = 0;
@@ -474,18 +491,18 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
     const int W = t->W, L = t->L, B = t->B;
     const StepArgs a = step_args(t, base, stride);
     const size_t l1_smem = (size_t)W * 16 * 4 + 4 * 32 * kTpStride;
-    if (t->act == 0) layer1_fwd_kernel<0><<<B / 32, 128, l1_smem, s>>>(a, t->Z[0], t->H[0], t->HT[0]);
-    else layer1_fwd_kernel<1><<<B / 32, 128, l1_smem, s>>>(a, t->Z[0], t->H[0], t->HT[0]);
+    if (t->act == 0) layer1_fwd_kernel<0><<<B / 32, 128, l1_smem, s>>>(a, t->Z[0], t->H[0], nullptr);
+    else layer1_fwd_kernel<1><<<B / 32, 128, l1_smem, s>>>(a, t->Z[0], t->H[0], nullptr);
     for (int l = 1; l <= L; ++l) {
         GemmArgs g{};
         g.n_mt = B / 128; g.n_nt = W / 256; g.n_ks = 1; g.k_len = W;
         g.ld_rows = W; g.ld_cols = B;
         g.bias = t->P + t->off_h + (long long)(l - 1) * ((long long)W * W + W) + (long long)W * W;
-        g.h_out = t->H[l]; g.z_out = t->Z[l]; g.ht_out = t->HT[l]; g.err = t->err;
+        g.h_out = t->H[l]; g.z_out = t->Z[l]; g.ht_out = nullptr; g.err = t->err;
         launch_train_gemm(kEpiFwd, t->act, t->mapH[l - 1].b, t->mapW[l - 1].b, g, t->n_sms, s);
     }
-    if (t->act == 0) head_kernel<0><<<B / 32, 128, 0, s>>>(a, t->H[L], t->Z[L], t->G[L], t->GT[L], grad ? 0 : 1);
-    else head_kernel<1><<<B / 32, 128, 0, s>>>(a, t->H[L], t->Z[L], t->G[L], t->GT[L], grad ? 0 : 1);
+    if (t->act == 0) head_kernel<0><<<B / 32, 128, 0, s>>>(a, t->H[L], t->Z[L], t->G[L], nullptr, grad ? 0 : 1);
+    else head_kernel<1><<<B / 32, 128, 0, s>>>(a, t->H[L], t->Z[L], t->G[L], nullptr, grad ? 0 : 1);
     reduce_kernel<<<1, 1, 0, s>>>(t->loss, B / 32, 1, t->loss_sum);
     if (!grad) return SVM_OK;
     reduce_kernel<<<grid_for(W + 1), 256, 0, s>>>(t->part, B / 32, W + 1, t->Gr + t->off_out);
@@ -495,13 +512,13 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
         const int k_len = B >= 2048 ? 2048 : B;
         g.n_mt = W / 128; g.n_nt = W / 256; g.n_ks = B / k_len; g.k_len = k_len;
         g.ld_rows = W; g.ld_cols = 0; g.dw = t->part; g.split_stride = (long long)W * W; g.err = t->err;
-        launch_train_gemm(kEpiWgrad, 0, t->mapGT[l].b, t->mapHT[l - 1].b, g, t->n_sms, s);
+        launch_train_gemm(kEpiWgrad, 0, t->mapGmn[l].b, t->mapHmn[l - 1].b, g, t->n_sms, s);
         reduce_kernel<<<grid_for((long long)W * W), 256, 0, s>>>(t->part, g.n_ks, (long long)W * W, t->Gr + woff);
-        colsum_kernel<<<W, 256, 0, s>>>(t->GT[l], B, t->Gr + woff + (long long)W * W);
+        colsum_rows_kernel<<<W / 8, 256, 0, s>>>(t->G[l], B, W, t->Gr + woff + (long long)W * W);
         GemmArgs d{};
         d.n_mt = B / 128; d.n_nt = W / 256; d.n_ks = 1; d.k_len = W;
         d.ld_rows = W; d.ld_cols = B; d.z_in = t->Z[l - 1];
-        d.h_out = t->G[l - 1]; d.ht_out = t->GT[l - 1]; d.err = t->err;
+        d.h_out = t->G[l - 1]; d.ht_out = nullptr; d.err = t->err;
         launch_train_gemm(kEpiDgrad, t->act, t->mapG[l].b, t->mapWT[l - 1].b, d, t->n_sms, s);
     }
     layer1_bwd_kernel<<<B / 256, 256, 0, s>>>(a, t->G[0]);
@@ -566,22 +583,22 @@ svm_status svm_train_create(const svm_model_desc* desc, int device, int32_t batc
     if ((st = talloc(t, &t->err, 256)) != SVM_OK) return fail_free(st);
     if ((st = talloc(t, &t->wb, L * W * W * 2)) != SVM_OK) return fail_free(st);
     if ((st = talloc(t, &t->wbt, L * W * W * 2)) != SVM_OK) return fail_free(st);
-    t->H.resize(L + 1); t->Z.resize(L + 1); t->HT.resize(L + 1); t->G.resize(L + 1); t->GT.resize(L + 1);
+    t->H.resize(L + 1); t->Z.resize(L + 1); t->G.resize(L + 1);
     for (int l = 0; l <= L; ++l)
-        for (auto* v : {&t->H, &t->Z, &t->HT, &t->G, &t->GT})
+        for (auto* v : {&t->H, &t->Z, &t->G})
             if ((st = talloc(t, &(*v)[l], B * W * 2)) != SVM_OK) return fail_free(st);
     cudaMemset(t->P, 0, t->np * 4);
     cudaMemset(t->Mo, 0, t->np * 4);
     cudaMemset(t->Vo, 0, t->np * 4);
     cudaMemset(t->err, 0, 4);
-    t->mapH.resize(L + 1); t->mapHT.resize(L + 1); t->mapG.resize(L + 1); t->mapGT.resize(L + 1);
+    t->mapH.resize(L + 1); t->mapG.resize(L + 1); t->mapHmn.resize(L + 1); t->mapGmn.resize(L + 1);
     t->mapW.resize(L); t->mapWT.resize(L);
     int bad = 0;
     for (int l = 0; l <= L; ++l) {
         bad |= train_make_map(t->mapH[l].b, t->H[l], B, W, 128);       // A of FWD
-        bad |= train_make_map(t->mapHT[l].b, t->HT[l], W, B, 256);     // B of WGRAD
         bad |= train_make_map(t->mapG[l].b, t->G[l], B, W, 128);       // A of DGRAD
-        bad |= train_make_map(t->mapGT[l].b, t->GT[l], W, B, 128);     // A of WGRAD
+        bad |= train_make_map(t->mapHmn[l].b, t->H[l], B, W, 64);      // B of WGRAD (MN-major)
+        bad |= train_make_map(t->mapGmn[l].b, t->G[l], B, W, 64);      // A of WGRAD (MN-major)
     }
     for (int l = 0; l < L; ++l) {
         bad |= train_make_map(t->mapW[l].b, t->wb + (long long)l * W * W, W, W, 256);    // B of FWD

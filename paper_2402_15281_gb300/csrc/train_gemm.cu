@@ -3,14 +3,20 @@
 // FP32 accumulation in TMEM, and three fused epilogues:
 //
 //   FWD    hidden layer forward, rows = samples:  z = acc + b, h = act(z);
-//          writes H [M][N] (the next layer's A), Z [M][N] (for act') and
-//          H^T [N][M] (the weight-gradient operand), all bfloat16.
+//          writes H [M][N] (the next layer's A) and Z [M][N] (for act'), and
+//          H^T [N][M] if asked (bfloat16).
 //   DGRAD  input gradient, rows = samples:  g = acc * act'(z_prev);
-//          writes G [M][N] and G^T [N][M] (bfloat16).
+//          writes G [M][N], and G^T [N][M] if asked (bfloat16).
 //   WGRAD  weight gradient dW = G^T H over a slice of the batch (split-K):
 //          stores the FP32 partial of split s into dW + s * M * N ([M][N]);
 //          the splits are summed afterwards in a fixed order, so the result
-//          does not depend on the order in which CTAs finish.
+//          does not depend on the order in which CTAs finish.  G and H are
+//          read as stored, [batch][features], as MN-major operands: per stage
+//          64 x 64 boxes (64 features of 64 batch rows, 128B swizzle), the
+//          descriptor's LBO the 8 KB between boxes along M / N and SBO the
+//          1 KB between 8-row groups along K (the K = batch step of one MMA
+//          is 16 rows, 2 KB); the instruction descriptor marks A and B
+//          MN-major.
 //
 // Persistent kernel, one CTA per SM, 10 warps: warp 0 streams A and B tiles
 // (128 x 64 and 256 x 64 bfloat16, 128B swizzle) with TMA into a 4-stage
@@ -51,6 +57,22 @@ constexpr int SMEM_DYN = OFF_MISC + 16 + 1024;
 static_assert(SMEM_DYN <= 232448, "shared memory budget");
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
+// the same with A and B MN-major (bits 15 and 16)
+constexpr uint32_t IDESC_MN = IDESC | (1u << 15) | (1u << 16);
+constexpr int MN_BOX_BYTES = 64 * BK * 2;                 // one 64-feature x 64-row box
+
+// Shared-memory descriptor of an MN-major operand, 128B swizzle: LBO = bytes
+// between 64-element boxes along M / N, SBO = bytes between 8-row groups along K.
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(MN_BOX_BYTES >> 4) << 16;   // LBO
+    d |= (uint64_t)(1024 >> 4) << 32;           // SBO
+    d |= (uint64_t)1 << 46;                     // version
+    d |= (uint64_t)2 << 61;                     // SWIZZLE_128B
+    return d;
+}
 
 __device__ __forceinline__ void st_global_v4(void* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
 {
@@ -177,8 +199,17 @@ __global__ void __launch_bounds__(THREADS, 1)
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, g.err)) { ok = false; break; }
                     mbar_arrive_tx(full_bar(stage), STAGE_BYTES);
                     const uint32_t dst = sbase + stage * STAGE_BYTES;
-                    tma_load_2d(dst, &amap, k0 + kk * BK, mt * BM, full_bar(stage));
-                    tma_load_2d(dst + A_BYTES, &bmap, k0 + kk * BK, nt * BN, full_bar(stage));
+                    if constexpr (EPI == kEpiWgrad) {
+                        // MN-major: boxes of 64 features x 64 batch rows, consecutive along M / N
+                        for (int j = 0; j < BM / 64; ++j)
+                            tma_load_2d(dst + j * MN_BOX_BYTES, &amap, mt * BM + 64 * j, k0 + kk * BK, full_bar(stage));
+                        for (int j = 0; j < BN / 64; ++j)
+                            tma_load_2d(dst + A_BYTES + j * MN_BOX_BYTES, &bmap, nt * BN + 64 * j, k0 + kk * BK,
+                                        full_bar(stage));
+                    } else {
+                        tma_load_2d(dst, &amap, k0 + kk * BK, mt * BM, full_bar(stage));
+                        tma_load_2d(dst + A_BYTES, &bmap, k0 + kk * BK, nt * BN, full_bar(stage));
+                    }
                     armed |= 1u << stage;
                     armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
                     if (++stage == STAGES) { stage = 0; phase ^= 1u; }
@@ -198,7 +229,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         int stage = 0;
         uint32_t phase = 0;
         uint32_t acce_phase0 = 0u, acce_phase1 = 0u;
-        const uint64_t a_desc0 = sdesc(sbase), b_desc0 = sdesc(sbase + A_BYTES);
+        constexpr bool MN = EPI == kEpiWgrad;
+        const uint64_t a_desc0 = MN ? sdesc_mn(sbase) : sdesc(sbase);
+        const uint64_t b_desc0 = MN ? sdesc_mn(sbase + A_BYTES) : sdesc(sbase + A_BYTES);
+        // one MMA step of K = 16: 32 bytes along a K-major row, 16 rows (2 KB) of an MN-major box
+        constexpr uint64_t kstep = MN ? (16 * 128) >> 4 : 2;
         bool ok = true;
         for (int i = 0; i < n_mine && ok; ++i) {
             const int b = i & 1;
@@ -214,7 +249,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const uint64_t bd = b_desc0 + (uint64_t)(stage * (STAGE_BYTES >> 4));
 #pragma unroll
                 for (int k = 0; k < BK / 16; ++k)
-                    mma_f16_warp(d_tmem, ad + 2 * k, bd + 2 * k, IDESC, (kk | k) != 0 ? 1u : 0u);
+                    mma_f16_warp(d_tmem, ad + kstep * k, bd + kstep * k, MN ? IDESC_MN : IDESC, (kk | k) != 0 ? 1u : 0u);
                 mma_commit_warp(empty_bar(stage));
                 if (++stage == STAGES) { stage = 0; phase ^= 1u; }
             }
@@ -261,7 +296,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     for (int q = 0; q < 32; ++q) v[q] = act_fwd<ACT>(z[q]);
                     store_row32(g.z_out + m * g.ld_rows + n0, z);
                     store_row32(g.h_out + m * g.ld_rows + n0, v);
-                    store_transposed32(tp, lane, v, g.ht_out + (long long)n0 * g.ld_cols + m0, g.ld_cols);
+                    if (g.ht_out) store_transposed32(tp, lane, v, g.ht_out + (long long)n0 * g.ld_cols + m0, g.ld_cols);
                 } else if constexpr (EPI == kEpiDgrad) {
                     const uint4* zp = reinterpret_cast<const uint4*>(g.z_in + m * g.ld_rows + n0);
 #pragma unroll
@@ -277,7 +312,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                         v[8 * q + 7] *= act_grad<ACT>(bf_hi(w.w));
                     }
                     store_row32(g.h_out + m * g.ld_rows + n0, v);
-                    store_transposed32(tp, lane, v, g.ht_out + (long long)n0 * g.ld_cols + m0, g.ld_cols);
+                    if (g.ht_out) store_transposed32(tp, lane, v, g.ht_out + (long long)n0 * g.ld_cols + m0, g.ld_cols);
                 } else {
                     float4* dst = reinterpret_cast<float4*>(g.dw + (long long)ks * g.split_stride + m * g.ld_rows + n0);
 #pragma unroll
