@@ -312,44 +312,93 @@ __global__ void __launch_bounds__(256) layer1_bwd_kernel(StepArgs a, const __nv_
     }
 }
 
-// Bias gradients: db[n] += sum over the batch of G[b][n] (G row-major [B][W]).
-// A block takes 8 adjacent columns (16 bytes of every row); each column is
-// summed in a fixed order -- thread t over rows t, t + 256, ..., then a warp
-// butterfly, then the 8 warp sums in order -- so a step is deterministic.
-__global__ void __launch_bounds__(256) colsum_rows_kernel(const __nv_bfloat16* G, long long B, int W, float* db)
+// Bias gradients db[n] += sum over the batch of G[b][n] (G row-major [B][W]),
+// in a fixed order, so a step is deterministic: 256 chains per column (chain
+// t sums rows t, t + 256, ... in order), then per group of 32 chains the
+// butterfly x_l += x_{l ^ s} (s = 16, 8, 4, 2, 1) read at lane 0, then the 8
+// group results in order.  Part 1 runs the chains: thread (t, q) of a block
+// sums columns 4q..4q+3 of its rows, a warp covering 128 contiguous columns
+// of one row (full sectors), and writes chain[t][n] (loads of 8 rows are
+// issued before their adds).  Part 2 (one warp per column) forms the tree.
+__global__ void __launch_bounds__(256) colsum_chains_kernel(const __nv_bfloat16* G, long long B, int W, float* chain)
 {
-    const int n0 = blockIdx.x * 8;
-    float s[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-    for (long long b = threadIdx.x; b < B; b += blockDim.x) {
-        const uint4 w = *reinterpret_cast<const uint4*>(G + b * W + n0);
-        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+    const int q = blockIdx.x * 32 + (threadIdx.x & 31);          // column quad
+    const int t = blockIdx.y * 8 + (threadIdx.x >> 5);           // chain (row class), 0..255
+    const int n0 = 4 * q;
+    float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    auto add = [&](uint2 w) {
+        s[0] += __uint_as_float(w.x << 16);
+        s[1] += __uint_as_float(w.x & 0xFFFF0000u);
+        s[2] += __uint_as_float(w.y << 16);
+        s[3] += __uint_as_float(w.y & 0xFFFF0000u);
+    };
+    long long b = t;
+    for (; b + 7 * 256 < B; b += 8 * 256) {
+        uint2 w[8];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            s[2 * i] += __uint_as_float(ws[i] << 16);
-            s[2 * i + 1] += __uint_as_float(ws[i] & 0xFFFF0000u);
-        }
-    }
-    __shared__ float red[8][8];                      // [column][warp]
+        for (int u = 0; u < 8; ++u) w[u] = *reinterpret_cast<const uint2*>(G + (b + u * 256) * W + n0);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-#pragma unroll
-        for (int sh = 16; sh > 0; sh >>= 1) s[j] += __shfl_xor_sync(0xffffffffu, s[j], sh);
-        if ((threadIdx.x & 31) == 0) red[j][threadIdx.x >> 5] = s[j];
+        for (int u = 0; u < 8; ++u) add(w[u]);
     }
-    __syncthreads();
-    if (threadIdx.x < 8) {
-        float t = 0.0f;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[threadIdx.x][i];
-        db[n0 + threadIdx.x] += t;
-    }
+    for (; b < B; b += 256) add(*reinterpret_cast<const uint2*>(G + b * W + n0));
+    *reinterpret_cast<float4*>(chain + (long long)t * W + n0) = make_float4(s[0], s[1], s[2], s[3]);
 }
 
-// dst[j] += sum_{p < P} part[p * n + j], summed in the order p = 0, 1, ...
+__global__ void __launch_bounds__(256) colsum_tree_kernel(const float* chain, int W, float* db)
+{
+    const int n = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (n >= W) return;
+    float total = 0.0f;
+    for (int w = 0; w < 8; ++w) {
+        float x = chain[(long long)(32 * w + lane) * W + n];
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) x += __shfl_xor_sync(0xffffffffu, x, sh);
+        total += x;
+    }
+    if (lane == 0) db[n] += total;
+}
+
+// dst[j] += sum_{p < P} part[p * n + j] for long sums (P in the thousands):
+// a block takes TJ outputs and stages tiles of 2048 / TJ partials x TJ outputs
+// in shared memory with coalesced loads; thread j then adds its column in the
+// order p = 0, 1, ... (the order of reduce_kernel).
+template <int TJ>
+__global__ void __launch_bounds__(256) reduce_long_kernel(const float* part, int P, long long n, float* dst)
+{
+    constexpr int TP = 2048 / TJ;
+    __shared__ float tile[TP][TJ + (TJ > 1 ? 1 : 0)];
+    const long long j0 = (long long)blockIdx.x * TJ;
+    float s = 0.0f;
+    for (int p0 = 0; p0 < P; p0 += TP) {
+        for (int i = threadIdx.x; i < TP * TJ; i += blockDim.x) {
+            const int pp = i / TJ, jj = i % TJ;
+            tile[pp][jj] = (p0 + pp < P && j0 + jj < n) ? part[(long long)(p0 + pp) * n + j0 + jj] : 0.0f;
+        }
+        __syncthreads();
+        if (threadIdx.x < TJ) {
+            const int lim = min(TP, P - p0);
+            for (int pp = 0; pp < lim; ++pp) s += tile[pp][threadIdx.x];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < TJ && j0 + threadIdx.x < n) dst[j0 + threadIdx.x] += s;
+}
+
+// dst[j] += sum_{p < P} part[p * n + j], summed in the order p = 0, 1, ...;
+// the loads of 8 partials are issued before their adds (same order of the adds).
 __global__ void reduce_kernel(const float* part, int P, long long n, float* dst)
 {
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
         float s = 0.0f;
-        for (int p = 0; p < P; ++p) s += part[(long long)p * n + j];
+        int p = 0;
+        for (; p + 8 <= P; p += 8) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = part[(long long)(p + u) * n + j];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s += v[u];
+        }
+        for (; p < P; ++p) s += part[(long long)p * n + j];
         dst[j] += s;
     }
 }
@@ -503,9 +552,9 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
     }
     if (t->act == 0) head_kernel<0><<<B / 32, 128, 0, s>>>(a, t->H[L], t->Z[L], t->G[L], nullptr, grad ? 0 : 1);
     else head_kernel<1><<<B / 32, 128, 0, s>>>(a, t->H[L], t->Z[L], t->G[L], nullptr, grad ? 0 : 1);
-    reduce_kernel<<<1, 1, 0, s>>>(t->loss, B / 32, 1, t->loss_sum);
+    reduce_long_kernel<1><<<1, 256, 0, s>>>(t->loss, B / 32, 1, t->loss_sum);
     if (!grad) return SVM_OK;
-    reduce_kernel<<<grid_for(W + 1), 256, 0, s>>>(t->part, B / 32, W + 1, t->Gr + t->off_out);
+    reduce_long_kernel<32><<<(W + 1 + 31) / 32, 256, 0, s>>>(t->part, B / 32, W + 1, t->Gr + t->off_out);
     for (int l = L; l >= 1; --l) {
         const long long woff = t->off_h + (long long)(l - 1) * ((long long)W * W + W);
         GemmArgs g{};
@@ -514,7 +563,9 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
         g.ld_rows = W; g.ld_cols = 0; g.dw = t->part; g.split_stride = (long long)W * W; g.err = t->err;
         launch_train_gemm(kEpiWgrad, 0, t->mapGmn[l].b, t->mapHmn[l - 1].b, g, t->n_sms, s);
         reduce_kernel<<<grid_for((long long)W * W), 256, 0, s>>>(t->part, g.n_ks, (long long)W * W, t->Gr + woff);
-        colsum_rows_kernel<<<W / 8, 256, 0, s>>>(t->G[l], B, W, t->Gr + woff + (long long)W * W);
+        // the split-K partials are reduced: part holds the bias-gradient chains next
+        colsum_chains_kernel<<<dim3(W / 128, 32), 256, 0, s>>>(t->G[l], B, W, t->part);
+        colsum_tree_kernel<<<W / 8, 256, 0, s>>>(t->part, W, t->Gr + woff + (long long)W * W);
         GemmArgs d{};
         d.n_mt = B / 128; d.n_nt = W / 256; d.n_ks = 1; d.k_len = W;
         d.ld_rows = W; d.ld_cols = B; d.z_in = t->Z[l - 1];
@@ -522,7 +573,7 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
         launch_train_gemm(kEpiDgrad, t->act, t->mapG[l].b, t->mapWT[l - 1].b, d, t->n_sms, s);
     }
     layer1_bwd_kernel<<<B / 256, 256, 0, s>>>(a, t->G[0]);
-    reduce_kernel<<<grid_for((long long)W * 16), 256, 0, s>>>(t->part, B / 256, (long long)W * 16, t->Gr + t->off_w1);
+    reduce_long_kernel<32><<<(W * 16 + 31) / 32, 256, 0, s>>>(t->part, B / 256, (long long)W * 16, t->Gr + t->off_w1);
     return SVM_OK;
 }
 
