@@ -71,6 +71,8 @@ def lib():
         L.orc_mlp_forward_rounded.argtypes = [_D, C.c_int, C.c_int, C.c_int, _I32, _D, _D, C.c_long, _D]
         L.orc_mlp_loss_grad.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, _D, C.c_long, _D]
         L.orc_mlp_loss_grad.restype = C.c_double
+        L.orc_mlp_loss_grad_bf16.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, _D, C.c_long, _D]
+        L.orc_mlp_loss_grad_bf16.restype = C.c_double
         L.orc_adam_step.argtypes = [_D, _D, _D, _D, C.c_long, C.c_long, C.c_double, C.c_double,
                                     C.c_double, C.c_double]
         L.orc_check_motions.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, C.c_double, _D,
@@ -269,6 +271,16 @@ def mlp_loss_grad(P, width, n_hidden, act, inputs, target):
     G = np.zeros(param_count(width, n_hidden))
     loss = lib().orc_mlp_loss_grad(_d(P), width, n_hidden, act, inputs, _d(target),
                                    inputs.shape[0], G)
+    return loss, G
+
+
+def mlp_loss_grad_bf16(P, width, n_hidden, act, inputs, target):
+    """mlp_loss_grad with bfloat16 rounding where a BF16 training step stores
+    values (hidden weights in the products, every Z and H, every layer's
+    gradient G); (loss, gradient)."""
+    inputs = _d(inputs).reshape(-1, 15)
+    G = np.zeros(param_count(width, n_hidden))
+    loss = lib().orc_mlp_loss_grad_bf16(_d(P), width, n_hidden, act, inputs, _d(target), inputs.shape[0], G)
     return loss, G
 
 

@@ -27,6 +27,10 @@
  *                             the flagged points, verdict "free iff > eps_S"
  *                             (Sec. IV-B, Algorithm 1).
  *   orc_mlp_loss_grad         L1 training loss and its gradient (backprop).
+ *   orc_mlp_loss_grad_bf16    the same backpropagation with bfloat16 rounding
+ *                             of the hidden weights in their products and of
+ *                             Z, H and each hidden layer's gradient G (the
+ *                             values a BF16 training step stores).
  *   orc_adam_step             Adam update with bias correction (Sec. V).
  *   orc_round_bf16,
  *   orc_round_e4m3            the quantisers that define the BF16 and FP8
@@ -40,6 +44,7 @@
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
+#include <stdlib.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -486,6 +491,85 @@ double orc_mlp_loss_grad(const double *P, int width, int n_hidden, int act,
             G[(long)width * 15 + o] += g[o];
         }
     }
+    return loss / (double)n;
+}
+
+/* orc_mlp_loss_grad with the values rounded to nearest-even bfloat16 where a
+ * BF16 training step stores them, everything else in double: the hidden
+ * weights inside the hidden layers' products, every layer's pre-activation
+ * Z_l and activation H_l = bf16(act(z_l)) (act of the unrounded z_l; layer 1
+ * included), the output layer's gradient G_L = bf16(df w_out act'(Z_L)) and
+ * every lower layer's G_{l-1} = bf16((W_l^T G_l) act'(Z_{l-1})), act' taken
+ * at the rounded Z.  The input layer, the output layer's weights and every
+ * bias stay unrounded.  It separates the arithmetic of a BF16 trainer from
+ * the rounding that the format itself brings. */
+static double rbf(double v) { return (double)orc_round_bf16((float)v); }
+
+double orc_mlp_loss_grad_bf16(const double *P, int width, int n_hidden, int act,
+                              const double *inputs, const double *target, long n, double *G)
+{
+    const long np = orc_param_count(width, n_hidden);
+    memset(G, 0, np * sizeof(double));
+    const long hs = (long)width * width + width;           /* one hidden layer: W then b */
+    const long off_h = (long)width * 15 + width;
+    const long off_out = np - (width + 1);
+    double *Wr = malloc(sizeof(double) * (size_t)(n_hidden > 0 ? n_hidden : 1) * width * width);
+    for (int l = 0; l < n_hidden; ++l)
+        for (long i = 0; i < (long)width * width; ++i) Wr[l * (long)width * width + i] = rbf(P[off_h + l * hs + i]);
+    double loss = 0.0;
+    double *Z = malloc(sizeof(double) * (size_t)(n_hidden + 1) * width);
+    double *H = malloc(sizeof(double) * (size_t)(n_hidden + 1) * width);
+    double *g = malloc(sizeof(double) * (size_t)width), *gp = malloc(sizeof(double) * (size_t)width);
+    for (long r = 0; r < n; ++r) {
+        const double *in = inputs + 15 * r;
+        for (int o = 0; o < width; ++o) {
+            double s = P[(long)width * 15 + o];
+            for (int k = 0; k < 15; ++k) s += P[(long)o * 15 + k] * in[k];
+            Z[o] = rbf(s);
+            H[o] = rbf(act_f(s, act));
+        }
+        for (int l = 1; l <= n_hidden; ++l) {
+            const double *Wl = Wr + (long)(l - 1) * width * width, *bl = P + off_h + (l - 1) * hs + (long)width * width;
+            for (int o = 0; o < width; ++o) {
+                double s = 0.0;
+                for (int i = 0; i < width; ++i) s += Wl[(long)o * width + i] * H[(long)(l - 1) * width + i];
+                s += bl[o];
+                Z[(long)l * width + o] = rbf(s);
+                H[(long)l * width + o] = rbf(act_f(s, act));
+            }
+        }
+        const double *Wo = P + off_out, *hl = H + (long)n_hidden * width, *zl = Z + (long)n_hidden * width;
+        double f = Wo[width];
+        for (int i = 0; i < width; ++i) f += Wo[i] * hl[i];
+        const double diff = f - target[r];
+        loss += fabs(diff);
+        const double df = (diff > 0.0 ? 1.0 : (diff < 0.0 ? -1.0 : 0.0)) / (double)n;
+        for (int i = 0; i < width; ++i) {
+            G[off_out + i] += df * hl[i];
+            g[i] = rbf(df * Wo[i] * act_df(zl[i], act));
+        }
+        G[off_out + width] += df;
+        for (int l = n_hidden; l >= 1; --l) {
+            const long off = off_h + (l - 1) * hs;
+            const double *Wl = Wr + (long)(l - 1) * width * width;
+            const double *hp = H + (long)(l - 1) * width, *zp = Z + (long)(l - 1) * width;
+            for (int o = 0; o < width; ++o) {
+                for (int i = 0; i < width; ++i) G[off + (long)o * width + i] += g[o] * hp[i];
+                G[off + (long)width * width + o] += g[o];
+            }
+            for (int i = 0; i < width; ++i) {
+                double s = 0.0;
+                for (int o = 0; o < width; ++o) s += Wl[(long)o * width + i] * g[o];
+                gp[i] = rbf(s * act_df(zp[i], act));
+            }
+            memcpy(g, gp, sizeof(double) * (size_t)width);
+        }
+        for (int o = 0; o < width; ++o) {
+            for (int k = 0; k < 15; ++k) G[(long)o * 15 + k] += g[o] * in[k];
+            G[(long)width * 15 + o] += g[o];
+        }
+    }
+    free(Wr); free(Z); free(H); free(g); free(gp);
     return loss / (double)n;
 }
 

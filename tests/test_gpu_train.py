@@ -2,12 +2,13 @@
 
 * data: the GPU generator's points and labels equal the oracle's generator
   (same SplitMix64 draws, FP64 geometry) within 1e-5 m;
-* gradient: the BF16 tensor-core backward pass matches the oracle's FP64
-  backpropagation of the mean L1 loss on the same FP32 weights, per parameter
-  group: cosine similarity >= 0.995 and relative L2 error <= 8 % (activations,
-  pre-activations and layer gradients are rounded to bfloat16; sums over the
-  batch with cancellation, such as the layer-1 weight gradient, show the
-  largest relative error, ~5 %); a wrong operand or a dropped term fails both;
+* gradient: the BF16 tensor-core backward pass against two oracles, per
+  parameter group: the FP64 backpropagation that rounds to bfloat16 where
+  the trainer stores values (hidden weights in their products, Z, H and every
+  layer's gradient G) isolates the kernels' own arithmetic -- relative L2
+  error <= 0.3 %, cosine >= 0.99999 (measured <= 0.08 %); the plain FP64 backpropagation bounds the
+  whole BF16 error -- cosine >= 0.995, relative L2 <= 8 % (sums over the
+  batch with cancellation, such as the layer-1 weight gradient, show ~5 %);
 * Adam: the first step moves every parameter by -lr g / (|g| + eps);
 * training lowers the held-out error, and a checkpoint resumes the run
   bit for bit (every batch sum is reduced in a fixed order).
@@ -85,16 +86,25 @@ def test_gradient_matches_oracle(svm, robot, width, n_hidden, act):
         P = oracle.flatten_params(layers)
         X = np.concatenate([x4[:, :3].astype(np.float64), q0[mid], q1[mid]], axis=1)
         ref_loss, G = oracle.mlp_loss_grad(P, width, n_hidden, act, X, x4[:, 3].astype(np.float64))
+        _, Gb = oracle.mlp_loss_grad_bf16(P, width, n_hidden, act, X, x4[:, 3].astype(np.float64))
         assert abs(loss - ref_loss) <= 1e-2 * ref_loss
+
+        def compare(gs, rs):
+            err = np.linalg.norm(gs - rs) / max(np.linalg.norm(rs), 1e-30)
+            cos = gs @ rs / max(np.linalg.norm(gs) * np.linalg.norm(rs), 1e-30)
+            return err, cos
+
         off = 0
         for li, (W, b) in enumerate(layers):
             for name, n in (("W", W.size), ("b", b.size)):
-                gs, rs = g[off:off + n].astype(np.float64), G[off:off + n]
+                gs = g[off:off + n].astype(np.float64)
+                err, cos = compare(gs, G[off:off + n])
+                eb, cb = compare(gs, Gb[off:off + n])
                 off += n
-                err = np.linalg.norm(gs - rs) / max(np.linalg.norm(rs), 1e-30)
-                cos = gs @ rs / max(np.linalg.norm(gs) * np.linalg.norm(rs), 1e-30)
-                print(f"layer {li} {name}: rel L2 {err:.3e} cos {cos:.6f}")
+                print(f"layer {li} {name}: vs FP64 rel L2 {err:.3e} cos {cos:.6f}; vs BF16 emulation rel L2 "
+                      f"{eb:.3e} cos {cb:.7f}")
                 assert err <= 8e-2 and cos >= 0.995, (li, name, err, cos)
+                assert eb <= 3e-3 and cb >= 0.99999, (li, name, eb, cb)
         assert off == g.size
         g2, loss2 = svm.svm_train_gradient(t, 0)      # deterministic: same batch, same bits
         np.testing.assert_array_equal(g, g2)

@@ -582,3 +582,65 @@ def test_training_points_near_surface_branch():
     np.testing.assert_allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-9)
     assert np.abs(d.mean(axis=0)).max() <= 4 / np.sqrt(3 * n)
     assert np.abs(d.T @ d / n - np.eye(3) / 3).max() <= 0.05
+
+
+def test_bf16_training_gradient_emulation():
+    """The BF16 training-gradient emulation (orc_mlp_loss_grad_bf16):
+    * with dyadic weights and inputs of few bits every value it rounds is
+      already a bfloat16, so it equals the FP64 backpropagation (itself pinned
+      by finite differences) bit for bit, in both activations;
+    * on a random network it equals torch's bfloat16 conversions applied at
+      the same places (Z, H, the hidden weights in their products, every
+      layer's gradient G) -- a library routine for the rounding;
+    * and it stays within the bfloat16 error of the FP64 gradient."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(0)
+    W, L, n = 4, 2, 8
+    npar = oracle.param_count(W, L)
+    P = rng.choice([-1.0, -0.5, -0.25, 0.25, 0.5, 1.0], npar) * rng.integers(0, 2, npar)
+    X = rng.choice([-1.0, -0.5, 0.0, 0.5, 1.0], (n, 15))
+    T = rng.choice([-2.0, 0.0, 2.0], n)
+    # ReLU: all values dyadic with few bits; SiLU values are not, so only ReLU is exact
+    l0, g0 = oracle.mlp_loss_grad(P, W, L, 0, X, T)
+    l1, g1 = oracle.mlp_loss_grad_bf16(P, W, L, 0, X, T)
+    assert l0 == l1
+    np.testing.assert_array_equal(g0, g1)
+    assert np.abs(g0).sum() > 0
+
+    def bf(a):
+        return torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).double().numpy()
+
+    for act in (0, 1):
+        W, L, n = 16, 2, 32
+        layers = S.xavier_weights(W, L, seed=7 + act)
+        P = oracle.flatten_params(layers)
+        X = rng.uniform(-1, 1, (n, 15))
+        T = rng.uniform(-0.2, 0.5, n)
+        loss, G = oracle.mlp_loss_grad_bf16(P, W, L, act, X, T)
+        Ls = [(w.astype(np.float64), b.astype(np.float64)) for w, b in layers]
+        fa = (lambda z: np.maximum(z, 0)) if act == 0 else (lambda z: z / (1 + np.exp(-z)))
+        da = (lambda z: (z > 0).astype(np.float64)) if act == 0 else \
+             (lambda z: (1 / (1 + np.exp(-z))) * (1 + z * (1 - 1 / (1 + np.exp(-z)))))
+        Zs, Hs = [], []
+        z = X @ Ls[0][0].T + Ls[0][1]
+        Zs.append(bf(z)); Hs.append(bf(fa(z)))
+        Wr = [bf(Ls[l][0]) for l in range(1, L + 1)]
+        for l in range(1, L + 1):
+            z = Hs[-1] @ Wr[l - 1].T + Ls[l][1]
+            Zs.append(bf(z)); Hs.append(bf(fa(z)))
+        wo, bo = Ls[L + 1][0][0], Ls[L + 1][1][0]
+        f = Hs[-1] @ wo + bo
+        e = f - T
+        df = np.sign(e) / n
+        grads = [None] * (L + 2)
+        grads[L + 1] = (df @ Hs[-1], np.array([df.sum()]))
+        g = bf(df[:, None] * wo[None, :] * da(Zs[-1]))
+        for l in range(L, 0, -1):
+            grads[l] = (g.T @ Hs[l - 1], g.sum(axis=0))
+            g = bf((g @ Wr[l - 1]) * da(Zs[l - 1]))
+        grads[0] = (g.T @ X, g.sum(axis=0))
+        want = np.concatenate([np.concatenate([gw.ravel(), gb.ravel()]) for gw, gb in grads])
+        np.testing.assert_allclose(G, want, rtol=1e-9, atol=1e-12)
+        assert abs(loss - np.abs(e).mean()) <= 1e-12
+        _, G64 = oracle.mlp_loss_grad(P, W, L, act, X, T)
+        assert np.linalg.norm(G - G64) <= 0.15 * np.linalg.norm(G64)     # rounding can flip a row's sign(e)
