@@ -38,7 +38,17 @@ using namespace svm;
 
 namespace {
 
-constexpr int kTpStride = 80;   // bytes per row of a 32 x 32 bfloat16 staging tile
+// cp.async of 4 or 8 bytes into shared memory (data in flight without
+// holding registers), its group commit and wait.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void* smem, const void* gmem)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // ------------------------------------------------------------ SplitMix64
 
@@ -150,166 +160,240 @@ __device__ __forceinline__ void input_row(const StepArgs& a, int r, float (&in)[
     delta = x.w;
 }
 
-__device__ __forceinline__ void store_bf16_row32(__nv_bfloat16* dst, const float (&v)[32])
-{
-    uint4* o = reinterpret_cast<uint4*>(dst);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        __nv_bfloat162 b0 = __floats2bfloat162_rn(v[8 * q + 0], v[8 * q + 1]);
-        __nv_bfloat162 b1 = __floats2bfloat162_rn(v[8 * q + 2], v[8 * q + 3]);
-        __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * q + 4], v[8 * q + 5]);
-        __nv_bfloat162 b3 = __floats2bfloat162_rn(v[8 * q + 6], v[8 * q + 7]);
-        o[q] = make_uint4(*reinterpret_cast<uint32_t*>(&b0), *reinterpret_cast<uint32_t*>(&b1),
-                          *reinterpret_cast<uint32_t*>(&b2), *reinterpret_cast<uint32_t*>(&b3));
-    }
-}
+// Layer 1 forward: a block takes 64 samples; thread t owns features 2t and
+// 2t + 1 (blockDim = W / 2) with their 15 weights and bias in registers, and
+// for each sample forms z = b + sum_k w_k in_k (fused multiply-adds in the
+// order k = 0..14), h = act(z), storing the feature pair of Z0 and H0 as one
+// bfloat16x2 word (a warp writes 128 contiguous bytes of a row).
+constexpr int kL1Rows = 64;
 
-// dst at [col0][row0] of a [cols][ld] matrix; lane = row, v = 32 columns.
-__device__ __forceinline__ void store_bf16_transposed32(unsigned char* tp, int lane, const float (&v)[32],
-                                                        __nv_bfloat16* dst, long long ld)
-{
-#pragma unroll
-    for (int c = 0; c < 32; ++c)
-        *reinterpret_cast<__nv_bfloat16*>(tp + c * kTpStride + lane * 2) = __float2bfloat16_rn(v[c]);
-    __syncwarp();
-    const uint4* src = reinterpret_cast<const uint4*>(tp + lane * kTpStride);
-    uint4* out = reinterpret_cast<uint4*>(dst + (long long)lane * ld);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) out[q] = src[q];
-    __syncwarp();
-}
-
-__device__ __forceinline__ void load_bf16_row32(const __nv_bfloat16* src, float (&v)[32])
-{
-    const uint4* p = reinterpret_cast<const uint4*>(src);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const uint4 w = p[q];
-        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            v[8 * q + 2 * i] = __uint_as_float(ws[i] << 16);
-            v[8 * q + 2 * i + 1] = __uint_as_float(ws[i] & 0xFFFF0000u);
-        }
-    }
-}
-
-// Layer 1 forward: 32 samples per block (lane = sample), warps split the
-// feature chunks.  Writes Z0, H0 (row-major) and, if H0T is given, H0^T.
 template <int ACT>
-__global__ void __launch_bounds__(128) layer1_fwd_kernel(StepArgs a, __nv_bfloat16* Z0, __nv_bfloat16* H0,
-                                                         __nv_bfloat16* H0T)
+__global__ void __launch_bounds__(256) layer1_fwd_kernel(StepArgs a, __nv_bfloat16* Z0, __nv_bfloat16* H0)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    float* w1 = reinterpret_cast<float*>(smem);                       // [W][15] then b1 [W]
-    unsigned char* tp = smem + (size_t)a.W * 16 * 4 + (threadIdx.x >> 5) * 32 * kTpStride;
-    for (int i = threadIdx.x; i < a.W * 15; i += blockDim.x) w1[i] = a.P[a.off_w1 + i];
-    for (int i = threadIdx.x; i < a.W; i += blockDim.x) w1[a.W * 15 + i] = a.P[a.off_b1 + i];
+    __shared__ __align__(16) float ins[kL1Rows][16];
+    const int r0 = blockIdx.x * kL1Rows;
+    for (int i = threadIdx.x; i < kL1Rows; i += blockDim.x) {
+        float in[15], delta;
+        input_row(a, r0 + i, in, delta);
+#pragma unroll
+        for (int k = 0; k < 15; ++k) ins[i][k] = in[k];
+        ins[i][15] = 0.0f;
+    }
+    const int o = 2 * threadIdx.x;
+    float wa[15], wb[15];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+        wa[k] = a.P[a.off_w1 + (long long)o * 15 + k];
+        wb[k] = a.P[a.off_w1 + (long long)(o + 1) * 15 + k];
+    }
+    const float ba = a.P[a.off_b1 + o], bb = a.P[a.off_b1 + o + 1];
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int r = blockIdx.x * 32 + lane;
-    float in[15], delta;
-    input_row(a, r, in, delta);
-    for (int c = warp; c < a.W / 32; c += 4) {
-        float z[32], h[32];
+#pragma unroll 2
+    for (int r = 0; r < kL1Rows; ++r) {
+        const float4* x4 = reinterpret_cast<const float4*>(ins[r]);
+        const float4 i0 = x4[0], i1 = x4[1], i2 = x4[2], i3 = x4[3];
+        const float in[15] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w,
+                              i2.x, i2.y, i2.z, i2.w, i3.x, i3.y, i3.z};
+        float za = ba, zb = bb;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const int o = c * 32 + i;
-            float s = w1[a.W * 15 + o];
-#pragma unroll
-            for (int k = 0; k < 15; ++k) s = fmaf(w1[o * 15 + k], in[k], s);
-            z[i] = s;
-            h[i] = actf<ACT>(s);
+        for (int k = 0; k < 15; ++k) {
+            za = fmaf(wa[k], in[k], za);
+            zb = fmaf(wb[k], in[k], zb);
         }
-        store_bf16_row32(Z0 + (long long)r * a.W + c * 32, z);
-        store_bf16_row32(H0 + (long long)r * a.W + c * 32, h);
-        if (H0T) store_bf16_transposed32(tp, lane, h, H0T + (long long)(c * 32) * a.B + blockIdx.x * 32, a.B);
+        const long long at = (long long)(r0 + r) * a.W + o;
+        const __nv_bfloat162 z2 = __floats2bfloat162_rn(za, zb);
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(actf<ACT>(za), actf<ACT>(zb));
+        *reinterpret_cast<__nv_bfloat162*>(Z0 + at) = z2;
+        *reinterpret_cast<__nv_bfloat162*>(H0 + at) = h2;
     }
 }
 
-// Output layer, loss and its gradient: f = w_out . h_L + b_out, e = f - delta;
-// block b writes its sum of |e| to loss[b]; with eval == 0 also df = sign(e)/B,
-// G_L = df * w_out * act'(z_L) (as G_L and, if GLT is given, G_L^T), and the block's partial
-// gradients of w_out and b_out to part[b][0..W].  Sums over blocks follow in
-// a fixed order (reduce_kernel), so the step is deterministic.
+// Output layer, loss and its gradient for 32 samples per block (128 threads):
+// f = w_out . h_L + b_out, e = f - delta; the block's sum of |e| goes to
+// loss[b]; with eval == 0 also df = sign(e)/B, G_L = (df w_out) act'(z_L) and
+// the block's partial gradients of w_out and b_out to part[b][0..W].
+// Arithmetic order, fixed (the step is bitwise reproducible): f is four
+// chains, chain w summing the features of the 32-wide chunks w, w + 4, ...
+// in ascending order by fused multiply-adds, then ((f_0 + f_1) + f_2) + f_3
+// + b_out; the sums over the block's 32 samples (|e|, df, df h) are the
+// butterfly x_l += x_{l ^ s}, s = 16, 8, 4, 2, 1, read at lane 0 (for df h
+// written as the same tree over registers).  The 32 rows of H_L and Z_L are
+// staged in shared memory with coalesced 16-byte loads; each row is padded by
+// 16 bytes, so the row-per-lane reads of the chains are free of bank
+// conflicts.
+constexpr int kHeadPad = 8;   // bfloat16 elements of padding per staged row
+
+size_t head_smem_bytes(int W) { return (size_t)2 * 32 * (W + kHeadPad) * sizeof(__nv_bfloat16); }
+
 template <int ACT>
 __global__ void __launch_bounds__(128) head_kernel(StepArgs a, const __nv_bfloat16* HL, const __nv_bfloat16* ZL,
-                                                   __nv_bfloat16* GL, __nv_bfloat16* GLT, int eval)
+                                                   __nv_bfloat16* GL, int eval)
 {
+    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float part[4][32];
-    __shared__ __align__(16) unsigned char tps[4 * 32 * kTpStride];
+    __shared__ float dfs[32];
+    const int W = a.W, ld = W + kHeadPad;
+    __nv_bfloat16* hs = reinterpret_cast<__nv_bfloat16*>(smem);
+    __nv_bfloat16* zs = hs + 32 * ld;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int r = blockIdx.x * 32 + lane;
-    unsigned char* tp = tps + warp * 32 * kTpStride;
+    const long long row0 = (long long)blockIdx.x * 32;
+    {
+        const int per_row = W / 8, n = 32 * per_row;     // 16-byte pieces
+        const uint4* gh = reinterpret_cast<const uint4*>(HL + row0 * W);
+        const uint4* gz = reinterpret_cast<const uint4*>(ZL + row0 * W);
+        for (int i0 = threadIdx.x; i0 < n; i0 += 8 * 128) {
+            uint4 vh[8], vz[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * 128;
+                if (i < n) {
+                    vh[u] = gh[i];
+                    if (!eval) vz[u] = gz[i];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * 128;
+                if (i < n) {
+                    const int rr = i / per_row, cc = i % per_row;
+                    *reinterpret_cast<uint4*>(hs + rr * ld + cc * 8) = vh[u];
+                    if (!eval) *reinterpret_cast<uint4*>(zs + rr * ld + cc * 8) = vz[u];
+                }
+            }
+        }
+    }
+    __syncthreads();
     const float* wo = a.P + a.off_out;
     float f = 0.0f;
-    for (int c = warp; c < a.W / 32; c += 4) {
-        float h[32];
-        load_bf16_row32(HL + (long long)r * a.W + c * 32, h);
+    for (int c = warp; c < W / 32; c += 4) {
+        const uint4* p = reinterpret_cast<const uint4*>(hs + lane * ld + c * 32);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) f = fmaf(wo[c * 32 + i], h[i], f);
+        for (int q = 0; q < 4; ++q) {
+            const uint4 w4 = p[q];
+            const uint32_t ws[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                f = fmaf(wo[c * 32 + 8 * q + 2 * i], __uint_as_float(ws[i] << 16), f);
+                f = fmaf(wo[c * 32 + 8 * q + 2 * i + 1], __uint_as_float(ws[i] & 0xFFFF0000u), f);
+            }
+        }
     }
     part[warp][lane] = f;
     __syncthreads();
-    float in[15], delta;
-    input_row(a, r, in, delta);
-    const float fr = part[0][lane] + part[1][lane] + part[2][lane] + part[3][lane] + wo[a.W];
-    const float e = fr - delta;
-    float ae = fabsf(e);
+    if (warp == 0) {
+        const long long s = a.base + (row0 + lane) * a.stride;
+        const float delta = a.X[s].w;
+        const float fr = part[0][lane] + part[1][lane] + part[2][lane] + part[3][lane] + wo[W];
+        const float e = fr - delta;
+        float ae = fabsf(e);
 #pragma unroll
-    for (int s = 16; s > 0; s >>= 1) ae += __shfl_xor_sync(0xffffffffu, ae, s);
-    if (lane == 0 && warp == 0) a.loss[blockIdx.x] = ae;
+        for (int sh = 16; sh > 0; sh >>= 1) ae += __shfl_xor_sync(0xffffffffu, ae, sh);
+        if (lane == 0) a.loss[blockIdx.x] = ae;
+        const float df = (e > 0.0f ? 1.0f : (e < 0.0f ? -1.0f : 0.0f)) / (float)a.B;
+        float dsum = df;
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, sh);
+        if (!eval && lane == 0) a.part[(long long)blockIdx.x * (W + 1) + W] = dsum;
+        dfs[lane] = df;
+    }
     if (eval) return;
-    float* pb = a.part + (long long)blockIdx.x * (a.W + 1);
-    const float df = (e > 0.0f ? 1.0f : (e < 0.0f ? -1.0f : 0.0f)) / (float)a.B;
-    float dsum = df;
+    __syncthreads();
+    float* pb = a.part + (long long)blockIdx.x * (W + 1);
+    for (int o = 2 * threadIdx.x; o < W; o += 2 * 128) {
+        const float wa = wo[o], wb = wo[o + 1];
+        float xa[32], xb[32];
 #pragma unroll
-    for (int s = 16; s > 0; s >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, s);
-    if (lane == 0 && warp == 0) pb[a.W] = dsum;
-    for (int c = warp; c < a.W / 32; c += 4) {
-        float h[32], z[32], gv[32];
-        load_bf16_row32(HL + (long long)r * a.W + c * 32, h);
-        load_bf16_row32(ZL + (long long)r * a.W + c * 32, z);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            gv[i] = df * wo[c * 32 + i] * actg<ACT>(z[i]);
-            float dw = df * h[i];
-#pragma unroll
-            for (int s = 16; s > 0; s >>= 1) dw += __shfl_xor_sync(0xffffffffu, dw, s);
-            if (lane == i) pb[c * 32 + i] = dw;
+        for (int r = 0; r < 32; ++r) {
+            const float df = dfs[r];
+            const uint32_t h2 = *reinterpret_cast<const uint32_t*>(hs + r * ld + o);
+            const uint32_t z2 = *reinterpret_cast<const uint32_t*>(zs + r * ld + o);
+            xa[r] = df * __uint_as_float(h2 << 16);
+            xb[r] = df * __uint_as_float(h2 & 0xFFFF0000u);
+            const float ga = df * wa * actg<ACT>(__uint_as_float(z2 << 16));
+            const float gb = df * wb * actg<ACT>(__uint_as_float(z2 & 0xFFFF0000u));
+            *reinterpret_cast<__nv_bfloat162*>(GL + (row0 + r) * W + o) = __floats2bfloat162_rn(ga, gb);
         }
-        store_bf16_row32(GL + (long long)r * a.W + c * 32, gv);
-        if (GLT) store_bf16_transposed32(tp, lane, gv, GLT + (long long)(c * 32) * a.B + blockIdx.x * 32, a.B);
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) {
+#pragma unroll
+            for (int l = 0; l < sh; ++l) {
+                xa[l] += xa[l + sh];
+                xb[l] += xb[l + sh];
+            }
+        }
+        pb[o] = xa[0];
+        pb[o + 1] = xb[0];
     }
 }
 
-// Layer-1 gradients of 256 samples per block (one thread per feature):
-// part[b][n * 15 + k] = sum G0[r][n] in_r[k], part[b][15 W + n] = sum G0[r][n]
-// -- the layout of W1 and b1 in the parameter vector.
-__global__ void __launch_bounds__(256) layer1_bwd_kernel(StepArgs a, const __nv_bfloat16* G0)
+// Layer-1 gradients of 256 samples per block row (blockIdx.x) and 256
+// features per block column (blockIdx.y); thread t owns features n, n + 1:
+// part[b][n * 15 + k] = sum_r G0[r][n] in_r[k], part[b][15 W + n] = sum_r
+// G0[r][n] -- the layout of W1 and b1 in the parameter vector -- each sum a
+// chain of fused multiply-adds over the block's samples in ascending order.
+// The G0 words reach shared memory by cp.async, 16 samples per group and two
+// groups in flight, so the loads do not wait on the arithmetic.
+__global__ void __launch_bounds__(128) layer1_bwd_kernel(StepArgs a, const __nv_bfloat16* G0)
 {
-    __shared__ float ins[256][16];
+    __shared__ __align__(16) float ins[256][16];
+    __shared__ uint32_t ring[2][16][128];
     const int r0 = blockIdx.x * 256;
-    {
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         float in[15], delta;
-        input_row(a, r0 + threadIdx.x, in, delta);
-        for (int k = 0; k < 15; ++k) ins[threadIdx.x][k] = in[k];
-        ins[threadIdx.x][15] = 1.0f;
+        input_row(a, r0 + i, in, delta);
+#pragma unroll
+        for (int k = 0; k < 15; ++k) ins[i][k] = in[k];
+        ins[i][15] = 1.0f;
     }
     __syncthreads();
-    for (int n = threadIdx.x; n < a.W; n += blockDim.x) {
-        float acc[16];
+    const int n = blockIdx.y * 256 + 2 * threadIdx.x;
+    float acc0[16], acc1[16];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) acc[k] = 0.0f;
-        for (int b = 0; b < 256; ++b) {
-            const float gv = __bfloat162float(G0[(long long)(r0 + b) * a.W + n]);
+    for (int k = 0; k < 16; ++k) acc0[k] = acc1[k] = 0.0f;
+    // G0[r0 + b][n, n + 1] for 16 samples per group, two groups in flight
+    const uint32_t* g = reinterpret_cast<const uint32_t*>(G0 + (long long)r0 * a.W + n);
+    const int ldw = a.W / 2;
+    auto issue = [&](int grp) {
+        uint32_t* dst = &ring[grp & 1][0][threadIdx.x];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) acc[k] = fmaf(gv, ins[b][k], acc[k]);
+        for (int u = 0; u < 16; ++u) cp_async_small<4>(dst + u * 128, g + (long long)(grp * 16 + u) * ldw);
+        cp_async_commit_group();
+    };
+    issue(0);
+    for (int grp = 0; grp < 16; ++grp) {
+        if (grp + 1 < 16) {
+            issue(grp + 1);
+            cp_async_wait_group<1>();
+        } else {
+            cp_async_wait_group<0>();
         }
-        float* pb = a.part + (long long)blockIdx.x * a.W * 16;
-        for (int k = 0; k < 15; ++k) pb[n * 15 + k] = acc[k];
-        pb[15 * a.W + n] = acc[15];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const uint32_t gv = ring[grp & 1][u][threadIdx.x];
+            const float g0 = __uint_as_float(gv << 16), g1 = __uint_as_float(gv & 0xFFFF0000u);
+            const float4* x4 = reinterpret_cast<const float4*>(ins[grp * 16 + u]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 x = x4[q];
+                acc0[4 * q + 0] = fmaf(g0, x.x, acc0[4 * q + 0]);
+                acc0[4 * q + 1] = fmaf(g0, x.y, acc0[4 * q + 1]);
+                acc0[4 * q + 2] = fmaf(g0, x.z, acc0[4 * q + 2]);
+                acc0[4 * q + 3] = fmaf(g0, x.w, acc0[4 * q + 3]);
+                acc1[4 * q + 0] = fmaf(g1, x.x, acc1[4 * q + 0]);
+                acc1[4 * q + 1] = fmaf(g1, x.y, acc1[4 * q + 1]);
+                acc1[4 * q + 2] = fmaf(g1, x.z, acc1[4 * q + 2]);
+                acc1[4 * q + 3] = fmaf(g1, x.w, acc1[4 * q + 3]);
+            }
+        }
     }
+    float* pb = a.part + (long long)blockIdx.x * a.W * 16;
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+        pb[(long long)n * 15 + k] = acc0[k];
+        pb[(long long)(n + 1) * 15 + k] = acc1[k];
+    }
+    pb[15LL * a.W + n] = acc0[15];
+    pb[15LL * a.W + n + 1] = acc1[15];
 }
 
 // Bias gradients db[n] += sum over the batch of G[b][n] (G row-major [B][W]),
@@ -318,29 +402,52 @@ __global__ void __launch_bounds__(256) layer1_bwd_kernel(StepArgs a, const __nv_
 // butterfly x_l += x_{l ^ s} (s = 16, 8, 4, 2, 1) read at lane 0, then the 8
 // group results in order.  Part 1 runs the chains: thread (t, q) of a block
 // sums columns 4q..4q+3 of its rows, a warp covering 128 contiguous columns
-// of one row (full sectors), and writes chain[t][n] (loads of 8 rows are
-// issued before their adds).  Part 2 (one warp per column) forms the tree.
+// of one row (full sectors), and writes chain[t][n]; its rows reach shared
+// memory by cp.async, 32 per group with two groups in flight, so enough bytes
+// are in flight to stream G at the memory's rate.  Part 2 (one warp per
+// column) forms the tree.
+constexpr int kCsDepth = 32;   // rows per cp.async group of the chains
+
+size_t colsum_smem_bytes() { return (size_t)2 * kCsDepth * 256 * sizeof(uint2); }
+
 __global__ void __launch_bounds__(256) colsum_chains_kernel(const __nv_bfloat16* G, long long B, int W, float* chain)
 {
+    extern __shared__ __align__(16) uint2 cs_ring[];              // [2][kCsDepth][256]
     const int q = blockIdx.x * 32 + (threadIdx.x & 31);          // column quad
     const int t = blockIdx.y * 8 + (threadIdx.x >> 5);           // chain (row class), 0..255
     const int n0 = 4 * q;
-    float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    auto add = [&](uint2 w) {
-        s[0] += __uint_as_float(w.x << 16);
-        s[1] += __uint_as_float(w.x & 0xFFFF0000u);
-        s[2] += __uint_as_float(w.y << 16);
-        s[3] += __uint_as_float(w.y & 0xFFFF0000u);
+    const long long rows = (B - t + 255) / 256;                   // rows t, t + 256, ... below B
+    const long long ng = (rows + kCsDepth - 1) / kCsDepth;
+    const __nv_bfloat16* src = G + (long long)t * W + n0;
+    const long long step = 256LL * W;
+    auto issue = [&](long long grp) {
+        uint2* dst = cs_ring + (grp & 1) * kCsDepth * 256 + threadIdx.x;
+        const long long r0 = grp * kCsDepth;
+#pragma unroll 8
+        for (int u = 0; u < kCsDepth; ++u)
+            if (r0 + u < rows) cp_async_small<8>(dst + u * 256, src + (r0 + u) * step);
+        cp_async_commit_group();
     };
-    long long b = t;
-    for (; b + 7 * 256 < B; b += 8 * 256) {
-        uint2 w[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) w[u] = *reinterpret_cast<const uint2*>(G + (b + u * 256) * W + n0);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) add(w[u]);
+    float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (ng > 0) issue(0);
+    for (long long grp = 0; grp < ng; ++grp) {
+        if (grp + 1 < ng) {
+            issue(grp + 1);
+            cp_async_wait_group<1>();
+        } else {
+            cp_async_wait_group<0>();
+        }
+        const uint2* buf = cs_ring + (grp & 1) * kCsDepth * 256 + threadIdx.x;
+        const int cnt = (int)min((long long)kCsDepth, rows - grp * kCsDepth);
+#pragma unroll 8
+        for (int u = 0; u < cnt; ++u) {
+            const uint2 w = buf[u * 256];
+            s[0] += __uint_as_float(w.x << 16);
+            s[1] += __uint_as_float(w.x & 0xFFFF0000u);
+            s[2] += __uint_as_float(w.y << 16);
+            s[3] += __uint_as_float(w.y & 0xFFFF0000u);
+        }
     }
-    for (; b < B; b += 256) add(*reinterpret_cast<const uint2*>(G + b * W + n0));
     *reinterpret_cast<float4*>(chain + (long long)t * W + n0) = make_float4(s[0], s[1], s[2], s[3]);
 }
 
@@ -358,31 +465,40 @@ __global__ void __launch_bounds__(256) colsum_tree_kernel(const float* chain, in
     if (lane == 0) db[n] += total;
 }
 
-// dst[j] += sum_{p < P} part[p * n + j] for long sums (P in the thousands):
-// a block takes TJ outputs and stages tiles of 2048 / TJ partials x TJ outputs
-// in shared memory with coalesced loads; thread j then adds its column in the
-// order p = 0, 1, ... (the order of reduce_kernel).
+// dst[j] += sum_{p < P} part[p * n + j] for long sums (P in the hundreds to
+// thousands): a block takes TJ outputs and stages tiles of 8192 / TJ partials
+// x TJ outputs (32 KB) in shared memory, each thread issuing its 32 loads
+// before storing them; thread j then adds its column in the order p = 0, 1,
+// ... (the order of reduce_kernel).
 template <int TJ>
 __global__ void __launch_bounds__(256) reduce_long_kernel(const float* part, int P, long long n, float* dst)
 {
-    constexpr int TP = 2048 / TJ;
-    __shared__ float tile[TP][TJ + (TJ > 1 ? 1 : 0)];
+    constexpr int TP = 8192 / TJ, PASS = 256 / TJ, PER = TP / PASS;
+    __shared__ float tile[TP * TJ];
     const long long j0 = (long long)blockIdx.x * TJ;
+    const int jj = threadIdx.x % TJ, pr = threadIdx.x / TJ;
+    const bool col_ok = j0 + jj < n;
     float s = 0.0f;
     for (int p0 = 0; p0 < P; p0 += TP) {
-        for (int i = threadIdx.x; i < TP * TJ; i += blockDim.x) {
-            const int pp = i / TJ, jj = i % TJ;
-            tile[pp][jj] = (p0 + pp < P && j0 + jj < n) ? part[(long long)(p0 + pp) * n + j0 + jj] : 0.0f;
+        float v[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int p = p0 + u * PASS + pr;
+            v[u] = (col_ok && p < P) ? part[(long long)p * n + j0 + jj] : 0.0f;
         }
+#pragma unroll
+        for (int u = 0; u < PER; ++u) tile[(u * PASS + pr) * TJ + jj] = v[u];
         __syncthreads();
         if (threadIdx.x < TJ) {
             const int lim = min(TP, P - p0);
-            for (int pp = 0; pp < lim; ++pp) s += tile[pp][threadIdx.x];
+#pragma unroll 8
+            for (int pp = 0; pp < lim; ++pp) s += tile[pp * TJ + threadIdx.x];
         }
         __syncthreads();
     }
     if (threadIdx.x < TJ && j0 + threadIdx.x < n) dst[j0 + threadIdx.x] += s;
 }
+constexpr int kRedCols = 8;
 
 // dst[j] += sum_{p < P} part[p * n + j], summed in the order p = 0, 1, ...;
 // the loads of 8 partials are issued before their adds (same order of the adds).
@@ -539,41 +655,41 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
 {
     const int W = t->W, L = t->L, B = t->B;
     const StepArgs a = step_args(t, base, stride);
-    const size_t l1_smem = (size_t)W * 16 * 4 + 4 * 32 * kTpStride;
-    if (t->act == 0) layer1_fwd_kernel<0><<<B / 32, 128, l1_smem, s>>>(a, t->Z[0], t->H[0], nullptr);
-    else layer1_fwd_kernel<1><<<B / 32, 128, l1_smem, s>>>(a, t->Z[0], t->H[0], nullptr);
+    if (t->act == 0) layer1_fwd_kernel<0><<<B / kL1Rows, W / 2, 0, s>>>(a, t->Z[0], t->H[0]);
+    else layer1_fwd_kernel<1><<<B / kL1Rows, W / 2, 0, s>>>(a, t->Z[0], t->H[0]);
     for (int l = 1; l <= L; ++l) {
         GemmArgs g{};
         g.n_mt = B / 128; g.n_nt = W / 256; g.n_ks = 1; g.k_len = W;
-        g.ld_rows = W; g.ld_cols = B;
+        g.ld_rows = W;
         g.bias = t->P + t->off_h + (long long)(l - 1) * ((long long)W * W + W) + (long long)W * W;
-        g.h_out = t->H[l]; g.z_out = t->Z[l]; g.ht_out = nullptr; g.err = t->err;
+        g.h_out = t->H[l]; g.z_out = t->Z[l]; g.err = t->err;
         launch_train_gemm(kEpiFwd, t->act, t->mapH[l - 1].b, t->mapW[l - 1].b, g, t->n_sms, s);
     }
-    if (t->act == 0) head_kernel<0><<<B / 32, 128, 0, s>>>(a, t->H[L], t->Z[L], t->G[L], nullptr, grad ? 0 : 1);
-    else head_kernel<1><<<B / 32, 128, 0, s>>>(a, t->H[L], t->Z[L], t->G[L], nullptr, grad ? 0 : 1);
+    const size_t head_smem = head_smem_bytes(W);
+    if (t->act == 0) head_kernel<0><<<B / 32, 128, head_smem, s>>>(a, t->H[L], t->Z[L], t->G[L], grad ? 0 : 1);
+    else head_kernel<1><<<B / 32, 128, head_smem, s>>>(a, t->H[L], t->Z[L], t->G[L], grad ? 0 : 1);
     reduce_long_kernel<1><<<1, 256, 0, s>>>(t->loss, B / 32, 1, t->loss_sum);
     if (!grad) return SVM_OK;
-    reduce_long_kernel<32><<<(W + 1 + 31) / 32, 256, 0, s>>>(t->part, B / 32, W + 1, t->Gr + t->off_out);
+    reduce_long_kernel<kRedCols><<<(W + 1 + kRedCols - 1) / kRedCols, 256, 0, s>>>(t->part, B / 32, W + 1, t->Gr + t->off_out);
     for (int l = L; l >= 1; --l) {
         const long long woff = t->off_h + (long long)(l - 1) * ((long long)W * W + W);
         GemmArgs g{};
         const int k_len = B >= 2048 ? 2048 : B;
         g.n_mt = W / 128; g.n_nt = W / 256; g.n_ks = B / k_len; g.k_len = k_len;
-        g.ld_rows = W; g.ld_cols = 0; g.dw = t->part; g.split_stride = (long long)W * W; g.err = t->err;
+        g.ld_rows = W; g.dw = t->part; g.split_stride = (long long)W * W; g.err = t->err;
         launch_train_gemm(kEpiWgrad, 0, t->mapGmn[l].b, t->mapHmn[l - 1].b, g, t->n_sms, s);
         reduce_kernel<<<grid_for((long long)W * W), 256, 0, s>>>(t->part, g.n_ks, (long long)W * W, t->Gr + woff);
         // the split-K partials are reduced: part holds the bias-gradient chains next
-        colsum_chains_kernel<<<dim3(W / 128, 32), 256, 0, s>>>(t->G[l], B, W, t->part);
+        colsum_chains_kernel<<<dim3(W / 128, 32), 256, colsum_smem_bytes(), s>>>(t->G[l], B, W, t->part);
         colsum_tree_kernel<<<W / 8, 256, 0, s>>>(t->part, W, t->Gr + woff + (long long)W * W);
         GemmArgs d{};
         d.n_mt = B / 128; d.n_nt = W / 256; d.n_ks = 1; d.k_len = W;
-        d.ld_rows = W; d.ld_cols = B; d.z_in = t->Z[l - 1];
-        d.h_out = t->G[l - 1]; d.ht_out = nullptr; d.err = t->err;
+        d.ld_rows = W; d.z_in = t->Z[l - 1];
+        d.h_out = t->G[l - 1]; d.err = t->err;
         launch_train_gemm(kEpiDgrad, t->act, t->mapG[l].b, t->mapWT[l - 1].b, d, t->n_sms, s);
     }
-    layer1_bwd_kernel<<<B / 256, 256, 0, s>>>(a, t->G[0]);
-    reduce_long_kernel<32><<<(W * 16 + 31) / 32, 256, 0, s>>>(t->part, B / 256, (long long)W * 16, t->Gr + t->off_w1);
+    layer1_bwd_kernel<<<dim3(B / 256, W / 256), 128, 0, s>>>(a, t->G[0]);
+    reduce_long_kernel<kRedCols><<<W * 16 / kRedCols, 256, 0, s>>>(t->part, B / 256, (long long)W * 16, t->Gr + t->off_w1);
     return SVM_OK;
 }
 
@@ -604,6 +720,10 @@ svm_status svm_train_create(const svm_model_desc* desc, int device, int32_t batc
     t->device = device;
     t->desc = d;
     cudaDeviceGetAttribute(&t->n_sms, cudaDevAttrMultiProcessorCount, device);
+    // the head stages 32 rows of H_L and Z_L: 66.5 KB at width 512
+    cudaFuncSetAttribute(head_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)head_smem_bytes(512));
+    cudaFuncSetAttribute(head_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)head_smem_bytes(512));
+    cudaFuncSetAttribute(colsum_chains_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)colsum_smem_bytes());
     for (int j = 0; j < 6; ++j) {
         t->rp.d[j] = d.dh[j][0]; t->rp.a[j] = d.dh[j][1];
         t->rp.ca[j] = std::cos(d.dh[j][2]); t->rp.sa[j] = std::sin(d.dh[j][2]); t->rp.th0[j] = d.dh[j][3];

@@ -3,10 +3,10 @@
 // FP32 accumulation in TMEM, and three fused epilogues:
 //
 //   FWD    hidden layer forward, rows = samples:  z = acc + b, h = act(z);
-//          writes H [M][N] (the next layer's A) and Z [M][N] (for act'), and
-//          H^T [N][M] if asked (bfloat16).
+//          writes H [M][N] (the next layer's A) and Z [M][N] (for act')
+//          (bfloat16).
 //   DGRAD  input gradient, rows = samples:  g = acc * act'(z_prev);
-//          writes G [M][N], and G^T [N][M] if asked (bfloat16).
+//          writes G [M][N] (bfloat16).
 //   WGRAD  weight gradient dW = G^T H over a slice of the batch (split-K):
 //          stores the FP32 partial of split s into dW + s * M * N ([M][N]);
 //          the splits are summed afterwards in a fixed order, so the result
@@ -24,8 +24,12 @@
 // loop, one elected lane) into one of two
 // TMEM accumulators; warps 2-9 drain the other accumulator (two warps per TMEM
 // lane quarter, 128 columns each), so the epilogue of one tile overlaps the
-// MMAs of the next.  Transposed outputs are staged per warp in shared memory
-// (a padded 32 x 32 tile) and written as 64-byte row segments.
+// MMAs of the next.  A warp's 32 x 32 blocks of bfloat16 outputs (and of
+// the Z input of DGRAD) pass through a padded 32-row tile in shared memory:
+// the accumulator gives a warp one row per lane, while global memory is
+// written (and read) as 64-byte row segments, four lanes per row and eight
+// rows per instruction -- full sectors and a quarter of the L1 wavefronts of
+// row-per-lane accesses.
 // All mbarrier waits are bounded (see tc_ptx.cuh).
 #include <mutex>
 #include <cuda_bf16.h>
@@ -105,29 +109,47 @@ __device__ __forceinline__ float act_grad(float z)
     }
 }
 
-// Row-major bfloat16 store of 32 values (64 bytes).
-__device__ __forceinline__ void store_row32(__nv_bfloat16* dst, const float (&v)[32])
+// The staging tile of a warp: 32 rows of 32 bfloat16 (64 bytes) at a
+// stride of 80 bytes, so row-per-lane 16-byte accesses are free of bank
+// conflicts.  stage_row: lane = row, v = its 32 values.
+__device__ __forceinline__ void stage_row(unsigned char* tp, int lane, const float (&v)[32])
 {
+    uint4* d = reinterpret_cast<uint4*>(tp + lane * TP_STRIDE);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-        st_global_v4(dst + 8 * q, bf2(v[8 * q], v[8 * q + 1]), bf2(v[8 * q + 2], v[8 * q + 3]),
-                     bf2(v[8 * q + 4], v[8 * q + 5]), bf2(v[8 * q + 6], v[8 * q + 7]));
+        d[q] = make_uint4(bf2(v[8 * q], v[8 * q + 1]), bf2(v[8 * q + 2], v[8 * q + 3]), bf2(v[8 * q + 4], v[8 * q + 5]),
+                          bf2(v[8 * q + 6], v[8 * q + 7]));
 }
 
-// Transposed store of a warp's 32 x 32 block: lane = row, v = 32 columns.
-// dst points at element [col0][row0] of a [cols][ld] bfloat16 matrix.
-__device__ __forceinline__ void store_transposed32(unsigned char* tp, int lane, const float (&v)[32],
-                                                   __nv_bfloat16* dst, long long ld)
+// Staged 32 x 32 block -> global rows (dst = element [row 0][col 0], row
+// stride ld): lane l writes 16-byte piece l % 4 of rows l / 4 + 8 j.
+__device__ __forceinline__ void flush_rows(const unsigned char* tp, int lane, __nv_bfloat16* dst, long long ld)
 {
+    const int piece = lane & 3;
 #pragma unroll
-    for (int c = 0; c < 32; ++c)
-        *reinterpret_cast<__nv_bfloat16*>(tp + c * TP_STRIDE + lane * 2) = __float2bfloat16_rn(v[c]);
-    __syncwarp();
-    const uint4* src = reinterpret_cast<const uint4*>(tp + lane * TP_STRIDE);
-    uint4* out = reinterpret_cast<uint4*>(dst + (long long)lane * ld);
+    for (int j = 0; j < 4; ++j) {
+        const int r = (lane >> 2) + 8 * j;
+        const uint4 w = *reinterpret_cast<const uint4*>(tp + r * TP_STRIDE + piece * 16);
+        st_global_v4(dst + r * ld + piece * 8, w.x, w.y, w.z, w.w);
+    }
+}
+
+// Global 32 x 32 block -> registers in the same coalesced pattern.
+__device__ __forceinline__ void load_rows(const __nv_bfloat16* src, long long ld, int lane, uint4 (&w)[4])
+{
+    const int piece = lane & 3;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) out[q] = src[q];
-    __syncwarp();
+    for (int j = 0; j < 4; ++j) {
+        const int r = (lane >> 2) + 8 * j;
+        w[j] = __ldg(reinterpret_cast<const uint4*>(src + r * ld + piece * 8));
+    }
+}
+
+__device__ __forceinline__ void stage_loaded(unsigned char* tp, int lane, const uint4 (&w)[4])
+{
+    const int piece = lane & 3;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) *reinterpret_cast<uint4*>(tp + ((lane >> 2) + 8 * j) * TP_STRIDE + piece * 16) = w[j];
 }
 
 template <int EPI, int ACT>
@@ -267,6 +289,16 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int row = quarter * 32 + lane;
         unsigned char* tp = dsm + OFF_TP + ew * TP_BYTES;
         uint32_t accf_phase[2] = {0u, 0u};
+        // DGRAD: the Z block of (unit, chunk), loaded one chunk ahead
+        uint4 zr[4];
+        auto z_block = [&](int i, int c) {
+            int ks, mt, nt;
+            unit_coords(i, ks, mt, nt);
+            return g.z_in + ((long long)mt * BM + quarter * 32) * g.ld_rows + nt * BN + half * 128 + c * 32;
+        };
+        if constexpr (EPI == kEpiDgrad) {
+            if (n_mine > 0) load_rows(z_block(0, 0), g.ld_rows, lane, zr);
+        }
         for (int i = 0; i < n_mine; ++i) {
             const int b = i & 1;
             if (!mbar_wait(accf_bar(b), accf_phase[b], abort_flag, g.err)) break;
@@ -281,24 +313,37 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int c = 0; c < 4; ++c) {
                 const int n0 = nt * BN + half * 128 + c * 32;
                 float v[32];
-                tmem_ld32(t_row + (uint32_t)(c * 32), v);
                 if constexpr (EPI == kEpiFwd) {
+                    float4 b4[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) b4[q] = __ldg(reinterpret_cast<const float4*>(g.bias + n0 + 4 * q));
+                    tmem_ld32(t_row + (uint32_t)(c * 32), v);
                     float z[32];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
-                        const float4 b4 = __ldg(reinterpret_cast<const float4*>(g.bias + n0 + 4 * q));
-                        z[4 * q + 0] = v[4 * q + 0] + b4.x;
-                        z[4 * q + 1] = v[4 * q + 1] + b4.y;
-                        z[4 * q + 2] = v[4 * q + 2] + b4.z;
-                        z[4 * q + 3] = v[4 * q + 3] + b4.w;
+                        z[4 * q + 0] = v[4 * q + 0] + b4[q].x;
+                        z[4 * q + 1] = v[4 * q + 1] + b4[q].y;
+                        z[4 * q + 2] = v[4 * q + 2] + b4[q].z;
+                        z[4 * q + 3] = v[4 * q + 3] + b4[q].w;
                     }
 #pragma unroll
                     for (int q = 0; q < 32; ++q) v[q] = act_fwd<ACT>(z[q]);
-                    store_row32(g.z_out + m * g.ld_rows + n0, z);
-                    store_row32(g.h_out + m * g.ld_rows + n0, v);
-                    if (g.ht_out) store_transposed32(tp, lane, v, g.ht_out + (long long)n0 * g.ld_cols + m0, g.ld_cols);
+                    stage_row(tp, lane, z);
+                    __syncwarp();
+                    flush_rows(tp, lane, g.z_out + m0 * g.ld_rows + n0, g.ld_rows);
+                    __syncwarp();
+                    stage_row(tp, lane, v);
+                    __syncwarp();
+                    flush_rows(tp, lane, g.h_out + m0 * g.ld_rows + n0, g.ld_rows);
+                    __syncwarp();
                 } else if constexpr (EPI == kEpiDgrad) {
-                    const uint4* zp = reinterpret_cast<const uint4*>(g.z_in + m * g.ld_rows + n0);
+                    stage_loaded(tp, lane, zr);
+                    // the next chunk's Z block is in flight while this one is used
+                    if (c + 1 < 4) load_rows(z_block(i, c + 1), g.ld_rows, lane, zr);
+                    else if (i + 1 < n_mine) load_rows(z_block(i + 1, 0), g.ld_rows, lane, zr);
+                    tmem_ld32(t_row + (uint32_t)(c * 32), v);
+                    __syncwarp();
+                    const uint4* zp = reinterpret_cast<const uint4*>(tp + lane * TP_STRIDE);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const uint4 w = zp[q];
@@ -311,9 +356,13 @@ __global__ void __launch_bounds__(THREADS, 1)
                         v[8 * q + 6] *= act_grad<ACT>(bf_lo(w.w));
                         v[8 * q + 7] *= act_grad<ACT>(bf_hi(w.w));
                     }
-                    store_row32(g.h_out + m * g.ld_rows + n0, v);
-                    if (g.ht_out) store_transposed32(tp, lane, v, g.ht_out + (long long)n0 * g.ld_cols + m0, g.ld_cols);
+                    __syncwarp();
+                    stage_row(tp, lane, v);
+                    __syncwarp();
+                    flush_rows(tp, lane, g.h_out + m0 * g.ld_rows + n0, g.ld_rows);
+                    __syncwarp();
                 } else {
+                    tmem_ld32(t_row + (uint32_t)(c * 32), v);
                     float4* dst = reinterpret_cast<float4*>(g.dw + (long long)ks * g.split_stride + m * g.ld_rows + n0);
 #pragma unroll
                     for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);

@@ -12,11 +12,9 @@ struct GemmArgs {
     int n_mt, n_nt, n_ks;           // tiles along M (128), N (256), K splits
     int k_len;                      // K elements per split (multiple of 64)
     long long ld_rows;              // row stride of the row-major [M][.] operands and outputs
-    long long ld_cols;              // row stride of the transposed [N][.] outputs
     const float* bias;              // FWD: [N]
     __nv_bfloat16* h_out;           // FWD: H; DGRAD: G
     __nv_bfloat16* z_out;           // FWD: Z
-    __nv_bfloat16* ht_out;          // FWD: H^T; DGRAD: G^T
     const __nv_bfloat16* z_in;      // DGRAD: Z of the previous layer
     float* dw;                      // WGRAD: FP32 partials [n_ks][M][N]
     long long split_stride;         // WGRAD: elements between the partials of two splits
