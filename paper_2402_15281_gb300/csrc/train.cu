@@ -584,7 +584,8 @@ struct svm_trainer {
     std::vector<__nv_bfloat16*> H, Z, G;             // per layer 0..L, [B][W]
     // A operands of the forward and input-gradient GEMMs (K-major, 128-row boxes) and the MN-major
     // operands of the weight-gradient GEMM (64 x 64 boxes)
-    std::vector<Map> mapH, mapG, mapHmn, mapGmn, mapW, mapWT;
+    std::vector<Map> mapH, mapG, mapHmn, mapGmn, mapW, mapWT, mapZst, mapHst, mapGst;
+    Map mapPst;
     // data
     float4* X = nullptr; int* MID = nullptr; double* q0 = nullptr; double* q1 = nullptr;
     int n_motions = 0; long long n_samples = 0;
@@ -663,7 +664,8 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
         g.ld_rows = W;
         g.bias = t->P + t->off_h + (long long)(l - 1) * ((long long)W * W + W) + (long long)W * W;
         g.h_out = t->H[l]; g.z_out = t->Z[l]; g.err = t->err;
-        launch_train_gemm(kEpiFwd, t->act, t->mapH[l - 1].b, t->mapW[l - 1].b, g, t->n_sms, s);
+        launch_train_gemm(kEpiFwd, t->act, t->mapH[l - 1].b, t->mapW[l - 1].b, t->mapZst[l].b, t->mapHst[l].b, g,
+                          t->n_sms, s);
     }
     const size_t head_smem = head_smem_bytes(W);
     if (t->act == 0) head_kernel<0><<<B / 32, 128, head_smem, s>>>(a, t->H[L], t->Z[L], t->G[L], grad ? 0 : 1);
@@ -677,7 +679,7 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
         const int k_len = B >= 2048 ? 2048 : B;
         g.n_mt = W / 128; g.n_nt = W / 256; g.n_ks = B / k_len; g.k_len = k_len;
         g.ld_rows = W; g.dw = t->part; g.split_stride = (long long)W * W; g.err = t->err;
-        launch_train_gemm(kEpiWgrad, 0, t->mapGmn[l].b, t->mapHmn[l - 1].b, g, t->n_sms, s);
+        launch_train_gemm(kEpiWgrad, 0, t->mapGmn[l].b, t->mapHmn[l - 1].b, t->mapPst.b, nullptr, g, t->n_sms, s);
         reduce_kernel<<<grid_for((long long)W * W), 256, 0, s>>>(t->part, g.n_ks, (long long)W * W, t->Gr + woff);
         // the split-K partials are reduced: part holds the bias-gradient chains next
         colsum_chains_kernel<<<dim3(W / 128, 32), 256, colsum_smem_bytes(), s>>>(t->G[l], B, W, t->part);
@@ -686,7 +688,8 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
         d.n_mt = B / 128; d.n_nt = W / 256; d.n_ks = 1; d.k_len = W;
         d.ld_rows = W; d.z_in = t->Z[l - 1];
         d.h_out = t->G[l - 1]; d.err = t->err;
-        launch_train_gemm(kEpiDgrad, t->act, t->mapG[l].b, t->mapWT[l - 1].b, d, t->n_sms, s);
+        launch_train_gemm(kEpiDgrad, t->act, t->mapG[l].b, t->mapWT[l - 1].b, t->mapGst[l - 1].b, nullptr, d, t->n_sms,
+                          s);
     }
     layer1_bwd_kernel<<<dim3(B / 256, W / 256), 128, 0, s>>>(a, t->G[0]);
     reduce_long_kernel<kRedCols><<<W * 16 / kRedCols, 256, 0, s>>>(t->part, B / 256, (long long)W * 16, t->Gr + t->off_w1);
@@ -764,8 +767,12 @@ svm_status svm_train_create(const svm_model_desc* desc, int device, int32_t batc
     cudaMemset(t->err, 0, 4);
     t->mapH.resize(L + 1); t->mapG.resize(L + 1); t->mapHmn.resize(L + 1); t->mapGmn.resize(L + 1);
     t->mapW.resize(L); t->mapWT.resize(L);
+    t->mapZst.resize(L + 1); t->mapHst.resize(L + 1); t->mapGst.resize(L + 1);
     int bad = 0;
     for (int l = 0; l <= L; ++l) {
+        bad |= train_make_store_map(t->mapZst[l].b, t->Z[l], B, W, 0);  // outputs of FWD and DGRAD
+        bad |= train_make_store_map(t->mapHst[l].b, t->H[l], B, W, 0);
+        bad |= train_make_store_map(t->mapGst[l].b, t->G[l], B, W, 0);
         bad |= train_make_map(t->mapH[l].b, t->H[l], B, W, 128);       // A of FWD
         bad |= train_make_map(t->mapG[l].b, t->G[l], B, W, 128);       // A of DGRAD
         bad |= train_make_map(t->mapHmn[l].b, t->H[l], B, W, 64);      // B of WGRAD (MN-major)
@@ -774,6 +781,11 @@ svm_status svm_train_create(const svm_model_desc* desc, int device, int32_t batc
     for (int l = 0; l < L; ++l) {
         bad |= train_make_map(t->mapW[l].b, t->wb + (long long)l * W * W, W, W, 256);    // B of FWD
         bad |= train_make_map(t->mapWT[l].b, t->wbt + (long long)l * W * W, W, W, 256);  // B of DGRAD
+    }
+    {
+        // the weight-gradient partials, [splits * W][W] FP32
+        const long long k_len = B >= 2048 ? 2048 : B;
+        bad |= train_make_store_map(t->mapPst.b, t->part, (B / k_len) * W, W, 1);
     }
     if (bad) return fail_free(SVM_E_CUDA);
     if (cudaDeviceSynchronize() != cudaSuccess) return fail_free(SVM_E_CUDA);

@@ -24,12 +24,13 @@
 // loop, one elected lane) into one of two
 // TMEM accumulators; warps 2-9 drain the other accumulator (two warps per TMEM
 // lane quarter, 128 columns each), so the epilogue of one tile overlaps the
-// MMAs of the next.  A warp's 32 x 32 blocks of bfloat16 outputs (and of
-// the Z input of DGRAD) pass through a padded 32-row tile in shared memory:
-// the accumulator gives a warp one row per lane, while global memory is
-// written (and read) as 64-byte row segments, four lanes per row and eight
-// rows per instruction -- full sectors and a quarter of the L1 wavefronts of
-// row-per-lane accesses.
+// MMAs of the next.  Outputs leave by TMA: a warp writes its 32-row block
+// (64 bfloat16 or 32 FP32 columns, 128 bytes a row) into its own 4 KB buffer
+// in the 128-byte-swizzled layout -- row-per-lane 16-byte stores free of bank
+// conflicts -- and one lane issues a tensor store of the box, so no global
+// store passes through the load/store unit.  The Z input of DGRAD is read
+// with coalesced 16-byte loads (eight lanes per 128-byte row) one block
+// ahead, and transposed to a row per lane through the same buffer.
 // All mbarrier waits are bounded (see tc_ptx.cuh).
 #include <mutex>
 #include <cuda_bf16.h>
@@ -51,10 +52,9 @@ constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = (2 + EPI_WARPS) * 32;
-constexpr int TP_STRIDE = 80;                         // bytes per staging row (64 + 16 padding)
-constexpr int TP_BYTES = 32 * TP_STRIDE;
-constexpr int OFF_TP = STAGES * STAGE_BYTES;
-constexpr int OFF_BAR = OFF_TP + EPI_WARPS * TP_BYTES;
+constexpr int BUF_BYTES = 32 * 128;                   // a warp's output box: 32 rows x 128 bytes
+constexpr int OFF_BUF = STAGES * STAGE_BYTES;          // 1024-byte aligned (the swizzle period)
+constexpr int OFF_BAR = OFF_BUF + EPI_WARPS * BUF_BYTES;
 constexpr int N_BARS = 2 * STAGES + 5;
 constexpr int OFF_MISC = OFF_BAR + 8 * N_BARS;
 constexpr int SMEM_DYN = OFF_MISC + 16 + 1024;
@@ -76,11 +76,6 @@ __device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr)
     d |= (uint64_t)1 << 46;                     // version
     d |= (uint64_t)2 << 61;                     // SWIZZLE_128B
     return d;
-}
-
-__device__ __forceinline__ void st_global_v4(void* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
-{
-    asm volatile("st.global.v4.b32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
 
 __device__ __forceinline__ uint32_t bf2(float lo, float hi)
@@ -109,52 +104,26 @@ __device__ __forceinline__ float act_grad(float z)
     }
 }
 
-// The staging tile of a warp: 32 rows of 32 bfloat16 (64 bytes) at a
-// stride of 80 bytes, so row-per-lane 16-byte accesses are free of bank
-// conflicts.  stage_row: lane = row, v = its 32 values.
-__device__ __forceinline__ void stage_row(unsigned char* tp, int lane, const float (&v)[32])
-{
-    uint4* d = reinterpret_cast<uint4*>(tp + lane * TP_STRIDE);
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        d[q] = make_uint4(bf2(v[8 * q], v[8 * q + 1]), bf2(v[8 * q + 2], v[8 * q + 3]), bf2(v[8 * q + 4], v[8 * q + 5]),
-                          bf2(v[8 * q + 6], v[8 * q + 7]));
-}
+// Byte offset of 16-byte piece j of row r in a 128-byte-swizzled box (the
+// layout TMA reads for CU_TENSOR_MAP_SWIZZLE_128B with 128-byte rows).
+__device__ __forceinline__ int swz(int r, int j) { return r * 128 + ((j ^ (r & 7)) << 4); }
 
-// Staged 32 x 32 block -> global rows (dst = element [row 0][col 0], row
-// stride ld): lane l writes 16-byte piece l % 4 of rows l / 4 + 8 j.
-__device__ __forceinline__ void flush_rows(const unsigned char* tp, int lane, __nv_bfloat16* dst, long long ld)
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int x, int y)
 {
-    const int piece = lane & 3;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int r = (lane >> 2) + 8 * j;
-        const uint4 w = *reinterpret_cast<const uint4*>(tp + r * TP_STRIDE + piece * 16);
-        st_global_v4(dst + r * ld + piece * 8, w.x, w.y, w.z, w.w);
-    }
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(src)
+                 : "memory");
 }
-
-// Global 32 x 32 block -> registers in the same coalesced pattern.
-__device__ __forceinline__ void load_rows(const __nv_bfloat16* src, long long ld, int lane, uint4 (&w)[4])
-{
-    const int piece = lane & 3;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int r = (lane >> 2) + 8 * j;
-        w[j] = __ldg(reinterpret_cast<const uint4*>(src + r * ld + piece * 8));
-    }
-}
-
-__device__ __forceinline__ void stage_loaded(unsigned char* tp, int lane, const uint4 (&w)[4])
-{
-    const int piece = lane & 3;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) *reinterpret_cast<uint4*>(tp + ((lane >> 2) + 8 * j) * TP_STRIDE + piece * 16) = w[j];
-}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 template <int EPI, int ACT>
 __global__ void __launch_bounds__(THREADS, 1)
-    train_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap, GemmArgs g)
+    train_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
+                      const __grid_constant__ CUtensorMap smap0, const __grid_constant__ CUtensorMap smap1, GemmArgs g)
 {
     extern __shared__ __align__(1024) unsigned char dsm_raw[];
     unsigned char* dsm =
@@ -286,18 +255,37 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int ew = warp - 2;
         const int quarter = warp & 3;
         const int half = ew >> 2;
-        const int row = quarter * 32 + lane;
-        unsigned char* tp = dsm + OFF_TP + ew * TP_BYTES;
+        unsigned char* buf = dsm + OFF_BUF + ew * BUF_BYTES;
+        const uint32_t buf_s = smem_u32(buf);
         uint32_t accf_phase[2] = {0u, 0u};
-        // DGRAD: the Z block of (unit, chunk), loaded one chunk ahead
-        uint4 zr[4];
-        auto z_block = [&](int i, int c) {
+        // the buffer is free once the previous tensor store has read it
+        auto wait_buf = [&]() {
+            if (lane == 0) bulk_wait_read();
+            __syncwarp();
+        };
+        // the lanes' shared-memory writes, then one lane stores the box at (x, y)
+        auto store_box = [&](const CUtensorMap* map, int x, int y) {
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                tma_store_2d(map, buf_s, x, y);
+                bulk_commit();
+            }
+        };
+        // DGRAD: the Z block (32 rows x 64 columns) of (unit, chunk), loaded one
+        // chunk ahead; lane l holds piece l % 8 of rows l / 8 + 4 j
+        uint4 zr[8];
+        auto load_z = [&](int i, int c) {
             int ks, mt, nt;
             unit_coords(i, ks, mt, nt);
-            return g.z_in + ((long long)mt * BM + quarter * 32) * g.ld_rows + nt * BN + half * 128 + c * 32;
+            const __nv_bfloat16* src =
+                g.z_in + ((long long)mt * BM + quarter * 32) * g.ld_rows + nt * BN + half * 128 + c * 64;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                zr[j] = __ldg(reinterpret_cast<const uint4*>(src + ((lane >> 3) + 4 * j) * g.ld_rows + (lane & 7) * 8));
         };
         if constexpr (EPI == kEpiDgrad) {
-            if (n_mine > 0) load_rows(z_block(0, 0), g.ld_rows, lane, zr);
+            if (n_mine > 0) load_z(0, 0);
         }
         for (int i = 0; i < n_mine; ++i) {
             const int b = i & 1;
@@ -306,72 +294,94 @@ __global__ void __launch_bounds__(THREADS, 1)
             tc_fence_after();
             int ks, mt, nt;
             unit_coords(i, ks, mt, nt);
-            const long long m = (long long)mt * BM + row;              // output row
-            const long long m0 = (long long)mt * BM + quarter * 32;    // first row of this warp
+            const int m0 = mt * BM + quarter * 32;                     // first row of this warp
             const uint32_t t_row = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + half * 128);
+            if constexpr (EPI == kEpiWgrad) {
 #pragma unroll 1
-            for (int c = 0; c < 4; ++c) {
-                const int n0 = nt * BN + half * 128 + c * 32;
-                float v[32];
-                if constexpr (EPI == kEpiFwd) {
-                    float4 b4[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) b4[q] = __ldg(reinterpret_cast<const float4*>(g.bias + n0 + 4 * q));
+                for (int c = 0; c < 4; ++c) {
+                    float v[32];
                     tmem_ld32(t_row + (uint32_t)(c * 32), v);
-                    float z[32];
+                    wait_buf();
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        z[4 * q + 0] = v[4 * q + 0] + b4[q].x;
-                        z[4 * q + 1] = v[4 * q + 1] + b4[q].y;
-                        z[4 * q + 2] = v[4 * q + 2] + b4[q].z;
-                        z[4 * q + 3] = v[4 * q + 3] + b4[q].w;
+                    for (int j = 0; j < 8; ++j)
+                        *reinterpret_cast<float4*>(buf + swz(lane, j)) =
+                            make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                    store_box(&smap0, nt * BN + half * 128 + c * 32, ks * g.n_mt * BM + m0);
+                }
+            } else {
+#pragma unroll 1
+                for (int c = 0; c < 2; ++c) {
+                    const int n0 = nt * BN + half * 128 + c * 64;
+                    float v[64];
+                    if constexpr (EPI == kEpiFwd) {
+                        tmem_ld32(t_row + (uint32_t)(c * 64), *reinterpret_cast<float(*)[32]>(v));
+                        tmem_ld32(t_row + (uint32_t)(c * 64 + 32), *reinterpret_cast<float(*)[32]>(v + 32));
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const float4 b4 = __ldg(reinterpret_cast<const float4*>(g.bias + n0 + 4 * q));
+                            v[4 * q + 0] += b4.x;
+                            v[4 * q + 1] += b4.y;
+                            v[4 * q + 2] += b4.z;
+                            v[4 * q + 3] += b4.w;
+                        }
+                        wait_buf();
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            *reinterpret_cast<uint4*>(buf + swz(lane, j)) =
+                                make_uint4(bf2(v[8 * j], v[8 * j + 1]), bf2(v[8 * j + 2], v[8 * j + 3]),
+                                           bf2(v[8 * j + 4], v[8 * j + 5]), bf2(v[8 * j + 6], v[8 * j + 7]));
+                        store_box(&smap0, n0, m0);                      // Z
+#pragma unroll
+                        for (int q = 0; q < 64; ++q) v[q] = act_fwd<ACT>(v[q]);
+                        wait_buf();
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            *reinterpret_cast<uint4*>(buf + swz(lane, j)) =
+                                make_uint4(bf2(v[8 * j], v[8 * j + 1]), bf2(v[8 * j + 2], v[8 * j + 3]),
+                                           bf2(v[8 * j + 4], v[8 * j + 5]), bf2(v[8 * j + 6], v[8 * j + 7]));
+                        store_box(&smap1, n0, m0);                      // H
+                    } else {
+                        wait_buf();
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            *reinterpret_cast<uint4*>(buf + swz((lane >> 3) + 4 * j, lane & 7)) = zr[j];
+                        __syncwarp();
+                        // the next Z block is in flight while this one is used
+                        if (c + 1 < 2) load_z(i, c + 1);
+                        else if (i + 1 < n_mine) load_z(i + 1, 0);
+                        // from here each lane reads and rewrites only its own row: g in place of z
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            float u[32];
+                            tmem_ld32(t_row + (uint32_t)(c * 64 + hh * 32), u);
+#pragma unroll
+                            for (int jj = 0; jj < 4; ++jj) {
+                                const int j = hh * 4 + jj;
+                                const uint4 zw = *reinterpret_cast<const uint4*>(buf + swz(lane, j));
+                                float* w = u + 8 * jj;
+                                w[0] *= act_grad<ACT>(bf_lo(zw.x));
+                                w[1] *= act_grad<ACT>(bf_hi(zw.x));
+                                w[2] *= act_grad<ACT>(bf_lo(zw.y));
+                                w[3] *= act_grad<ACT>(bf_hi(zw.y));
+                                w[4] *= act_grad<ACT>(bf_lo(zw.z));
+                                w[5] *= act_grad<ACT>(bf_hi(zw.z));
+                                w[6] *= act_grad<ACT>(bf_lo(zw.w));
+                                w[7] *= act_grad<ACT>(bf_hi(zw.w));
+                                *reinterpret_cast<uint4*>(buf + swz(lane, j)) =
+                                    make_uint4(bf2(w[0], w[1]), bf2(w[2], w[3]), bf2(w[4], w[5]), bf2(w[6], w[7]));
+                            }
+                        }
+                        store_box(&smap0, n0, m0);                      // G
                     }
-#pragma unroll
-                    for (int q = 0; q < 32; ++q) v[q] = act_fwd<ACT>(z[q]);
-                    stage_row(tp, lane, z);
-                    __syncwarp();
-                    flush_rows(tp, lane, g.z_out + m0 * g.ld_rows + n0, g.ld_rows);
-                    __syncwarp();
-                    stage_row(tp, lane, v);
-                    __syncwarp();
-                    flush_rows(tp, lane, g.h_out + m0 * g.ld_rows + n0, g.ld_rows);
-                    __syncwarp();
-                } else if constexpr (EPI == kEpiDgrad) {
-                    stage_loaded(tp, lane, zr);
-                    // the next chunk's Z block is in flight while this one is used
-                    if (c + 1 < 4) load_rows(z_block(i, c + 1), g.ld_rows, lane, zr);
-                    else if (i + 1 < n_mine) load_rows(z_block(i + 1, 0), g.ld_rows, lane, zr);
-                    tmem_ld32(t_row + (uint32_t)(c * 32), v);
-                    __syncwarp();
-                    const uint4* zp = reinterpret_cast<const uint4*>(tp + lane * TP_STRIDE);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const uint4 w = zp[q];
-                        v[8 * q + 0] *= act_grad<ACT>(bf_lo(w.x));
-                        v[8 * q + 1] *= act_grad<ACT>(bf_hi(w.x));
-                        v[8 * q + 2] *= act_grad<ACT>(bf_lo(w.y));
-                        v[8 * q + 3] *= act_grad<ACT>(bf_hi(w.y));
-                        v[8 * q + 4] *= act_grad<ACT>(bf_lo(w.z));
-                        v[8 * q + 5] *= act_grad<ACT>(bf_hi(w.z));
-                        v[8 * q + 6] *= act_grad<ACT>(bf_lo(w.w));
-                        v[8 * q + 7] *= act_grad<ACT>(bf_hi(w.w));
-                    }
-                    __syncwarp();
-                    stage_row(tp, lane, v);
-                    __syncwarp();
-                    flush_rows(tp, lane, g.h_out + m0 * g.ld_rows + n0, g.ld_rows);
-                    __syncwarp();
-                } else {
-                    tmem_ld32(t_row + (uint32_t)(c * 32), v);
-                    float4* dst = reinterpret_cast<float4*>(g.dw + (long long)ks * g.split_stride + m * g.ld_rows + n0);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
                 }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acce_bar(b));
         }
+        // the tensor stores have completed before the CTA ends
+        if (lane == 0) bulk_wait_all();
+        __syncwarp();
     }
 
     tc_fence_before();
@@ -383,7 +393,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 template <int EPI, int ACT>
-void launch_t(const CUtensorMap& a, const CUtensorMap& b, const GemmArgs& g, int grid, cudaStream_t s)
+void launch_t(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& s0, const CUtensorMap& s1,
+              const GemmArgs& g, int grid, cudaStream_t s)
 {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -392,7 +403,7 @@ void launch_t(const CUtensorMap& a, const CUtensorMap& b, const GemmArgs& g, int
         std::call_once(done[dev], [] {
             cudaFuncSetAttribute(train_gemm_kernel<EPI, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_DYN);
         });
-    train_gemm_kernel<EPI, ACT><<<grid, THREADS, SMEM_DYN, s>>>(a, b, g);
+    train_gemm_kernel<EPI, ACT><<<grid, THREADS, SMEM_DYN, s>>>(a, b, s0, s1, g);
 }
 
 }  // namespace
@@ -426,21 +437,51 @@ int train_make_map(void* map, const void* base, long long rows, long long cols, 
     return r == CUDA_SUCCESS ? 0 : -2;
 }
 
-void launch_train_gemm(int epi, int act, const void* amap, const void* bmap, const GemmArgs& g, int n_sms,
-                       cudaStream_t s)
+void launch_train_gemm(int epi, int act, const void* amap, const void* bmap, const void* smap0, const void* smap1,
+                       const GemmArgs& g, int n_sms, cudaStream_t s)
 {
     const int units = g.n_ks * g.n_mt * g.n_nt;
     if (units <= 0) return;
     const int grid = units < n_sms ? units : n_sms;
     const CUtensorMap& a = *reinterpret_cast<const CUtensorMap*>(amap);
     const CUtensorMap& b = *reinterpret_cast<const CUtensorMap*>(bmap);
+    const CUtensorMap& s0 = *reinterpret_cast<const CUtensorMap*>(smap0);
+    const CUtensorMap& s1 = *reinterpret_cast<const CUtensorMap*>(smap1 ? smap1 : smap0);
     if (epi == kEpiFwd) {
-        if (act == 0) launch_t<kEpiFwd, 0>(a, b, g, grid, s); else launch_t<kEpiFwd, 1>(a, b, g, grid, s);
+        if (act == 0) launch_t<kEpiFwd, 0>(a, b, s0, s1, g, grid, s); else launch_t<kEpiFwd, 1>(a, b, s0, s1, g, grid, s);
     } else if (epi == kEpiDgrad) {
-        if (act == 0) launch_t<kEpiDgrad, 0>(a, b, g, grid, s); else launch_t<kEpiDgrad, 1>(a, b, g, grid, s);
+        if (act == 0) launch_t<kEpiDgrad, 0>(a, b, s0, s1, g, grid, s);
+        else launch_t<kEpiDgrad, 1>(a, b, s0, s1, g, grid, s);
     } else {
-        launch_t<kEpiWgrad, 0>(a, b, g, grid, s);
+        launch_t<kEpiWgrad, 0>(a, b, s0, s1, g, grid, s);
     }
+}
+
+// Tensor map of a row-major [rows][cols] matrix written in boxes of 32 rows x
+// 128 bytes (64 bfloat16 or 32 FP32 columns), 128-byte swizzle.
+int train_make_store_map(void* map, const void* base, long long rows, long long cols, int fp32)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+    if (!enc) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return -1;
+        enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    const int es = fp32 ? 4 : 2;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * es};
+    const cuuint32_t box[2] = {(cuuint32_t)(128 / es), 32};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(reinterpret_cast<CUtensorMap*>(map),
+                           fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                           const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : -2;
 }
 
 }  // namespace svm

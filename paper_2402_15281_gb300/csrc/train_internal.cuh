@@ -25,7 +25,10 @@ int train_gemm_bm();
 int train_gemm_bn();
 int train_gemm_bk();
 int train_make_map(void* map, const void* base, long long rows, long long cols, int box_rows);
-void launch_train_gemm(int epi, int act, const void* amap, const void* bmap, const GemmArgs& g, int n_sms,
-                       cudaStream_t s);
+int train_make_store_map(void* map, const void* base, long long rows, long long cols, int fp32);
+// smap0 / smap1: tensor maps of the outputs (FWD: Z, H; DGRAD: G; WGRAD: the
+// FP32 partials as [n_ks * M][N])
+void launch_train_gemm(int epi, int act, const void* amap, const void* bmap, const void* smap0, const void* smap1,
+                       const GemmArgs& g, int n_sms, cudaStream_t s);
 
 }  // namespace svm
