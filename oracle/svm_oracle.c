@@ -29,8 +29,10 @@
  *   orc_mlp_loss_grad         L1 training loss and its gradient (backprop).
  *   orc_mlp_loss_grad_bf16    the same backpropagation with bfloat16 rounding
  *                             of the hidden weights in their products and of
- *                             Z, H and each hidden layer's gradient G (the
- *                             values a BF16 training step stores).
+ *                             H = act(z), D = act'(z) (both of the unrounded
+ *                             pre-activation) and each hidden layer's
+ *                             gradient G (the values a BF16 training step
+ *                             stores).
  *   orc_adam_step             Adam update with bias correction (Sec. V).
  *   orc_round_bf16,
  *   orc_round_e4m3            the quantisers that define the BF16 and FP8
@@ -517,7 +519,7 @@ double orc_mlp_loss_grad_bf16(const double *P, int width, int n_hidden, int act,
     for (int l = 0; l < n_hidden; ++l)
         for (long i = 0; i < (long)width * width; ++i) Wr[l * (long)width * width + i] = rbf(P[off_h + l * hs + i]);
     double loss = 0.0;
-    double *Z = malloc(sizeof(double) * (size_t)(n_hidden + 1) * width);
+    double *D = malloc(sizeof(double) * (size_t)(n_hidden + 1) * width);
     double *H = malloc(sizeof(double) * (size_t)(n_hidden + 1) * width);
     double *g = malloc(sizeof(double) * (size_t)width), *gp = malloc(sizeof(double) * (size_t)width);
     for (long r = 0; r < n; ++r) {
@@ -525,7 +527,7 @@ double orc_mlp_loss_grad_bf16(const double *P, int width, int n_hidden, int act,
         for (int o = 0; o < width; ++o) {
             double s = P[(long)width * 15 + o];
             for (int k = 0; k < 15; ++k) s += P[(long)o * 15 + k] * in[k];
-            Z[o] = rbf(s);
+            D[o] = rbf(act_df(s, act));
             H[o] = rbf(act_f(s, act));
         }
         for (int l = 1; l <= n_hidden; ++l) {
@@ -534,11 +536,11 @@ double orc_mlp_loss_grad_bf16(const double *P, int width, int n_hidden, int act,
                 double s = 0.0;
                 for (int i = 0; i < width; ++i) s += Wl[(long)o * width + i] * H[(long)(l - 1) * width + i];
                 s += bl[o];
-                Z[(long)l * width + o] = rbf(s);
+                D[(long)l * width + o] = rbf(act_df(s, act));
                 H[(long)l * width + o] = rbf(act_f(s, act));
             }
         }
-        const double *Wo = P + off_out, *hl = H + (long)n_hidden * width, *zl = Z + (long)n_hidden * width;
+        const double *Wo = P + off_out, *hl = H + (long)n_hidden * width, *dl = D + (long)n_hidden * width;
         double f = Wo[width];
         for (int i = 0; i < width; ++i) f += Wo[i] * hl[i];
         const double diff = f - target[r];
@@ -546,13 +548,13 @@ double orc_mlp_loss_grad_bf16(const double *P, int width, int n_hidden, int act,
         const double df = (diff > 0.0 ? 1.0 : (diff < 0.0 ? -1.0 : 0.0)) / (double)n;
         for (int i = 0; i < width; ++i) {
             G[off_out + i] += df * hl[i];
-            g[i] = rbf(df * Wo[i] * act_df(zl[i], act));
+            g[i] = rbf(df * Wo[i] * dl[i]);
         }
         G[off_out + width] += df;
         for (int l = n_hidden; l >= 1; --l) {
             const long off = off_h + (l - 1) * hs;
             const double *Wl = Wr + (long)(l - 1) * width * width;
-            const double *hp = H + (long)(l - 1) * width, *zp = Z + (long)(l - 1) * width;
+            const double *hp = H + (long)(l - 1) * width, *dp = D + (long)(l - 1) * width;
             for (int o = 0; o < width; ++o) {
                 for (int i = 0; i < width; ++i) G[off + (long)o * width + i] += g[o] * hp[i];
                 G[off + (long)width * width + o] += g[o];
@@ -560,7 +562,7 @@ double orc_mlp_loss_grad_bf16(const double *P, int width, int n_hidden, int act,
             for (int i = 0; i < width; ++i) {
                 double s = 0.0;
                 for (int o = 0; o < width; ++o) s += Wl[(long)o * width + i] * g[o];
-                gp[i] = rbf(s * act_df(zp[i], act));
+                gp[i] = rbf(s * dp[i]);
             }
             memcpy(g, gp, sizeof(double) * (size_t)width);
         }
@@ -569,7 +571,7 @@ double orc_mlp_loss_grad_bf16(const double *P, int width, int n_hidden, int act,
             G[(long)width * 15 + o] += g[o];
         }
     }
-    free(Wr); free(Z); free(H); free(g); free(gp);
+    free(Wr); free(D); free(H); free(g); free(gp);
     return loss / (double)n;
 }
 

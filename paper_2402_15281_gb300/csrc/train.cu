@@ -14,7 +14,9 @@
 //
 // Step (loss: mean |f - delta|, the error the paper reports as MAE):
 //   layer 1 (15 -> W) in FP32 on CUDA cores, hidden layers as BF16 tcgen05
-//   GEMMs (train_gemm.cu), output layer, loss and its gradient on CUDA cores;
+//   GEMMs (train_gemm.cu), each layer storing h = act(z) and d = act'(z)
+//   (bfloat16, rounded once from the FP32 z) for the backward pass; output
+//   layer, loss and its gradient on CUDA cores;
 //   backward: per hidden layer a split-K weight-gradient GEMM (reading G and
 //   H as stored, [batch][features], as MN-major operands) and an input-
 //   gradient GEMM, bias gradients by column sums, layer-1 gradient on CUDA
@@ -130,20 +132,20 @@ struct StepArgs {
     long long off_w1, off_b1, off_out;
 };
 
+// h = act(z) and d = act'(z), the values the step stores (bfloat16) for the
+// forward and backward passes.  SiLU: with s = 1 / (1 + e^-z) (fast
+// reciprocal, within a few ulp of the division), h = z s and d = s (1 + z (1 -
+// s)).  ReLU: d = 1 where the bfloat16 z is positive, else 0.
 template <int ACT>
-__device__ __forceinline__ float actf(float z)
+__device__ __forceinline__ void act_hd(float z, float& h, float& d)
 {
-    if constexpr (ACT == 0) return fmaxf(z, 0.0f);
-    else return __fdividef(z, 1.0f + __expf(-z));   // fast reciprocal: within a few ulp of the division
-}
-
-template <int ACT>
-__device__ __forceinline__ float actg(float z)
-{
-    if constexpr (ACT == 0) return z > 0.0f ? 1.0f : 0.0f;
-    else {
+    if constexpr (ACT == 0) {
+        h = fmaxf(z, 0.0f);
+        d = __bfloat162float(__float2bfloat16_rn(z)) > 0.0f ? 1.0f : 0.0f;
+    } else {
         const float s = __fdividef(1.0f, 1.0f + __expf(-z));
-        return s * (1.0f + z * (1.0f - s));
+        h = z * s;
+        d = s * (1.0f + z * (1.0f - s));
     }
 }
 
@@ -163,12 +165,13 @@ __device__ __forceinline__ void input_row(const StepArgs& a, int r, float (&in)[
 // Layer 1 forward: a block takes 64 samples; thread t owns features 2t and
 // 2t + 1 (blockDim = W / 2) with their 15 weights and bias in registers, and
 // for each sample forms z = b + sum_k w_k in_k (fused multiply-adds in the
-// order k = 0..14), h = act(z), storing the feature pair of Z0 and H0 as one
-// bfloat16x2 word (a warp writes 128 contiguous bytes of a row).
+// order k = 0..14), h = act(z) and d = act'(z), storing the feature pair of
+// D0 and H0 as one bfloat16x2 word each (a warp writes 128 contiguous bytes of
+// a row).
 constexpr int kL1Rows = 64;
 
 template <int ACT>
-__global__ void __launch_bounds__(256) layer1_fwd_kernel(StepArgs a, __nv_bfloat16* Z0, __nv_bfloat16* H0)
+__global__ void __launch_bounds__(256) layer1_fwd_kernel(StepArgs a, __nv_bfloat16* D0, __nv_bfloat16* H0)
 {
     __shared__ __align__(16) float ins[kL1Rows][16];
     const int r0 = blockIdx.x * kL1Rows;
@@ -201,23 +204,24 @@ __global__ void __launch_bounds__(256) layer1_fwd_kernel(StepArgs a, __nv_bfloat
             zb = fmaf(wb[k], in[k], zb);
         }
         const long long at = (long long)(r0 + r) * a.W + o;
-        const __nv_bfloat162 z2 = __floats2bfloat162_rn(za, zb);
-        const __nv_bfloat162 h2 = __floats2bfloat162_rn(actf<ACT>(za), actf<ACT>(zb));
-        *reinterpret_cast<__nv_bfloat162*>(Z0 + at) = z2;
-        *reinterpret_cast<__nv_bfloat162*>(H0 + at) = h2;
+        float ha, hb, da, db;
+        act_hd<ACT>(za, ha, da);
+        act_hd<ACT>(zb, hb, db);
+        *reinterpret_cast<__nv_bfloat162*>(D0 + at) = __floats2bfloat162_rn(da, db);
+        *reinterpret_cast<__nv_bfloat162*>(H0 + at) = __floats2bfloat162_rn(ha, hb);
     }
 }
 
 // Output layer, loss and its gradient for 32 samples per block (128 threads):
 // f = w_out . h_L + b_out, e = f - delta; the block's sum of |e| goes to
-// loss[b]; with eval == 0 also df = sign(e)/B, G_L = (df w_out) act'(z_L) and
+// loss[b]; with eval == 0 also df = sign(e)/B, G_L = (df w_out) d_L (d = act'(z)) and
 // the block's partial gradients of w_out and b_out to part[b][0..W].
 // Arithmetic order, fixed (the step is bitwise reproducible): f is four
 // chains, chain w summing the features of the 32-wide chunks w, w + 4, ...
 // in ascending order by fused multiply-adds, then ((f_0 + f_1) + f_2) + f_3
 // + b_out; the sums over the block's 32 samples (|e|, df, df h) are the
 // butterfly x_l += x_{l ^ s}, s = 16, 8, 4, 2, 1, read at lane 0 (for df h
-// written as the same tree over registers).  The 32 rows of H_L and Z_L are
+// written as the same tree over registers).  The 32 rows of H_L and D_L are
 // staged in shared memory with coalesced 16-byte loads; each row is padded by
 // 16 bytes, so the row-per-lane reads of the chains are free of bank
 // conflicts.
@@ -226,7 +230,7 @@ constexpr int kHeadPad = 8;   // bfloat16 elements of padding per staged row
 size_t head_smem_bytes(int W) { return (size_t)2 * 32 * (W + kHeadPad) * sizeof(__nv_bfloat16); }
 
 template <int ACT>
-__global__ void __launch_bounds__(128) head_kernel(StepArgs a, const __nv_bfloat16* HL, const __nv_bfloat16* ZL,
+__global__ void __launch_bounds__(128) head_kernel(StepArgs a, const __nv_bfloat16* HL, const __nv_bfloat16* DL,
                                                    __nv_bfloat16* GL, int eval)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -234,13 +238,13 @@ __global__ void __launch_bounds__(128) head_kernel(StepArgs a, const __nv_bfloat
     __shared__ float dfs[32];
     const int W = a.W, ld = W + kHeadPad;
     __nv_bfloat16* hs = reinterpret_cast<__nv_bfloat16*>(smem);
-    __nv_bfloat16* zs = hs + 32 * ld;
+    __nv_bfloat16* ds = hs + 32 * ld;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long row0 = (long long)blockIdx.x * 32;
     {
         const int per_row = W / 8, n = 32 * per_row;     // 16-byte pieces
         const uint4* gh = reinterpret_cast<const uint4*>(HL + row0 * W);
-        const uint4* gz = reinterpret_cast<const uint4*>(ZL + row0 * W);
+        const uint4* gz = reinterpret_cast<const uint4*>(DL + row0 * W);
         for (int i0 = threadIdx.x; i0 < n; i0 += 8 * 128) {
             uint4 vh[8], vz[8];
 #pragma unroll
@@ -257,7 +261,7 @@ __global__ void __launch_bounds__(128) head_kernel(StepArgs a, const __nv_bfloat
                 if (i < n) {
                     const int rr = i / per_row, cc = i % per_row;
                     *reinterpret_cast<uint4*>(hs + rr * ld + cc * 8) = vh[u];
-                    if (!eval) *reinterpret_cast<uint4*>(zs + rr * ld + cc * 8) = vz[u];
+                    if (!eval) *reinterpret_cast<uint4*>(ds + rr * ld + cc * 8) = vz[u];
                 }
             }
         }
@@ -306,11 +310,11 @@ __global__ void __launch_bounds__(128) head_kernel(StepArgs a, const __nv_bfloat
         for (int r = 0; r < 32; ++r) {
             const float df = dfs[r];
             const uint32_t h2 = *reinterpret_cast<const uint32_t*>(hs + r * ld + o);
-            const uint32_t z2 = *reinterpret_cast<const uint32_t*>(zs + r * ld + o);
+            const uint32_t d2 = *reinterpret_cast<const uint32_t*>(ds + r * ld + o);
             xa[r] = df * __uint_as_float(h2 << 16);
             xb[r] = df * __uint_as_float(h2 & 0xFFFF0000u);
-            const float ga = df * wa * actg<ACT>(__uint_as_float(z2 << 16));
-            const float gb = df * wb * actg<ACT>(__uint_as_float(z2 & 0xFFFF0000u));
+            const float ga = df * wa * __uint_as_float(d2 << 16);
+            const float gb = df * wb * __uint_as_float(d2 & 0xFFFF0000u);
             *reinterpret_cast<__nv_bfloat162*>(GL + (row0 + r) * W + o) = __floats2bfloat162_rn(ga, gb);
         }
 #pragma unroll
@@ -581,10 +585,10 @@ struct svm_trainer {
     long long part_n = 0;
     unsigned int* err = nullptr;
     __nv_bfloat16* wb = nullptr; __nv_bfloat16* wbt = nullptr;
-    std::vector<__nv_bfloat16*> H, Z, G;             // per layer 0..L, [B][W]
+    std::vector<__nv_bfloat16*> H, D, G;             // per layer 0..L, [B][W]; D = act'(z)
     // A operands of the forward and input-gradient GEMMs (K-major, 128-row boxes) and the MN-major
     // operands of the weight-gradient GEMM (64 x 64 boxes)
-    std::vector<Map> mapH, mapG, mapHmn, mapGmn, mapW, mapWT, mapZst, mapHst, mapGst;
+    std::vector<Map> mapH, mapG, mapHmn, mapGmn, mapW, mapWT, mapDst, mapHst, mapGst;
     Map mapPst;
     // data
     float4* X = nullptr; int* MID = nullptr; double* q0 = nullptr; double* q1 = nullptr;
@@ -656,20 +660,20 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
 {
     const int W = t->W, L = t->L, B = t->B;
     const StepArgs a = step_args(t, base, stride);
-    if (t->act == 0) layer1_fwd_kernel<0><<<B / kL1Rows, W / 2, 0, s>>>(a, t->Z[0], t->H[0]);
-    else layer1_fwd_kernel<1><<<B / kL1Rows, W / 2, 0, s>>>(a, t->Z[0], t->H[0]);
+    if (t->act == 0) layer1_fwd_kernel<0><<<B / kL1Rows, W / 2, 0, s>>>(a, t->D[0], t->H[0]);
+    else layer1_fwd_kernel<1><<<B / kL1Rows, W / 2, 0, s>>>(a, t->D[0], t->H[0]);
     for (int l = 1; l <= L; ++l) {
         GemmArgs g{};
         g.n_mt = B / 128; g.n_nt = W / 256; g.n_ks = 1; g.k_len = W;
         g.ld_rows = W;
         g.bias = t->P + t->off_h + (long long)(l - 1) * ((long long)W * W + W) + (long long)W * W;
-        g.h_out = t->H[l]; g.z_out = t->Z[l]; g.err = t->err;
-        launch_train_gemm(kEpiFwd, t->act, t->mapH[l - 1].b, t->mapW[l - 1].b, t->mapZst[l].b, t->mapHst[l].b, g,
+        g.err = t->err;
+        launch_train_gemm(kEpiFwd, t->act, t->mapH[l - 1].b, t->mapW[l - 1].b, t->mapDst[l].b, t->mapHst[l].b, g,
                           t->n_sms, s);
     }
     const size_t head_smem = head_smem_bytes(W);
-    if (t->act == 0) head_kernel<0><<<B / 32, 128, head_smem, s>>>(a, t->H[L], t->Z[L], t->G[L], grad ? 0 : 1);
-    else head_kernel<1><<<B / 32, 128, head_smem, s>>>(a, t->H[L], t->Z[L], t->G[L], grad ? 0 : 1);
+    if (t->act == 0) head_kernel<0><<<B / 32, 128, head_smem, s>>>(a, t->H[L], t->D[L], t->G[L], grad ? 0 : 1);
+    else head_kernel<1><<<B / 32, 128, head_smem, s>>>(a, t->H[L], t->D[L], t->G[L], grad ? 0 : 1);
     reduce_long_kernel<1><<<1, 256, 0, s>>>(t->loss, B / 32, 1, t->loss_sum);
     if (!grad) return SVM_OK;
     reduce_long_kernel<kRedCols><<<(W + 1 + kRedCols - 1) / kRedCols, 256, 0, s>>>(t->part, B / 32, W + 1, t->Gr + t->off_out);
@@ -686,8 +690,8 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
         colsum_tree_kernel<<<W / 8, 256, 0, s>>>(t->part, W, t->Gr + woff + (long long)W * W);
         GemmArgs d{};
         d.n_mt = B / 128; d.n_nt = W / 256; d.n_ks = 1; d.k_len = W;
-        d.ld_rows = W; d.z_in = t->Z[l - 1];
-        d.h_out = t->G[l - 1]; d.err = t->err;
+        d.ld_rows = W; d.d_in = t->D[l - 1];
+        d.err = t->err;
         launch_train_gemm(kEpiDgrad, t->act, t->mapG[l].b, t->mapWT[l - 1].b, t->mapGst[l - 1].b, nullptr, d, t->n_sms,
                           s);
     }
@@ -723,7 +727,7 @@ svm_status svm_train_create(const svm_model_desc* desc, int device, int32_t batc
     t->device = device;
     t->desc = d;
     cudaDeviceGetAttribute(&t->n_sms, cudaDevAttrMultiProcessorCount, device);
-    // the head stages 32 rows of H_L and Z_L: 66.5 KB at width 512
+    // the head stages 32 rows of H_L and D_L: 66.5 KB at width 512
     cudaFuncSetAttribute(head_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)head_smem_bytes(512));
     cudaFuncSetAttribute(head_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)head_smem_bytes(512));
     cudaFuncSetAttribute(colsum_chains_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)colsum_smem_bytes());
@@ -757,9 +761,9 @@ svm_status svm_train_create(const svm_model_desc* desc, int device, int32_t batc
     if ((st = talloc(t, &t->err, 256)) != SVM_OK) return fail_free(st);
     if ((st = talloc(t, &t->wb, L * W * W * 2)) != SVM_OK) return fail_free(st);
     if ((st = talloc(t, &t->wbt, L * W * W * 2)) != SVM_OK) return fail_free(st);
-    t->H.resize(L + 1); t->Z.resize(L + 1); t->G.resize(L + 1);
+    t->H.resize(L + 1); t->D.resize(L + 1); t->G.resize(L + 1);
     for (int l = 0; l <= L; ++l)
-        for (auto* v : {&t->H, &t->Z, &t->G})
+        for (auto* v : {&t->H, &t->D, &t->G})
             if ((st = talloc(t, &(*v)[l], B * W * 2)) != SVM_OK) return fail_free(st);
     cudaMemset(t->P, 0, t->np * 4);
     cudaMemset(t->Mo, 0, t->np * 4);
@@ -767,10 +771,10 @@ svm_status svm_train_create(const svm_model_desc* desc, int device, int32_t batc
     cudaMemset(t->err, 0, 4);
     t->mapH.resize(L + 1); t->mapG.resize(L + 1); t->mapHmn.resize(L + 1); t->mapGmn.resize(L + 1);
     t->mapW.resize(L); t->mapWT.resize(L);
-    t->mapZst.resize(L + 1); t->mapHst.resize(L + 1); t->mapGst.resize(L + 1);
+    t->mapDst.resize(L + 1); t->mapHst.resize(L + 1); t->mapGst.resize(L + 1);
     int bad = 0;
     for (int l = 0; l <= L; ++l) {
-        bad |= train_make_store_map(t->mapZst[l].b, t->Z[l], B, W, 0);  // outputs of FWD and DGRAD
+        bad |= train_make_store_map(t->mapDst[l].b, t->D[l], B, W, 0);  // outputs of FWD and DGRAD
         bad |= train_make_store_map(t->mapHst[l].b, t->H[l], B, W, 0);
         bad |= train_make_store_map(t->mapGst[l].b, t->G[l], B, W, 0);
         bad |= train_make_map(t->mapH[l].b, t->H[l], B, W, 128);       // A of FWD

@@ -2,11 +2,11 @@
 // [M][K] and B [N][K] both K-major (row-major, K contiguous) in global memory,
 // FP32 accumulation in TMEM, and three fused epilogues:
 //
-//   FWD    hidden layer forward, rows = samples:  z = acc + b, h = act(z);
-//          writes H [M][N] (the next layer's A) and Z [M][N] (for act')
+//   FWD    hidden layer forward, rows = samples:  z = acc + b, h = act(z),
+//          d = act'(z); writes H [M][N] (the next layer's A) and D [M][N]
+//          (bfloat16, both rounded once from the FP32 z).
+//   DGRAD  input gradient, rows = samples:  g = acc * d_prev; writes G [M][N]
 //          (bfloat16).
-//   DGRAD  input gradient, rows = samples:  g = acc * act'(z_prev);
-//          writes G [M][N] (bfloat16).
 //   WGRAD  weight gradient dW = G^T H over a slice of the batch (split-K):
 //          stores the FP32 partial of split s into dW + s * M * N ([M][N]);
 //          the splits are summed afterwards in a fixed order, so the result
@@ -28,7 +28,7 @@
 // (64 bfloat16 or 32 FP32 columns, 128 bytes a row) into its own 4 KB buffer
 // in the 128-byte-swizzled layout -- row-per-lane 16-byte stores free of bank
 // conflicts -- and one lane issues a tensor store of the box, so no global
-// store passes through the load/store unit.  The Z input of DGRAD is read
+// store passes through the load/store unit.  The D input of DGRAD is read
 // with coalesced 16-byte loads (eight lanes per 128-byte row) one block
 // ahead, and transposed to a row per lane through the same buffer.
 // All mbarrier waits are bounded (see tc_ptx.cuh).
@@ -54,7 +54,8 @@ constexpr int EPI_WARPS = 8;
 constexpr int THREADS = (2 + EPI_WARPS) * 32;
 constexpr int BUF_BYTES = 32 * 128;                   // a warp's output box: 32 rows x 128 bytes
 constexpr int OFF_BUF = STAGES * STAGE_BYTES;          // 1024-byte aligned (the swizzle period)
-constexpr int OFF_BAR = OFF_BUF + EPI_WARPS * BUF_BYTES;
+constexpr int OFF_BIAS = OFF_BUF + EPI_WARPS * BUF_BYTES;     // FWD: the CTA's 256 bias values
+constexpr int OFF_BAR = OFF_BIAS + BN * 4;
 constexpr int N_BARS = 2 * STAGES + 5;
 constexpr int OFF_MISC = OFF_BAR + 8 * N_BARS;
 constexpr int SMEM_DYN = OFF_MISC + 16 + 1024;
@@ -87,20 +88,19 @@ __device__ __forceinline__ uint32_t bf2(float lo, float hi)
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
+// h = act(z) and d = act'(z).  SiLU: with s = 1 / (1 + e^-z) (fast
+// reciprocal, within a few ulp of the division), h = z s and d = s (1 + z (1 - s)).
+// ReLU: d = 1 where the bfloat16 z is positive, else 0.
 template <int ACT>
-__device__ __forceinline__ float act_fwd(float z)
+__device__ __forceinline__ void act_hd(float z, float& h, float& d)
 {
-    if constexpr (ACT == 0) return fmaxf(z, 0.0f);
-    else return __fdividef(z, 1.0f + __expf(-z));   // fast reciprocal: within a few ulp of the division
-}
-
-template <int ACT>
-__device__ __forceinline__ float act_grad(float z)
-{
-    if constexpr (ACT == 0) return z > 0.0f ? 1.0f : 0.0f;
-    else {
+    if constexpr (ACT == 0) {
+        h = fmaxf(z, 0.0f);
+        d = __bfloat162float(__float2bfloat16_rn(z)) > 0.0f ? 1.0f : 0.0f;
+    } else {
         const float s = __fdividef(1.0f, 1.0f + __expf(-z));
-        return s * (1.0f + z * (1.0f - s));
+        h = z * s;
+        d = s * (1.0f + z * (1.0f - s));
     }
 }
 
@@ -272,20 +272,29 @@ __global__ void __launch_bounds__(THREADS, 1)
                 bulk_commit();
             }
         };
-        // DGRAD: the Z block (32 rows x 64 columns) of (unit, chunk), loaded one
+        // DGRAD: the D block (32 rows x 64 columns) of (unit, chunk), loaded one
         // chunk ahead; lane l holds piece l % 8 of rows l / 8 + 4 j
-        uint4 zr[8];
-        auto load_z = [&](int i, int c) {
+        uint4 dr[8];
+        auto load_d = [&](int i, int c) {
             int ks, mt, nt;
             unit_coords(i, ks, mt, nt);
             const __nv_bfloat16* src =
-                g.z_in + ((long long)mt * BM + quarter * 32) * g.ld_rows + nt * BN + half * 128 + c * 64;
+                g.d_in + ((long long)mt * BM + quarter * 32) * g.ld_rows + nt * BN + half * 128 + c * 64;
 #pragma unroll
             for (int j = 0; j < 8; ++j)
-                zr[j] = __ldg(reinterpret_cast<const uint4*>(src + ((lane >> 3) + 4 * j) * g.ld_rows + (lane & 7) * 8));
+                dr[j] = __ldg(reinterpret_cast<const uint4*>(src + ((lane >> 3) + 4 * j) * g.ld_rows + (lane & 7) * 8));
         };
         if constexpr (EPI == kEpiDgrad) {
-            if (n_mine > 0) load_z(0, 0);
+            if (n_mine > 0) load_d(0, 0);
+        }
+        // FWD: when every unit of this CTA has the same N tile (grid a multiple of
+        // the N tiles), its 256 bias values are staged once in shared memory
+        const float* bias_s = reinterpret_cast<const float*>(dsm + OFF_BIAS);
+        const bool bias_staged = EPI == kEpiFwd && (int)gridDim.x % g.n_nt == 0;
+        if (bias_staged) {
+            const int nt0 = (int)blockIdx.x % g.n_nt;
+            reinterpret_cast<float*>(dsm + OFF_BIAS)[ew * 32 + lane] = g.bias[nt0 * BN + ew * 32 + lane];
+            asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32) : "memory");
         }
         for (int i = 0; i < n_mine; ++i) {
             const int b = i & 1;
@@ -318,21 +327,25 @@ __global__ void __launch_bounds__(THREADS, 1)
                         tmem_ld32(t_row + (uint32_t)(c * 64 + 32), *reinterpret_cast<float(*)[32]>(v + 32));
 #pragma unroll
                         for (int q = 0; q < 16; ++q) {
-                            const float4 b4 = __ldg(reinterpret_cast<const float4*>(g.bias + n0 + 4 * q));
+                            const float4 b4 = bias_staged
+                                                  ? *reinterpret_cast<const float4*>(bias_s + half * 128 + c * 64 + 4 * q)
+                                                  : __ldg(reinterpret_cast<const float4*>(g.bias + n0 + 4 * q));
                             v[4 * q + 0] += b4.x;
                             v[4 * q + 1] += b4.y;
                             v[4 * q + 2] += b4.z;
                             v[4 * q + 3] += b4.w;
                         }
+                        // D box from z, with h = act(z) left in v
                         wait_buf();
 #pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            *reinterpret_cast<uint4*>(buf + swz(lane, j)) =
-                                make_uint4(bf2(v[8 * j], v[8 * j + 1]), bf2(v[8 * j + 2], v[8 * j + 3]),
-                                           bf2(v[8 * j + 4], v[8 * j + 5]), bf2(v[8 * j + 6], v[8 * j + 7]));
-                        store_box(&smap0, n0, m0);                      // Z
+                        for (int j = 0; j < 8; ++j) {
+                            float d[8];
 #pragma unroll
-                        for (int q = 0; q < 64; ++q) v[q] = act_fwd<ACT>(v[q]);
+                            for (int e = 0; e < 8; ++e) act_hd<ACT>(v[8 * j + e], v[8 * j + e], d[e]);
+                            *reinterpret_cast<uint4*>(buf + swz(lane, j)) =
+                                make_uint4(bf2(d[0], d[1]), bf2(d[2], d[3]), bf2(d[4], d[5]), bf2(d[6], d[7]));
+                        }
+                        store_box(&smap0, n0, m0);                      // D
                         wait_buf();
 #pragma unroll
                         for (int j = 0; j < 8; ++j)
@@ -344,12 +357,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                         wait_buf();
 #pragma unroll
                         for (int j = 0; j < 8; ++j)
-                            *reinterpret_cast<uint4*>(buf + swz((lane >> 3) + 4 * j, lane & 7)) = zr[j];
+                            *reinterpret_cast<uint4*>(buf + swz((lane >> 3) + 4 * j, lane & 7)) = dr[j];
                         __syncwarp();
-                        // the next Z block is in flight while this one is used
-                        if (c + 1 < 2) load_z(i, c + 1);
-                        else if (i + 1 < n_mine) load_z(i + 1, 0);
-                        // from here each lane reads and rewrites only its own row: g in place of z
+                        // the next D block is in flight while this one is used
+                        if (c + 1 < 2) load_d(i, c + 1);
+                        else if (i + 1 < n_mine) load_d(i + 1, 0);
+                        // from here each lane reads and rewrites only its own row: g in place of d
 #pragma unroll
                         for (int hh = 0; hh < 2; ++hh) {
                             float u[32];
@@ -357,16 +370,16 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
                             for (int jj = 0; jj < 4; ++jj) {
                                 const int j = hh * 4 + jj;
-                                const uint4 zw = *reinterpret_cast<const uint4*>(buf + swz(lane, j));
+                                const uint4 dv = *reinterpret_cast<const uint4*>(buf + swz(lane, j));
                                 float* w = u + 8 * jj;
-                                w[0] *= act_grad<ACT>(bf_lo(zw.x));
-                                w[1] *= act_grad<ACT>(bf_hi(zw.x));
-                                w[2] *= act_grad<ACT>(bf_lo(zw.y));
-                                w[3] *= act_grad<ACT>(bf_hi(zw.y));
-                                w[4] *= act_grad<ACT>(bf_lo(zw.z));
-                                w[5] *= act_grad<ACT>(bf_hi(zw.z));
-                                w[6] *= act_grad<ACT>(bf_lo(zw.w));
-                                w[7] *= act_grad<ACT>(bf_hi(zw.w));
+                                w[0] *= bf_lo(dv.x);
+                                w[1] *= bf_hi(dv.x);
+                                w[2] *= bf_lo(dv.y);
+                                w[3] *= bf_hi(dv.y);
+                                w[4] *= bf_lo(dv.z);
+                                w[5] *= bf_hi(dv.z);
+                                w[6] *= bf_lo(dv.w);
+                                w[7] *= bf_hi(dv.w);
                                 *reinterpret_cast<uint4*>(buf + swz(lane, j)) =
                                     make_uint4(bf2(w[0], w[1]), bf2(w[2], w[3]), bf2(w[4], w[5]), bf2(w[6], w[7]));
                             }

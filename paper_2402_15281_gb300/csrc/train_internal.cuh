@@ -13,9 +13,7 @@ struct GemmArgs {
     int k_len;                      // K elements per split (multiple of 64)
     long long ld_rows;              // row stride of the row-major [M][.] operands and outputs
     const float* bias;              // FWD: [N]
-    __nv_bfloat16* h_out;           // FWD: H; DGRAD: G
-    __nv_bfloat16* z_out;           // FWD: Z
-    const __nv_bfloat16* z_in;      // DGRAD: Z of the previous layer
+    const __nv_bfloat16* d_in;      // DGRAD: D = act'(z) of the previous layer
     float* dw;                      // WGRAD: FP32 partials [n_ks][M][N]
     long long split_stride;         // WGRAD: elements between the partials of two splits
     unsigned int* err;              // bounded-wait error word
@@ -26,7 +24,7 @@ int train_gemm_bn();
 int train_gemm_bk();
 int train_make_map(void* map, const void* base, long long rows, long long cols, int box_rows);
 int train_make_store_map(void* map, const void* base, long long rows, long long cols, int fp32);
-// smap0 / smap1: tensor maps of the outputs (FWD: Z, H; DGRAD: G; WGRAD: the
+// smap0 / smap1: tensor maps of the outputs (FWD: D, H; DGRAD: G; WGRAD: the
 // FP32 partials as [n_ks * M][N])
 void launch_train_gemm(int epi, int act, const void* amap, const void* bmap, const void* smap0, const void* smap1,
                        const GemmArgs& g, int n_sms, cudaStream_t s);

@@ -590,8 +590,9 @@ def test_bf16_training_gradient_emulation():
       already a bfloat16, so it equals the FP64 backpropagation (itself pinned
       by finite differences) bit for bit, in both activations;
     * on a random network it equals torch's bfloat16 conversions applied at
-      the same places (Z, H, the hidden weights in their products, every
-      layer's gradient G) -- a library routine for the rounding;
+      the same places (act(z) and act'(z) of the unrounded pre-activation,
+      the hidden weights in their products, every layer's gradient G) -- a
+      library routine for the rounding;
     * and it stays within the bfloat16 error of the FP64 gradient."""
     torch = pytest.importorskip("torch")
     rng = np.random.default_rng(0)
@@ -621,23 +622,23 @@ def test_bf16_training_gradient_emulation():
         fa = (lambda z: np.maximum(z, 0)) if act == 0 else (lambda z: z / (1 + np.exp(-z)))
         da = (lambda z: (z > 0).astype(np.float64)) if act == 0 else \
              (lambda z: (1 / (1 + np.exp(-z))) * (1 + z * (1 - 1 / (1 + np.exp(-z)))))
-        Zs, Hs = [], []
+        Ds, Hs = [], []
         z = X @ Ls[0][0].T + Ls[0][1]
-        Zs.append(bf(z)); Hs.append(bf(fa(z)))
+        Ds.append(bf(da(z))); Hs.append(bf(fa(z)))
         Wr = [bf(Ls[l][0]) for l in range(1, L + 1)]
         for l in range(1, L + 1):
             z = Hs[-1] @ Wr[l - 1].T + Ls[l][1]
-            Zs.append(bf(z)); Hs.append(bf(fa(z)))
+            Ds.append(bf(da(z))); Hs.append(bf(fa(z)))
         wo, bo = Ls[L + 1][0][0], Ls[L + 1][1][0]
         f = Hs[-1] @ wo + bo
         e = f - T
         df = np.sign(e) / n
         grads = [None] * (L + 2)
         grads[L + 1] = (df @ Hs[-1], np.array([df.sum()]))
-        g = bf(df[:, None] * wo[None, :] * da(Zs[-1]))
+        g = bf(df[:, None] * wo[None, :] * Ds[-1])
         for l in range(L, 0, -1):
             grads[l] = (g.T @ Hs[l - 1], g.sum(axis=0))
-            g = bf((g @ Wr[l - 1]) * da(Zs[l - 1]))
+            g = bf((g @ Wr[l - 1]) * Ds[l - 1])
         grads[0] = (g.T @ X, g.sum(axis=0))
         want = np.concatenate([np.concatenate([gw.ravel(), gb.ravel()]) for gw, gb in grads])
         np.testing.assert_allclose(G, want, rtol=1e-9, atol=1e-12)
