@@ -149,6 +149,25 @@ __device__ __forceinline__ void act_hd(float z, float& h, float& d)
     }
 }
 
+// Packed FP32 pairs (sm_100+): each half is rounded as the scalar operation
+// would round it, so pairing changes no result bit.
+__device__ __forceinline__ uint64_t f2(float lo, float hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_split(uint64_t v, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 __device__ __forceinline__ void input_row(const StepArgs& a, int r, float (&in)[15], float& delta)
 {
     const long long s = a.base + (long long)r * a.stride;
@@ -167,48 +186,62 @@ __device__ __forceinline__ void input_row(const StepArgs& a, int r, float (&in)[
 // for each sample forms z = b + sum_k w_k in_k (fused multiply-adds in the
 // order k = 0..14), h = act(z) and d = act'(z), storing the feature pair of
 // D0 and H0 as one bfloat16x2 word each (a warp writes 128 contiguous bytes of
-// a row).
+// a row).  Two samples go through one packed multiply-add (fma.rn.f32x2, the
+// inputs of samples 2p and 2p + 1 interleaved in shared memory).
 constexpr int kL1Rows = 64;
 
 template <int ACT>
 __global__ void __launch_bounds__(256) layer1_fwd_kernel(StepArgs a, __nv_bfloat16* D0, __nv_bfloat16* H0)
 {
-    __shared__ __align__(16) float ins[kL1Rows][16];
+    __shared__ __align__(16) float2 ins[kL1Rows / 2][16];     // [sample pair][k] = (in_2p[k], in_2p+1[k])
     const int r0 = blockIdx.x * kL1Rows;
     for (int i = threadIdx.x; i < kL1Rows; i += blockDim.x) {
         float in[15], delta;
         input_row(a, r0 + i, in, delta);
+        float* dst = reinterpret_cast<float*>(ins[i >> 1]) + (i & 1);
 #pragma unroll
-        for (int k = 0; k < 15; ++k) ins[i][k] = in[k];
-        ins[i][15] = 0.0f;
+        for (int k = 0; k < 15; ++k) dst[2 * k] = in[k];
+        dst[30] = 0.0f;
     }
     const int o = 2 * threadIdx.x;
-    float wa[15], wb[15];
+    uint64_t wa[15], wb[15];
 #pragma unroll
     for (int k = 0; k < 15; ++k) {
-        wa[k] = a.P[a.off_w1 + (long long)o * 15 + k];
-        wb[k] = a.P[a.off_w1 + (long long)(o + 1) * 15 + k];
+        const float x = a.P[a.off_w1 + (long long)o * 15 + k], y = a.P[a.off_w1 + (long long)(o + 1) * 15 + k];
+        wa[k] = f2(x, x);
+        wb[k] = f2(y, y);
     }
     const float ba = a.P[a.off_b1 + o], bb = a.P[a.off_b1 + o + 1];
+    const uint64_t ba2 = f2(ba, ba), bb2 = f2(bb, bb);
     __syncthreads();
 #pragma unroll 2
-    for (int r = 0; r < kL1Rows; ++r) {
-        const float4* x4 = reinterpret_cast<const float4*>(ins[r]);
-        const float4 i0 = x4[0], i1 = x4[1], i2 = x4[2], i3 = x4[3];
-        const float in[15] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w,
-                              i2.x, i2.y, i2.z, i2.w, i3.x, i3.y, i3.z};
-        float za = ba, zb = bb;
+    for (int p = 0; p < kL1Rows / 2; ++p) {
+        const ulonglong2* x2 = reinterpret_cast<const ulonglong2*>(ins[p]);
+        uint64_t in2[16];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const ulonglong2 v = x2[q];
+            in2[2 * q] = v.x;
+            in2[2 * q + 1] = v.y;
+        }
+        uint64_t za = ba2, zb = bb2;          // (sample 2p, sample 2p + 1) of features o and o + 1
 #pragma unroll
         for (int k = 0; k < 15; ++k) {
-            za = fmaf(wa[k], in[k], za);
-            zb = fmaf(wb[k], in[k], zb);
+            za = f2_fma(wa[k], in2[k], za);
+            zb = f2_fma(wb[k], in2[k], zb);
         }
-        const long long at = (long long)(r0 + r) * a.W + o;
-        float ha, hb, da, db;
-        act_hd<ACT>(za, ha, da);
-        act_hd<ACT>(zb, hb, db);
-        *reinterpret_cast<__nv_bfloat162*>(D0 + at) = __floats2bfloat162_rn(da, db);
-        *reinterpret_cast<__nv_bfloat162*>(H0 + at) = __floats2bfloat162_rn(ha, hb);
+        float z[2][2];
+        f2_split(za, z[0][0], z[1][0]);
+        f2_split(zb, z[0][1], z[1][1]);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const long long at = (long long)(r0 + 2 * p + e) * a.W + o;
+            float ha, hb, da, db;
+            act_hd<ACT>(z[e][0], ha, da);
+            act_hd<ACT>(z[e][1], hb, db);
+            *reinterpret_cast<__nv_bfloat162*>(D0 + at) = __floats2bfloat162_rn(da, db);
+            *reinterpret_cast<__nv_bfloat162*>(H0 + at) = __floats2bfloat162_rn(ha, hb);
+        }
     }
 }
 
@@ -334,9 +367,10 @@ __global__ void __launch_bounds__(128) head_kernel(StepArgs a, const __nv_bfloat
 // features per block column (blockIdx.y); thread t owns features n, n + 1:
 // part[b][n * 15 + k] = sum_r G0[r][n] in_r[k], part[b][15 W + n] = sum_r
 // G0[r][n] -- the layout of W1 and b1 in the parameter vector -- each sum a
-// chain of fused multiply-adds over the block's samples in ascending order.
-// The G0 words reach shared memory by cp.async, 16 samples per group and two
-// groups in flight, so the loads do not wait on the arithmetic.
+// chain of fused multiply-adds over the block's samples in ascending order
+// (two chains per packed fma.rn.f32x2).  The G0 words reach shared memory by
+// cp.async, 16 samples per group and two groups in flight, so the loads do
+// not wait on the arithmetic.
 __global__ void __launch_bounds__(128) layer1_bwd_kernel(StepArgs a, const __nv_bfloat16* G0)
 {
     __shared__ __align__(16) float ins[256][16];
@@ -351,9 +385,10 @@ __global__ void __launch_bounds__(128) layer1_bwd_kernel(StepArgs a, const __nv_
     }
     __syncthreads();
     const int n = blockIdx.y * 256 + 2 * threadIdx.x;
-    float acc0[16], acc1[16];
+    // (acc[k], acc[k + 1]) of features n and n + 1 as packed pairs
+    uint64_t acc0[8], acc1[8];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) acc0[k] = acc1[k] = 0.0f;
+    for (int k = 0; k < 8; ++k) acc0[k] = acc1[k] = 0ull;
     // G0[r0 + b][n, n + 1] for 16 samples per group, two groups in flight
     const uint32_t* g = reinterpret_cast<const uint32_t*>(G0 + (long long)r0 * a.W + n);
     const int ldw = a.W / 2;
@@ -375,29 +410,32 @@ __global__ void __launch_bounds__(128) layer1_bwd_kernel(StepArgs a, const __nv_
         for (int u = 0; u < 16; ++u) {
             const uint32_t gv = ring[grp & 1][u][threadIdx.x];
             const float g0 = __uint_as_float(gv << 16), g1 = __uint_as_float(gv & 0xFFFF0000u);
-            const float4* x4 = reinterpret_cast<const float4*>(ins[grp * 16 + u]);
+            const uint64_t g00 = f2(g0, g0), g11 = f2(g1, g1);
+            const ulonglong2* x2 = reinterpret_cast<const ulonglong2*>(ins[grp * 16 + u]);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float4 x = x4[q];
-                acc0[4 * q + 0] = fmaf(g0, x.x, acc0[4 * q + 0]);
-                acc0[4 * q + 1] = fmaf(g0, x.y, acc0[4 * q + 1]);
-                acc0[4 * q + 2] = fmaf(g0, x.z, acc0[4 * q + 2]);
-                acc0[4 * q + 3] = fmaf(g0, x.w, acc0[4 * q + 3]);
-                acc1[4 * q + 0] = fmaf(g1, x.x, acc1[4 * q + 0]);
-                acc1[4 * q + 1] = fmaf(g1, x.y, acc1[4 * q + 1]);
-                acc1[4 * q + 2] = fmaf(g1, x.z, acc1[4 * q + 2]);
-                acc1[4 * q + 3] = fmaf(g1, x.w, acc1[4 * q + 3]);
+                const ulonglong2 x = x2[q];            // (in[4q], in[4q+1]), (in[4q+2], in[4q+3])
+                acc0[2 * q] = f2_fma(g00, x.x, acc0[2 * q]);
+                acc0[2 * q + 1] = f2_fma(g00, x.y, acc0[2 * q + 1]);
+                acc1[2 * q] = f2_fma(g11, x.x, acc1[2 * q]);
+                acc1[2 * q + 1] = f2_fma(g11, x.y, acc1[2 * q + 1]);
             }
         }
     }
     float* pb = a.part + (long long)blockIdx.x * a.W * 16;
+    float s0[16], s1[16];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        f2_split(acc0[k], s0[2 * k], s0[2 * k + 1]);
+        f2_split(acc1[k], s1[2 * k], s1[2 * k + 1]);
+    }
 #pragma unroll
     for (int k = 0; k < 15; ++k) {
-        pb[(long long)n * 15 + k] = acc0[k];
-        pb[(long long)(n + 1) * 15 + k] = acc1[k];
+        pb[(long long)n * 15 + k] = s0[k];
+        pb[(long long)(n + 1) * 15 + k] = s1[k];
     }
-    pb[15LL * a.W + n] = acc0[15];
-    pb[15LL * a.W + n + 1] = acc1[15];
+    pb[15LL * a.W + n] = s0[15];
+    pb[15LL * a.W + n + 1] = s1[15];
 }
 
 // Bias gradients db[n] += sum over the batch of G[b][n] (G row-major [B][W]),
@@ -412,24 +450,27 @@ __global__ void __launch_bounds__(128) layer1_bwd_kernel(StepArgs a, const __nv_
 // column) forms the tree.
 constexpr int kCsDepth = 32;   // rows per cp.async group of the chains
 
-size_t colsum_smem_bytes() { return (size_t)2 * kCsDepth * 256 * sizeof(uint2); }
+constexpr int kCsThreads = 128;   // 4 chains x 32 column quads per block
 
-__global__ void __launch_bounds__(256) colsum_chains_kernel(const __nv_bfloat16* G, long long B, int W, float* chain)
+size_t colsum_smem_bytes() { return (size_t)2 * kCsDepth * kCsThreads * sizeof(uint2); }
+
+__global__ void __launch_bounds__(kCsThreads) colsum_chains_kernel(const __nv_bfloat16* G, long long B, int W,
+                                                                  float* chain)
 {
-    extern __shared__ __align__(16) uint2 cs_ring[];              // [2][kCsDepth][256]
+    extern __shared__ __align__(16) uint2 cs_ring[];              // [2][kCsDepth][kCsThreads]
     const int q = blockIdx.x * 32 + (threadIdx.x & 31);          // column quad
-    const int t = blockIdx.y * 8 + (threadIdx.x >> 5);           // chain (row class), 0..255
+    const int t = blockIdx.y * (kCsThreads / 32) + (threadIdx.x >> 5);   // chain (row class), 0..255
     const int n0 = 4 * q;
     const long long rows = (B - t + 255) / 256;                   // rows t, t + 256, ... below B
     const long long ng = (rows + kCsDepth - 1) / kCsDepth;
     const __nv_bfloat16* src = G + (long long)t * W + n0;
     const long long step = 256LL * W;
     auto issue = [&](long long grp) {
-        uint2* dst = cs_ring + (grp & 1) * kCsDepth * 256 + threadIdx.x;
+        uint2* dst = cs_ring + (grp & 1) * kCsDepth * kCsThreads + threadIdx.x;
         const long long r0 = grp * kCsDepth;
 #pragma unroll 8
         for (int u = 0; u < kCsDepth; ++u)
-            if (r0 + u < rows) cp_async_small<8>(dst + u * 256, src + (r0 + u) * step);
+            if (r0 + u < rows) cp_async_small<8>(dst + u * kCsThreads, src + (r0 + u) * step);
         cp_async_commit_group();
     };
     float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -441,11 +482,11 @@ __global__ void __launch_bounds__(256) colsum_chains_kernel(const __nv_bfloat16*
         } else {
             cp_async_wait_group<0>();
         }
-        const uint2* buf = cs_ring + (grp & 1) * kCsDepth * 256 + threadIdx.x;
+        const uint2* buf = cs_ring + (grp & 1) * kCsDepth * kCsThreads + threadIdx.x;
         const int cnt = (int)min((long long)kCsDepth, rows - grp * kCsDepth);
 #pragma unroll 8
         for (int u = 0; u < cnt; ++u) {
-            const uint2 w = buf[u * 256];
+            const uint2 w = buf[u * kCsThreads];
             s[0] += __uint_as_float(w.x << 16);
             s[1] += __uint_as_float(w.x & 0xFFFF0000u);
             s[2] += __uint_as_float(w.y << 16);
@@ -686,7 +727,8 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
         launch_train_gemm(kEpiWgrad, 0, t->mapGmn[l].b, t->mapHmn[l - 1].b, t->mapPst.b, nullptr, g, t->n_sms, s);
         reduce_kernel<<<grid_for((long long)W * W), 256, 0, s>>>(t->part, g.n_ks, (long long)W * W, t->Gr + woff);
         // the split-K partials are reduced: part holds the bias-gradient chains next
-        colsum_chains_kernel<<<dim3(W / 128, 32), 256, colsum_smem_bytes(), s>>>(t->G[l], B, W, t->part);
+        colsum_chains_kernel<<<dim3(W / 128, 256 / (kCsThreads / 32)), kCsThreads, colsum_smem_bytes(), s>>>(t->G[l], B, W,
+                                                                                                        t->part);
         colsum_tree_kernel<<<W / 8, 256, 0, s>>>(t->part, W, t->Gr + woff + (long long)W * W);
         GemmArgs d{};
         d.n_mt = B / 128; d.n_nt = W / 256; d.n_ks = 1; d.k_len = W;
