@@ -564,6 +564,22 @@ __global__ void reduce_kernel(const float* part, int P, long long n, float* dst)
     }
 }
 
+// dst[0] += sum_{p < P} part[p] in the order p = 0, 1, ... (the order of
+// reduce_kernel), by one warp: 32 partials per coalesced load, added
+// in order through shuffles.  It needs no shared memory, so it can share SMs
+// with a running GEMM.
+__global__ void reduce_scalar_kernel(const float* part, int P, float* dst)
+{
+    const int lane = threadIdx.x & 31;
+    float s = 0.0f;
+    for (int p0 = 0; p0 < P; p0 += 32) {
+        const float v = p0 + lane < P ? part[p0 + lane] : 0.0f;
+        const int lim = min(32, P - p0);
+        for (int j = 0; j < lim; ++j) s += __shfl_sync(0xffffffffu, v, j);
+    }
+    if (lane == 0) dst[0] += s;
+}
+
 // Adam on the FP32 master parameters; refreshes the BF16 copies of the
 // hidden weights (W [out][in] and W^T [in][out]).
 __global__ void adam_kernel(float* P, const float* G, float* Mo, float* Vo, long long n, float lr, float b1, float b2,
@@ -622,15 +638,22 @@ struct svm_trainer {
     float* P = nullptr; float* Gr = nullptr; float* Mo = nullptr; float* Vo = nullptr;
     float* loss = nullptr;            // per-block loss partials (B / 32)
     float* loss_sum = nullptr;        // batch-summed losses of the current call
-    float* part = nullptr;            // partial gradients (largest of the three uses)
+    float* part = nullptr;            // per-block partials of the head and of layer 1
     long long part_n = 0;
+    float* kpart[2] = {nullptr, nullptr};   // split-K weight-gradient partials, alternating by layer
+    float* chain[2] = {nullptr, nullptr};   // bias-gradient chains [256][W], alternating by layer
+    // the second stream: per layer, the split-K reduction and the bias-sum tree run
+    // beside the next GEMMs (no shared memory, so they share SMs with them)
+    cudaStream_t side = nullptr;
+    std::vector<cudaEvent_t> ev_w, ev_c, ev_s;   // per layer: partials ready, chains ready, side done
+    cudaEvent_t ev_head = nullptr, ev_side = nullptr;
     unsigned int* err = nullptr;
     __nv_bfloat16* wb = nullptr; __nv_bfloat16* wbt = nullptr;
     std::vector<__nv_bfloat16*> H, D, G;             // per layer 0..L, [B][W]; D = act'(z)
     // A operands of the forward and input-gradient GEMMs (K-major, 128-row boxes) and the MN-major
     // operands of the weight-gradient GEMM (64 x 64 boxes)
     std::vector<Map> mapH, mapG, mapHmn, mapGmn, mapW, mapWT, mapDst, mapHst, mapGst;
-    Map mapPst;
+    Map mapPst[2];
     // data
     float4* X = nullptr; int* MID = nullptr; double* q0 = nullptr; double* q1 = nullptr;
     int n_motions = 0; long long n_samples = 0;
@@ -715,21 +738,34 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
     const size_t head_smem = head_smem_bytes(W);
     if (t->act == 0) head_kernel<0><<<B / 32, 128, head_smem, s>>>(a, t->H[L], t->D[L], t->G[L], grad ? 0 : 1);
     else head_kernel<1><<<B / 32, 128, head_smem, s>>>(a, t->H[L], t->D[L], t->G[L], grad ? 0 : 1);
-    reduce_long_kernel<1><<<1, 256, 0, s>>>(t->loss, B / 32, 1, t->loss_sum);
-    if (!grad) return SVM_OK;
+    if (!grad) {
+        reduce_scalar_kernel<<<1, 32, 0, s>>>(t->loss, B / 32, t->loss_sum);
+        return SVM_OK;
+    }
+    cudaStream_t s2 = t->side;
+    cudaEventRecord(t->ev_head, s);
+    cudaStreamWaitEvent(s2, t->ev_head, 0);
+    reduce_scalar_kernel<<<1, 32, 0, s2>>>(t->loss, B / 32, t->loss_sum);
     reduce_long_kernel<kRedCols><<<(W + 1 + kRedCols - 1) / kRedCols, 256, 0, s>>>(t->part, B / 32, W + 1, t->Gr + t->off_out);
     for (int l = L; l >= 1; --l) {
         const long long woff = t->off_h + (long long)(l - 1) * ((long long)W * W + W);
+        const int buf = l & 1;
+        // the buffers of layer l + 2 are free once the side stream has reduced them
+        if (l + 2 <= L) cudaStreamWaitEvent(s, t->ev_s[l + 2], 0);
         GemmArgs g{};
         const int k_len = B >= 2048 ? 2048 : B;
         g.n_mt = W / 128; g.n_nt = W / 256; g.n_ks = B / k_len; g.k_len = k_len;
-        g.ld_rows = W; g.dw = t->part; g.split_stride = (long long)W * W; g.err = t->err;
-        launch_train_gemm(kEpiWgrad, 0, t->mapGmn[l].b, t->mapHmn[l - 1].b, t->mapPst.b, nullptr, g, t->n_sms, s);
-        reduce_kernel<<<grid_for((long long)W * W), 256, 0, s>>>(t->part, g.n_ks, (long long)W * W, t->Gr + woff);
-        // the split-K partials are reduced: part holds the bias-gradient chains next
+        g.ld_rows = W; g.dw = t->kpart[buf]; g.split_stride = (long long)W * W; g.err = t->err;
+        launch_train_gemm(kEpiWgrad, 0, t->mapGmn[l].b, t->mapHmn[l - 1].b, t->mapPst[buf].b, nullptr, g, t->n_sms, s);
+        cudaEventRecord(t->ev_w[l], s);
         colsum_chains_kernel<<<dim3(W / 128, 256 / (kCsThreads / 32)), kCsThreads, colsum_smem_bytes(), s>>>(t->G[l], B, W,
-                                                                                                        t->part);
-        colsum_tree_kernel<<<W / 8, 256, 0, s>>>(t->part, W, t->Gr + woff + (long long)W * W);
+                                                                                                        t->chain[buf]);
+        cudaEventRecord(t->ev_c[l], s);
+        cudaStreamWaitEvent(s2, t->ev_w[l], 0);
+        reduce_kernel<<<grid_for((long long)W * W), 256, 0, s2>>>(t->kpart[buf], g.n_ks, (long long)W * W, t->Gr + woff);
+        cudaStreamWaitEvent(s2, t->ev_c[l], 0);
+        colsum_tree_kernel<<<W / 8, 256, 0, s2>>>(t->chain[buf], W, t->Gr + woff + (long long)W * W);
+        cudaEventRecord(t->ev_s[l], s2);
         GemmArgs d{};
         d.n_mt = B / 128; d.n_nt = W / 256; d.n_ks = 1; d.k_len = W;
         d.ld_rows = W; d.d_in = t->D[l - 1];
@@ -739,6 +775,9 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
     }
     layer1_bwd_kernel<<<dim3(B / 256, W / 256), 128, 0, s>>>(a, t->G[0]);
     reduce_long_kernel<kRedCols><<<W * 16 / kRedCols, 256, 0, s>>>(t->part, B / 256, (long long)W * 16, t->Gr + t->off_w1);
+    // the step ends when the side stream's sums are in the gradient too
+    cudaEventRecord(t->ev_side, s2);
+    cudaStreamWaitEvent(s, t->ev_side, 0);
     return SVM_OK;
 }
 
@@ -797,9 +836,21 @@ svm_status svm_train_create(const svm_model_desc* desc, int device, int32_t batc
     if ((st = talloc(t, &t->loss_sum, 256)) != SVM_OK) return fail_free(st);
     {
         const long long k_len = B >= 2048 ? 2048 : B;
-        t->part_n = std::max({(B / k_len) * W * W, (B / 32) * (W + 1), (B / 256) * W * 16});
+        t->part_n = std::max((B / 32) * (W + 1), (B / 256) * W * 16);
+        for (int b = 0; b < 2; ++b) {
+            if ((st = talloc(t, &t->kpart[b], (B / k_len) * W * W * 4)) != SVM_OK) return fail_free(st);
+            if ((st = talloc(t, &t->chain[b], 256LL * W * 4)) != SVM_OK) return fail_free(st);
+        }
     }
     if ((st = talloc(t, &t->part, t->part_n * 4)) != SVM_OK) return fail_free(st);
+    if (cudaStreamCreateWithFlags(&t->side, cudaStreamNonBlocking) != cudaSuccess) return fail_free(SVM_E_CUDA);
+    t->ev_w.assign(L + 1, nullptr); t->ev_c.assign(L + 1, nullptr); t->ev_s.assign(L + 1, nullptr);
+    for (int l = 0; l <= L; ++l)
+        for (auto* v : {&t->ev_w, &t->ev_c, &t->ev_s})
+            if (cudaEventCreateWithFlags(&(*v)[l], cudaEventDisableTiming) != cudaSuccess) return fail_free(SVM_E_CUDA);
+    if (cudaEventCreateWithFlags(&t->ev_head, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&t->ev_side, cudaEventDisableTiming) != cudaSuccess)
+        return fail_free(SVM_E_CUDA);
     if ((st = talloc(t, &t->err, 256)) != SVM_OK) return fail_free(st);
     if ((st = talloc(t, &t->wb, L * W * W * 2)) != SVM_OK) return fail_free(st);
     if ((st = talloc(t, &t->wbt, L * W * W * 2)) != SVM_OK) return fail_free(st);
@@ -831,7 +882,7 @@ svm_status svm_train_create(const svm_model_desc* desc, int device, int32_t batc
     {
         // the weight-gradient partials, [splits * W][W] FP32
         const long long k_len = B >= 2048 ? 2048 : B;
-        bad |= train_make_store_map(t->mapPst.b, t->part, (B / k_len) * W, W, 1);
+        for (int b = 0; b < 2; ++b) bad |= train_make_store_map(t->mapPst[b].b, t->kpart[b], (B / k_len) * W, W, 1);
     }
     if (bad) return fail_free(SVM_E_CUDA);
     if (cudaDeviceSynchronize() != cudaSuccess) return fail_free(SVM_E_CUDA);
@@ -847,6 +898,12 @@ svm_status svm_train_destroy(svm_trainer* t)
         cudaDeviceSynchronize();
         for (void* p : t->allocs)
             if (p) cudaFree(p);
+        for (auto* v : {&t->ev_w, &t->ev_c, &t->ev_s})
+            for (cudaEvent_t e : *v)
+                if (e) cudaEventDestroy(e);
+        if (t->ev_head) cudaEventDestroy(t->ev_head);
+        if (t->ev_side) cudaEventDestroy(t->ev_side);
+        if (t->side) cudaStreamDestroy(t->side);
     }
     delete t;
     return SVM_OK;
