@@ -146,8 +146,8 @@ __device__ __forceinline__ void add_xpart(const float* w, const float3 (&x4)[4],
 
 template <bool HAS_WX, bool LAST>
 __device__ __forceinline__ void block_chunk(uint32_t abase, uint32_t t_addr, int q, int lane, int c0, const float* cl,
-                                            const float* s, const float* t, const float* wx, const float* wf,
-                                            const float3 (&x4)[4], uint64_t (&acc4)[4])
+                                            const float* crec, const float* wf, const float3 (&x4)[4],
+                                            uint64_t (&acc4)[4])
 {
     float v[32];
     tmem_ld_frag32(t_addr, v);
@@ -160,15 +160,25 @@ __device__ __forceinline__ void block_chunk(uint32_t abase, uint32_t t_addr, int
         uint32_t hp[4];
         ldmatrix_x4(act_addr(abase, q * 32 + 16 * (j >> 1) + 8 * (j & 1) + i8, (c0 + 8 * g) >> 3), hp[0], hp[1],
                     hp[2], hp[3]);
-        const float2 b = ldg2(cl + c), sc = ldg2(s + c), sh = ldg2(t + c);
+        // the column pair's record: (s, s'), (t, t'), wx of c, wx of c + 1
+        const float4* rec = reinterpret_cast<const float4*>(crec + 6 * c);
+        const float2 b = ldg2(cl + c);
+        const float4 st = __ldg(rec);
         uint64_t z[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int vi = 16 * (k >> 1) + 4 * g + 2 * (k & 1);
             z[k] = f2_add(f2(v[vi], v[vi + 1]), f2(b.x, b.y));
         }
-        if constexpr (HAS_WX) add_xpart(wx + 3 * c, x4, z);
-        const uint64_t s2 = f2(sc.x, sc.y), t2 = f2(sh.x, sh.y);
+        if constexpr (HAS_WX) {
+            const float4 wa = __ldg(rec + 1), wb = __ldg(rec + 2);   // (x, y, z, x'), (y', z', 0, 0)
+            const uint64_t wx = f2(wa.x, wa.w), wy = f2(wa.y, wb.x), wz = f2(wa.z, wb.y);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                z[k] = f2_fma(wz, f2(x4[k].z, x4[k].z),
+                              f2_fma(wy, f2(x4[k].y, x4[k].y), f2_fma(wx, f2(x4[k].x, x4[k].x), z[k])));
+        }
+        const uint64_t s2 = f2(st.x, st.y), t2 = f2(st.z, st.w);
         uint64_t w2 = 0;
         if constexpr (LAST) {
             const float2 w = ldg2(wf + c);
@@ -387,9 +397,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const float* cm = A.cbias + (long long)m * cbs;
             for (int l = 1; l <= L && ok; ++l) {
                 const float* cl = cm + (long long)l * WB;
-                const float* s = Wt.blk_s + (long long)(l - 1) * WB;
-                const float* t = Wt.blk_t + (long long)(l - 1) * WB;
-                const float* wx = Wt.blk_wx + (long long)(l - 1) * WB * 3;
+                const float* crec = Wt.blk_pk + (long long)(l - 1) * WB * 6;   // [W/2][12] of block l
                 int nm = 0;
                 long long np0 = 0, npe = 0;
                 float3 xn[4];
@@ -405,11 +413,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll 1
                     for (int o = 0; o < 4; ++o) {
                         if (l == 1)
-                            block_chunk<false, false>(abase, t_row + (uint32_t)(32 * o), q, lane, col0 + 32 * o, cl, s,
-                                                      t, wx, Wt.wout, x4, acc4);
+                            block_chunk<false, false>(abase, t_row + (uint32_t)(32 * o), q, lane, col0 + 32 * o, cl, crec,
+                                                      Wt.wout, x4, acc4);
                         else
-                            block_chunk<true, false>(abase, t_row + (uint32_t)(32 * o), q, lane, col0 + 32 * o, cl, s,
-                                                     t, wx, Wt.wout, x4, acc4);
+                            block_chunk<true, false>(abase, t_row + (uint32_t)(32 * o), q, lane, col0 + 32 * o, cl, crec,
+                                                      Wt.wout, x4, acc4);
                     }
                     fence_async_smem();
                     tc_fence_before();
@@ -421,11 +429,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll 1
                 for (int o = 0; o < 4; ++o) {
                     if (l == 1)
-                        block_chunk<false, true>(abase, t_row + (uint32_t)(32 * o), q, lane, col0 + 32 * o, cl, s, t,
-                                                 wx, Wt.wout, x4, acc4);
+                        block_chunk<false, true>(abase, t_row + (uint32_t)(32 * o), q, lane, col0 + 32 * o, cl, crec,
+                                                 Wt.wout, x4, acc4);
                     else
-                        block_chunk<true, true>(abase, t_row + (uint32_t)(32 * o), q, lane, col0 + 32 * o, cl, s, t,
-                                                wx, Wt.wout, x4, acc4);
+                        block_chunk<true, true>(abase, t_row + (uint32_t)(32 * o), q, lane, col0 + 32 * o, cl, crec,
+                                                 Wt.wout, x4, acc4);
                 }
                 // every read of this tile's TMEM and activation tile is done: the next tile's h_0
                 if (has_next) stage_h0(nm, xn);

@@ -217,11 +217,28 @@ svm_status load_block_weights(svm_model* m, const unsigned char* p, size_t bytes
         }
     }
 
+    // the block kernel's per-column-pair record (see DevWeights::blk_pk)
+    std::vector<float> blk_pk;
+    if (d.arch == SVM_ARCH_BLOCKS && W % 2 == 0) {
+        blk_pk.assign((size_t)L * (W / 2) * 12, 0.0f);
+        for (int l = 0; l < L; ++l)
+            for (int c = 0; c < W; c += 2) {
+                float* r = &blk_pk[((size_t)l * (W / 2) + c / 2) * 12];
+                r[0] = blk_s[l * W + c];
+                r[1] = blk_s[l * W + c + 1];
+                r[2] = blk_t[l * W + c];
+                r[3] = blk_t[l * W + c + 1];
+                for (int k = 0; k < 3; ++k) {
+                    r[4 + k] = blk_wx[((size_t)l * W + c) * 3 + k];
+                    r[7 + k] = blk_wx[((size_t)l * W + c + 1) * 3 + k];
+                }
+            }
+    }
     DeviceGuard g(m->device);
     CK(cudaDeviceSynchronize());
     size_t total = 0;
     const std::vector<const std::vector<float>*> parts = {&w1x, &wT, &wout, &blk_wx, &blk_wq, &blk_b, &blk_s,
-                                                          &blk_t, &out_wx, &out_wq};
+                                                          &blk_t, &out_wx, &out_wq, &blk_pk};
     for (auto* v : parts) total += align256(std::max<size_t>(1, v->size()) * 4);
     const size_t wh_at = total;
     total += align256(wh.size() * 2);
@@ -247,6 +264,7 @@ svm_status load_block_weights(svm_model* m, const unsigned char* p, size_t bytes
     dw.blk_t = dev[7];
     dw.out_wx = dev[8];
     dw.out_wq = dev[9];
+    dw.blk_pk = dev[10];
     dw.bout = bout;
     if (bf16) {
         CK(cudaMemcpy(base + wh_at, wh.data(), wh.size() * 2, cudaMemcpyHostToDevice));
