@@ -276,8 +276,9 @@ def mlp_loss_grad(P, width, n_hidden, act, inputs, target):
 
 def mlp_loss_grad_bf16(P, width, n_hidden, act, inputs, target):
     """mlp_loss_grad with bfloat16 rounding where a BF16 training step stores
-    values (hidden weights in the products, every Z and H, every layer's
-    gradient G); (loss, gradient)."""
+    values (hidden weights in the products, act(z) and act'(z) of every
+    layer's unrounded pre-activation, every layer's gradient G); (loss,
+    gradient)."""
     inputs = _d(inputs).reshape(-1, 15)
     G = np.zeros(param_count(width, n_hidden))
     loss = lib().orc_mlp_loss_grad_bf16(_d(P), width, n_hidden, act, inputs, _d(target), inputs.shape[0], G)

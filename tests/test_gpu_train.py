@@ -4,7 +4,8 @@
   (same SplitMix64 draws, FP64 geometry) within 1e-5 m;
 * gradient: the BF16 tensor-core backward pass against two oracles, per
   parameter group: the FP64 backpropagation that rounds to bfloat16 where
-  the trainer stores values (hidden weights in their products, Z, H and every
+  the trainer stores values (hidden weights in their products, act(z) and
+  act'(z) of the unrounded pre-activation, and every
   layer's gradient G) isolates the kernels' own arithmetic -- relative L2
   error <= 0.3 %, cosine >= 0.99999 (measured <= 0.08 %); the plain FP64 backpropagation bounds the
   whole BF16 error -- cosine >= 0.995, relative L2 <= 8 % (sums over the
