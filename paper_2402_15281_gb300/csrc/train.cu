@@ -254,13 +254,13 @@ __global__ void __launch_bounds__(256) layer1_fwd_kernel(StepArgs a, __nv_bfloat
 // in ascending order by fused multiply-adds, then ((f_0 + f_1) + f_2) + f_3
 // + b_out; the sums over the block's 32 samples (|e|, df, df h) are the
 // butterfly x_l += x_{l ^ s}, s = 16, 8, 4, 2, 1, read at lane 0 (for df h
-// written as the same tree over registers).  The 32 rows of H_L and D_L are
-// staged in shared memory with coalesced 16-byte loads; each row is padded by
-// 16 bytes, so the row-per-lane reads of the chains are free of bank
-// conflicts.
+// written as the same tree over registers).  The 32 rows of H_L are staged in
+// shared memory with coalesced 16-byte loads; each row is padded by 16 bytes,
+// so the row-per-lane reads of the chains are free of bank conflicts.  D_L is
+// read where G_L is formed, a feature pair per lane (coalesced).
 constexpr int kHeadPad = 8;   // bfloat16 elements of padding per staged row
 
-size_t head_smem_bytes(int W) { return (size_t)2 * 32 * (W + kHeadPad) * sizeof(__nv_bfloat16); }
+size_t head_smem_bytes(int W) { return (size_t)32 * (W + kHeadPad) * sizeof(__nv_bfloat16); }
 
 template <int ACT>
 __global__ void __launch_bounds__(128) head_kernel(StepArgs a, const __nv_bfloat16* HL, const __nv_bfloat16* DL,
@@ -271,30 +271,24 @@ __global__ void __launch_bounds__(128) head_kernel(StepArgs a, const __nv_bfloat
     __shared__ float dfs[32];
     const int W = a.W, ld = W + kHeadPad;
     __nv_bfloat16* hs = reinterpret_cast<__nv_bfloat16*>(smem);
-    __nv_bfloat16* ds = hs + 32 * ld;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long row0 = (long long)blockIdx.x * 32;
     {
         const int per_row = W / 8, n = 32 * per_row;     // 16-byte pieces
         const uint4* gh = reinterpret_cast<const uint4*>(HL + row0 * W);
-        const uint4* gz = reinterpret_cast<const uint4*>(DL + row0 * W);
-        for (int i0 = threadIdx.x; i0 < n; i0 += 8 * 128) {
-            uint4 vh[8], vz[8];
+        for (int i0 = threadIdx.x; i0 < n; i0 += 16 * 128) {
+            uint4 vh[16];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < 16; ++u) {
                 const int i = i0 + u * 128;
-                if (i < n) {
-                    vh[u] = gh[i];
-                    if (!eval) vz[u] = gz[i];
-                }
+                if (i < n) vh[u] = gh[i];
             }
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < 16; ++u) {
                 const int i = i0 + u * 128;
                 if (i < n) {
                     const int rr = i / per_row, cc = i % per_row;
                     *reinterpret_cast<uint4*>(hs + rr * ld + cc * 8) = vh[u];
-                    if (!eval) *reinterpret_cast<uint4*>(ds + rr * ld + cc * 8) = vz[u];
                 }
             }
         }
@@ -343,7 +337,7 @@ __global__ void __launch_bounds__(128) head_kernel(StepArgs a, const __nv_bfloat
         for (int r = 0; r < 32; ++r) {
             const float df = dfs[r];
             const uint32_t h2 = *reinterpret_cast<const uint32_t*>(hs + r * ld + o);
-            const uint32_t d2 = *reinterpret_cast<const uint32_t*>(ds + r * ld + o);
+            const uint32_t d2 = __ldg(reinterpret_cast<const unsigned int*>(DL + (row0 + r) * W + o));
             xa[r] = df * __uint_as_float(h2 << 16);
             xb[r] = df * __uint_as_float(h2 & 0xFFFF0000u);
             const float ga = df * wa * __uint_as_float(d2 << 16);
@@ -580,31 +574,63 @@ __global__ void reduce_scalar_kernel(const float* part, int P, float* dst)
     if (lane == 0) dst[0] += s;
 }
 
-// Adam on the FP32 master parameters; refreshes the BF16 copies of the
-// hidden weights (W [out][in] and W^T [in][out]).
-__global__ void adam_kernel(float* P, const float* G, float* Mo, float* Vo, long long n, float lr, float b1, float b2,
-                            float eps, float c1, float c2, int W, int L, long long off_h, __nv_bfloat16* wb,
-                            __nv_bfloat16* wbt)
+// Adam on the FP32 master parameters (two kernels); refreshes the BF16 copies
+// of the hidden weights (W [out][in] and W^T [in][out]).
+__device__ __forceinline__ float adam_update(float* P, const float* G, float* Mo, float* Vo, long long i, float lr,
+                                             float b1, float b2, float eps, float c1, float c2)
 {
-    const long long stride_l = (long long)W * W + W;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float g = G[i];
-        const float m = b1 * Mo[i] + (1.0f - b1) * g;
-        const float v = b2 * Vo[i] + (1.0f - b2) * g * g;
-        Mo[i] = m;
-        Vo[i] = v;
-        const float p = P[i] - lr * (m / c1) / (sqrtf(v / c2) + eps);
-        P[i] = p;
-        const long long j = i - off_h;
-        if (j >= 0 && j < stride_l * L) {
-            const long long l = j / stride_l, w = j % stride_l;
-            if (w < (long long)W * W) {
-                const long long o = w / W, k = w % W;
-                const __nv_bfloat16 pb = __float2bfloat16_rn(p);
-                wb[l * W * W + o * W + k] = pb;
-                wbt[l * W * W + k * W + o] = pb;
-            }
+    const float g = G[i];
+    const float m = b1 * Mo[i] + (1.0f - b1) * g;
+    const float v = b2 * Vo[i] + (1.0f - b2) * g * g;
+    Mo[i] = m;
+    Vo[i] = v;
+    const float p = P[i] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+    P[i] = p;
+    return p;
+}
+
+// The hidden-layer weight matrices, one 32 x 32 tile (outputs o0.., inputs
+// k0..) of layer blockIdx.z per block: coalesced reads and writes of the FP32
+// state and of W (bfloat16), and W^T written through a shared-memory tile.
+__global__ void __launch_bounds__(256) adam_hidden_kernel(float* P, const float* G, float* Mo, float* Vo, float lr,
+                                                          float b1, float b2, float eps, float c1, float c2, int W,
+                                                          long long off_h, __nv_bfloat16* wb, __nv_bfloat16* wbt)
+{
+    __shared__ __nv_bfloat16 tile[32][34];
+    const int l = blockIdx.z, o0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const long long base = off_h + (long long)l * ((long long)W * W + W);
+    const long long lw = (long long)l * W * W;
+#pragma unroll
+    for (int r = ty; r < 32; r += 8) {
+        const long long w = (long long)(o0 + r) * W + k0 + tx;
+        const float p = adam_update(P, G, Mo, Vo, base + w, lr, b1, b2, eps, c1, c2);
+        const __nv_bfloat16 pb = __float2bfloat16_rn(p);
+        wb[lw + w] = pb;
+        tile[r][tx] = pb;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = ty; r < 32; r += 8) wbt[lw + (long long)(k0 + r) * W + o0 + tx] = tile[tx][r];
+}
+
+// Every other parameter: layer 1 (weights and bias), the hidden biases, the
+// output layer.
+__global__ void adam_rest_kernel(float* P, const float* G, float* Mo, float* Vo, float lr, float b1, float b2, float eps,
+                                 float c1, float c2, int W, int L, long long off_h, long long off_out)
+{
+    const long long n = off_h + (long long)L * W + W + 1;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        long long i;
+        if (t < off_h) {
+            i = t;
+        } else if (t < off_h + (long long)L * W) {
+            const long long u = t - off_h, l = u / W;
+            i = off_h + l * ((long long)W * W + W) + (long long)W * W + (u - l * W);
+        } else {
+            i = off_out + (t - off_h - (long long)L * W);
         }
+        adam_update(P, G, Mo, Vo, i, lr, b1, b2, eps, c1, c2);
     }
 }
 
@@ -808,7 +834,7 @@ svm_status svm_train_create(const svm_model_desc* desc, int device, int32_t batc
     t->device = device;
     t->desc = d;
     cudaDeviceGetAttribute(&t->n_sms, cudaDevAttrMultiProcessorCount, device);
-    // the head stages 32 rows of H_L and D_L: 66.5 KB at width 512
+    // the head stages 32 rows of H_L: 33 KB at width 512
     cudaFuncSetAttribute(head_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)head_smem_bytes(512));
     cudaFuncSetAttribute(head_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)head_smem_bytes(512));
     cudaFuncSetAttribute(colsum_chains_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)colsum_smem_bytes());
@@ -1094,8 +1120,10 @@ svm_status svm_train_adam(svm_trainer* t, float lr)
     t->step += 1;
     const double b1 = 0.9, b2 = 0.999;
     const float c1 = (float)(1.0 - std::pow(b1, (double)t->step)), c2 = (float)(1.0 - std::pow(b2, (double)t->step));
-    adam_kernel<<<grid_for(t->np), 256>>>(t->P, t->Gr, t->Mo, t->Vo, t->np, lr, (float)b1, (float)b2, 1e-8f, c1, c2,
-                                         t->W, t->L, t->off_h, t->wb, t->wbt);
+    adam_hidden_kernel<<<dim3(t->W / 32, t->W / 32, t->L), 256>>>(t->P, t->Gr, t->Mo, t->Vo, lr, (float)b1, (float)b2,
+                                                                   1e-8f, c1, c2, t->W, t->off_h, t->wb, t->wbt);
+    adam_rest_kernel<<<grid_for(t->off_h + (long long)t->L * t->W + t->W + 1), 256>>>(
+        t->P, t->Gr, t->Mo, t->Vo, lr, (float)b1, (float)b2, 1e-8f, c1, c2, t->W, t->L, t->off_h, t->off_out);
     TCK(cudaGetLastError());
     return SVM_OK;
 }
