@@ -530,14 +530,22 @@ __global__ void __launch_bounds__(256) reduce_long_kernel(const float* part, int
         __syncthreads();
         if (threadIdx.x < TJ) {
             const int lim = min(TP, P - p0);
-#pragma unroll 8
-            for (int pp = 0; pp < lim; ++pp) s += tile[pp * TJ + threadIdx.x];
+            int pp = 0;
+            for (; pp + 16 <= lim; pp += 16) {       // 16 reads issued before their adds
+                float v[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) v[u] = tile[(pp + u) * TJ + threadIdx.x];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) s += v[u];
+            }
+            for (; pp < lim; ++pp) s += tile[pp * TJ + threadIdx.x];
         }
         __syncthreads();
     }
     if (threadIdx.x < TJ && j0 + threadIdx.x < n) dst[j0 + threadIdx.x] += s;
 }
-constexpr int kRedCols = 8;
+constexpr int kRedCols = 4;        // the output-layer gradient (2 048 partials of W + 1 sums)
+constexpr int kRedColsL1 = 8;      // the layer-1 gradient (256 partials of 16 W sums)
 
 // dst[j] += sum_{p < P} part[p * n + j], summed in the order p = 0, 1, ...;
 // the loads of 8 partials are issued before their adds (same order of the adds).
@@ -800,7 +808,7 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
                           s);
     }
     layer1_bwd_kernel<<<dim3(B / 256, W / 256), 128, 0, s>>>(a, t->G[0]);
-    reduce_long_kernel<kRedCols><<<W * 16 / kRedCols, 256, 0, s>>>(t->part, B / 256, (long long)W * 16, t->Gr + t->off_w1);
+    reduce_long_kernel<kRedColsL1><<<W * 16 / kRedColsL1, 256, 0, s>>>(t->part, B / 256, (long long)W * 16, t->Gr + t->off_w1);
     // the step ends when the side stream's sums are in the gradient too
     cudaEventRecord(t->ev_side, s2);
     cudaStreamWaitEvent(s, t->ev_side, 0);
