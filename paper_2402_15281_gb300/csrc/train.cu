@@ -681,6 +681,13 @@ struct svm_trainer {
     cudaStream_t side = nullptr;
     std::vector<cudaEvent_t> ev_w, ev_c, ev_s;   // per layer: partials ready, chains ready, side done
     cudaEvent_t ev_head = nullptr, ev_side = nullptr;
+    // an epoch replays one captured step (gradient reset, forward, backward) on
+    // the stream `main`, with the batch's sample offset patched into the three
+    // kernels that read samples (layer 1 forward, head, layer 1 backward)
+    cudaStream_t main = nullptr;
+    cudaGraph_t step_graph = nullptr;
+    cudaGraphExec_t step_exec = nullptr;
+    cudaGraphNode_t node_l1f = nullptr, node_head = nullptr, node_l1b = nullptr;
     unsigned int* err = nullptr;
     __nv_bfloat16* wb = nullptr; __nv_bfloat16* wbt = nullptr;
     std::vector<__nv_bfloat16*> H, D, G;             // per layer 0..L, [B][W]; D = act'(z)
@@ -878,6 +885,8 @@ svm_status svm_train_create(const svm_model_desc* desc, int device, int32_t batc
     }
     if ((st = talloc(t, &t->part, t->part_n * 4)) != SVM_OK) return fail_free(st);
     if (cudaStreamCreateWithFlags(&t->side, cudaStreamNonBlocking) != cudaSuccess) return fail_free(SVM_E_CUDA);
+    // blocking: it orders with the default stream the other trainer calls use
+    if (cudaStreamCreate(&t->main) != cudaSuccess) return fail_free(SVM_E_CUDA);
     t->ev_w.assign(L + 1, nullptr); t->ev_c.assign(L + 1, nullptr); t->ev_s.assign(L + 1, nullptr);
     for (int l = 0; l <= L; ++l)
         for (auto* v : {&t->ev_w, &t->ev_c, &t->ev_s})
@@ -938,6 +947,9 @@ svm_status svm_train_destroy(svm_trainer* t)
         if (t->ev_head) cudaEventDestroy(t->ev_head);
         if (t->ev_side) cudaEventDestroy(t->ev_side);
         if (t->side) cudaStreamDestroy(t->side);
+        if (t->step_exec) cudaGraphExecDestroy(t->step_exec);
+        if (t->step_graph) cudaGraphDestroy(t->step_graph);
+        if (t->main) cudaStreamDestroy(t->main);
     }
     delete t;
     return SVM_OK;
@@ -1121,18 +1133,90 @@ svm_status svm_train_gradient(svm_trainer* t, int64_t sample_begin, float* grad_
     return SVM_OK;
 }
 
+svm_status adam_on(svm_trainer* t, float lr, cudaStream_t s);
+
 svm_status svm_train_adam(svm_trainer* t, float lr)
 {
     if (!t || !(lr > 0)) return SVM_E_INVALID;
     DevGuard gd(t->device);
+    return adam_on(t, lr, 0);
+}
+
+svm_status adam_on(svm_trainer* t, float lr, cudaStream_t s)
+{
     t->step += 1;
     const double b1 = 0.9, b2 = 0.999;
     const float c1 = (float)(1.0 - std::pow(b1, (double)t->step)), c2 = (float)(1.0 - std::pow(b2, (double)t->step));
-    adam_hidden_kernel<<<dim3(t->W / 32, t->W / 32, t->L), 256>>>(t->P, t->Gr, t->Mo, t->Vo, lr, (float)b1, (float)b2,
-                                                                   1e-8f, c1, c2, t->W, t->off_h, t->wb, t->wbt);
-    adam_rest_kernel<<<grid_for(t->off_h + (long long)t->L * t->W + t->W + 1), 256>>>(
+    adam_hidden_kernel<<<dim3(t->W / 32, t->W / 32, t->L), 256, 0, s>>>(t->P, t->Gr, t->Mo, t->Vo, lr, (float)b1,
+                                                                         (float)b2, 1e-8f, c1, c2, t->W, t->off_h, t->wb,
+                                                                         t->wbt);
+    adam_rest_kernel<<<grid_for(t->off_h + (long long)t->L * t->W + t->W + 1), 256, 0, s>>>(
         t->P, t->Gr, t->Mo, t->Vo, lr, (float)b1, (float)b2, 1e-8f, c1, c2, t->W, t->L, t->off_h, t->off_out);
     TCK(cudaGetLastError());
+    return SVM_OK;
+}
+
+// Captures one training step (gradient reset and run_batch) on t->main as a
+// graph and finds the kernel nodes that take the batch's sample offset.
+svm_status capture_step(svm_trainer* t, long long base, long long stride)
+{
+    cudaGraph_t g = nullptr;
+    TCK(cudaStreamBeginCapture(t->main, cudaStreamCaptureModeThreadLocal));
+    cudaMemsetAsync(t->Gr, 0, t->np * 4, t->main);
+    const svm_status st = run_batch(t, base, stride, true, t->main);
+    const cudaError_t ce = cudaStreamEndCapture(t->main, &g);
+    if (st != SVM_OK || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return st != SVM_OK ? st : tfail(t, SVM_E_CUDA, "training step capture failed");
+    }
+    size_t n = 0;
+    TCK(cudaGraphGetNodes(g, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    TCK(cudaGraphGetNodes(g, nodes.data(), &n));
+    const void* f_l1f = t->act == 0 ? (const void*)layer1_fwd_kernel<0> : (const void*)layer1_fwd_kernel<1>;
+    const void* f_head = t->act == 0 ? (const void*)head_kernel<0> : (const void*)head_kernel<1>;
+    const void* f_l1b = (const void*)layer1_bwd_kernel;
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp{};
+        if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
+        if (kp.func == f_l1f) t->node_l1f = nd;
+        else if (kp.func == f_head) t->node_head = nd;
+        else if (kp.func == f_l1b) t->node_l1b = nd;
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (!t->node_l1f || !t->node_head || !t->node_l1b || cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        t->node_l1f = t->node_head = t->node_l1b = nullptr;
+        return tfail(t, SVM_E_CUDA, "training step graph setup failed");
+    }
+    t->step_graph = g;
+    t->step_exec = ex;
+    return SVM_OK;
+}
+
+// Replays the captured step for the batch at `base`.
+svm_status replay_step(svm_trainer* t, long long base, long long stride)
+{
+    StepArgs a = step_args(t, base, stride);
+    auto patch = [&](cudaGraphNode_t nd, void** args) {
+        cudaKernelNodeParams kp{};
+        if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) return false;
+        kp.kernelParams = args;
+        kp.extra = nullptr;
+        return cudaGraphExecKernelNodeSetParams(t->step_exec, nd, &kp) == cudaSuccess;
+    };
+    const int W = t->W, L = t->L;
+    (void)W;
+    __nv_bfloat16 *d0 = t->D[0], *h0 = t->H[0], *hl = t->H[L], *dl = t->D[L], *gl = t->G[L], *g0 = t->G[0];
+    int eval = 0;
+    void* a_l1f[] = {&a, &d0, &h0};
+    void* a_head[] = {&a, &hl, &dl, &gl, &eval};
+    void* a_l1b[] = {&a, &g0};
+    if (!patch(t->node_l1f, a_l1f) || !patch(t->node_head, a_head) || !patch(t->node_l1b, a_l1b))
+        return tfail(t, SVM_E_CUDA, "training step graph update failed");
+    TCK(cudaGraphLaunch(t->step_exec, t->main));
     return SVM_OK;
 }
 
@@ -1151,10 +1235,18 @@ svm_status svm_train_epoch(svm_trainer* t, int64_t sample_begin, int64_t sample_
     DevGuard gd(t->device);
     TCK(cudaMemset(t->loss_sum, 0, 4));
     for (long long i = 0; i < nb; ++i) {
-        TCK(cudaMemsetAsync(t->Gr, 0, t->np * 4, 0));
-        svm_status st = run_batch(t, sample_begin + perm[i], nb, true, 0);
+        const long long base = sample_begin + perm[i];
+        svm_status st = SVM_OK;
+        if (i == 0 || !t->step_exec) {
+            // eager (the first batch also makes every one-time kernel setting)
+            TCK(cudaMemsetAsync(t->Gr, 0, t->np * 4, t->main));
+            st = run_batch(t, base, nb, true, t->main);
+            if (st == SVM_OK && i == 0 && !t->step_exec) st = capture_step(t, base, nb);
+        } else {
+            st = replay_step(t, base, nb);
+        }
         if (st != SVM_OK) return st;
-        st = svm_train_adam(t, lr);
+        st = adam_on(t, lr, t->main);
         if (st != SVM_OK) return st;
     }
     TCK(cudaGetLastError());
