@@ -15,23 +15,35 @@
 
 namespace svm {
 
-__global__ void __launch_bounds__(128) prologue_kernel(CallArgs A, RobotParams R, DevWeights Wt)
+constexpr int kProThreads = 256;   // samples per round of the FK chains
+
+__global__ void __launch_bounds__(kProThreads) prologue_kernel(CallArgs A, RobotParams R, DevWeights Wt)
 {
     const int m = blockIdx.x;
     const double* q0 = A.q0 + m * kDof;
     const double* q1 = A.q1 + m * kDof;
     const int N = A.N;
+    // sin and cos of every joint angle of the round's samples, computed by all
+    // threads in parallel before the per-sample chains use them
+    __shared__ double sc[kProThreads][kDof][2];
 
-    // (a) one thread per sample
-    for (int k = threadIdx.x; k <= N; k += blockDim.x) {
+    // (a) one thread per sample, kProThreads samples per round
+    for (int k0 = 0; k0 <= N; k0 += kProThreads) {
+        const int nk = min(kProThreads, N + 1 - k0);
+        for (int idx = threadIdx.x; idx < nk * kDof; idx += blockDim.x) {
+            const int kk = idx / kDof, j = idx - kk * kDof, k = k0 + kk;
+            const double qk = ((double)(N - k) * q0[j] + (double)k * q1[j]) / (double)N;
+            sincos(qk + R.th0[j], &sc[kk][j][0], &sc[kk][j][1]);
+        }
+        __syncthreads();
+        const int k = k0 + threadIdx.x;
+        if (threadIdx.x < nk) {
         double Rm[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
         double p[3] = {0, 0, 0};
         double o[kDof + 1][3];
         o[0][0] = o[0][1] = o[0][2] = 0.0;
         for (int j = 0; j < kDof; ++j) {
-            const double qk = ((double)(N - k) * q0[j] + (double)k * q1[j]) / (double)N;
-            double st, ct;
-            sincos(qk + R.th0[j], &st, &ct);
+            const double st = sc[threadIdx.x][j][0], ct = sc[threadIdx.x][j][1];
             const double ca = R.ca[j], sa = R.sa[j];
             // link transform rotation columns and translation (standard DH)
             const double c0[3] = {ct, st, 0.0};
@@ -69,6 +81,8 @@ __global__ void __launch_bounds__(128) prologue_kernel(CallArgs A, RobotParams R
                                   ee > 0.0 ? (float)(1.0 / ee) : 0.0f);
             out[j] = c;
         }
+        }
+        __syncthreads();
     }
 
     // (b) c_m = W1q [q0; q1] + b1, q cast to FP32 once.  Block architecture:
@@ -119,7 +133,7 @@ __global__ void __launch_bounds__(128) prologue_kernel(CallArgs A, RobotParams R
 
 void launch_prologue_fk(const CallArgs& a, const RobotParams& rp, const DevWeights& w, cudaStream_t s)
 {
-    if (a.M > 0) prologue_kernel<<<a.M, 128, 0, s>>>(a, rp, w);
+    if (a.M > 0) prologue_kernel<<<a.M, kProThreads, 0, s>>>(a, rp, w);
 }
 
 }  // namespace svm
