@@ -12,7 +12,8 @@ struct TcModel {
     int act = 0;                        // SVM_RELU or SVM_SILU
     int arch = 0;                       // SVM_ARCH_MLP or SVM_ARCH_BLOCKS
     alignas(64) unsigned char wmap[128];  // CUtensorMap of the hidden weights
-    alignas(64) unsigned char w1map[128]; // CUtensorMap of the padded layer-1 x-weights
+    alignas(64) unsigned char w1map[128]; // CUtensorMap of the padded x-weights (the plain network's
+                                          // layer 1; the blocks' jump inputs)
 };
 
 int tc_tile_rows();                                    // pairs per tile
@@ -22,7 +23,8 @@ void tc_release(TcModel& t);
 int tc_launch(TcModel& t, const CallArgs& a, const DevWeights& w, int n_tiles, void* ws, int n_sms,
               cudaStream_t s);
 // The block architecture (width 512, BF16, ReLU) on the tensor cores: wh is the
-// blocks' h-weights, [n_hidden * 512][512] bfloat16 (outputs x inputs) on the device.
+// blocks' h-weights, [n_hidden * 512][512] bfloat16 (outputs x inputs), followed
+// by their padded jump x-weights, [n_hidden * 512][16] bfloat16, on the device.
 int tc_block_prepare(TcModel& t, const svm_model_desc& d, const void* wh);
 int tc_block_launch(const TcModel& t, const CallArgs& a, const DevWeights& w, int n_tiles, int grid, cudaStream_t s);
 

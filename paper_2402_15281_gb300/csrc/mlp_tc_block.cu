@@ -10,26 +10,35 @@
 //   f = w_f [h_L; u] + b_f                              final layer
 // BatchNorm at inference is folded into a per-channel scale s_l and shift t_l
 // at load.  Every layer's q-part and bias is a per-motion constant c_{l,m}
-// (the prologue), every x-part (K = 3) runs on the CUDA cores in the epilogue,
-// and the h-parts are 128 x 512 x 512 tcgen05 GEMMs (two N = 256 halves).
+// (the prologue), the h-parts are 128 x 512 x 512 tcgen05 GEMMs (two N = 256
+// halves), and the jump x-part of blocks 2..L (K = 3) is one more K = 16 MMA
+// per half on (x_hi, y_hi, z_hi, x_lo, y_lo, z_lo, 0, ...), x = x_hi + x_lo in
+// two bfloat16 parts (x to about 2^-17 relative), against the block's
+// bfloat16 x-weights repeated twice.  The initial layer's x-part runs on the
+// CUDA cores.
 //
 // Persistent kernel, one CTA per SM, 18 warps:
-//   warp 0       TMA producer: weight slices of 64 K x 256 output rows (32 KB,
-//                128B swizzle, K-major B operand) into a 3-stage ring;
+//   warp 0       producer: weight slices of 64 K x 256 output rows (32 KB,
+//                128B swizzle, K-major B operand) by TMA into a 3-stage ring;
+//                for blocks 2..L, ahead of each half's slices, an x entry: the
+//                half's x-weights (256 rows x 16 K, 32B swizzle) by TMA and the
+//                tile's (x_hi, .., z_lo) rows, written by the warp's 32 lanes
+//                into the same stage (the A operand, 32B swizzle);
 //   warp 1       allocates the 512 TMEM columns and issues tcgen05.mma (one
-//                elected lane, warp-uniform loop): per block two N = 256 halves
-//                x 8 K-slices of 4 MMAs (K = 16);
-//   warps 2-17   epilogue: warp w reads TMEM lane quarter w % 4 and owns 128
-//                output columns, 128 * ((w - 2) / 4) onwards.
+//                elected lane, warp-uniform loop): per block and N = 256 half
+//                the x entry's MMA, then 8 K-slices of 4 MMAs (K = 16);
+//   warps 2-17   epilogue: warp w reads TMEM lane quarter w % 4 and owns 64
+//                columns of each column half, 64 * ((w - 2) / 4) onwards.
 // One 128-pair tile is in flight per CTA: its 512-wide FP32 accumulator fills
 // the TMEM, and the layer's input -- a 128 x 512 bfloat16 tile in shared
 // memory (K-major, 128B swizzle), which is also its skip term -- is updated in
-// place by the epilogue.  The epilogue works in two column halves: a block
-// issues [output half 0 x input half 0], [half 0 x input half 1], [half 1 x
-// input half 0], then commits -- output half 0 is final and input half 0 has
-// been read by both halves, so the epilogue of columns 0-255 runs while the
-// last quarter [half 1 x input half 1] computes; the next block's first
-// quarter needs only that half of its input.
+// place by the epilogue.  The epilogue works in two column halves, each taken
+// by all 16 warps: a block issues [output half 0 x input half 0], [half 0 x
+// input half 1], [half 1 x input half 0], then commits -- output half 0 is
+// final and input half 0 has been read by both halves, so the epilogue of
+// columns 0-255 runs while the last quarter [half 1 x input half 1] computes;
+// the next block's first quarter needs only that half of its input, and its
+// second quarter the other half.
 // The epilogue reads the accumulator in the 16x256b fragment shape (thread t:
 // two adjacent columns of two rows per 8-column group), reads the skip term
 // with ldmatrix and writes the new activation with stmatrix.  The final layer
@@ -61,6 +70,8 @@ constexpr int BK = 64;                       // K elements per weight slice (128
 constexpr int KSL = WB / BK;                 // 8 slices per half and block
 constexpr int STAGES = 3;
 constexpr int STAGE_BYTES = NH * 128;        // 32 KB
+constexpr int XW_BYTES = NH * 32;            // x entry: the half's x-weights, 256 rows x 32 bytes
+constexpr int XT_OFF = XW_BYTES;             // x entry: the tile's x rows, 128 x 32 bytes, after them
 constexpr int KBLOCK_BYTES = TM * 128;       // one 128-byte K-block of the activation tile
 constexpr int ACT_BYTES = TM * WB * 2;       // 128 KB
 constexpr int NUM_EPI_WARPS = 16;
@@ -126,6 +137,24 @@ __device__ __forceinline__ float4 ld_stream_f4(const float4* p)
     return v;
 }
 
+// Shared-memory matrix descriptor of a K-major operand with 32-byte rows (K =
+// 16 bfloat16) in the 32B swizzle: 8-row groups 256 bytes apart (SBO).
+__device__ __forceinline__ uint64_t sdesc32(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                 // LBO (unused: one swizzle atom spans the MMA's K)
+    d |= (uint64_t)(256 >> 4) << 32;        // SBO
+    d |= (uint64_t)1 << 46;                 // version
+    d |= (uint64_t)6 << 61;                 // SWIZZLE_32B
+    return d;
+}
+
+// Byte offset of 16-byte chunk c (0, 1) of row r in a tile of 32-byte rows,
+// 32B swizzle (the layout TMA writes and the descriptor above reads): the
+// chunk index flips with bit 2 of the row.
+__device__ __forceinline__ uint32_t swz32(int r, int c) { return (uint32_t)(r * 32 + ((c ^ ((r >> 2) & 1)) << 4)); }
+
 // Shared-memory address of row `row`, 16-byte chunk of column c8 * 8, of the
 // activation tile (K-major, 128B swizzle: the layout the MMA descriptor reads).
 __device__ __forceinline__ uint32_t act_addr(uint32_t base, int row, int c8)
@@ -144,10 +173,9 @@ __device__ __forceinline__ void add_xpart(const float* w, const float3 (&x4)[4],
         z[k] = f2_fma(wz, f2(x4[k].z, x4[k].z), f2_fma(wy, f2(x4[k].y, x4[k].y), f2_fma(wx, f2(x4[k].x, x4[k].x), z[k])));
 }
 
-template <bool HAS_WX, bool LAST>
+template <bool LAST>
 __device__ __forceinline__ void block_chunk(uint32_t abase, uint32_t t_addr, int q, int lane, int c0, const float* cl,
-                                            const float* crec, const float* wf, const float3 (&x4)[4],
-                                            uint64_t (&acc4)[4])
+                                            const float* crec, const float* wf, uint64_t (&acc4)[4])
 {
     float v[32];
     tmem_ld_frag32(t_addr, v);
@@ -160,25 +188,10 @@ __device__ __forceinline__ void block_chunk(uint32_t abase, uint32_t t_addr, int
         uint32_t hp[4];
         ldmatrix_x4(act_addr(abase, q * 32 + 16 * (j >> 1) + 8 * (j & 1) + i8, (c0 + 8 * g) >> 3), hp[0], hp[1],
                     hp[2], hp[3]);
-        // the column pair's record: (s, s'), (t, t'), wx of c, wx of c + 1
-        const float4* rec = reinterpret_cast<const float4*>(crec + 6 * c);
+        // the column pair's record (s, s', t, t') and its per-motion constants
+        const float4 st = __ldg(reinterpret_cast<const float4*>(crec + 2 * c));
         const float2 b = ldg2(cl + c);
-        const float4 st = __ldg(rec);
-        uint64_t z[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int vi = 16 * (k >> 1) + 4 * g + 2 * (k & 1);
-            z[k] = f2_add(f2(v[vi], v[vi + 1]), f2(b.x, b.y));
-        }
-        if constexpr (HAS_WX) {
-            const float4 wa = __ldg(rec + 1), wb = __ldg(rec + 2);   // (x, y, z, x'), (y', z', 0, 0)
-            const uint64_t wx = f2(wa.x, wa.w), wy = f2(wa.y, wb.x), wz = f2(wa.z, wb.y);
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                z[k] = f2_fma(wz, f2(x4[k].z, x4[k].z),
-                              f2_fma(wy, f2(x4[k].y, x4[k].y), f2_fma(wx, f2(x4[k].x, x4[k].x), z[k])));
-        }
-        const uint64_t s2 = f2(st.x, st.y), t2 = f2(st.z, st.w);
+        const uint64_t s2 = f2(st.x, st.y), t2 = f2(st.z, st.w), b2 = f2(b.x, b.y);
         uint64_t w2 = 0;
         if constexpr (LAST) {
             const float2 w = ldg2(wf + c);
@@ -186,7 +199,9 @@ __device__ __forceinline__ void block_chunk(uint32_t abase, uint32_t t_addr, int
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const uint64_t h = f2_add(f2_fma(f2_relu(z[k]), s2, t2), bf16x2_to_f2(hp[k]));
+            const int vi = 16 * (k >> 1) + 4 * g + 2 * (k & 1);
+            const uint64_t z = f2_add(f2(v[vi], v[vi + 1]), b2);
+            const uint64_t h = f2_add(f2_fma(f2_relu(z), s2, t2), bf16x2_to_f2(hp[k]));
             if constexpr (LAST) acc4[k] = f2_fma(w2, h, acc4[k]);
             else pk[4 * k + g] = bf16x2(h);
         }
@@ -199,14 +214,14 @@ __device__ __forceinline__ void block_chunk(uint32_t abase, uint32_t t_addr, int
     }
 }
 
-// h_0 = W_0x x + c_0 (no activation) for the warp's 32 rows and 128 columns
+// h_0 = W_0x x + c_0 (no activation) for the warp's 32 rows and 64 columns
 // from col0, rounded to bfloat16, as the first block's input.
 __device__ __forceinline__ void initial_layer(uint32_t abase, int q, int lane, int col0, const float* w0x,
                                               const float* c0m, const float3 (&x4)[4])
 {
     const int c2 = 2 * (lane & 3), i8 = lane & 7, j = lane >> 3;
 #pragma unroll 1
-    for (int o0 = col0; o0 < col0 + 128; o0 += 32) {
+    for (int o0 = col0; o0 < col0 + 64; o0 += 32) {
         uint32_t pk[16];
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
@@ -227,7 +242,8 @@ __device__ __forceinline__ void initial_layer(uint32_t abase, int q, int lane, i
 }
 
 __global__ void __launch_bounds__(NUM_THREADS, 1)
-    mlp_tc_block_kernel(const __grid_constant__ CUtensorMap wmap, CallArgs A, DevWeights Wt, int n_tiles)
+    mlp_tc_block_kernel(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ CUtensorMap xmap, CallArgs A,
+                        DevWeights Wt, int n_tiles)
 {
     extern __shared__ __align__(1024) unsigned char dsm_raw[];
     unsigned char* dsm =
@@ -240,7 +256,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     auto full_bar = [&](int s) { return bar0 + 8 * s; };
     auto empty_bar = [&](int s) { return bar0 + 8 * (STAGES + s); };
     // acc_bar(0): the first output half is final and the first input half consumed by both halves;
-    // acc_bar(1): the whole block.  epi_bar(e): column half e of the next input written (8 warps)
+    // acc_bar(1): the whole block.  epi_bar(e): column half e of the next input written (16 warps)
     auto acc_bar = [&](int e) { return bar0 + 8 * (2 * STAGES + e); };
     auto epi_bar = [&](int e) { return bar0 + 8 * (2 * STAGES + 2 + e); };
     const uint32_t drain_bar = bar0 + 8 * (2 * STAGES + 4);
@@ -259,7 +275,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
         for (int e = 0; e < 2; ++e) {
             mbar_init(acc_bar(e), 1);
-            mbar_init(epi_bar(e), NUM_EPI_WARPS / 2);
+            mbar_init(epi_bar(e), NUM_EPI_WARPS);
         }
         mbar_init(drain_bar, 1);
         *abort_flag = 0;
@@ -277,25 +293,72 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const uint32_t tmem_base = *tmem_slot;
 
     if (warp == 0) {
-        // ------------------------------------------------ TMA producer
+        // ------------------------------------------------ producer (whole warp; lane 0 issues the copies)
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&wmap)) : "memory");
-            int stage = 0;
-            uint32_t phase = 0, armed = 0, armed_par = 0;
-            bool ok = true;
-            for (int i = 0; i < n_mine && ok; ++i)
-                for (int l = 1; l <= L && ok; ++l)
-                    for (int h = 0; h < 2 && ok; ++h)
-                        for (int kk = 0; kk < KSL; ++kk) {
-                            if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, A.dev_err)) { ok = false; break; }
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&xmap)) : "memory");
+        }
+        int stage = 0;
+        uint32_t phase = 0, armed = 0, armed_par = 0;
+        bool ok = true;
+        auto advance = [&]() {
+            armed |= 1u << stage;
+            armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        };
+        for (int i = 0; i < n_mine && ok; ++i) {
+            // the tile's x rows lane + 32 j as bfloat16 pairs (x_hi, y_hi), (z_hi, x_lo), (y_lo, z_lo):
+            // the hi parts are the nearest bfloat16, the differences are exact in FP32
+            uint32_t xw[4][3];
+            {
+                const int t = (int)blockIdx.x + i * (int)gridDim.x;
+                const int m = find_segment(A.tile_off, A.M, t);
+                const long long p0 = A.pbeg[m] + (long long)(t - A.tile_off[m]) * TM, pe = A.pend[m];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const long long p = p0 + lane + 32 * j;
+                    const float4 x = p < pe ? ld_stream_f4(A.points + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float xl = x.x - __bfloat162float(__float2bfloat16_rn(x.x));
+                    const float yl = x.y - __bfloat162float(__float2bfloat16_rn(x.y));
+                    const float zl = x.z - __bfloat162float(__float2bfloat16_rn(x.z));
+                    xw[j][0] = pack_bf16<false>(x.x, x.y);
+                    xw[j][1] = pack_bf16<false>(x.z, xl);
+                    xw[j][2] = pack_bf16<false>(yl, zl);
+                }
+            }
+            for (int l = 1; l <= L && ok; ++l)
+                for (int h = 0; h < 2 && ok; ++h) {
+                    if (l >= 2) {
+                        // x entry: the x rows (generic stores, then the proxy fence), then the x-weights
+                        if (!mbar_wait_warp(empty_bar(stage), phase ^ 1u, abort_flag, A.dev_err)) { ok = false; break; }
+                        const uint32_t sb = w_base + stage * STAGE_BYTES;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int r = lane + 32 * j;
+                            st_shared_v4(sb + XT_OFF + swz32(r, 0), xw[j][0], xw[j][1], xw[j][2], 0u);
+                            st_shared_v4(sb + XT_OFF + swz32(r, 1), 0u, 0u, 0u, 0u);
+                        }
+                        fence_async_smem();
+                        __syncwarp();
+                        if (lane == 0) {
+                            mbar_arrive_tx(full_bar(stage), XW_BYTES);
+                            tma_load_2d(sb, &xmap, 0, (l - 1) * WB + h * NH, full_bar(stage));
+                        }
+                        advance();
+                    }
+                    for (int kk = 0; kk < KSL; ++kk) {
+                        if (!mbar_wait_warp(empty_bar(stage), phase ^ 1u, abort_flag, A.dev_err)) { ok = false; break; }
+                        if (lane == 0) {
                             mbar_arrive_tx(full_bar(stage), STAGE_BYTES);
                             tma_load_2d(w_base + stage * STAGE_BYTES, &wmap, kk * BK, (l - 1) * WB + h * NH,
                                         full_bar(stage));
-                            armed |= 1u << stage;
-                            armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
-                            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                         }
-            // wait (bounded) for every copy this thread started
+                        advance();
+                    }
+                }
+        }
+        // wait (bounded) for every copy this warp started
+        if (lane == 0)
             for (int s = 0; s < STAGES; ++s)
                 if (armed & (1u << s)) {
                     const uint32_t par = (armed_par >> s) & 1u;
@@ -303,18 +366,27 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     while (!mbar_try(full_bar(s), par) && globaltimer() - t0 < kTimeoutNs) {
                     }
                 }
-        }
+        __syncwarp();
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
-        // Per block: [N-half 0, K 0-3] (needs input half 0), [N-half 0, K 4-7] (needs input half 1),
-        // [N-half 1, K 0-3], commit acc_bar(0), [N-half 1, K 4-7], commit acc_bar(1).  The epilogue
-        // of output half 0 then overlaps the last quarter of the block's MMAs, and the next block's
-        // first quarter waits only for it.
+        // Per block: [N-half 0: x entry, K 0-3] (needs input half 0), [N-half 0, K 4-7] (needs input
+        // half 1), [N-half 1: x entry, K 0-3], commit acc_bar(0), [N-half 1, K 4-7], commit acc_bar(1);
+        // block 1 has no x entries.  The epilogue of output half 0 then overlaps the last quarter of the
+        // block's MMAs, and the next block's first quarter waits only for it.
         const uint64_t a_desc0 = sdesc(abase), b_desc0 = sdesc(w_base);
         int stage = 0;
         uint32_t phase = 0, ep0 = 0, ep1 = 0;
         bool ok = true;
-        auto quarter_block = [&](int h, int k0) {
+        // the x entry of half h: D = x rows x x-weights (overwrites the half's accumulator)
+        auto x_entry = [&](int h) {
+            if (!mbar_wait_warp(full_bar(stage), phase, abort_flag, A.dev_err)) { ok = false; return; }
+            tc_fence_after();
+            const uint32_t sb = w_base + stage * STAGE_BYTES;
+            mma_f16_warp(tmem_base + (uint32_t)(h * NH), sdesc32(sb + XT_OFF), sdesc32(sb), IDESC, 0u);
+            mma_commit_warp(empty_bar(stage));
+            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        };
+        auto quarter_block = [&](int h, int k0, bool accumulate) {
             const uint32_t d_tmem = tmem_base + (uint32_t)(h * NH);
             for (int kk = k0; kk < k0 + KSL / 2; ++kk) {
                 if (!mbar_wait_warp(full_bar(stage), phase, abort_flag, A.dev_err)) { ok = false; return; }
@@ -323,25 +395,28 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const uint64_t bd = b_desc0 + (uint64_t)(stage * (STAGE_BYTES >> 4));
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
-                    mma_f16_warp(d_tmem, ad + 2 * k, bd + 2 * k, IDESC, (kk | k) != 0 ? 1u : 0u);
+                    mma_f16_warp(d_tmem, ad + 2 * k, bd + 2 * k, IDESC, (accumulate || (kk | k) != 0) ? 1u : 0u);
                 mma_commit_warp(empty_bar(stage));
                 if (++stage == STAGES) { stage = 0; phase ^= 1u; }
             }
         };
         for (int i = 0; i < n_mine && ok; ++i)
             for (int l = 1; l <= L && ok; ++l) {
+                const bool xe = l >= 2;
                 if (!mbar_wait_warp(epi_bar(0), ep0, abort_flag, A.dev_err)) { ok = false; break; }
                 ep0 ^= 1u;
                 tc_fence_after();
-                quarter_block(0, 0);
+                if (xe) x_entry(0);
+                if (ok) quarter_block(0, 0, xe);
                 if (!ok) break;
                 if (!mbar_wait_warp(epi_bar(1), ep1, abort_flag, A.dev_err)) { ok = false; break; }
                 ep1 ^= 1u;
                 tc_fence_after();
-                quarter_block(0, KSL / 2);
-                if (ok) quarter_block(1, 0);
+                quarter_block(0, KSL / 2, true);
+                if (ok && xe) x_entry(1);
+                if (ok) quarter_block(1, 0, xe);
                 if (ok) mma_commit_warp(acc_bar(0));
-                if (ok) quarter_block(1, KSL / 2);
+                if (ok) quarter_block(1, KSL / 2, true);
                 if (ok) mma_commit_warp(acc_bar(1));
             }
         // every MMA issued by this warp has completed before TMEM is freed
@@ -353,11 +428,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     } else {
         // ------------------------------------------------ epilogue warps
         const int q = warp & 3;                      // TMEM lane quarter: rows 32 q ..
-        const int cq = (warp - 2) >> 2;              // column quarter: columns 128 cq ..
-        const int col0 = cq * 128;
-        const int eh = cq >> 1;                      // column half: 0 for columns 0-255, 1 for 256-511
+        const int cq = (warp - 2) >> 2;              // columns 64 cq .. of each column half
         const int r = q * 32 + lane;                 // this lane's row (gate, reduction)
-        const uint32_t t_row = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)col0;
+        const uint32_t t_row = tmem_base + ((uint32_t)(q * 32) << 16);
         const int cbs = A.cb_stride;
         uint32_t acc_phase = 0;
         bool ok = true;
@@ -377,12 +450,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 x4[k] = make_float3(v.x, v.y, v.z);
             }
         };
-        auto stage_h0 = [&](int m, const float3 (&x4)[4]) {
-            initial_layer(abase, q, lane, col0, Wt.w1x, A.cbias + (long long)m * cbs, x4);
+        // h_0 of column half e (the warp's 64 columns of it), then the half's arrival
+        auto stage_h0 = [&](int e, int m, const float3 (&x4)[4]) {
+            initial_layer(abase, q, lane, e * NH + 64 * cq, Wt.w1x, A.cbias + (long long)m * cbs, x4);
             fence_async_smem();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(epi_bar(eh));
+            if (lane == 0) mbar_arrive(epi_bar(e));
         };
         int m = 0;
         long long p0 = 0, pe = 0;
@@ -390,53 +464,52 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         if (n_mine > 0) {
             tile_of(0, m, p0, pe);
             load_x4(p0, pe, x4);
-            if (!(A.test_stall && blockIdx.x == 0)) stage_h0(m, x4);
+            if (!(A.test_stall && blockIdx.x == 0)) {
+                stage_h0(0, m, x4);
+                stage_h0(1, m, x4);
+            }
         }
         for (int i = 0; i < n_mine && ok; ++i) {
             const bool has_next = i + 1 < n_mine;
             const float* cm = A.cbias + (long long)m * cbs;
+            int nm = 0;
+            long long np0 = 0, npe = 0;
+            float3 xn[4];
             for (int l = 1; l <= L && ok; ++l) {
                 const float* cl = cm + (long long)l * WB;
-                const float* crec = Wt.blk_pk + (long long)(l - 1) * WB * 6;   // [W/2][12] of block l
-                int nm = 0;
-                long long np0 = 0, npe = 0;
-                float3 xn[4];
+                const float* crec = Wt.blk_pk + (long long)(l - 1) * WB * 2;   // [W/2][4] of block l
                 if (l == L && has_next) {
                     tile_of(i + 1, nm, np0, npe);
                     load_x4(np0, npe, xn);
                 }
-                if (!mbar_wait(acc_bar(eh), acc_phase, abort_flag, A.dev_err)) { ok = false; break; }
-                acc_phase ^= 1u;
-                tc_fence_after();
                 uint64_t acc4[4] = {0ull, 0ull, 0ull, 0ull};
-                if (l < L) {
+                // column half e: its accumulator is final (and for e = 0 input half 0 read by both MMA
+                // halves); the next block's input half e, or on the last block the final layer's partial
+                // sums and then the next tile's h_0 half e (every read of this tile's half is done)
+                for (int e = 0; e < 2 && ok; ++e) {
+                    if (!mbar_wait(acc_bar(e), acc_phase, abort_flag, A.dev_err)) { ok = false; break; }
+                    tc_fence_after();
+                    const int c0 = e * NH + 64 * cq;
+                    if (l < L) {
 #pragma unroll 1
-                    for (int o = 0; o < 4; ++o) {
-                        if (l == 1)
-                            block_chunk<false, false>(abase, t_row + (uint32_t)(32 * o), q, lane, col0 + 32 * o, cl, crec,
-                                                      Wt.wout, x4, acc4);
-                        else
-                            block_chunk<true, false>(abase, t_row + (uint32_t)(32 * o), q, lane, col0 + 32 * o, cl, crec,
-                                                      Wt.wout, x4, acc4);
+                        for (int o = 0; o < 2; ++o)
+                            block_chunk<false>(abase, t_row + (uint32_t)(c0 + 32 * o), q, lane, c0 + 32 * o, cl, crec,
+                                               Wt.wout, acc4);
+                        fence_async_smem();
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(epi_bar(e));
+                    } else {
+#pragma unroll 1
+                        for (int o = 0; o < 2; ++o)
+                            block_chunk<true>(abase, t_row + (uint32_t)(c0 + 32 * o), q, lane, c0 + 32 * o, cl, crec,
+                                              Wt.wout, acc4);
+                        if (has_next) stage_h0(e, nm, xn);
                     }
-                    fence_async_smem();
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(epi_bar(eh));
-                    continue;
                 }
-                // ---- last block and the final layer
-#pragma unroll 1
-                for (int o = 0; o < 4; ++o) {
-                    if (l == 1)
-                        block_chunk<false, true>(abase, t_row + (uint32_t)(32 * o), q, lane, col0 + 32 * o, cl, crec,
-                                                 Wt.wout, x4, acc4);
-                    else
-                        block_chunk<true, true>(abase, t_row + (uint32_t)(32 * o), q, lane, col0 + 32 * o, cl, crec,
-                                                 Wt.wout, x4, acc4);
-                }
-                // every read of this tile's TMEM and activation tile is done: the next tile's h_0
-                if (has_next) stage_h0(nm, xn);
+                acc_phase ^= 1u;
+                if (l < L || !ok) continue;
+                // ---- the final layer
                 float sk[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -538,6 +611,15 @@ int tc_block_prepare(TcModel& t, const svm_model_desc& d, const void* wh)
             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return -2;
+    // their padded jump x-weights after them, [L * 512 rows][16] bfloat16: boxes of 256 rows x 32 bytes
+    const void* wx = static_cast<const char*>(wh) + (size_t)d.n_hidden * WB * WB * 2;
+    const cuuint64_t xdims[2] = {16, (cuuint64_t)WB * d.n_hidden};
+    const cuuint64_t xstrides[1] = {32};
+    const cuuint32_t xbox[2] = {16, (cuuint32_t)NH};
+    if (enc(reinterpret_cast<CUtensorMap*>(t.w1map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(wx), xdims,
+            xstrides, xbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return -2;
     t.ready = true;
     return 0;
 }
@@ -554,7 +636,8 @@ int tc_block_launch(const TcModel& t, const CallArgs& a, const DevWeights& w, in
             cudaFuncSetAttribute(mlp_tc_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_DYN);
         });
     if (grid > n_tiles) grid = n_tiles;
-    mlp_tc_block_kernel<<<grid, NUM_THREADS, SMEM_DYN, s>>>(*reinterpret_cast<const CUtensorMap*>(t.wmap), a, w,
+    mlp_tc_block_kernel<<<grid, NUM_THREADS, SMEM_DYN, s>>>(*reinterpret_cast<const CUtensorMap*>(t.wmap),
+                                                             *reinterpret_cast<const CUtensorMap*>(t.w1map), a, w,
                                                              n_tiles);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

@@ -202,36 +202,40 @@ svm_status load_block_weights(svm_model* m, const unsigned char* p, size_t bytes
     for (int c = 0; c < 3; ++c) out_wx[c] = fin[W + c];
     for (int c = 0; c < 12; ++c) out_wq[c] = fin[W + 3 + c];
     const float bout = fin[J];
-    // BF16: the blocks' h-weights for the tensor cores, [L][W outputs][W inputs] bfloat16 (K-major B operand)
+    // BF16: the blocks' weights for the tensor cores (K-major B operands, bfloat16): the h-weights,
+    // [L][W outputs][W inputs], then the jump x-weights padded to K = 16, [L][W outputs][16] with row
+    // (w_x, w_y, w_z, w_x, w_y, w_z, 0, ...) applied to (x_hi, y_hi, z_hi, x_lo, y_lo, z_lo, 0, ...)
+    // (block 1, which has no jump input, is zero).  The weights are BF16-rounded above, so the upper
+    // half of each FP32 word is the exact value.
     std::vector<uint16_t> wh;
     if (bf16) {
-        wh.resize((size_t)L * W * W);
+        auto hi16 = [](float v) {
+            uint32_t u;
+            std::memcpy(&u, &v, 4);
+            return (uint16_t)(u >> 16);
+        };
+        wh.assign((size_t)L * W * W + (size_t)L * W * 16, 0);
         for (long long l = 0; l < L; ++l) {
             const long long in = l == 0 ? W : J;
-            for (long long o = 0; o < W; ++o)
-                for (long long i = 0; i < W; ++i) {
-                    uint32_t u;
-                    std::memcpy(&u, &blk[l][o * in + i], 4);
-                    wh[((size_t)l * W + o) * W + i] = (uint16_t)(u >> 16);
-                }
+            for (long long o = 0; o < W; ++o) {
+                for (long long i = 0; i < W; ++i) wh[((size_t)l * W + o) * W + i] = hi16(blk[l][o * in + i]);
+                uint16_t* xr = &wh[(size_t)L * W * W + ((size_t)l * W + o) * 16];
+                for (int c = 0; c < 3; ++c) xr[c] = xr[3 + c] = hi16(blk_wx[((size_t)l * W + o) * 3 + c]);
+            }
         }
     }
 
     // the block kernel's per-column-pair record (see DevWeights::blk_pk)
     std::vector<float> blk_pk;
     if (d.arch == SVM_ARCH_BLOCKS && W % 2 == 0) {
-        blk_pk.assign((size_t)L * (W / 2) * 12, 0.0f);
+        blk_pk.assign((size_t)L * (W / 2) * 4, 0.0f);
         for (int l = 0; l < L; ++l)
             for (int c = 0; c < W; c += 2) {
-                float* r = &blk_pk[((size_t)l * (W / 2) + c / 2) * 12];
+                float* r = &blk_pk[((size_t)l * (W / 2) + c / 2) * 4];
                 r[0] = blk_s[l * W + c];
                 r[1] = blk_s[l * W + c + 1];
                 r[2] = blk_t[l * W + c];
                 r[3] = blk_t[l * W + c + 1];
-                for (int k = 0; k < 3; ++k) {
-                    r[4 + k] = blk_wx[((size_t)l * W + c) * 3 + k];
-                    r[7 + k] = blk_wx[((size_t)l * W + c + 1) * 3 + k];
-                }
             }
     }
     DeviceGuard g(m->device);

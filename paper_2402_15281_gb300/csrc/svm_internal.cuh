@@ -155,9 +155,8 @@ struct DevWeights {
     const float* blk_b;   // [L+1][W]    biases: initial layer, then blocks
     const float* blk_s;   // [L][W]      folded BatchNorm scale gamma / sqrt(var + eps)
     const float* blk_t;   // [L][W]      folded BatchNorm shift beta - mean * scale
-    const float* blk_pk;  // [L][W/2][12] per column pair (c, c+1) of block l: s_c, s_c+1, t_c, t_c+1,
-                          // wx_c (x, y, z), wx_c+1 (x, y, z), 0, 0 -- one 48-byte record, three
-                          // 16-byte loads in the tensor-core block kernel's epilogue
+    const float* blk_pk;  // [L][W/2][4] per column pair (c, c+1) of block l: s_c, s_c+1, t_c, t_c+1 --
+                          // one 16-byte load in the tensor-core block kernel's epilogue
     const float* out_wx;  // [3]         final-layer weights of x, y, z
     const float* out_wq;  // [12]        final-layer weights of q0, q1
 };
