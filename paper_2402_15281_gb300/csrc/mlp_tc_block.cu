@@ -173,30 +173,46 @@ __device__ __forceinline__ void add_xpart(const float* w, const float3 (&x4)[4],
         z[k] = f2_fma(wz, f2(x4[k].z, x4[k].z), f2_fma(wy, f2(x4[k].y, x4[k].y), f2_fma(wx, f2(x4[k].x, x4[k].x), z[k])));
 }
 
+// The per-column constants of a 32-column chunk from c0, one load per lane
+// (taken before the wait for the accumulator, so that they arrive while the
+// MMAs run): lanes 0-15 hold column pair c0 + 2 (lane % 16)'s record (s, s',
+// t, t') in ka and, for the final layer, its output weights in kb; lanes 16-31
+// hold its per-motion constants (c, c') in ka.xy.
+__device__ __forceinline__ void chunk_consts(int lane, int c0, const float* cl, const float* crec, const float* wf,
+                                             bool last, float4& ka, float2& kb)
+{
+    const int c = c0 + 2 * (lane & 15);
+    kb = make_float2(0.f, 0.f);
+    if (lane < 16) {
+        ka = __ldg(reinterpret_cast<const float4*>(crec + 2 * c));
+        if (last) kb = ldg2(wf + c);
+    } else {
+        const float2 b = ldg2(cl + c);
+        ka = make_float4(b.x, b.y, 0.f, 0.f);
+    }
+}
+
 template <bool LAST>
-__device__ __forceinline__ void block_chunk(uint32_t abase, uint32_t t_addr, int q, int lane, int c0, const float* cl,
-                                            const float* crec, const float* wf, uint64_t (&acc4)[4])
+__device__ __forceinline__ void block_chunk(uint32_t abase, uint32_t t_addr, int q, int lane, int c0, float4 ka,
+                                            float2 kb, uint64_t (&acc4)[4])
 {
     float v[32];
     tmem_ld_frag32(t_addr, v);
-    const int c2 = 2 * (lane & 3), i8 = lane & 7, j = lane >> 3;
+    const int i8 = lane & 7, j = lane >> 3;
     uint32_t pk[16];                                  // [row block k][group g]
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
-        const int c = c0 + 8 * g + c2;                // even: columns c and c + 1
+        // this thread's columns c0 + 8 g + 2 (lane % 4) and the next: pair pi of the chunk
+        const int pi = 4 * g + (lane & 3);
         // the skip term: the block's input at the same rows and columns
         uint32_t hp[4];
         ldmatrix_x4(act_addr(abase, q * 32 + 16 * (j >> 1) + 8 * (j & 1) + i8, (c0 + 8 * g) >> 3), hp[0], hp[1],
                     hp[2], hp[3]);
-        // the column pair's record (s, s', t, t') and its per-motion constants
-        const float4 st = __ldg(reinterpret_cast<const float4*>(crec + 2 * c));
-        const float2 b = ldg2(cl + c);
-        const uint64_t s2 = f2(st.x, st.y), t2 = f2(st.z, st.w), b2 = f2(b.x, b.y);
+        const uint64_t s2 = f2(__shfl_sync(0xffffffffu, ka.x, pi), __shfl_sync(0xffffffffu, ka.y, pi));
+        const uint64_t t2 = f2(__shfl_sync(0xffffffffu, ka.z, pi), __shfl_sync(0xffffffffu, ka.w, pi));
+        const uint64_t b2 = f2(__shfl_sync(0xffffffffu, ka.x, 16 + pi), __shfl_sync(0xffffffffu, ka.y, 16 + pi));
         uint64_t w2 = 0;
-        if constexpr (LAST) {
-            const float2 w = ldg2(wf + c);
-            w2 = f2(w.x, w.y);
-        }
+        if constexpr (LAST) w2 = f2(__shfl_sync(0xffffffffu, kb.x, pi), __shfl_sync(0xffffffffu, kb.y, pi));
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int vi = 16 * (k >> 1) + 4 * g + 2 * (k & 1);
@@ -487,23 +503,23 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 // halves); the next block's input half e, or on the last block the final layer's partial
                 // sums and then the next tile's h_0 half e (every read of this tile's half is done)
                 for (int e = 0; e < 2 && ok; ++e) {
+                    const int c0 = e * NH + 64 * cq;
+                    float4 ka0, ka1;
+                    float2 kb0, kb1;
+                    chunk_consts(lane, c0, cl, crec, Wt.wout, l == L, ka0, kb0);
+                    chunk_consts(lane, c0 + 32, cl, crec, Wt.wout, l == L, ka1, kb1);
                     if (!mbar_wait(acc_bar(e), acc_phase, abort_flag, A.dev_err)) { ok = false; break; }
                     tc_fence_after();
-                    const int c0 = e * NH + 64 * cq;
                     if (l < L) {
-#pragma unroll 1
-                        for (int o = 0; o < 2; ++o)
-                            block_chunk<false>(abase, t_row + (uint32_t)(c0 + 32 * o), q, lane, c0 + 32 * o, cl, crec,
-                                               Wt.wout, acc4);
+                        block_chunk<false>(abase, t_row + (uint32_t)c0, q, lane, c0, ka0, kb0, acc4);
+                        block_chunk<false>(abase, t_row + (uint32_t)(c0 + 32), q, lane, c0 + 32, ka1, kb1, acc4);
                         fence_async_smem();
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(epi_bar(e));
                     } else {
-#pragma unroll 1
-                        for (int o = 0; o < 2; ++o)
-                            block_chunk<true>(abase, t_row + (uint32_t)(c0 + 32 * o), q, lane, c0 + 32 * o, cl, crec,
-                                              Wt.wout, acc4);
+                        block_chunk<true>(abase, t_row + (uint32_t)c0, q, lane, c0, ka0, kb0, acc4);
+                        block_chunk<true>(abase, t_row + (uint32_t)(c0 + 32), q, lane, c0 + 32, ka1, kb1, acc4);
                         if (has_next) stage_h0(e, nm, xn);
                     }
                 }
