@@ -24,7 +24,8 @@ int tc_launch(TcModel& t, const CallArgs& a, const DevWeights& w, int n_tiles, v
               cudaStream_t s);
 // The block architecture (width 512, BF16, ReLU) on the tensor cores: wh is the
 // blocks' h-weights, [n_hidden * 512][512] bfloat16 (outputs x inputs), followed
-// by their padded jump x-weights, [n_hidden * 512][16] bfloat16, on the device.
+// by the padded x-weights, [n_hidden * 512][16] bfloat16 (the initial layer's in
+// the place of block 1, then the blocks' jump x-weights), on the device.
 int tc_block_prepare(TcModel& t, const svm_model_desc& d, const void* wh);
 int tc_block_launch(const TcModel& t, const CallArgs& a, const DevWeights& w, int n_tiles, int grid, cudaStream_t s);
 

@@ -12,21 +12,21 @@
 // at load.  Every layer's q-part and bias is a per-motion constant c_{l,m}
 // (the prologue), the h-parts are 128 x 512 x 512 tcgen05 GEMMs (two N = 256
 // halves), and the jump x-part of blocks 2..L (K = 3) is one more K = 16 MMA
-// per half on (x_hi, y_hi, z_hi, x_lo, y_lo, z_lo, 0, ...), x = x_hi + x_lo in
-// two bfloat16 parts (x to about 2^-17 relative), against the block's
-// bfloat16 x-weights repeated twice.  The initial layer's x-part runs on the
-// CUDA cores.
+// per half on (x_hi, y_hi, z_hi, x_mid, .., z_lo, 0, ...), x = x_hi + x_mid +
+// x_lo in three bfloat16 parts (x to about 2^-24 relative), against the
+// block's bfloat16 x-weights repeated three times.  The initial layer is such an MMA too: a
+// layer 0 of x entries only, whose epilogue adds c_0 and rounds h_0.
 //
 // Persistent kernel, one CTA per SM, 18 warps:
 //   warp 0       producer: weight slices of 64 K x 256 output rows (32 KB,
 //                128B swizzle, K-major B operand) by TMA into a 3-stage ring;
-//                for blocks 2..L, ahead of each half's slices, an x entry: the
-//                half's x-weights (256 rows x 16 K, 32B swizzle) by TMA and the
-//                tile's (x_hi, .., z_lo) rows, written by the warp's 32 lanes
-//                into the same stage (the A operand, 32B swizzle);
+//                for layer 0 and blocks 2..L, ahead of each half's slices, an x
+//                entry: the half's x-weights (256 rows x 16 K, 32B swizzle) by
+//                TMA and the tile's (x_hi, .., z_lo) rows, written by the warp's
+//                32 lanes into the same stage (the A operand, 32B swizzle);
 //   warp 1       allocates the 512 TMEM columns and issues tcgen05.mma (one
-//                elected lane, warp-uniform loop): per block and N = 256 half
-//                the x entry's MMA, then 8 K-slices of 4 MMAs (K = 16);
+//                elected lane, warp-uniform loop): per layer and N = 256 half
+//                the x entry's MMA, then (blocks) 8 K-slices of 4 MMAs (K = 16);
 //   warps 2-17   epilogue: warp w reads TMEM lane quarter w % 4 and owns 64
 //                columns of each column half, 64 * ((w - 2) / 4) onwards.
 // One 128-pair tile is in flight per CTA: its 512-wide FP32 accumulator fills
@@ -162,17 +162,6 @@ __device__ __forceinline__ uint32_t act_addr(uint32_t base, int row, int c8)
     return base + (uint32_t)((c8 >> 3) * KBLOCK_BYTES + row * 128 + (((c8 & 7) ^ (row & 7)) << 4));
 }
 
-// Linear x-part of 2 columns for the thread's 4 fragment rows: w = the 6
-// weights (x, y, z of column c, then of c + 1), added to z[k].
-__device__ __forceinline__ void add_xpart(const float* w, const float3 (&x4)[4], uint64_t (&z)[4])
-{
-    const float2 w0 = ldg2(w), w1 = ldg2(w + 2), w2 = ldg2(w + 4);
-    const uint64_t wx = f2(w0.x, w1.y), wy = f2(w0.y, w2.x), wz = f2(w1.x, w2.y);
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-        z[k] = f2_fma(wz, f2(x4[k].z, x4[k].z), f2_fma(wy, f2(x4[k].y, x4[k].y), f2_fma(wx, f2(x4[k].x, x4[k].x), z[k])));
-}
-
 // The per-column constants of a 32-column chunk from c0, one load per lane
 // (taken before the wait for the accumulator, so that they arrive while the
 // MMAs run): lanes 0-15 hold column pair c0 + 2 (lane % 16)'s record (s, s',
@@ -230,31 +219,30 @@ __device__ __forceinline__ void block_chunk(uint32_t abase, uint32_t t_addr, int
     }
 }
 
-// h_0 = W_0x x + c_0 (no activation) for the warp's 32 rows and 64 columns
-// from col0, rounded to bfloat16, as the first block's input.
-__device__ __forceinline__ void initial_layer(uint32_t abase, int q, int lane, int col0, const float* w0x,
-                                              const float* c0m, const float3 (&x4)[4])
+// h_0 = W_0x x + c_0 (no activation) for the warp's 32 rows and the 32 columns
+// from c0: the accumulator holds W_0x x (the tile's layer-0 x entry); c_0 of
+// column pair i of the chunk is in lane base + i (kc = (c, c')).  Rounded to
+// bfloat16, it is the first block's input.
+__device__ __forceinline__ void h0_chunk(uint32_t abase, uint32_t t_addr, int q, int lane, int c0, float2 kc, int base)
 {
-    const int c2 = 2 * (lane & 3), i8 = lane & 7, j = lane >> 3;
-#pragma unroll 1
-    for (int o0 = col0; o0 < col0 + 64; o0 += 32) {
-        uint32_t pk[16];
+    float v[32];
+    tmem_ld_frag32(t_addr, v);
+    const int i8 = lane & 7, j = lane >> 3;
+    uint32_t pk[16];
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            const int c = o0 + 8 * g + c2;
-            const float2 b = ldg2(c0m + c);
-            uint64_t z[4];
+    for (int g = 0; g < 4; ++g) {
+        const int pi = base + 4 * g + (lane & 3);
+        const uint64_t b2 = f2(__shfl_sync(0xffffffffu, kc.x, pi), __shfl_sync(0xffffffffu, kc.y, pi));
 #pragma unroll
-            for (int k = 0; k < 4; ++k) z[k] = f2(b.x, b.y);
-            add_xpart(w0x + 3 * c, x4, z);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) pk[4 * k + g] = bf16x2(z[k]);
+        for (int k = 0; k < 4; ++k) {
+            const int vi = 16 * (k >> 1) + 4 * g + 2 * (k & 1);
+            pk[4 * k + g] = bf16x2(f2_add(f2(v[vi], v[vi + 1]), b2));
         }
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            stmatrix_x4(act_addr(abase, q * 32 + 16 * (k >> 1) + 8 * (k & 1) + i8, (o0 >> 3) + j), pk[4 * k + 0],
-                        pk[4 * k + 1], pk[4 * k + 2], pk[4 * k + 3]);
     }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        stmatrix_x4(act_addr(abase, q * 32 + 16 * (k >> 1) + 8 * (k & 1) + i8, (c0 >> 3) + j), pk[4 * k + 0],
+                    pk[4 * k + 1], pk[4 * k + 2], pk[4 * k + 3]);
 }
 
 __global__ void __launch_bounds__(NUM_THREADS, 1)
@@ -323,9 +311,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             if (++stage == STAGES) { stage = 0; phase ^= 1u; }
         };
         for (int i = 0; i < n_mine && ok; ++i) {
-            // the tile's x rows lane + 32 j as bfloat16 pairs (x_hi, y_hi), (z_hi, x_lo), (y_lo, z_lo):
-            // the hi parts are the nearest bfloat16, the differences are exact in FP32
-            uint32_t xw[4][3];
+            // the tile's x rows lane + 32 j in three bfloat16 parts, x = x_hi + x_mid + x_lo (each part
+            // the nearest bfloat16 of what the previous ones leave, the remainders exact in FP32; x to
+            // about 2^-24 relative), as pairs (x_hi, y_hi), (z_hi, x_mid), (y_mid, z_mid), (x_lo, y_lo),
+            // (z_lo, 0)
+            uint32_t xw[4][5];
             {
                 const int t = (int)blockIdx.x + i * (int)gridDim.x;
                 const int m = find_segment(A.tile_off, A.M, t);
@@ -334,35 +324,46 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 for (int j = 0; j < 4; ++j) {
                     const long long p = p0 + lane + 32 * j;
                     const float4 x = p < pe ? ld_stream_f4(A.points + p) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    const float xl = x.x - __bfloat162float(__float2bfloat16_rn(x.x));
-                    const float yl = x.y - __bfloat162float(__float2bfloat16_rn(x.y));
-                    const float zl = x.z - __bfloat162float(__float2bfloat16_rn(x.z));
-                    xw[j][0] = pack_bf16<false>(x.x, x.y);
-                    xw[j][1] = pack_bf16<false>(x.z, xl);
-                    xw[j][2] = pack_bf16<false>(yl, zl);
+                    float hi[3], mid[3], lo[3];
+                    const float xs[3] = {x.x, x.y, x.z};
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        hi[c] = __bfloat162float(__float2bfloat16_rn(xs[c]));
+                        const float r1 = xs[c] - hi[c];
+                        mid[c] = __bfloat162float(__float2bfloat16_rn(r1));
+                        lo[c] = r1 - mid[c];
+                    }
+                    xw[j][0] = pack_bf16<false>(hi[0], hi[1]);
+                    xw[j][1] = pack_bf16<false>(hi[2], mid[0]);
+                    xw[j][2] = pack_bf16<false>(mid[1], mid[2]);
+                    xw[j][3] = pack_bf16<false>(lo[0], lo[1]);
+                    xw[j][4] = pack_bf16<false>(lo[2], 0.0f);
                 }
             }
-            for (int l = 1; l <= L && ok; ++l)
+            // layer l = 0 is the initial layer: an x entry per half and nothing else; blocks 2..L
+            // have an x entry ahead of each half's slices; block 1 has none (its x-weight rows hold the
+            // initial layer's)
+            for (int l = 0; l <= L && ok; ++l)
                 for (int h = 0; h < 2 && ok; ++h) {
-                    if (l >= 2) {
+                    if (l != 1) {
                         // x entry: the x rows (generic stores, then the proxy fence), then the x-weights
                         if (!mbar_wait_warp(empty_bar(stage), phase ^ 1u, abort_flag, A.dev_err)) { ok = false; break; }
                         const uint32_t sb = w_base + stage * STAGE_BYTES;
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
                             const int r = lane + 32 * j;
-                            st_shared_v4(sb + XT_OFF + swz32(r, 0), xw[j][0], xw[j][1], xw[j][2], 0u);
-                            st_shared_v4(sb + XT_OFF + swz32(r, 1), 0u, 0u, 0u, 0u);
+                            st_shared_v4(sb + XT_OFF + swz32(r, 0), xw[j][0], xw[j][1], xw[j][2], xw[j][3]);
+                            st_shared_v4(sb + XT_OFF + swz32(r, 1), xw[j][4], 0u, 0u, 0u);
                         }
                         fence_async_smem();
                         __syncwarp();
                         if (lane == 0) {
                             mbar_arrive_tx(full_bar(stage), XW_BYTES);
-                            tma_load_2d(sb, &xmap, 0, (l - 1) * WB + h * NH, full_bar(stage));
+                            tma_load_2d(sb, &xmap, 0, (l == 0 ? 0 : (l - 1) * WB) + h * NH, full_bar(stage));
                         }
                         advance();
                     }
-                    for (int kk = 0; kk < KSL; ++kk) {
+                    for (int kk = 0; kk < (l == 0 ? 0 : KSL); ++kk) {
                         if (!mbar_wait_warp(empty_bar(stage), phase ^ 1u, abort_flag, A.dev_err)) { ok = false; break; }
                         if (lane == 0) {
                             mbar_arrive_tx(full_bar(stage), STAGE_BYTES);
@@ -417,7 +418,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             }
         };
         for (int i = 0; i < n_mine && ok; ++i)
-            for (int l = 1; l <= L && ok; ++l) {
+            for (int l = 0; l <= L && ok; ++l) {
+                if (l == 0) {
+                    // the initial layer's x-part, one x entry per half, each half once its TMEM and its
+                    // input columns are free
+                    for (int h = 0; h < 2 && ok; ++h) {
+                        if (!mbar_wait_warp(epi_bar(h), h == 0 ? ep0 : ep1, abort_flag, A.dev_err)) { ok = false; break; }
+                        if (h == 0) ep0 ^= 1u;
+                        else ep1 ^= 1u;
+                        tc_fence_after();
+                        x_entry(h);
+                        if (ok) mma_commit_warp(acc_bar(h));
+                    }
+                    continue;
+                }
                 const bool xe = l >= 2;
                 if (!mbar_wait_warp(epi_bar(0), ep0, abort_flag, A.dev_err)) { ok = false; break; }
                 ep0 ^= 1u;
@@ -457,51 +471,45 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             p0 = A.pbeg[m] + (long long)(t - A.tile_off[m]) * TM;
             pe = A.pend[m];
         };
-        // points of the thread's four fragment rows: row 16 (k >> 1) + 8 (k & 1) + lane / 4 of the quarter
-        auto load_x4 = [&](long long p0, long long pe, float3 (&x4)[4]) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const long long p = p0 + q * 32 + 16 * (k >> 1) + 8 * (k & 1) + (lane >> 2);
-                const float4 v = p < pe ? ld_stream_f4(A.points + p) : make_float4(0.f, 0.f, 0.f, 0.f);
-                x4[k] = make_float3(v.x, v.y, v.z);
+        // layer 0 of the tile of motion m_: h_0 = (W_0x x from the accumulator) + c_0, per column half, then
+        // the half's arrival.  c_0 of the warp's 64 columns of a half: one pair per lane.
+        auto l0_pass = [&](int m_) {
+            const float* c0m = A.cbias + (long long)m_ * cbs;
+            for (int e = 0; e < 2 && ok; ++e) {
+                const int c0 = e * NH + 64 * cq;
+                const float2 kc = ldg2(c0m + c0 + 2 * lane);
+                if (!mbar_wait(acc_bar(e), acc_phase, abort_flag, A.dev_err)) { ok = false; break; }
+                tc_fence_after();
+                h0_chunk(abase, t_row + (uint32_t)c0, q, lane, c0, kc, 0);
+                h0_chunk(abase, t_row + (uint32_t)(c0 + 32), q, lane, c0 + 32, kc, 16);
+                fence_async_smem();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(epi_bar(e));
             }
-        };
-        // h_0 of column half e (the warp's 64 columns of it), then the half's arrival
-        auto stage_h0 = [&](int e, int m, const float3 (&x4)[4]) {
-            initial_layer(abase, q, lane, e * NH + 64 * cq, Wt.w1x, A.cbias + (long long)m * cbs, x4);
-            fence_async_smem();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(epi_bar(e));
+            acc_phase ^= 1u;
         };
         int m = 0;
         long long p0 = 0, pe = 0;
-        float3 x4[4];
         if (n_mine > 0) {
             tile_of(0, m, p0, pe);
-            load_x4(p0, pe, x4);
-            if (!(A.test_stall && blockIdx.x == 0)) {
-                stage_h0(0, m, x4);
-                stage_h0(1, m, x4);
+            // the TMEM and the input tile are free: the first tile's layer 0 may start
+            if (!(A.test_stall && blockIdx.x == 0) && lane == 0) {
+                mbar_arrive(epi_bar(0));
+                mbar_arrive(epi_bar(1));
             }
+            l0_pass(m);
         }
         for (int i = 0; i < n_mine && ok; ++i) {
             const bool has_next = i + 1 < n_mine;
             const float* cm = A.cbias + (long long)m * cbs;
-            int nm = 0;
-            long long np0 = 0, npe = 0;
-            float3 xn[4];
             for (int l = 1; l <= L && ok; ++l) {
                 const float* cl = cm + (long long)l * WB;
                 const float* crec = Wt.blk_pk + (long long)(l - 1) * WB * 2;   // [W/2][4] of block l
-                if (l == L && has_next) {
-                    tile_of(i + 1, nm, np0, npe);
-                    load_x4(np0, npe, xn);
-                }
                 uint64_t acc4[4] = {0ull, 0ull, 0ull, 0ull};
                 // column half e: its accumulator is final (and for e = 0 input half 0 read by both MMA
                 // halves); the next block's input half e, or on the last block the final layer's partial
-                // sums and then the next tile's h_0 half e (every read of this tile's half is done)
+                // sums; then the half is handed over (on the last block to the next tile's layer 0)
                 for (int e = 0; e < 2 && ok; ++e) {
                     const int c0 = e * NH + 64 * cq;
                     float4 ka0, ka1;
@@ -513,14 +521,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     if (l < L) {
                         block_chunk<false>(abase, t_row + (uint32_t)c0, q, lane, c0, ka0, kb0, acc4);
                         block_chunk<false>(abase, t_row + (uint32_t)(c0 + 32), q, lane, c0 + 32, ka1, kb1, acc4);
+                    } else {
+                        block_chunk<true>(abase, t_row + (uint32_t)c0, q, lane, c0, ka0, kb0, acc4);
+                        block_chunk<true>(abase, t_row + (uint32_t)(c0 + 32), q, lane, c0 + 32, ka1, kb1, acc4);
+                    }
+                    if (l < L || has_next) {
                         fence_async_smem();
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(epi_bar(e));
-                    } else {
-                        block_chunk<true>(abase, t_row + (uint32_t)c0, q, lane, c0, ka0, kb0, acc4);
-                        block_chunk<true>(abase, t_row + (uint32_t)(c0 + 32), q, lane, c0 + 32, ka1, kb1, acc4);
-                        if (has_next) stage_h0(e, nm, xn);
                     }
                 }
                 acc_phase ^= 1u;
@@ -542,6 +551,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 for (int k = 0; k < 4; ++k) {
                     const float v = __shfl_sync(0xffffffffu, sk[k], 4 * (lane & 7));
                     if ((lane >> 3) == k) f = v;
+                }
+                // the next tile's layer 0 first (its MMAs ran meanwhile), so that this tile's reduction and
+                // gate overlap the next tile's first block
+                int nm = 0;
+                long long np0 = 0, npe = 0;
+                if (has_next) {
+                    tile_of(i + 1, nm, np0, npe);
+                    l0_pass(nm);
+                    if (!ok) break;
                 }
                 // the four column quarters of a row meet in shared memory
                 if (cq > 0) red[(cq - 1) * TM + r] = f;
@@ -577,8 +595,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     m = nm;
                     p0 = np0;
                     pe = npe;
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) x4[k] = xn[k];
                 }
             }
         }

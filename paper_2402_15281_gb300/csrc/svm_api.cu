@@ -203,10 +203,10 @@ svm_status load_block_weights(svm_model* m, const unsigned char* p, size_t bytes
     for (int c = 0; c < 12; ++c) out_wq[c] = fin[W + 3 + c];
     const float bout = fin[J];
     // BF16: the blocks' weights for the tensor cores (K-major B operands, bfloat16): the h-weights,
-    // [L][W outputs][W inputs], then the jump x-weights padded to K = 16, [L][W outputs][16] with row
-    // (w_x, w_y, w_z, w_x, w_y, w_z, 0, ...) applied to (x_hi, y_hi, z_hi, x_lo, y_lo, z_lo, 0, ...)
-    // (block 1, which has no jump input, is zero).  The weights are BF16-rounded above, so the upper
-    // half of each FP32 word is the exact value.
+    // [L][W outputs][W inputs], then the x-weights padded to K = 16, [L][W outputs][16] with row
+    // (w_x, w_y, w_z) three times, then zeros, applied to (x_hi, y_hi, z_hi, x_mid, .., z_lo, 0, ...):
+    // block l's jump x-weights, and in the place of block 1 (which has no jump input) the initial
+    // layer's.  The weights are BF16-rounded above, so the upper half of each FP32 word is the exact value.
     std::vector<uint16_t> wh;
     if (bf16) {
         auto hi16 = [](float v) {
@@ -220,7 +220,9 @@ svm_status load_block_weights(svm_model* m, const unsigned char* p, size_t bytes
             for (long long o = 0; o < W; ++o) {
                 for (long long i = 0; i < W; ++i) wh[((size_t)l * W + o) * W + i] = hi16(blk[l][o * in + i]);
                 uint16_t* xr = &wh[(size_t)L * W * W + ((size_t)l * W + o) * 16];
-                for (int c = 0; c < 3; ++c) xr[c] = xr[3 + c] = hi16(blk_wx[((size_t)l * W + o) * 3 + c]);
+                for (int c = 0; c < 3; ++c)
+                    xr[c] = xr[3 + c] = xr[6 + c] =
+                        hi16(l == 0 ? w1x[o * 3 + c] : blk_wx[((size_t)l * W + o) * 3 + c]);
             }
         }
     }

@@ -184,3 +184,38 @@ def test_block_tc_throughput_roofline(svm):
         print(f"BF16 blocks {nb}x512, 16 motions x 200 000 points: network {t:.3f} ms = {tf:.0f} TFLOP/s = "
               f"{tf / peak:.2f} of the measured burst BF16 peak")
         assert tf > 0
+
+
+def test_block_tc_bounded_wait_expiry_is_reported_and_recoverable(svm):
+    """The block kernel's failure path, without a GPU fault: the test hook
+    withholds CTA 0's first hand-over (its TMEM and input tile free for the
+    first tile's layer 0), the MMA warp's wait expires after 2 s, every role
+    leaves its loop, every record of that call carries status 1, and the next
+    call on the same model and context gives the normal records."""
+    import time
+    robot = S.make_robot(1)
+    P = S.block_weights(512, 3, seed=11)
+    q0, q1 = S.uniform_motions(robot, 4, seed=11)
+    pts = torch.from_numpy(S.cube_cloud(20000, seed=11)).cuda()
+    h = _model(svm, robot, P, svm.SVM_BF16)
+    try:
+        res = svm.new_results(4)
+        svm.svm_check_motions(h, q0, q1, pts, 0.05, 32, svm.SVM_NO_EARLY_EXIT, res)
+        torch.cuda.synchronize()
+        want = svm.results_to_numpy(res)[:4].copy()
+        assert np.all(want["status"] == 0)
+        svm.svm_test_expire_wait(h, 1)
+        t = time.perf_counter()
+        svm.svm_check_motions(h, q0, q1, pts, 0.05, 32, svm.SVM_NO_EARLY_EXIT, res)
+        torch.cuda.synchronize()
+        waited = time.perf_counter() - t
+        bad = svm.results_to_numpy(res)[:4].copy()
+        assert np.all(bad["status"] == 1) and 1.5 < waited < 30
+        svm.svm_check_motions(h, q0, q1, pts, 0.05, 32, svm.SVM_NO_EARLY_EXIT, res)
+        torch.cuda.synchronize()
+        again = svm.results_to_numpy(res)[:4]
+        assert np.all(again["status"] == 0)
+        for k in ("collision", "d_min", "dhat_min", "n_flagged", "n_verified"):
+            np.testing.assert_array_equal(again[k], want[k], err_msg=k)
+    finally:
+        svm.svm_destroy_model(h)
