@@ -186,7 +186,8 @@ __device__ __forceinline__ void input_row(const StepArgs& a, int r, float (&in)[
 // for each sample forms z = b + sum_k w_k in_k (fused multiply-adds in the
 // order k = 0..14), h = act(z) and d = act'(z), storing the feature pair of
 // D0 and H0 as one bfloat16x2 word each (a warp writes 128 contiguous bytes of
-// a row).  Two samples go through one packed multiply-add (fma.rn.f32x2, the
+// a row).  ReLU stores no D0: d = [h > 0] of the stored bfloat16 h (rounding
+// is monotone, so h > 0 exactly where the bfloat16 z is positive).  Two samples go through one packed multiply-add (fma.rn.f32x2, the
 // inputs of samples 2p and 2p + 1 interleaved in shared memory).
 constexpr int kL1Rows = 64;
 
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(256) layer1_fwd_kernel(StepArgs a, __nv_bfloat
             float ha, hb, da, db;
             act_hd<ACT>(z[e][0], ha, da);
             act_hd<ACT>(z[e][1], hb, db);
-            *reinterpret_cast<__nv_bfloat162*>(D0 + at) = __floats2bfloat162_rn(da, db);
+            if constexpr (ACT != 0) *reinterpret_cast<__nv_bfloat162*>(D0 + at) = __floats2bfloat162_rn(da, db);
             *reinterpret_cast<__nv_bfloat162*>(H0 + at) = __floats2bfloat162_rn(ha, hb);
         }
     }
@@ -257,7 +258,8 @@ __global__ void __launch_bounds__(256) layer1_fwd_kernel(StepArgs a, __nv_bfloat
 // written as the same tree over registers).  The 32 rows of H_L are staged in
 // shared memory with coalesced 16-byte loads; each row is padded by 16 bytes,
 // so the row-per-lane reads of the chains are free of bank conflicts.  D_L is
-// read where G_L is formed, a feature pair per lane (coalesced).
+// read where G_L is formed, a feature pair per lane (coalesced); ReLU takes
+// d = [h > 0] from the staged H_L instead (DL unused).
 constexpr int kHeadPad = 8;   // bfloat16 elements of padding per staged row
 
 size_t head_smem_bytes(int W) { return (size_t)32 * (W + kHeadPad) * sizeof(__nv_bfloat16); }
@@ -337,11 +339,19 @@ __global__ void __launch_bounds__(128) head_kernel(StepArgs a, const __nv_bfloat
         for (int r = 0; r < 32; ++r) {
             const float df = dfs[r];
             const uint32_t h2 = *reinterpret_cast<const uint32_t*>(hs + r * ld + o);
-            const uint32_t d2 = __ldg(reinterpret_cast<const unsigned int*>(DL + (row0 + r) * W + o));
             xa[r] = df * __uint_as_float(h2 << 16);
             xb[r] = df * __uint_as_float(h2 & 0xFFFF0000u);
-            const float ga = df * wa * __uint_as_float(d2 << 16);
-            const float gb = df * wb * __uint_as_float(d2 & 0xFFFF0000u);
+            float da, db;
+            if constexpr (ACT == 0) {
+                da = __uint_as_float(h2 << 16) > 0.0f ? 1.0f : 0.0f;
+                db = __uint_as_float(h2 & 0xFFFF0000u) > 0.0f ? 1.0f : 0.0f;
+            } else {
+                const uint32_t d2 = __ldg(reinterpret_cast<const unsigned int*>(DL + (row0 + r) * W + o));
+                da = __uint_as_float(d2 << 16);
+                db = __uint_as_float(d2 & 0xFFFF0000u);
+            }
+            const float ga = df * wa * da;
+            const float gb = df * wb * db;
             *reinterpret_cast<__nv_bfloat162*>(GL + (row0 + r) * W + o) = __floats2bfloat162_rn(ga, gb);
         }
 #pragma unroll
@@ -773,8 +783,9 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
         g.ld_rows = W;
         g.bias = t->P + t->off_h + (long long)(l - 1) * ((long long)W * W + W) + (long long)W * W;
         g.err = t->err;
-        launch_train_gemm(kEpiFwd, t->act, t->mapH[l - 1].b, t->mapW[l - 1].b, t->mapDst[l].b, t->mapHst[l].b, g,
-                          t->n_sms, s);
+        // ReLU stores no D (its first store map is unused)
+        const unsigned char* dmap = t->act == 0 ? t->mapHst[l].b : t->mapDst[l].b;
+        launch_train_gemm(kEpiFwd, t->act, t->mapH[l - 1].b, t->mapW[l - 1].b, dmap, t->mapHst[l].b, g, t->n_sms, s);
     }
     const size_t head_smem = head_smem_bytes(W);
     if (t->act == 0) head_kernel<0><<<B / 32, 128, head_smem, s>>>(a, t->H[L], t->D[L], t->G[L], grad ? 0 : 1);
@@ -809,7 +820,7 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
         cudaEventRecord(t->ev_s[l], s2);
         GemmArgs d{};
         d.n_mt = B / 128; d.n_nt = W / 256; d.n_ks = 1; d.k_len = W;
-        d.ld_rows = W; d.d_in = t->D[l - 1];
+        d.ld_rows = W; d.d_in = t->act == 0 ? t->H[l - 1] : t->D[l - 1];   // ReLU: d = [h > 0]
         d.err = t->err;
         launch_train_gemm(kEpiDgrad, t->act, t->mapG[l].b, t->mapWT[l - 1].b, t->mapGst[l - 1].b, nullptr, d, t->n_sms,
                           s);
@@ -897,10 +908,10 @@ svm_status svm_train_create(const svm_model_desc* desc, int device, int32_t batc
     if ((st = talloc(t, &t->err, 256)) != SVM_OK) return fail_free(st);
     if ((st = talloc(t, &t->wb, L * W * W * 2)) != SVM_OK) return fail_free(st);
     if ((st = talloc(t, &t->wbt, L * W * W * 2)) != SVM_OK) return fail_free(st);
-    t->H.resize(L + 1); t->D.resize(L + 1); t->G.resize(L + 1);
+    t->H.resize(L + 1); t->D.assign(L + 1, nullptr); t->G.resize(L + 1);
     for (int l = 0; l <= L; ++l)
         for (auto* v : {&t->H, &t->D, &t->G})
-            if ((st = talloc(t, &(*v)[l], B * W * 2)) != SVM_OK) return fail_free(st);
+            if ((v != &t->D || t->act != 0) && (st = talloc(t, &(*v)[l], B * W * 2)) != SVM_OK) return fail_free(st);
     cudaMemset(t->P, 0, t->np * 4);
     cudaMemset(t->Mo, 0, t->np * 4);
     cudaMemset(t->Vo, 0, t->np * 4);
@@ -910,7 +921,7 @@ svm_status svm_train_create(const svm_model_desc* desc, int device, int32_t batc
     t->mapDst.resize(L + 1); t->mapHst.resize(L + 1); t->mapGst.resize(L + 1);
     int bad = 0;
     for (int l = 0; l <= L; ++l) {
-        bad |= train_make_store_map(t->mapDst[l].b, t->D[l], B, W, 0);  // outputs of FWD and DGRAD
+        if (t->act != 0) bad |= train_make_store_map(t->mapDst[l].b, t->D[l], B, W, 0);  // outputs of FWD and DGRAD
         bad |= train_make_store_map(t->mapHst[l].b, t->H[l], B, W, 0);
         bad |= train_make_store_map(t->mapGst[l].b, t->G[l], B, W, 0);
         bad |= train_make_map(t->mapH[l].b, t->H[l], B, W, 128);       // A of FWD

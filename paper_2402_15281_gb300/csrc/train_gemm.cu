@@ -4,9 +4,11 @@
 //
 //   FWD    hidden layer forward, rows = samples:  z = acc + b, h = act(z),
 //          d = act'(z); writes H [M][N] (the next layer's A) and D [M][N]
-//          (bfloat16, both rounded once from the FP32 z).
+//          (bfloat16, both rounded once from the FP32 z).  ReLU writes only
+//          H: its d is [h > 0] of the stored h.
 //   DGRAD  input gradient, rows = samples:  g = acc * d_prev; writes G [M][N]
-//          (bfloat16).
+//          (bfloat16).  ReLU reads H_prev and multiplies by [h_prev > 0], the
+//          same factor as its D (0 or 1).
 //   WGRAD  weight gradient dW = G^T H over a slice of the batch (split-K):
 //          stores the FP32 partial of split s into dW + s * M * N ([M][N]);
 //          the splits are summed afterwards in a fixed order, so the result
@@ -28,7 +30,8 @@
 // (64 bfloat16 or 32 FP32 columns, 128 bytes a row) into its own 4 KB buffer
 // in the 128-byte-swizzled layout -- row-per-lane 16-byte stores free of bank
 // conflicts -- and one lane issues a tensor store of the box, so no global
-// store passes through the load/store unit.  The D input of DGRAD is read
+// store passes through the load/store unit.  The D input of DGRAD (ReLU: the
+// previous layer's H) is read
 // with coalesced 16-byte loads (eight lanes per 128-byte row) one block
 // ahead, and transposed to a row per lane through the same buffer.
 // All mbarrier waits are bounded (see tc_ptx.cuh).
@@ -335,17 +338,23 @@ __global__ void __launch_bounds__(THREADS, 1)
                             v[4 * q + 2] += b4.z;
                             v[4 * q + 3] += b4.w;
                         }
-                        // D box from z, with h = act(z) left in v
-                        wait_buf();
+                        if constexpr (ACT == 0) {
+                            // ReLU: h = max(z, 0) only
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            float d[8];
+                            for (int e = 0; e < 64; ++e) v[e] = fmaxf(v[e], 0.0f);
+                        } else {
+                            // D box from z, with h = act(z) left in v
+                            wait_buf();
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) act_hd<ACT>(v[8 * j + e], v[8 * j + e], d[e]);
-                            *reinterpret_cast<uint4*>(buf + swz(lane, j)) =
-                                make_uint4(bf2(d[0], d[1]), bf2(d[2], d[3]), bf2(d[4], d[5]), bf2(d[6], d[7]));
+                            for (int j = 0; j < 8; ++j) {
+                                float d[8];
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) act_hd<ACT>(v[8 * j + e], v[8 * j + e], d[e]);
+                                *reinterpret_cast<uint4*>(buf + swz(lane, j)) =
+                                    make_uint4(bf2(d[0], d[1]), bf2(d[2], d[3]), bf2(d[4], d[5]), bf2(d[6], d[7]));
+                            }
+                            store_box(&smap0, n0, m0);                  // D
                         }
-                        store_box(&smap0, n0, m0);                      // D
                         wait_buf();
 #pragma unroll
                         for (int j = 0; j < 8; ++j)
@@ -372,14 +381,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                                 const int j = hh * 4 + jj;
                                 const uint4 dv = *reinterpret_cast<const uint4*>(buf + swz(lane, j));
                                 float* w = u + 8 * jj;
-                                w[0] *= bf_lo(dv.x);
-                                w[1] *= bf_hi(dv.x);
-                                w[2] *= bf_lo(dv.y);
-                                w[3] *= bf_hi(dv.y);
-                                w[4] *= bf_lo(dv.z);
-                                w[5] *= bf_hi(dv.z);
-                                w[6] *= bf_lo(dv.w);
-                                w[7] *= bf_hi(dv.w);
+                                const float dd[8] = {bf_lo(dv.x), bf_hi(dv.x), bf_lo(dv.y), bf_hi(dv.y),
+                                                     bf_lo(dv.z), bf_hi(dv.z), bf_lo(dv.w), bf_hi(dv.w)};
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) w[e] *= ACT == 0 ? (dd[e] > 0.0f ? 1.0f : 0.0f) : dd[e];
                                 *reinterpret_cast<uint4*>(buf + swz(lane, j)) =
                                     make_uint4(bf2(w[0], w[1]), bf2(w[2], w[3]), bf2(w[4], w[5]), bf2(w[6], w[7]));
                             }
