@@ -335,6 +335,61 @@ __device__ __forceinline__ void epilogue32_bf16_frag(uint32_t base, int quarter,
         }
 }
 
+// FP8 ReLU epilogue of 32 columns (o0..o0+31) of a warp's 32 rows in the
+// accumulator-fragment shape (thread t: columns 8 g + 2 (t % 4), +1 of rows
+// t / 4 and t / 4 + 8 of each 16-row block), stored with stmatrix.  Two E4M3
+// values are one 16-bit element, so the columns of each 16-column block are
+// stored in the order pi(j) = 4 ((j & 7) >> 1) + 2 (j >> 3) + (j & 1): thread
+// t's pairs from groups 2p and 2p + 1 become the 4 adjacent bytes 4 (t % 4) ..
+// of 16-byte chunk p, which is the element pair stmatrix takes from it.  The
+// next layer's weights hold their K columns in the same order (host), so the
+// products are unchanged.  Layer 0: h = relu((acc + b) c), b one per lane
+// (lane i: column o0 + i); hidden: h = relu(acc c + b), b from the
+// shared-memory table at brow (column o0 first).
+template <bool LAYER0>
+__device__ __forceinline__ void epilogue32_e4m3_frag(uint32_t base, int quarter, int lane, int o0, const float (&v)[32],
+                                                     float bl, uint32_t brow, float c)
+{
+    const int c2 = 2 * (lane & 3);
+    const uint64_t cc = f2(c, c);
+    uint32_t pk[8];                                    // [16-row block][8-row half][16-column block]
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        uint32_t e16[2][4];                            // [group 2p, 2p + 1][16-row block, 8-row half]
+#pragma unroll
+        for (int gg = 0; gg < 2; ++gg) {
+            const int g = 2 * p + gg;
+            uint64_t b;
+            if constexpr (LAYER0) {
+                b = f2(__shfl_sync(0xffffffffu, bl, 8 * g + c2), __shfl_sync(0xffffffffu, bl, 8 * g + c2 + 1));
+            } else {
+                uint64_t t;
+                asm volatile("ld.shared.b64 %0, [%1];" : "=l"(t) : "r"(brow + (uint32_t)((8 * g + c2) * 4)));
+                b = t;
+            }
+#pragma unroll
+            for (int rb = 0; rb < 2; ++rb)
+#pragma unroll
+                for (int rh = 0; rh < 2; ++rh) {
+                    const int i = 16 * rb + 4 * g + 2 * rh;
+                    const uint64_t a = f2(v[i], v[i + 1]);
+                    const uint64_t z = LAYER0 ? f2_mul(f2_add(a, b), cc) : f2_fma(a, cc, b);
+                    e16[gg][2 * rb + rh] = relu_e4m3x2(z);
+                }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) pk[2 * k + p] = (e16[0][k] & 0xFFFFu) | (e16[1][k] << 16);
+    }
+    // stmatrix k (16-row block rb): lane l addresses row l % 8 of matrix l / 8 = (8-row half, 16-column block)
+    const int i = lane & 7, j = lane >> 3, rh = j >> 1, p = j & 1;
+    const int kb = o0 >> 7, c16 = ((o0 & 127) >> 4) + p;
+#pragma unroll
+    for (int rb = 0; rb < 2; ++rb) {
+        const int r = quarter * 32 + 16 * rb + 8 * rh + i;
+        stmatrix_x4(act_chunk_addr(base, kb, r, c16), pk[4 * rb + 0], pk[4 * rb + 1], pk[4 * rb + 2], pk[4 * rb + 3]);
+    }
+}
+
 // ------------------------------------------------------------------ kernel
 
 template <int PREC, int ACT>
@@ -518,6 +573,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         // BF16 ReLU reads the accumulator in the fragment shape (two biases per thread and
         // 8-column group, stmatrix stores); FP8 and SiLU keep the row-per-lane shape
         constexpr bool kFrag = PREC == SVM_BF16 && ACT == SVM_RELU;
+        constexpr bool kFrag8 = PREC == SVM_FP8_E4M3 && ACT == SVM_RELU;   // hidden stores only
         const int ew = warp - 2;
         const int s = ew / EPI_PER_SLOT;           // tile slot
         const int half = (ew % EPI_PER_SLOT) / 4;  // column half [half*128, half*128+128)
@@ -653,6 +709,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         if constexpr (kFrag) {
                             tmem_ld_frag32(t_row + (uint32_t)o0, v);
                             epilogue32_bf16_frag(abase, quarter, lane, col0 + o0, v, bl0);
+                            bl0 = bl1;
+                            bl1 = bl2;
+                            bl2 = bl3;
+                            continue;
+                        }
+                        if constexpr (kFrag8) {
+                            tmem_ld_frag32(t_row + (uint32_t)o0, v);
+                            if (l == 0)
+                                epilogue32_e4m3_frag<true>(abase, quarter, lane, col0 + o0, v, bl0, 0u, inv_next);
+                            else
+                                epilogue32_e4m3_frag<false>(abase, quarter, lane, col0 + o0, v, 0.0f,
+                                                            sb + (uint32_t)(((l - 1) * WN + col0 + o0) * 4),
+                                                            scale * inv_next);
                             bl0 = bl1;
                             bl1 = bl2;
                             bl2 = bl3;

@@ -547,6 +547,19 @@ svm_status svm_load_weights(svm_model* m, const void* blob, size_t bytes)
     dw.wT = (const float*)put(wT.data(), L * W * W * 4, n_wT);
     dw.bh = (const float*)put(bh.data(), L * W * 4, n_bh);
     dw.wout = (const float*)put(wout.data(), W * 4, n_wout);
+    if (d.prec == SVM_FP8_E4M3 && d.act == SVM_RELU) {
+        // The FP8 ReLU kernel stores each activation's 16-column blocks in the order
+        // pi(j) = 4 ((j & 7) >> 1) + 2 (j >> 3) + (j & 1) (its fragment-shape stores); the hidden
+        // weights take their K columns in the same order, so every product is unchanged.
+        std::vector<uint8_t> e4p(e4.size());
+        for (long long row = 0; row < L * W; ++row)
+            for (long long k = 0; k < W; ++k) {
+                const int j = (int)(k & 15);
+                const long long pk = (k & ~15LL) + 4 * ((j & 7) >> 1) + 2 * (j >> 3) + (j & 1);
+                e4p[row * W + pk] = e4[row * W + k];
+            }
+        e4.swap(e4p);
+    }
     if (d.prec == SVM_BF16) dw.wq = put(bf.data(), L * W * W * 2, n_wq);
     else if (d.prec == SVM_FP8_E4M3) dw.wq = put(e4.data(), L * W * W, n_wq);
     else dw.wq = put(nullptr, 0, n_wq);
