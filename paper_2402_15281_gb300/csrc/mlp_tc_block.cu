@@ -14,8 +14,12 @@
 // halves), and the jump x-part of blocks 2..L (K = 3) is one more K = 16 MMA
 // per half on (x_hi, y_hi, z_hi, x_mid, .., z_lo, 0, ...), x = x_hi + x_mid +
 // x_lo in three bfloat16 parts (x to about 2^-24 relative), against the
-// block's bfloat16 x-weights repeated three times.  The initial layer is such an MMA too: a
-// layer 0 of x entries only, whose epilogue adds c_0 and rounds h_0.
+// block's bfloat16 x-weights repeated three times.  The initial layer is such
+// an MMA too: a layer 0 of x entries only, whose epilogue adds c_0 and rounds
+// h_0.  At a tile change each column half of the last block is handed to the
+// next tile's layer 0 as soon as it is read, and the finished tile's
+// reduction and gate follow the next tile's layer-0 epilogue, beside the next
+// tile's first block.
 //
 // Persistent kernel, one CTA per SM, 18 warps:
 //   warp 0       producer: weight slices of 64 K x 256 output rows (32 KB,
@@ -260,7 +264,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     auto full_bar = [&](int s) { return bar0 + 8 * s; };
     auto empty_bar = [&](int s) { return bar0 + 8 * (STAGES + s); };
     // acc_bar(0): the first output half is final and the first input half consumed by both halves;
-    // acc_bar(1): the whole block.  epi_bar(e): column half e of the next input written (16 warps)
+    // acc_bar(1): the whole block (layer 0: acc_bar(e) after the x entry of half e).
+    // epi_bar(e), 16 warps: column half e of the next input written; ahead of a tile's layer 0, the
+    // half's TMEM and input columns free (after the previous tile's last block, or at the start)
     auto acc_bar = [&](int e) { return bar0 + 8 * (2 * STAGES + e); };
     auto epi_bar = [&](int e) { return bar0 + 8 * (2 * STAGES + 2 + e); };
     const uint32_t drain_bar = bar0 + 8 * (2 * STAGES + 4);
