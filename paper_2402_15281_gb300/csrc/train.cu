@@ -677,6 +677,8 @@ struct svm_trainer {
     svm_model_desc desc{};
     RobotParams rp{};
     int W = 0, L = 0, act = 0, B = 0;
+    // weight-gradient split of the batch: wg_ks splits of wg_klen rows, the last wg_klast
+    int wg_ks = 1, wg_klen = 0, wg_klast = 0;
     long long np = 0, off_w1 = 0, off_b1 = 0, off_h = 0, off_out = 0;
     long long step = 0;
     float* P = nullptr; float* Gr = nullptr; float* Mo = nullptr; float* Vo = nullptr;
@@ -805,8 +807,7 @@ svm_status run_batch(svm_trainer* t, long long base, long long stride, bool grad
         // the buffers of layer l + 2 are free once the side stream has reduced them
         if (l + 2 <= L) cudaStreamWaitEvent(s, t->ev_s[l + 2], 0);
         GemmArgs g{};
-        const int k_len = B >= 2048 ? 2048 : B;
-        g.n_mt = W / 128; g.n_nt = W / 256; g.n_ks = B / k_len; g.k_len = k_len;
+        g.n_mt = W / 128; g.n_nt = W / 256; g.n_ks = t->wg_ks; g.k_len = t->wg_klen; g.k_last = t->wg_klast;
         g.ld_rows = W; g.dw = t->kpart[buf]; g.split_stride = (long long)W * W; g.err = t->err;
         launch_train_gemm(kEpiWgrad, 0, t->mapGmn[l].b, t->mapHmn[l - 1].b, t->mapPst[buf].b, nullptr, g, t->n_sms, s);
         cudaEventRecord(t->ev_w[l], s);
@@ -887,10 +888,27 @@ svm_status svm_train_create(const svm_model_desc* desc, int device, int32_t batc
     if ((st = talloc(t, &t->loss, (B / 32) * 4)) != SVM_OK) return fail_free(st);
     if ((st = talloc(t, &t->loss_sum, 256)) != SVM_OK) return fail_free(st);
     {
-        const long long k_len = B >= 2048 ? 2048 : B;
+        // The weight-gradient GEMM has (W / 128) (W / 256) output tiles and cuts the batch into splits of
+        // 2048 rows (smaller batches: one split).  Where tiles x splits is more than one unit per SM (a
+        // second, partial wave), it takes fewer, longer splits instead -- multiples of 64 rows, about one
+        // unit per SM, the last split the remainder -- which also means fewer partials to sum; elsewhere
+        // more splits would only add partial traffic.  Each split's FP32 partial is summed afterwards
+        // in split order.
+        const long long tiles = (W / 128) * (W / 256);
+        long long kl = B >= 2048 ? 2048 : B;
+        long long ks = B / kl;
+        if (tiles * ks > t->n_sms) {
+            const long long target = std::max<long long>(1, t->n_sms / tiles);
+            kl = (B + target - 1) / target;
+            kl = (kl + 63) / 64 * 64;
+            ks = (B + kl - 1) / kl;
+        }
+        t->wg_klen = (int)kl;
+        t->wg_ks = (int)ks;
+        t->wg_klast = (int)(B - (ks - 1) * kl);
         t->part_n = std::max((B / 32) * (W + 1), (B / 256) * W * 16);
         for (int b = 0; b < 2; ++b) {
-            if ((st = talloc(t, &t->kpart[b], (B / k_len) * W * W * 4)) != SVM_OK) return fail_free(st);
+            if ((st = talloc(t, &t->kpart[b], (long long)t->wg_ks * W * W * 4)) != SVM_OK) return fail_free(st);
             if ((st = talloc(t, &t->chain[b], 256LL * W * 4)) != SVM_OK) return fail_free(st);
         }
     }
@@ -935,8 +953,8 @@ svm_status svm_train_create(const svm_model_desc* desc, int device, int32_t batc
     }
     {
         // the weight-gradient partials, [splits * W][W] FP32
-        const long long k_len = B >= 2048 ? 2048 : B;
-        for (int b = 0; b < 2; ++b) bad |= train_make_store_map(t->mapPst[b].b, t->kpart[b], (B / k_len) * W, W, 1);
+        for (int b = 0; b < 2; ++b)
+            bad |= train_make_store_map(t->mapPst[b].b, t->kpart[b], (long long)t->wg_ks * W, W, 1);
     }
     if (bad) return fail_free(SVM_E_CUDA);
     if (cudaDeviceSynchronize() != cudaSuccess) return fail_free(SVM_E_CUDA);

@@ -145,7 +145,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int n_units = g.n_ks * g.n_mt * g.n_nt;
     const int n_mine =
         n_units > (int)blockIdx.x ? (n_units - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
-    const int k_slices = g.k_len / BK;
+    // K slices of split ks: k_len, the last split k_last (the splits of WGRAD cover the batch exactly)
+    const int k_last = g.k_last > 0 ? g.k_last : g.k_len;
+    auto k_slices_of = [&](int ks) { return (ks == g.n_ks - 1 ? k_last : g.k_len) / BK; };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -189,6 +191,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 int ks, mt, nt;
                 unit_coords(i, ks, mt, nt);
                 const int k0 = ks * g.k_len;
+                const int k_slices = k_slices_of(ks);
                 for (int kk = 0; kk < k_slices; ++kk) {
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, g.err)) { ok = false; break; }
                     mbar_arrive_tx(full_bar(stage), STAGE_BYTES);
@@ -236,6 +239,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             ap ^= 1u;
             tc_fence_after();
             const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
+            int ks, mt, nt;
+            unit_coords(i, ks, mt, nt);
+            const int k_slices = k_slices_of(ks);
             for (int kk = 0; kk < k_slices; ++kk) {
                 if (!mbar_wait_warp(full_bar(stage), phase, abort_flag, g.err)) { ok = false; break; }
                 tc_fence_after();

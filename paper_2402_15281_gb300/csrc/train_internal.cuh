@@ -11,6 +11,7 @@ constexpr int kEpiFwd = 0, kEpiDgrad = 1, kEpiWgrad = 2;
 struct GemmArgs {
     int n_mt, n_nt, n_ks;           // tiles along M (128), N (256), K splits
     int k_len;                      // K elements per split (multiple of 64)
+    int k_last;                     // K elements of the last split (multiple of 64; 0: k_len)
     long long ld_rows;              // row stride of the row-major [M][.] operands and outputs
     const float* bias;              // FWD: [N]
     const __nv_bfloat16* d_in;      // DGRAD: D = act'(z) of the previous layer
